@@ -1,0 +1,398 @@
+"""Benchmark: direction-optimising BFS with the per-level frontier codec, R-MAT scale 24.
+
+One step = one BFS from one root over the resident scale-24 R-MAT graph (16,777,216 vertices,
+edgefactor 16, initiator 0.57/0.19/0.19/0.05), with every level's frontier encoded as a sorted
+queue stream (Q_d) and a bitmap stream (B_d), the visited bitmap as V_d, the consumed form
+decoded and expanded on the device.  value = GTEPS = undirected edges inside the reached
+components / timed seconds (whole job).  The CSR (2.2 GB) is larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fqbfs|reference] [--scale S]
+
+--impl reference times the CPU oracle (the plain, single-threaded C oracle of oracle/) on the
+same graph and roots: each step is one root's oracle BFS plus the oracle encoding of that
+root's per-level streams.
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU over its own
+share of roots (weak scaling); the only collectives are the timing barrier and max.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS GTEPS and frontier codec GB/s + compression ratio vs HBM roofline, batched vs plain"
+SEED = 20170402
+N_ROOTS = 64
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=16)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fqbfs", choices=["fqbfs", "reference"])
+    p.add_argument("--scale", type=int, default=24)
+    p.add_argument("--edgefactor", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_roots(roots, world, rank, k):
+    """The k roots rank `rank` runs: its stride-world share of the root list, cycled."""
+    mine = roots[rank::world] or roots
+    return [mine[i % len(mine)] for i in range(k)]
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        smax = max(r[1] for r in rows)
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(kclass: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None when
+    the kernel source changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    ent = t.get(kclass)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1704_00513_gb300", "csrc", ent["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != ent.get("source_sha256_16"):
+        return None
+    return ent.get("dram_bytes_per_launch_fullsize")
+
+
+def make_graph(scale, edgefactor, device):
+    from paper_1704_00513_gb300 import inputs
+    off, cols = inputs.rmat_csr(scale, edgefactor, seed=SEED, device=device)
+    roots = inputs.pick_roots(off, N_ROOTS, seed=SEED)
+    return off, cols, roots
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+def oracle_step(off_h, cols_h, root):
+    """One root on the CPU oracle: FIFO BFS + encoding of every level's Q_d, B_d, V_d."""
+    import oracle
+    depth, parent = oracle.bfs(off_h, cols_h, root)
+    streams = oracle.level_streams(depth, record_visited=True)
+    reached = depth >= 0
+    edges = int(np.diff(off_h)[reached].sum()) // 2
+    return edges, sum(s["Q"].size + s["B"].size + s["V"].size for s in streams)
+
+
+def cpu_baseline(off_h, cols_h, roots, budget_s=12.0, max_roots=3):
+    t0 = time.perf_counter()
+    edges = 0
+    done = 0
+    for r in roots[:max_roots]:
+        e, _ = oracle_step(off_h, cols_h, r)
+        edges += e
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": edges / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {len(roots)} roots of the same graph: oracle FIFO BFS + oracle FQ/FB encoding of "
+                      f"every level's Q_d, B_d, V_d ({dt:.1f} s, single-threaded C)"}
+
+
+# ----------------------------------------------------------------------------- main arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    off, cols, roots = make_graph(args.scale, args.edgefactor, dev)
+    off_h = off.cpu().numpy()
+    cols_h = cols.cpu().numpy().view(np.uint32)
+    del off, cols
+    import oracle
+    oracle.build()
+    steps = shard_roots(roots, 1, 0, args.warmup + args.steps)
+    for r in steps[: args.warmup]:
+        oracle_step(off_h, cols_h, r)
+    t0 = time.perf_counter()
+    edges = 0
+    for r in steps[args.warmup:]:
+        e, _ = oracle_step(off_h, cols_h, r)
+        edges += e
+    dt = time.perf_counter() - t0
+    value = edges / dt / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic R-MAT (seeded)",
+            "impl": "reference",
+            "config": {"workload": f"rmat{args.scale}_dobfs_codec", "scale": args.scale, "edgefactor": args.edgefactor,
+                       "roots": args.steps},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} roots, one per step: oracle FIFO BFS + oracle encoding of every "
+                                       f"level's Q_d, B_d, V_d (single-threaded C)"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fqbfs(args, world, rank, local):
+    from paper_1704_00513_gb300 import build as fqbuild
+    fqbuild.build()
+    from paper_1704_00513_gb300 import fqbfs
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    off, cols, roots = make_graph(args.scale, args.edgefactor, dev)
+    n = off.numel() - 1
+    g = fqbfs.Graph(off, cols)
+    depth = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_TIMING
+    my_roots = shard_roots(roots, world, rank, args.warmup + args.steps)
+    stream = torch.cuda.current_stream()
+
+    for r in my_roots[: args.warmup]:
+        g.bfs(r, depth=depth, parent=parent, flags=flags)
+    torch.cuda.synchronize()
+
+    kms = {k: 0.0 for k in fqbfs.KCLASS}
+    kbytes = {k: 0 for k in fqbfs.KCLASS}
+    klaunch = {k: 0 for k in fqbfs.KCLASS}
+    edges = 0
+    qraw = qenc = braw = benc = venc = 0
+    levels = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for r in my_roots[args.warmup:]:
+            res = g.bfs(r, depth=depth, parent=parent, flags=flags)
+            s = res.stats
+            edges += s["reached_edges"]
+            qraw += s["raw_queue_bytes"]; qenc += s["enc_queue_bytes"]
+            braw += s["raw_bitmap_bytes"]; benc += s["enc_bitmap_bytes"]; venc += s["enc_visited_bytes"]
+            levels.append(s["levels"])
+            for k in fqbfs.KCLASS:
+                kms[k] += s["kernel_ms"][k]
+                kbytes[k] += s["kernel_bytes"][k]
+                klaunch[k] += s["kernel_launches"][k]
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.summary()
+    ms = start.elapsed_time(stop)
+    t_max = max_over_ranks(ms, world)
+    edges_all = sum_over_ranks(float(edges), world)
+    value = edges_all / (t_max / 1e3) / 1e9
+
+    # dominant kernel class and its roofline (algorithmic bytes / event-timed duration)
+    peaks, peak_kind = measured_peaks()
+    dom = max(("top_down", "bottom_up", "compact", "encode", "decode"), key=lambda k: kms[k])
+    achieved = kbytes[dom] / (kms[dom] / 1e3) / 1e9 if kms[dom] > 0 else 0.0
+    traffic = kernel_traffic(dom)
+    launches = klaunch[dom]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": dom, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": kbytes[dom] / max(1, launches),
+                "launches": launches, "avg_launch_ms": kms[dom] / max(1, launches)}
+    codec = {"queue_ratio": qraw / max(1, qenc), "bitmap_ratio": braw / max(1, benc),
+             "visited_ratio": braw / max(1, venc),
+             "queue_bits_per_id": 8.0 * qenc / max(1, qraw / 4),
+             "encode_GBps": kbytes["encode"] / max(1e-9, kms["encode"] / 1e3) / 1e9,
+             "decode_GBps": kbytes["decode"] / max(1e-9, kms["decode"] / 1e3) / 1e9,
+             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, off, cols, my_roots[args.warmup:], world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        off_h = off.cpu().numpy()
+        cols_h = cols.cpu().numpy().view(np.uint32)
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+        cpu = cpu_baseline(off_h, cols_h, my_roots[args.warmup:])
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic R-MAT (seeded)",
+                "config": {"workload": f"rmat{args.scale}_dobfs_codec", "scale": args.scale,
+                           "edgefactor": args.edgefactor, "vertices": n, "directed_edges": int(cols.numel()),
+                           "roots_per_rank": args.steps, "streams": "Q_d, B_d, V_d encoded every level",
+                           "l2": "no flush: the 2.2 GB CSR exceeds L2", "levels_mean": statistics.mean(levels),
+                           "parallelism": f"replicas{world}"},
+                "roofline": roofline, "codec": codec, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, off, cols, roots, world):
+    """Same metric through the C ABI with host buffers: upload the CSR from pinned memory, build
+    the handle, run the roots and copy each depth/parent array back, all inside the timed
+    region."""
+    from paper_1704_00513_gb300 import fqbfs
+    n = off.numel() - 1
+    off_h = off.cpu().pin_memory()
+    cols_h = cols.cpu().pin_memory()
+    depth_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    parent_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    dev = off.device
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    off_d = off_h.to(dev, non_blocking=True)
+    cols_d = cols_h.to(dev, non_blocking=True)
+    g = fqbfs.Graph(off_d, cols_d)
+    edges = 0
+    for r in roots:
+        res = g.bfs(r, flags=fqbfs.FQ_BFS_VISITED_STREAM)
+        depth_h.copy_(res.depth, non_blocking=True)
+        parent_h.copy_(res.parent, non_blocking=True)
+        edges += res.stats["reached_edges"]
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    g.close()
+    dt = max_over_ranks(dt, world)
+    edges = sum_over_ranks(float(edges), world)
+    k = len(roots)
+    return {"value": edges / dt / 1e9, "unit": "GTEPS",
+            "h2d_bytes_per_step": int((off.numel() * 8 + cols.numel() * 4) / k + 4),
+            "d2h_bytes_per_step": int(8 * n + 512)}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_fqbfs(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * fqbfs.h -- C ABI of the compressed-frontier BFS library (libfqbfs.so, CUDA, sm_103a).
+ *
+ * The library runs the data-parallel hot path of "Optimizing Communication by Compression for
+ * Multi-GPU Scalable Breadth-First Searches" (arXiv 1704.00513) on one GPU: a level-synchronous,
+ * direction-optimising BFS over a CSR graph in which every level's frontier is compressed with
+ * delta coding + binary packing in blocks of 128 (the thesis' S4-BP128 choice, sec. 5.3),
+ * measured in bytes, decompressed and consumed on the device -- the codec stage that the thesis
+ * wraps around its two per-level exchanges (Alg. "Our BFS algorithm with SpVM and
+ * compression", compress -> ALLGATHERV -> decompress, compress -> ALLTOALLV -> decompress).
+ *
+ * Conventions for every call
+ *  - Pointers named d_* are device pointers, h_* host pointers.  The caller owns every buffer.
+ *    Streams are cudaStream_t values passed as void* (NULL = the legacy default stream).
+ *  - Calls are asynchronous on the given stream unless stated otherwise.  Argument errors are
+ *    returned before anything is enqueued.  Errors found by the device (unsorted input, a corrupt
+ *    stream, a short output buffer) are written to the status record at the start of the
+ *    workspace and read back with fq_work_status(), which synchronises the stream.
+ *  - No call allocates device memory except fq_graph_create (which owns what it allocates until
+ *    fq_graph_destroy).  Codec calls take a caller-provided workspace of fq_workspace_bytes().
+ *  - Every device buffer passed to a codec call must be 16-byte aligned (the codec moves 128-bit
+ *    vectors); a misaligned pointer returns FQ_EINVAL.
+ *  - One workspace (or graph handle) must not be used by two calls that may overlap in time.
+ *
+ * Stream formats (all little-endian; sizes are multiples of 16 bytes)
+ *  FQ, a strictly increasing uint32 sequence v[0..n) (a frontier queue, sec. 4.1.3):
+ *    packed  {u32 'FQP1', n, nb = ceil(n/128), payload_words}, u32 base[nb], u8 b[nb],
+ *            zeros to 16 B, then per block k the 128 slots at b_k bits each (4*b_k u32 words;
+ *            slot j at bits [j*b_k, (j+1)*b_k), LSB first).  Slot 0 is 0 and base_k = v[128k]
+ *            (frame of reference, Eq. 5); slot j >= 1 is v[128k+j] - v[128k+j-1] - 1 (delta
+ *            coding, sec. 5.2); slots past n are 0; b_k = bit length of the block's largest
+ *            slot (Eq. 6 read as a ceiling, Eq. 7).
+ *    raw     {u32 'FQR1', n, 0, n}, u32 v[n], zeros to 16 B.
+ *    The packed form is written only when strictly smaller than the raw one (sec. 5.2
+ *    "Lossless": the encoding must be smaller than the input; sec. 5.4.2 thresholds).
+ *  FB, a bitmap of N bits in uint64 words (bit i = bit i%64 of word i/64):
+ *    {u32 'FBM1', u32 mode, u64 N} then either an FQ stream of the set positions (mode 1, when
+ *    2*popcount <= N) or of the clear positions below N (mode 2), or -- when that is not
+ *    strictly smaller -- the raw words with bits >= N cleared, zero-padded to 16 B (mode 0).
+ */
+#ifndef FQBFS_H
+#define FQBFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+typedef int32_t fq_status;
+#define FQ_OK 0
+#define FQ_EINVAL 1     /* bad argument (NULL, misaligned, size out of range)             */
+#define FQ_ENOMEM 2     /* fq_graph_create could not allocate its workspace                 */
+#define FQ_ENOSPC 3     /* output capacity too small; the status detail is the size needed  */
+#define FQ_ECORRUPT 4   /* a stream failed validation; the status detail locates the fault  */
+#define FQ_EUNSORTED 5  /* encoder input not strictly increasing; detail = first bad index  */
+#define FQ_ETIMEOUT 6   /* a bounded device-side wait gave up                               */
+#define FQ_ECUDA 7      /* a CUDA runtime call failed                                       */
+#define FQ_EBUSY 8      /* resource in use                                                  */
+
+/* Human-readable name of a status code (static storage). */
+const char *fq_status_string(fq_status s);
+
+/* ------------------------------------------------------------------ sizes */
+
+/* Largest FQ stream for n ids: 16 + pad16(4n) bytes (the raw form; packed is chosen only when
+ * strictly smaller).  A capacity of this many bytes never yields FQ_ENOSPC. */
+uint64_t fq_queue_bound(uint64_t n);
+
+/* Largest FB stream for a bitmap of nbits bits: 16 + pad16(8 * ceil(nbits/64)) bytes. */
+uint64_t fq_bitmap_bound(uint64_t nbits);
+
+/* Workspace bytes for codec calls on up to max_ids ids and bitmaps of up to max_nbits bits.
+ * The first 64 bytes hold the status record (struct fq_device_status). */
+uint64_t fq_workspace_bytes(uint64_t max_ids, uint64_t max_nbits);
+
+typedef struct fq_device_status {
+    int32_t code;    /* fq_status of the last call that used this workspace              */
+    uint32_t where;  /* internal stage that set it (0 = none)                            */
+    uint64_t detail; /* ENOSPC: bytes needed; EUNSORTED: first bad index; ECORRUPT: a byte
+                        or element index near the fault                                  */
+} fq_device_status;
+
+/* Synchronise `stream`, then read the status record of workspace d_work.  Returns its code
+ * (FQ_OK if the device found nothing wrong); *h_detail (may be NULL) receives the detail. */
+fq_status fq_work_status(const void *d_work, void *stream, uint64_t *h_detail);
+
+/* ------------------------------------------------------------------ frontier queue codec */
+
+/* Encode the strictly increasing ids d_ids[0..n) (n < 2^32) as an FQ stream at d_out
+ * (capacity cap bytes).  The stream's size is written to the device u64 *d_out_bytes (0 on a
+ * device-detected error; the needed size on FQ_ENOSPC).  Device errors: FQ_EUNSORTED,
+ * FQ_ENOSPC.  The frontier queue compress step of Alg. "Our BFS algorithm with SpVM and
+ * compression" (delta + binary packing, sec. 5.2-5.3). */
+fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
+                             uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
+
+/* Decode the FQ stream d_in[0..in_bytes) into d_ids (room for cap ids); the number of ids is
+ * written to the device u64 *d_n.  The stream is validated (magic, nb, widths <= 32, sizes
+ * against in_bytes, zero padding and slots, strictly increasing values without u32 overflow);
+ * a failure sets FQ_ECORRUPT.  Header-level faults are caught before any output is written;
+ * value-level faults may leave d_ids partly written.  Never writes more than cap ids
+ * (FQ_ENOSPC if the stream holds more).  The decompress step of the same algorithm. */
+fq_status fq_frontier_decode(const uint8_t *d_in, uint64_t in_bytes, uint32_t *d_ids, uint64_t cap,
+                             uint64_t *d_n, void *d_work, uint64_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ bitmap codec */
+
+/* Encode the bitmap d_words (ceil(nbits/64) words; bits >= nbits ignored) as an FB stream at
+ * d_out (capacity cap); size to *d_out_bytes.  nbits <= 2^32.  Bitmap frontiers, sec. 3.3
+ * ("Sparse vector with pop counting"), coded with the queue codec. */
+fq_status fq_bitmap_encode(const uint64_t *d_words, uint64_t nbits, uint8_t *d_out, uint64_t cap,
+                           uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
+
+/* Decode the FB stream d_in[0..in_bytes) into d_words (ceil(nbits/64) words, every word
+ * written; bits >= nbits cleared).  The header's N must equal nbits.  FQ_ECORRUPT on any
+ * inconsistency, including a position >= N or raw tail bits set. */
+fq_status fq_bitmap_decode(const uint8_t *d_in, uint64_t in_bytes, uint64_t *d_words, uint64_t nbits,
+                           void *d_work, uint64_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ BFS */
+
+typedef struct fq_graph fq_graph;
+
+/* Wrap an undirected graph in CSR form: d_offsets[n+1] (int64, offsets[0] = 0,
+ * offsets[n] = m), d_cols[m] (uint32 < n, each row sorted, symmetric, no self-loops).  The
+ * handle borrows both arrays (the caller keeps them alive and unchanged) and allocates its
+ * workspace (about 30 bytes per vertex) with cudaMalloc on the current device.  n < 2^32.
+ * Synchronous. */
+fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, uint64_t m,
+                          fq_graph **out);
+
+/* Free a handle's workspace (synchronises the device first). */
+fq_status fq_graph_destroy(fq_graph *g);
+
+#define FQ_TOP_DOWN 0
+#define FQ_BOTTOM_UP 1
+
+/* fq_bfs_opts.flags */
+#define FQ_BFS_VISITED_STREAM 0x1u /* also encode the visited bitmap V_d every level          */
+#define FQ_BFS_FORCE_TOP_DOWN 0x2u /* ignore the switching rule: top-down at every level        */
+#define FQ_BFS_FORCE_BOTTOM_UP 0x4u/* bottom-up at every level after level 0                    */
+#define FQ_BFS_TIMING 0x8u         /* time every kernel class with CUDA events (fills stats)    */
+
+typedef struct fq_bfs_opts {
+    uint32_t alpha; /* top-down -> bottom-up when m_f * alpha > m_u   (0 selects 14) */
+    uint32_t beta;  /* bottom-up -> top-down when n_f * beta < n      (0 selects 24) */
+    uint32_t flags;
+    uint32_t reserved;
+} fq_bfs_opts;
+
+/* kernel classes reported by FQ_BFS_TIMING */
+#define FQ_K_TOP_DOWN 0
+#define FQ_K_BOTTOM_UP 1
+#define FQ_K_COMPACT 2
+#define FQ_K_ENCODE 3
+#define FQ_K_DECODE 4
+#define FQ_K_OTHER 5
+#define FQ_NUM_KCLASS 6
+
+typedef struct fq_bfs_stats {
+    uint32_t levels;          /* non-empty levels = max depth + 1                               */
+    uint32_t directions;      /* bit d set = level d expanded bottom-up (first 32 levels)       */
+    uint64_t reached;         /* vertices with depth >= 0                                       */
+    uint64_t reached_edges;   /* undirected edges inside the reached component (TEPS numerator) */
+    uint64_t edges_examined;  /* adjacency entries read by the expansion kernels                */
+    uint64_t raw_queue_bytes; /* sum over levels of 4 * n_f                                      */
+    uint64_t enc_queue_bytes; /* sum over levels of |Q_d|                                        */
+    uint64_t raw_bitmap_bytes;/* sum over levels of N/8 (frontier bitmaps)                       */
+    uint64_t enc_bitmap_bytes;/* sum over levels of |B_d|                                        */
+    uint64_t enc_visited_bytes;/* sum over levels of |V_d| (FQ_BFS_VISITED_STREAM)              */
+    double kernel_ms[FQ_NUM_KCLASS];       /* FQ_BFS_TIMING: summed kernel time per class       */
+    uint64_t kernel_launches[FQ_NUM_KCLASS];/* launches per class                               */
+    uint64_t kernel_bytes[FQ_NUM_KCLASS];  /* algorithmic bytes per class (design model)        */
+} fq_bfs_stats;
+
+typedef struct fq_level_record {
+    uint32_t level;
+    uint32_t direction;       /* FQ_TOP_DOWN or FQ_BOTTOM_UP used to expand this level          */
+    uint64_t n_f;             /* |F_d|                                                          */
+    uint64_t m_f;             /* sum of degrees over F_d                                        */
+    uint64_t m_u;             /* sum of degrees over vertices not yet visited                   */
+    uint64_t examined;        /* adjacency entries read while expanding F_d                     */
+    uint64_t q_bytes, b_bytes, v_bytes; /* |Q_d|, |B_d|, |V_d| (0 when not encoded)             */
+    uint64_t log_offset;      /* offset of Q_d, then B_d, then V_d in the stream log (or ~0)    */
+} fq_level_record;
+
+/* Breadth-first search from root.  Writes d_depth[n] (hop distance, -1 unreachable) and, if
+ * d_parent is not NULL, d_parent[n] (a BFS tree: parent[root] = root, UINT32_MAX unreachable).
+ * Level d: encode F_d as Q_d (queue) and B_d (bitmap) [and V_d], decide the direction from
+ * (n_f, m_f, m_u), decode the form that direction consumes, expand it (top-down over the
+ * decoded queue, or bottom-up against the decoded bitmap), compact the next frontier into a
+ * sorted queue.  Stops when the next frontier is empty.
+ * h_stats (may be NULL) and h_levels[0..max_levels) (may be NULL) receive the per-run and
+ * per-level records.  If d_stream_log is not NULL every level's Q_d, B_d [, V_d] are copied
+ * there back to back (fails with FQ_ENOSPC when stream_log_cap is exceeded).
+ * Synchronous (the level loop reads two counters per level).  Not thread-safe per handle. */
+fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_parent, const fq_bfs_opts *opts,
+                     fq_bfs_stats *h_stats, fq_level_record *h_levels, uint32_t max_levels, uint8_t *d_stream_log,
+                     uint64_t stream_log_cap, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FQBFS_H */

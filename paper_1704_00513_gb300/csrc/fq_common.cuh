@@ -1,0 +1,185 @@
+// fq_common.cuh -- shared device helpers and the internal (C++) interface between the codec
+// (codec.cu) and the BFS level loop (bfs.cu) of libfqbfs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fqbfs.h"
+
+namespace fq {
+
+constexpr uint32_t kBlock = 128;          // B: ids per packed block (sec. 5.2, S4-BP128 in sec. 5.3)
+constexpr uint32_t kEncThreads = 256;     // CTA size of the block-parallel codec kernels
+constexpr uint32_t kEncWarps = kEncThreads / 32;
+constexpr uint32_t kBlocksPerWarp = 8;    // 128-id blocks one warp handles per tile
+constexpr uint32_t kTileBlocks = kEncWarps * kBlocksPerWarp;  // 64 blocks = 8192 ids per tile
+constexpr uint32_t kBitThreads = 256;     // CTA size of the bitmap kernels
+constexpr uint32_t kWordsPerThread = 8;   // uint64 words per thread in the bitmap kernels
+constexpr uint32_t kTileWords = kBitThreads * kWordsPerThread;  // 2048 words = 131072 bits
+constexpr uint32_t kScanThreads = 1024;   // single-CTA plan/scan kernels
+
+// stream magics: ASCII 'F','Q','P','1' etc. read as little-endian u32
+constexpr uint32_t kMagicPacked = 0x31505146u;  // "FQP1"
+constexpr uint32_t kMagicRaw = 0x31525146u;     // "FQR1"
+constexpr uint32_t kMagicBitmap = 0x314D4246u;  // "FBM1"
+
+enum : uint32_t { kFbRaw = 0, kFbSet = 1, kFbClear = 2 };
+
+// result of a plan kernel
+enum : uint32_t {
+    kModeNone = 0,      // error: write nothing
+    kModePacked = 1,    // FQ packed
+    kModeRaw = 2,       // FQ raw
+    kModeFbRaw = 3,     // FB raw words
+};
+
+// internal stage ids recorded in fq_device_status.where
+enum : uint32_t {
+    kWhereEncWidths = 1, kWhereEncPlan = 2, kWhereDecPlan = 3, kWhereDecUnpack = 4,
+    kWhereFbDecode = 5, kWhereBfs = 6,
+};
+
+// Control block at the start of every codec workspace.  The first 16 bytes are the public
+// fq_device_status record.
+struct Ctl {
+    int32_t code;
+    uint32_t where;
+    unsigned long long detail;
+    uint32_t mode;        // kMode*
+    uint32_t fb_mode;     // kFb* chosen by the bitmap plan
+    unsigned long long n; // ids being encoded (FB: positions count) or decoded
+    unsigned long long nb;
+    unsigned long long popcount;
+    unsigned long long total_b;
+    unsigned long long out_bytes;
+    unsigned long long fq_offset;  // byte offset of the FQ stream inside the container
+    uint32_t pad[2];
+};
+static_assert(sizeof(Ctl) <= 256, "control block must fit its slot");
+
+// Pointers into one codec workspace (computed on the host from its base and capacities).
+struct Scratch {
+    Ctl *ctl;
+    uint8_t *widths;      // [nb_cap]
+    uint32_t *bases;      // [nb_cap]
+    uint32_t *block_off;  // [nb_cap] decode: payload word offset of each block
+    uint32_t *tile_sum;   // [etiles_cap]
+    uint32_t *tile_off;   // [etiles_cap]
+    uint32_t *btile_cnt;  // [btiles_cap]
+    uint32_t *btile_off;  // [btiles_cap]
+    uint32_t *positions;  // [pos_cap]  bitmap positions (FB)
+    uint64_t ids_cap;     // largest id count an encode/decode may see
+    uint64_t nbits_cap;
+    uint64_t nb_cap, etiles_cap, btiles_cap, pos_cap;
+};
+
+uint64_t workspace_bytes(uint64_t max_ids, uint64_t max_nbits);
+Scratch carve(void *base, uint64_t max_ids, uint64_t max_nbits);
+// Largest (max_ids, max_nbits) a workspace of `bytes` serves, with max_nbits fixed by caller.
+bool workspace_fits(uint64_t bytes, uint64_t ids, uint64_t nbits);
+
+inline uint64_t pad16(uint64_t b) { return (b + 15u) / 16u * 16u; }
+inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------------ internal launches
+// Every launch helper enqueues on `st` and returns cudaGetLastError().
+
+// FQ-encode ids[0..n).  n is *n_dev when n_dev != nullptr (device-resident count, then
+// n_max bounds it for the grid), else n_host.  Container: FQ stream at out (fb == false) or an
+// FB stream whose inner FQ starts at out + 16 (fb == true; positions come from the bitmap plan).
+cudaError_t encode_fq(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max, uint8_t *out,
+                      uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st);
+cudaError_t encode_fb(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap, uint64_t *out_bytes,
+                      const Scratch &s, cudaStream_t st);
+// Decode: in_bytes is in_bytes_host unless in_bytes_dev != nullptr.
+cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t *in_bytes_dev, uint32_t *ids,
+                      uint64_t cap, uint64_t *n_out, const Scratch &s, cudaStream_t st);
+cudaError_t decode_fb(const uint8_t *in, uint64_t in_bytes_host, const uint64_t *in_bytes_dev, uint64_t *words,
+                      uint64_t nbits, const Scratch &s, cudaStream_t st);
+// Reset the status record to FQ_OK.
+cudaError_t reset_status(const Scratch &s, cudaStream_t st);
+
+// Bitmap -> sorted positions, shared with the BFS compaction: tile counts then extraction.
+int num_sms();
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ uint32_t bitlen32(uint32_t x) { return 32u - __clz(x); }
+
+__device__ __forceinline__ void set_error(Ctl *c, int32_t code, uint32_t where, unsigned long long detail)
+{
+    // first error wins; detail keeps the smallest index reported for that code
+    int32_t prev = atomicCAS(&c->code, 0, code);
+    if (prev == 0 || prev == code) {
+        if (prev == 0) c->where = where;
+        atomicMin(&c->detail, detail);
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long x)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint32_t warp_max(uint32_t x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Exclusive scan over a CTA of NT threads (NT multiple of 32, <= 1024) of one u64 per thread.
+// Returns the thread's exclusive prefix; *total receives the CTA total.  Uses `sm` (32 u64).
+template <int NT>
+__device__ __forceinline__ unsigned long long cta_excl_scan64(unsigned long long x, unsigned long long *sm,
+                                                              unsigned long long *total)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    unsigned long long incl = warp_incl_scan64(x);
+    if (lane == 31) sm[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = (lane < NT / 32) ? sm[lane] : 0ull;
+        unsigned long long wi = warp_incl_scan64(w);
+        sm[lane] = wi - w;
+        if (lane == 31) sm[32] = wi;
+    }
+    __syncthreads();
+    unsigned long long r = sm[warp] + incl - x;
+    *total = sm[32];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace fq
+
+#define FQ_CUDA_TRY(expr)                         \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return _e;         \
+    } while (0)

@@ -1,0 +1,295 @@
+"""Python binding of libfqbfs (include/fqbfs.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module turns torch tensors into device
+pointers, passes the current CUDA stream, and reads back small results.  The C entry points are
+available under their C names (``fq_frontier_encode`` ...) through ``lib()``; the functions of
+the same names below take torch tensors.
+
+The library must have been built (``paper_1704_00513_gb300.build.build()``); importing the
+binding does not build it, and every call fails loudly when ``libfqbfs.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfqbfs.so")
+
+FQ_OK, FQ_EINVAL, FQ_ENOMEM, FQ_ENOSPC, FQ_ECORRUPT, FQ_EUNSORTED, FQ_ETIMEOUT, FQ_ECUDA, FQ_EBUSY = range(9)
+FQ_TOP_DOWN, FQ_BOTTOM_UP = 0, 1
+FQ_BFS_VISITED_STREAM, FQ_BFS_FORCE_TOP_DOWN, FQ_BFS_FORCE_BOTTOM_UP, FQ_BFS_TIMING = 1, 2, 4, 8
+KCLASS = ("top_down", "bottom_up", "compact", "encode", "decode", "other")
+
+_u64, _u32, _i32, _vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
+
+
+class FqError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: int = 0):
+        self.status = status
+        self.detail = detail
+        name = _status_name(status)
+        super().__init__(f"{what}: {name} (detail {detail})")
+
+
+class fq_bfs_opts(ctypes.Structure):
+    _fields_ = [("alpha", _u32), ("beta", _u32), ("flags", _u32), ("reserved", _u32)]
+
+
+class fq_bfs_stats(ctypes.Structure):
+    _fields_ = [("levels", _u32), ("directions", _u32), ("reached", _u64), ("reached_edges", _u64),
+                ("edges_examined", _u64), ("raw_queue_bytes", _u64), ("enc_queue_bytes", _u64),
+                ("raw_bitmap_bytes", _u64), ("enc_bitmap_bytes", _u64), ("enc_visited_bytes", _u64),
+                ("kernel_ms", ctypes.c_double * 6), ("kernel_launches", _u64 * 6), ("kernel_bytes", _u64 * 6)]
+
+
+class fq_level_record(ctypes.Structure):
+    _fields_ = [("level", _u32), ("direction", _u32), ("n_f", _u64), ("m_f", _u64), ("m_u", _u64),
+                ("examined", _u64), ("q_bytes", _u64), ("b_bytes", _u64), ("v_bytes", _u64),
+                ("log_offset", _u64)]
+
+
+_lib = None
+
+_SIGS = {
+    "fq_status_string": ([_i32], ctypes.c_char_p),
+    "fq_queue_bound": ([_u64], _u64),
+    "fq_bitmap_bound": ([_u64], _u64),
+    "fq_workspace_bytes": ([_u64, _u64], _u64),
+    "fq_work_status": ([_vp, _vp, ctypes.POINTER(_u64)], _i32),
+    "fq_frontier_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_frontier_decode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_bitmap_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_bitmap_decode": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp], _i32),
+    "fq_graph_create": ([_vp, _vp, _u64, _u64, ctypes.POINTER(_vp)], _i32),
+    "fq_graph_destroy": ([_vp], _i32),
+    "fq_bfs_run": ([_vp, _u32, _vp, _vp, ctypes.POINTER(fq_bfs_opts), ctypes.POINTER(fq_bfs_stats),
+                    ctypes.POINTER(fq_level_record), _u32, _vp, _u64, _vp], _i32),
+}
+
+
+def lib():
+    """The loaded libfqbfs.so (ctypes.CDLL).  Raises if the library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfqbfs.so is not built ({LIB_PATH}); run paper_1704_00513_gb300.build.build()")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(l, name)
+            fn.argtypes, fn.restype = args, res
+        _lib = l
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().fq_status_string(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(status: int, what: str):
+    if status != FQ_OK:
+        raise FqError(status, what)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _device_status(work: torch.Tensor, stream, what: str):
+    detail = _u64(0)
+    st = lib().fq_work_status(_ptr(work), _stream(stream), ctypes.byref(detail))
+    if st != FQ_OK:
+        raise FqError(st, what, detail.value)
+
+
+# ----------------------------------------------------------------------------- sizes
+
+def fq_queue_bound(n: int) -> int:
+    return int(lib().fq_queue_bound(n))
+
+
+def fq_bitmap_bound(nbits: int) -> int:
+    return int(lib().fq_bitmap_bound(nbits))
+
+
+def fq_workspace_bytes(max_ids: int, max_nbits: int) -> int:
+    return int(lib().fq_workspace_bytes(max_ids, max_nbits))
+
+
+def workspace(max_ids: int, max_nbits: int, device="cuda") -> torch.Tensor:
+    """A codec workspace tensor (uint8) for calls on up to max_ids ids / max_nbits bits."""
+    return torch.empty(fq_workspace_bytes(max_ids, max_nbits), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------------------- codec calls
+
+def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work: torch.Tensor | None = None,
+                       stream=None, sync: bool = True):
+    """Encode sorted unique uint32 ids (an int32/uint32 CUDA tensor).  Returns (stream bytes, size)
+    when sync, else (out buffer, device size tensor)."""
+    n = ids.numel()
+    if out is None:
+        out = torch.empty(fq_queue_bound(n), dtype=torch.uint8, device=ids.device)
+    if work is None:
+        work = workspace(n, 0, ids.device)
+    nbytes = torch.zeros(1, dtype=torch.int64, device=ids.device)
+    _check(lib().fq_frontier_encode(_ptr(ids), n, _ptr(out), out.numel(), _ptr(nbytes), _ptr(work), work.numel(),
+                                    _stream(stream)), "fq_frontier_encode")
+    if not sync:
+        return out, nbytes
+    _device_status(work, stream, "fq_frontier_encode")
+    size = int(nbytes.item())
+    return out[:size], size
+
+
+def fq_frontier_decode(stream_bytes: torch.Tensor, cap: int, out: torch.Tensor | None = None,
+                       work: torch.Tensor | None = None, stream=None, in_bytes: int | None = None):
+    """Decode an FQ stream (uint8 CUDA tensor) into at most cap ids; returns the int32 ids."""
+    dev = stream_bytes.device
+    if out is None:
+        out = torch.empty(max(cap, 4), dtype=torch.int32, device=dev)
+    if work is None:
+        work = workspace(cap, 0, dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    nb = stream_bytes.numel() if in_bytes is None else in_bytes
+    _check(lib().fq_frontier_decode(_ptr(stream_bytes), nb, _ptr(out), cap, _ptr(n), _ptr(work), work.numel(),
+                                    _stream(stream)), "fq_frontier_decode")
+    _device_status(work, stream, "fq_frontier_decode")
+    return out[: int(n.item())]
+
+
+def fq_bitmap_encode(words: torch.Tensor, nbits: int, out: torch.Tensor | None = None,
+                     work: torch.Tensor | None = None, stream=None):
+    """Encode a bitmap held in a CUDA tensor (any integer dtype, uint64 word layout)."""
+    dev = words.device
+    if out is None:
+        out = torch.empty(fq_bitmap_bound(nbits), dtype=torch.uint8, device=dev)
+    if work is None:
+        work = workspace(0, nbits, dev)
+    nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check(lib().fq_bitmap_encode(_ptr(words), nbits, _ptr(out), out.numel(), _ptr(nbytes), _ptr(work), work.numel(),
+                                  _stream(stream)), "fq_bitmap_encode")
+    _device_status(work, stream, "fq_bitmap_encode")
+    size = int(nbytes.item())
+    return out[:size], size
+
+
+def fq_bitmap_decode(stream_bytes: torch.Tensor, nbits: int, out: torch.Tensor | None = None,
+                     work: torch.Tensor | None = None, stream=None, in_bytes: int | None = None):
+    """Decode an FB stream; returns the bitmap as int32 words (uint64 layout, 2 per uint64 word)."""
+    dev = stream_bytes.device
+    nwords64 = (nbits + 63) // 64
+    if out is None:
+        out = torch.empty(2 * max(nwords64, 1), dtype=torch.int32, device=dev)
+    if work is None:
+        work = workspace(0, nbits, dev)
+    nb = stream_bytes.numel() if in_bytes is None else in_bytes
+    _check(lib().fq_bitmap_decode(_ptr(stream_bytes), nb, _ptr(out), nbits, _ptr(work), work.numel(), _stream(stream)),
+           "fq_bitmap_decode")
+    _device_status(work, stream, "fq_bitmap_decode")
+    return out[: 2 * nwords64]
+
+
+# ----------------------------------------------------------------------------- BFS
+
+@dataclass
+class BfsResult:
+    depth: torch.Tensor
+    parent: torch.Tensor | None
+    stats: dict
+    levels: list
+    stream_log: torch.Tensor | None = None
+    streams: list = field(default_factory=list)
+
+
+def _stats_dict(s: fq_bfs_stats) -> dict:
+    d = {k: getattr(s, k) for k, _ in fq_bfs_stats._fields_ if not k.startswith("kernel")}
+    d["kernel_ms"] = dict(zip(KCLASS, list(s.kernel_ms)))
+    d["kernel_launches"] = dict(zip(KCLASS, list(s.kernel_launches)))
+    d["kernel_bytes"] = dict(zip(KCLASS, list(s.kernel_bytes)))
+    return d
+
+
+class Graph:
+    """fq_graph handle over a CSR graph resident on the GPU (offsets int64[n+1], cols int32[m]).
+    The tensors are kept referenced for the handle's lifetime."""
+
+    def __init__(self, offsets: torch.Tensor, cols: torch.Tensor):
+        assert offsets.is_cuda and cols.is_cuda and offsets.dtype == torch.int64
+        self.offsets, self.cols = offsets.contiguous(), cols.contiguous()
+        self.n = offsets.numel() - 1
+        self.m = cols.numel()
+        h = _vp()
+        with torch.cuda.device(offsets.device):
+            _check(lib().fq_graph_create(_ptr(self.offsets), _ptr(self.cols), self.n, self.m, ctypes.byref(h)),
+                   "fq_graph_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fq_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bfs(self, root: int, depth: torch.Tensor | None = None, parent: torch.Tensor | None | bool = True,
+            alpha: int = 14, beta: int = 24, flags: int = 0, record_streams: bool = False, max_levels: int = 4096,
+            stream=None) -> BfsResult:
+        dev = self.offsets.device
+        if depth is None:
+            depth = torch.empty(self.n, dtype=torch.int32, device=dev)
+        if parent is True:
+            parent = torch.empty(self.n, dtype=torch.int32, device=dev)
+        elif parent is False:
+            parent = None
+        opts = fq_bfs_opts(alpha, beta, flags, 0)
+        stats = fq_bfs_stats()
+        levels = (fq_level_record * max_levels)()
+        log = None
+        log_cap = 0
+        if record_streams:
+            log_cap = 3 * (fq_queue_bound(self.n) + 2 * fq_bitmap_bound(self.n)) + (1 << 20)
+            log = torch.empty(log_cap, dtype=torch.uint8, device=dev)
+        st = lib().fq_bfs_run(self._h, root, _ptr(depth), _ptr(parent), ctypes.byref(opts), ctypes.byref(stats),
+                              levels, max_levels, _ptr(log), log_cap, _stream(stream))
+        if st == FQ_ENOSPC and record_streams:
+            # grow the log to the total reported and run again
+            total = sum(levels[i].q_bytes + levels[i].b_bytes + levels[i].v_bytes for i in range(min(stats.levels, max_levels)))
+            log_cap = max(2 * total, log_cap * 4)
+            log = torch.empty(log_cap, dtype=torch.uint8, device=dev)
+            st = lib().fq_bfs_run(self._h, root, _ptr(depth), _ptr(parent), ctypes.byref(opts), ctypes.byref(stats),
+                                  levels, max_levels, _ptr(log), log_cap, _stream(stream))
+        _check(st, "fq_bfs_run")
+        lv = []
+        for i in range(min(stats.levels, max_levels)):
+            r = levels[i]
+            lv.append({k: getattr(r, k) for k, _ in fq_level_record._fields_})
+        res = BfsResult(depth, parent, _stats_dict(stats), lv, log)
+        if record_streams:
+            for r in lv:
+                o = r["log_offset"]
+                q = log[o: o + r["q_bytes"]]
+                b = log[o + r["q_bytes"]: o + r["q_bytes"] + r["b_bytes"]]
+                v = log[o + r["q_bytes"] + r["b_bytes"]: o + r["q_bytes"] + r["b_bytes"] + r["v_bytes"]]
+                res.streams.append(dict(level=r["level"], Q=q, B=b, V=v))
+        return res

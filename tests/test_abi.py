@@ -1,0 +1,54 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry point that
+include/fqbfs.h declares; its pure-host size functions agree with the stream-size definitions
+(no device computation runs here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_1704_00513_gb300 import build as fqbuild
+from paper_1704_00513_gb300 import fqbfs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fqbfs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fqbuild.build()
+    return fqbfs.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(fq_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["fq_frontier_encode", "fq_frontier_decode", "fq_bitmap_encode", "fq_bitmap_decode",
+                     "fq_graph_create", "fq_graph_destroy", "fq_bfs_run", "fq_workspace_bytes", "fq_work_status"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert names
+    for name in names:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+    assert set(names) <= set(fqbfs.exported_symbols())
+
+
+def test_host_size_functions_match_stream_definitions(lib):
+    for n in [0, 1, 3, 4, 5, 127, 128, 1000, 2**20 + 3]:
+        assert fqbfs.fq_queue_bound(n) == oracle.fq_raw_size(n) == 16 + (4 * n + 15) // 16 * 16
+    for nbits in [0, 1, 63, 64, 65, 128, 129, 2**24]:
+        assert fqbfs.fq_bitmap_bound(nbits) == oracle.fb_raw_size(nbits)
+    a = fqbfs.fq_workspace_bytes(1000, 0)
+    assert a >= 256 and fqbfs.fq_workspace_bytes(10**6, 0) > a
+    assert fqbfs.fq_workspace_bytes(0, 2**24) >= 4 * (2**23)    # room for the minority positions
+    assert lib.fq_status_string(4) == b"FQ_ECORRUPT"
