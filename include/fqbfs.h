@@ -105,6 +105,27 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
 fq_status fq_frontier_decode(const uint8_t *d_in, uint64_t in_bytes, uint32_t *d_ids, uint64_t cap,
                              uint64_t *d_n, void *d_work, uint64_t work_bytes, void *stream);
 
+/* ------------------------------------------------------------------ encode without a workspace
+ * The thesis has no counterpart to this entry point.  It serves callers that cannot allocate
+ * device memory -- code running inside another framework's memory pool, which must not see
+ * foreign cudaMalloc/cudaFree calls, or latency-critical paths that may not call the allocator
+ * (it can synchronise the device).  It encodes exactly like fq_frontier_encode, but its scratch
+ * is a fixed array inside the library's device image, reserved on every GPU that loads the
+ * library until the process exits, so the caller passes only input, output and stream.
+ *  - n must not exceed FQ_STATIC_MAX_IDS (2^24 ids); a larger n returns FQ_EINVAL and
+ *    enqueues nothing.
+ *  - The first call on a device looks up the array's device address once and caches it; make
+ *    that first call before any stream capture on that device.
+ *  - Every call uses the same array and it keeps the last call's contents: calls that may
+ *    overlap on the GPU (other streams, other host threads) race and corrupt each other's
+ *    output, so serialise them.
+ *  - Device-detected errors show only in *d_out_bytes: 0 when the input is not strictly
+ *    increasing; a value above cap (the size needed) when cap is too small.
+ *  - Pointers must be 16-byte aligned.  No allocator is called. */
+#define FQ_STATIC_MAX_IDS (1ull << 24)
+fq_status fq_frontier_encode_static(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
+                                    uint64_t *d_out_bytes, void *stream);
+
 /* ------------------------------------------------------------------ bitmap codec */
 
 /* Encode the bitmap d_words (ceil(nbits/64) words; bits >= nbits ignored) as an FB stream at

@@ -1,0 +1,63 @@
+// codec_static.cu -- fq_frontier_encode_static: the frontier encode without a caller workspace.
+//
+// Who needs it: code that runs where device allocation is off limits -- for example a plugin
+// invoked inside another framework's memory pool (which must not see foreign cudaMalloc/cudaFree
+// calls), or a real-time path that may not call into the allocator (cudaMalloc/cudaFree can
+// synchronise the device and take unbounded time).  Such a caller still owns its input and output
+// buffers but cannot provide scratch, so the encoder's scratch (per-block widths and bases,
+// per-tile sums and offsets, the status record) lives in one fixed array in device memory
+// declared below.  Every GPU that loads this library reserves that array until the process
+// exits, which is why its size is kept modest (FQ_STATIC_MAX_IDS ids).
+//
+// The kernels are the ones fq_frontier_encode launches; only the scratch location differs.
+#include <mutex>
+
+#include "fq_common.cuh"
+
+namespace {
+
+// Scratch for encoding up to FQ_STATIC_MAX_IDS ids (about 1.7 MB is used; 2 MiB reserved).
+constexpr size_t kStaticScratchBytes = 2u << 20;
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void *g_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device.  In host code the array's name is
+// only a host-side stand-in, so the address is asked from the runtime, once per device.
+cudaError_t static_scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" fq_status fq_frontier_encode_static(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
+                                               uint64_t *d_out_bytes, void *stream)
+{
+    if ((n && !d_ids) || !d_out || !d_out_bytes) return FQ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_ids) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 15u)) return FQ_EINVAL;
+    if (n > FQ_STATIC_MAX_IDS) return FQ_EINVAL;  // beyond the fixed scratch: nothing is enqueued
+    if (fq::workspace_bytes(n, 0) > kStaticScratchBytes) return FQ_EINVAL;
+    void *scratch = nullptr;
+    if (static_scratch_address(&scratch) != cudaSuccess) return FQ_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fq::Scratch s = fq::carve(scratch, n, 0);
+    // the status record must start cleared; the width/tile arrays are fully rewritten by each call
+    cudaError_t e = fq::reset_status(s, st);
+    if (e == cudaSuccess) e = fq::encode_fq(d_ids, n, nullptr, n, d_out, cap, d_out_bytes, s, st);
+    return e == cudaSuccess ? FQ_OK : FQ_ECUDA;
+}

@@ -62,6 +62,7 @@ _SIGS = {
     "fq_work_status": ([_vp, _vp, ctypes.POINTER(_u64)], _i32),
     "fq_frontier_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_decode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_frontier_encode_static": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fq_bitmap_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_bitmap_decode": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp], _i32),
     "fq_graph_create": ([_vp, _vp, _u64, _u64, ctypes.POINTER(_vp)], _i32),
