@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--edgefactor", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-codec", action="store_true")
+    p.add_argument("--codec-only", action="store_true",
+                   help="only the standalone codec points (sorted sets, geometric gaps); prints them as JSON")
     return p.parse_args()
 
 
@@ -321,6 +324,8 @@ def run_fqbfs(args, world, rank, local):
              "decode_GBps": kbytes["decode"] / max(1e-9, kms["decode"] / 1e3) / 1e9,
              "kernel_ms": {k: round(v, 3) for k, v in kms.items()}}
 
+    if not args.no_codec:
+        codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, off, cols, my_roots[args.warmup:], world)
@@ -345,6 +350,54 @@ def run_fqbfs(args, world, rank, local):
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
+
+
+def codec_points(dev, peak_gbs, points=((26, 1.0), (26, 16.0), (24, 256.0), (28, 4.0), (28, 15.0)), reps=5):
+    """Standalone frontier codec throughput on sorted sets with geometric gaps (the codec sweep's
+    shape): algorithmic bytes (4n + stream) / event-timed seconds, and the compression ratio."""
+    from paper_1704_00513_gb300 import fqbfs, inputs
+    res = []
+    stream = torch.cuda.current_stream()
+    for logn, mu in points:
+        n = 1 << logn
+        v = inputs.geometric_set(n, mu, seed=logn * 1000 + int(mu), device=dev)
+        if int(v[-1]) >= 2**32:
+            continue
+        ids = torch.where(v >= 2**31, v - 2**32, v).to(torch.int32)
+        del v
+        out = torch.empty(fqbfs.fq_queue_bound(n), dtype=torch.uint8, device=dev)
+        work = fqbfs.workspace(n, 0, dev)
+        nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+        dec = torch.empty(n, dtype=torch.int32, device=dev)
+        ndec = torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            fqbfs.fq_frontier_encode(ids, out=out, work=work, sync=False, nbytes=nbytes)
+        torch.cuda.synchronize()
+        size = int(nbytes.item())
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            fqbfs.fq_frontier_encode(ids, out=out, work=work, sync=False, nbytes=nbytes)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        t_enc = s0.elapsed_time(s1) / reps / 1e3
+        for _ in range(3):
+            fqbfs.fq_frontier_decode(out, cap=n, out=dec, work=work, in_bytes=size, sync=False, n_out=ndec)
+        s0.record(stream)
+        for _ in range(reps):
+            fqbfs.fq_frontier_decode(out, cap=n, out=dec, work=work, in_bytes=size, sync=False, n_out=ndec)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        t_dec = s0.elapsed_time(s1) / reps / 1e3
+        ok = bool(torch.equal(dec, ids))
+        alg = 4 * n + size
+        res.append({"n": n, "mean_gap": mu, "bytes": size, "ratio": 4 * n / size, "bits_per_id": 8 * size / n,
+                    "encode_GBps": alg / t_enc / 1e9, "decode_GBps": alg / t_dec / 1e9,
+                    "encode_frac": alg / t_enc / 1e9 / peak_gbs, "decode_frac": alg / t_dec / 1e9 / peak_gbs,
+                    "roundtrip_ok": ok})
+        del ids, out, work, dec
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_e2e(args, off, cols, roots, world):
@@ -385,6 +438,13 @@ def run_e2e(args, off, cols, roots, world):
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
+    if args.codec_only:
+        from paper_1704_00513_gb300 import build as fqbuild
+        fqbuild.build()
+        peaks, _ = measured_peaks()
+        print(json.dumps({"codec_sweep": codec_points(torch.device("cuda", torch.cuda.current_device()),
+                                                      peaks["hbm_gbs"])}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

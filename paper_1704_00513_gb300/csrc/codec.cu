@@ -23,7 +23,7 @@ namespace fq {
 
 namespace {
 struct Layout {
-    uint64_t widths, bases, block_off, tile_sum, tile_off, btile_cnt, btile_off, positions, total;
+    uint64_t widths, bases, block_off, tile_sum, tile_off, btile_cnt, btile_off, positions, tile_status, total;
     uint64_t ids_cap, nb_cap, etiles_cap, btiles_cap, pos_cap;
 };
 
@@ -46,6 +46,7 @@ Layout layout(uint64_t max_ids, uint64_t max_nbits)
     L.btile_cnt = o; o = align256(o + 4 * L.btiles_cap);
     L.btile_off = o; o = align256(o + 4 * L.btiles_cap);
     L.positions = o; o = align256(o + 4 * L.pos_cap);
+    L.tile_status = o; o = align256(o + 8 * L.etiles_cap);
     L.total = o;
     return L;
 }
@@ -69,6 +70,7 @@ Scratch carve(void *base, uint64_t max_ids, uint64_t max_nbits)
     s.btile_cnt = reinterpret_cast<uint32_t *>(b + L.btile_cnt);
     s.btile_off = reinterpret_cast<uint32_t *>(b + L.btile_off);
     s.positions = reinterpret_cast<uint32_t *>(b + L.positions);
+    s.tile_status = reinterpret_cast<unsigned long long *>(b + L.tile_status);
     s.ids_cap = L.ids_cap;
     s.nbits_cap = max_nbits;
     s.nb_cap = L.nb_cap;
@@ -107,6 +109,13 @@ struct EncArgs {
     uint64_t nbits;
     const uint64_t *fb_words;
     Scratch s;
+    // optional mirror: the same ids also written as an FB (SET) stream at m_out
+    uint8_t *m_out;
+    uint64_t m_cap;
+    uint64_t *m_out_bytes;
+    const uint64_t *m_words;
+    uint64_t m_nbits;
+    uint32_t subs;          // 32 KB sub-tiles per look-back tile (1 for small inputs, kSubs for large)
 };
 
 struct DecArgs {
@@ -128,254 +137,489 @@ __device__ __forceinline__ uint64_t dcdiv(uint64_t a, uint64_t b) { return (a + 
 
 __device__ __forceinline__ uint32_t ld_u32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
-// Four consecutive ids starting at i (a multiple of 4); ids past n are flagged invalid.
-__device__ __forceinline__ void load4(const uint32_t *ids, uint64_t i, uint64_t n, uint32_t v[4], bool valid[4])
+// ---- single-pass encode ----
+//
+// One kernel computes widths, the payload offsets and the packed words in one read of the ids.
+// Tiles of 64 blocks (8192 ids) are handed out in order through a ticket counter; each CTA keeps
+// its tile's ids in registers (8 blocks x 4 ids per lane), publishes the tile's width sum, finds
+// the sum over all earlier tiles by a decoupled look-back over their published words, then packs.
+// Tiles are taken in ticket order, so every tile a CTA waits for is held by a CTA that is already
+// running; the waits are bounded anyway (kSpinLimit polls, then FQ_ETIMEOUT).  Packed words are
+// written only where they fit below the raw size: if the raw form wins, enc_fixup_kernel writes
+// it over them.  The CTA holding the last tile decides packed/raw and writes the headers.
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
 {
-    if (i + 3 < n) {
-        uint4 q = *reinterpret_cast<const uint4 *>(ids + i);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        valid[0] = valid[1] = valid[2] = valid[3] = true;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            valid[j] = (i + j) < n;
-            v[j] = valid[j] ? ids[i + j] : 0u;
-        }
-    }
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
 }
 
-// Gaps of the four slots lane*4 .. lane*4+3 of block k: slot 0 of the block is 0; slot j >= 1
-// is v[j] - v[j-1] - 1; slots past n are 0.  Also reports the first unsorted index.
-__device__ __forceinline__ void block_gaps(const uint32_t *ids, uint64_t k, uint64_t n, uint32_t lane, uint32_t v[4],
-                                           uint32_t g[4], unsigned long long *bad)
+__device__ __forceinline__ void publish(unsigned long long *status, uint64_t t, unsigned long long flag,
+                                        unsigned long long value)
 {
-    bool valid[4];
-    const uint64_t i0 = k * kBlock + lane * 4u;
-    load4(ids, i0, n, v, valid);
-    uint32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
-    bool has_prev = lane > 0;
-    if (lane == 0 && k > 0) {
-        prev = ids[k * kBlock - 1];
-        has_prev = true;
-    }
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        g[j] = 0;
-        if (!valid[j]) continue;
-        const uint32_t p = (j == 0) ? prev : v[j - 1];
-        const bool hp = (j == 0) ? has_prev : true;
-        if (hp) {
-            if (v[j] <= p) {
-                *bad = min(*bad, (unsigned long long)(i0 + j));
-            } else if (!(lane == 0 && j == 0)) {
-                g[j] = v[j] - p - 1u;
+    __threadfence();
+    atomicExch(status + t, flag | (value & kValueMask));
+}
+
+// CTA-wide: sum of the width sums of tiles 0 .. t-1 (t >= 1), by decoupled look-back.  Every
+// thread polls one predecessor, so one round covers kEncThreads tiles: the running prefix moves
+// that many tiles per L2 round trip.  All threads of the CTA must call it.
+__device__ unsigned long long lookback(unsigned long long *status, uint64_t t, Ctl *c, unsigned long long *red,
+                                       uint32_t *s_first)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    unsigned long long excl = 0;
+    long long base = (long long)t - 1;
+    for (;;) {
+        const long long idx = base - (long long)tid;
+        unsigned long long w = kFlagPrefix;  // before tile 0: an empty prefix
+        if (idx >= 0) {
+            uint32_t spins = 0;
+            w = ld_volatile_u64(status + idx);
+            while ((w >> 62) == 0ull) {
+                if (++spins > kSpinLimit) {
+                    set_error(c, FQ_ETIMEOUT, kWhereEncWidths, (unsigned long long)idx);
+                    w = kFlagPrefix;
+                    break;
+                }
+                __nanosleep(32);
+                w = ld_volatile_u64(status + idx);
             }
         }
+        __threadfence();
+        if (tid == 0) *s_first = kEncThreads;
+        __syncthreads();
+        if ((w >> 62) == 2ull) atomicMin(s_first, tid);  // nearest predecessor holding a full prefix
+        __syncthreads();
+        const uint32_t first = *s_first;
+        unsigned long long val = (tid <= first) ? (w & kValueMask) : 0ull;
+        val = warp_sum64(val);
+        if (lane == 0) red[warp] = val;
+        __syncthreads();
+        unsigned long long sum = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kEncWarps; i++) sum += red[i];
+        __syncthreads();
+        excl += sum;
+        if (first < kEncThreads) return excl;
+        base -= kEncThreads;
     }
 }
 
-// E1: one warp per block -- width b_k, base_k, per-tile width sums.
-__global__ void __launch_bounds__(kEncThreads) enc_widths_kernel(EncArgs a)
-{
-    const uint64_t n = enc_count(a);
-    const uint64_t nb = dcdiv(n, kBlock);
-    const uint32_t tile = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    if ((uint64_t)tile * kTileBlocks >= nb) return;
-    __shared__ uint32_t wsum[kEncWarps];
-    uint32_t sum = 0;
-    unsigned long long bad = ~0ull;
-    for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
-        const uint64_t k = (uint64_t)tile * kTileBlocks + warp * kBlocksPerWarp + i;
-        if (k >= nb) break;
-        uint32_t v[4], g[4];
-        block_gaps(a.ids, k, n, lane, v, g, &bad);
-        const uint32_t mg = warp_max(max(max(g[0], g[1]), max(g[2], g[3])));
-        const uint32_t b = bitlen32(mg);
-        if (lane == 0) {
-            a.s.widths[k] = (uint8_t)b;
-            a.s.bases[k] = v[0];
-        }
-        sum += b;
-    }
-    if (lane == 0) wsum[warp] = sum;
-    if (bad != ~0ull) set_error(a.s.ctl, FQ_EUNSORTED, kWhereEncWidths, bad);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (uint32_t w = 0; w < kEncWarps; w++) t += wsum[w];
-        a.s.tile_sum[tile] = t;
-    }
-}
+__device__ __forceinline__ uint64_t fb_raw_size(uint64_t nbits) { return 16u + dpad16(8u * dcdiv(nbits, 64)); }
 
-// E2: one CTA -- exclusive scan of the tile width sums, packed/raw (and FB raw) decision,
-// capacity check, headers.
-__global__ void __launch_bounds__(kScanThreads) enc_plan_kernel(EncArgs a)
+// Decide the modes, write headers and sizes.  Called by one thread after every tile published.
+__device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total)
 {
-    __shared__ unsigned long long sm[33];
-    const uint64_t n = enc_count(a);
-    const uint64_t nb = dcdiv(n, kBlock);
-    const uint64_t ntiles = dcdiv(nb, kTileBlocks);
-    const uint64_t chunk = dcdiv(ntiles, kScanThreads);
-    const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
-    unsigned long long local = 0, total = 0;
-    for (uint64_t t = t0; t < t1; t++) local += a.s.tile_sum[t];
-    unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
-    for (uint64_t t = t0; t < t1; t++) {
-        a.s.tile_off[t] = (uint32_t)run;
-        run += a.s.tile_sum[t];
-    }
-    if (threadIdx.x != 0) return;
     Ctl *c = a.s.ctl;
+    __threadfence();
     c->n = n;
     c->nb = nb;
     c->total_b = total;
     c->fq_offset = a.fb ? 16u : 0u;
-    if (c->code != FQ_OK) {
+    const int32_t code = *reinterpret_cast<volatile int32_t *>(&c->code);
+    if (code != FQ_OK) {
         c->mode = kModeNone;
+        c->mode2 = kModeNone;
         *a.out_bytes = 0;
+        if (a.m_out) *a.m_out_bytes = 0;
         return;
     }
     const uint64_t packed = 16u + dpad16(5u * nb) + 16u * total;
     const uint64_t raw = 16u + dpad16(4u * n);
     const bool is_packed = n > 0 && packed < raw;
     const uint64_t fq_size = is_packed ? packed : raw;
-    uint32_t mode = is_packed ? kModePacked : kModeRaw;
+    const uint32_t fq_mode = is_packed ? kModePacked : kModeRaw;
+    uint32_t mode = fq_mode;
     uint64_t size = fq_size;
     if (a.fb) {
-        const uint64_t fb_raw = 16u + dpad16(8u * dcdiv(a.nbits, 64));
-        if (16u + fq_size >= fb_raw) {
+        const uint64_t fbr = fb_raw_size(a.nbits);
+        if (16u + fq_size >= fbr) {
             mode = kModeFbRaw;
-            size = fb_raw;
+            size = fbr;
         } else {
             size = 16u + fq_size;
+        }
+    }
+    uint32_t mode2 = kModeNone;
+    uint64_t size2 = 0;
+    if (a.m_out) {
+        const uint64_t fbr = fb_raw_size(a.m_nbits);
+        if (2u * n > a.m_nbits) {
+            set_error(c, FQ_EINVAL, kWhereEncPlan, n);  // the mirror is only defined for SET mode
+        } else if (16u + fq_size >= fbr) {
+            mode2 = kModeFbRaw;
+            size2 = fbr;
+        } else {
+            mode2 = fq_mode;
+            size2 = 16u + fq_size;
+        }
+        if (size2 > a.m_cap) {
+            set_error(c, FQ_ENOSPC, kWhereEncPlan, size2);
+            mode2 = kModeNone;
         }
     }
     if (size > a.cap) {
         set_error(c, FQ_ENOSPC, kWhereEncPlan, size);
         c->mode = kModeNone;
+        c->mode2 = kModeNone;
         *a.out_bytes = size;
+        if (a.m_out) *a.m_out_bytes = 0;
         return;
     }
-    uint32_t *h = reinterpret_cast<uint32_t *>(a.out);
-    if (a.fb) {
-        h[0] = kMagicBitmap;
-        h[1] = (mode == kModeFbRaw) ? kFbRaw : c->fb_mode;
-        h[2] = (uint32_t)(a.nbits & 0xffffffffu);
-        h[3] = (uint32_t)(a.nbits >> 32);
-        h += 4;
-    }
-    if (mode == kModePacked) {
-        h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
-    } else if (mode == kModeRaw) {
-        h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
+    // headers (+ the zero pad between the width bytes and the payload of a packed stream)
+    for (int which = 0; which < 2; which++) {
+        uint8_t *base = which == 0 ? a.out : a.m_out;
+        const uint32_t md = which == 0 ? mode : mode2;
+        if (!base || md == kModeNone) continue;
+        uint32_t *h = reinterpret_cast<uint32_t *>(base);
+        const bool fbc = which == 1 || a.fb;
+        if (fbc) {
+            const uint64_t nbits = which == 0 ? a.nbits : a.m_nbits;
+            h[0] = kMagicBitmap;
+            h[1] = (md == kModeFbRaw) ? kFbRaw : (which == 0 ? c->fb_mode : kFbSet);
+            h[2] = (uint32_t)(nbits & 0xffffffffu);
+            h[3] = (uint32_t)(nbits >> 32);
+            h += 4;
+        }
+        if (md == kModePacked) {
+            h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
+            uint8_t *fq = reinterpret_cast<uint8_t *>(h);
+            for (uint64_t p = 16u + 5u * nb; p < 16u + dpad16(5u * nb); p++) fq[p] = 0;
+        } else if (md == kModeRaw) {
+            h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
+        }
     }
     c->mode = mode;
+    c->mode2 = mode2;
     c->out_bytes = size;
+    c->out2_bytes = size2;
     *a.out_bytes = size;
+    if (a.m_out) *a.m_out_bytes = size2;
 }
 
-// E3: one warp per block -- pack the gaps of block k into 4*b_k words.
-__global__ void __launch_bounds__(kEncThreads) enc_pack_kernel(EncArgs a)
-{
-    const Ctl *c = a.s.ctl;
-    const uint32_t mode = c->mode;
-    if (mode != kModePacked && mode != kModeRaw) return;
-    const uint64_t n = c->n, nb = c->nb;
-    uint8_t *fq = a.out + c->fq_offset;
-    const uint32_t tile = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+// ---- TMA staging helpers (1-D bulk copies into shared memory, completion on an mbarrier) ----
 
-    if (mode == kModeRaw) {
-        const uint64_t per_tile = (uint64_t)kTileBlocks * kBlock;
-        const uint64_t i0 = (uint64_t)tile * per_tile, i1 = min(n, i0 + per_tile);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(fq + 16);
-        for (uint64_t i = i0 + 4u * threadIdx.x; i < i1; i += 4u * kEncThreads) {
-            if (i + 3 < n) {
-                *reinterpret_cast<uint4 *>(dst + i) = *reinterpret_cast<const uint4 *>(a.ids + i);
-            } else {
-                for (uint64_t j = i; j < n; j++) dst[j] = a.ids[j];
-            }
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Issue a bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) global -> shared,
+// arriving on `bar` with the byte count as its transaction.
+__device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(sdst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Wait until phase `parity` of `bar` completes; bounded: gives up after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+constexpr uint32_t kSubIds = kTileBlocks * kBlock;    // 8192 ids = 32 KB per TMA stage
+constexpr uint32_t kSubs = 4;                         // sub-tiles per encode tile
+constexpr uint32_t kEncTileBlocks = kSubs * kTileBlocks;  // 256 blocks = 32768 ids per look-back
+constexpr size_t kOnepassSmem = 2 * kSubIds * sizeof(uint32_t);
+
+
+// Gaps of the four slots lane*4 .. lane*4+3 of block k from its four ids v; prev is the id
+// before the block (used only for the sortedness check of slot 0).
+__device__ __forceinline__ void gaps_of(const uint32_t v[4], uint32_t prev_block_last, bool has_prev_block, uint64_t k,
+                                        uint64_t n, uint32_t lane, uint32_t g[4], unsigned long long *bad)
+{
+    uint32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
+    bool has_prev = lane > 0;
+    if (lane == 0) {
+        prev = prev_block_last;
+        has_prev = has_prev_block;
+    }
+    const uint64_t i0 = k * kBlock + 4u * lane;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        g[j] = 0;
+        if (i0 + j >= n) continue;
+        const uint32_t p = (j == 0) ? prev : v[j - 1];
+        const bool hp = (j == 0) ? has_prev : true;
+        if (hp) {
+            if (v[j] <= p) *bad = min(*bad, (unsigned long long)(i0 + j));
+            else if (!(lane == 0 && j == 0)) g[j] = v[j] - p - 1u;
         }
-        // zero the pad [16 + 4n, 16 + pad16(4n)) -- owned by the tile holding id n-1 (tile 0 if n == 0)
-        const uint64_t last_tile = n ? (n - 1) / per_tile : 0;
-        if (tile == last_tile && threadIdx.x == 0)
-            for (uint64_t j = n; j < dcdiv(n, 4) * 4; j++) dst[j] = 0u;
+    }
+}
+
+__device__ __forceinline__ void load4_guard(const uint32_t *ids, uint64_t i, uint64_t n, uint32_t v[4])
+{
+    if (i + 3 < n) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(ids + i);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = (i + j < n) ? ids[i + j] : 0u;
+    }
+}
+
+// Single pass over the ids: tiles of 256 blocks are handed out in ticket order.  Pass A streams
+// the tile's four 32 KB sub-tiles through two shared-memory stages filled by TMA bulk copies
+// (the next sub-tile is in flight while one is measured) and records every block's width and
+// base; one decoupled look-back per tile gives the payload offset; pass B re-reads the tile's
+// ids (L2-resident by then) and packs.  The CTA holding the last tile decides packed/raw.
+__global__ void __launch_bounds__(kEncThreads, 3) enc_onepass_kernel(EncArgs a)
+{
+    extern __shared__ __align__(128) uint32_t sbuf[];  // [2][kSubIds]
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ uint32_t s_tile, s_next;
+    __shared__ uint32_t sw[kEncTileBlocks];     // widths of the tile's blocks
+    __shared__ uint32_t spre[kEncTileBlocks];   // exclusive prefix of the widths inside the tile
+    __shared__ unsigned long long s_excl, s_total;
+    __shared__ unsigned long long s_red[kEncWarps];
+    __shared__ uint32_t s_first;
+    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
+    Ctl *c = a.s.ctl;
+    const uint64_t n = enc_count(a);
+    const uint64_t nb = dcdiv(n, kBlock);
+    const uint32_t subs = a.subs;
+    const uint64_t nsubs = dcdiv(nb, kTileBlocks);
+    const uint64_t ntiles = dcdiv(nsubs, subs);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint64_t fq_off = a.fb ? 16u : 0u;
+    const uint64_t payload = 16u + dpad16(5u * nb);
+    // bytes of each output that may be written before the mode is known: anything beyond is only
+    // needed by a packed stream that is not smaller than the raw form, which is never kept
+    uint64_t bound = min(a.cap, fq_off + 16u + dpad16(4u * n));
+    if (a.fb) bound = min(bound, fb_raw_size(a.nbits));
+    uint64_t bound2 = 0;
+    if (a.m_out) bound2 = min(a.m_cap, min(16u + 16u + dpad16(4u * n), fb_raw_size(a.m_nbits)));
+
+    if (ntiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, 0ull);
         return;
     }
-
-    const uint64_t ntiles = dcdiv(nb, kTileBlocks);
-    if (tile >= ntiles) return;
-    __shared__ uint32_t sb[kTileBlocks];     // exclusive prefix of widths inside the tile
-    __shared__ uint8_t swidth[kTileBlocks];
-    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
-    if (threadIdx.x < kTileBlocks) {
-        const uint64_t k = (uint64_t)tile * kTileBlocks + threadIdx.x;
-        const uint32_t b = (k < nb) ? a.s.widths[k] : 0u;
-        swidth[threadIdx.x] = (uint8_t)b;
-        if (k < nb) {
-            reinterpret_cast<uint32_t *>(fq + 16)[k] = a.s.bases[k];
-            fq[16 + 4 * nb + k] = (uint8_t)b;
-        }
-    }
-    if (tile == 0 && threadIdx.x >= kTileBlocks && threadIdx.x < kTileBlocks + 16) {
-        const uint64_t p = 16u + 5u * nb + (threadIdx.x - kTileBlocks);
-        if (p < 16u + dpad16(5u * nb)) fq[p] = 0;
-    }
-    __syncthreads();
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.ids) & 15u) == 0;
+    auto bulk_sub = [&](uint64_t sub) { return aligned && (sub + 1) * kSubIds <= n; };
     if (threadIdx.x == 0) {
-        uint32_t r = 0;
-        for (uint32_t i = 0; i < kTileBlocks; i++) {
-            sb[i] = r;
-            r += swidth[i];
-        }
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+        s_next = atomicAdd(&c->tile_ticket, 1u);
     }
     __syncthreads();
-    const uint64_t payload = 16u + dpad16(5u * nb);
-    const uint64_t tile_base = a.s.tile_off[tile];
-    unsigned long long bad = ~0ull;
-    for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
-        const uint32_t local = warp * kBlocksPerWarp + i;
-        const uint64_t k = (uint64_t)tile * kTileBlocks + local;
-        if (k >= nb) break;
-        const uint32_t b = swidth[local];
-        if (b == 0) continue;
-        uint32_t v[4], g[4];
-        block_gaps(a.ids, k, n, lane, v, g, &bad);
-#pragma unroll
-        for (int j = 0; j < 4; j++) pk[warp][4 * lane + j] = 0u;
-        if (lane == 0) pk[warp][128] = 0u;
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (g[j] == 0u) continue;
-            const uint32_t pos = (4u * lane + j) * b;
-            const uint32_t w0 = pos >> 5, sh = pos & 31u;
-            atomicOr(&pk[warp][w0], g[j] << sh);
-            if (sh + b > 32u) atomicOr(&pk[warp][w0 + 1], g[j] >> (32u - sh));
+    uint32_t phase0 = 0u, phase1 = 0u;  // completed-phase parity of each stage's barrier
+    // Sub-tiles are consumed in the sequence: tile t's subs, then tile tn's subs, ...; element i
+    // is staged in stage i & 1.  Starting on element i issues the copy of element i + 1 into the
+    // other stage, whose previous element was consumed before the last barrier.
+    uint32_t seq = 0;
+    if (threadIdx.x == 0 && s_next < ntiles) {
+        const uint64_t sub = (uint64_t)s_next * subs;
+        if (sub < nsubs && bulk_sub(sub)) bulk_load(sbuf, a.ids + sub * kSubIds, kSubIds * 4u, &bars[0]);
+    }
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = s_next;
+            s_next = (s_next < ntiles) ? atomicAdd(&c->tile_ticket, 1u) : (uint32_t)ntiles;
         }
-        __syncwarp();
-        if (lane < b) {
-            uint4 q = make_uint4(pk[warp][4 * lane], pk[warp][4 * lane + 1], pk[warp][4 * lane + 2], pk[warp][4 * lane + 3]);
-            *reinterpret_cast<uint4 *>(fq + payload + 16u * (tile_base + sb[local] + lane)) = q;
+        __syncthreads();
+        const uint64_t t = s_tile, tn = s_next;
+        if (t >= ntiles) break;
+
+        // pass A: widths and bases, sub-tile by sub-tile
+        unsigned long long bad = ~0ull;
+        for (uint32_t j = 0; j < subs; j++, seq++) {
+            const uint64_t sub = t * subs + j;
+            const uint32_t stage = seq & 1u;
+            uint32_t *s = sbuf + stage * kSubIds;
+            if (threadIdx.x == 0) {
+                const uint64_t nxt = (j + 1 < subs) ? sub + 1 : (tn < ntiles ? (uint64_t)tn * subs : nsubs);
+                if (nxt < nsubs && bulk_sub(nxt))
+                    bulk_load(sbuf + (stage ^ 1u) * kSubIds, a.ids + nxt * kSubIds, kSubIds * 4u, &bars[stage ^ 1u]);
+            }
+            if (sub < nsubs) {
+                if (bulk_sub(sub)) {
+                    if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(c, FQ_ETIMEOUT, kWhereEncWidths, sub);
+                    if (stage) phase1 ^= 1u;
+                    else phase0 ^= 1u;
+                } else {  // ragged end (or unaligned ids): plain loads, zero past n
+                    for (uint32_t i = threadIdx.x; i < kSubIds; i += kEncThreads) {
+                        const uint64_t gi = sub * kSubIds + i;
+                        s[i] = gi < n ? a.ids[gi] : 0u;
+                    }
+                    __syncthreads();
+                }
+#pragma unroll 4
+                for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+                    const uint32_t lb = warp * kBlocksPerWarp + i;  // block inside the sub-tile
+                    const uint64_t k = sub * kTileBlocks + lb;
+                    uint32_t b = 0;
+                    if (k < nb) {
+                        const uint4 q = *reinterpret_cast<const uint4 *>(s + lb * kBlock + 4u * lane);
+                        const uint32_t v[4] = {q.x, q.y, q.z, q.w};
+                        uint32_t prevb = 0;
+                        if (lane == 0 && k > 0) prevb = lb > 0 ? s[lb * kBlock - 1] : a.ids[k * kBlock - 1];
+                        uint32_t g[4];
+                        gaps_of(v, prevb, k > 0, k, n, lane, g, &bad);
+                        b = bitlen32(__reduce_max_sync(0xffffffffu, max(max(g[0], g[1]), max(g[2], g[3]))));
+                        if (lane == 0) {
+                            const uint64_t pb = fq_off + 16u + 4u * k;
+                            if (pb + 4 <= bound) *reinterpret_cast<uint32_t *>(a.out + pb) = v[0];
+                            if (a.m_out && 32u + 4u * k + 4 <= bound2) *reinterpret_cast<uint32_t *>(a.m_out + 32u + 4u * k) = v[0];
+                        }
+                    }
+                    if (lane == 0) sw[j * kTileBlocks + lb] = b;
+                }
+            } else {
+                if (threadIdx.x < kTileBlocks) sw[j * kTileBlocks + threadIdx.x] = 0;
+            }
+            __syncthreads();  // stage consumed: it may be refilled from the next element on
         }
-        __syncwarp();
+        if (bad != ~0ull) set_error(c, FQ_EUNSORTED, kWhereEncWidths, bad);
+        if (subs < kSubs && threadIdx.x >= subs * kTileBlocks) sw[threadIdx.x] = 0;  // unused width slots
+        __syncthreads();
+
+        // tile prefix over its 256 widths (warp 0: 8 per lane), publication, look-back
+        if (warp == 0) {
+            uint32_t x[8], sum = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                x[i] = sw[8 * lane + i];
+                sum += x[i];
+            }
+            const uint32_t incl = warp_incl_scan(sum);
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                spre[8 * lane + i] = run;
+                run += x[i];
+            }
+            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 0) {
+                publish(a.s.tile_status, t, t == 0 ? kFlagPrefix : kFlagAgg, total);
+                s_total = total;
+            }
+        }
+        __syncthreads();
+        unsigned long long excl = 0;
+        if (t > 0) excl = lookback(a.s.tile_status, t, c, s_red, &s_first);
+        if (threadIdx.x == 0) {
+            if (t > 0) publish(a.s.tile_status, t, kFlagPrefix, excl + s_total);
+            s_excl = excl;
+        }
+        __syncthreads();
+        excl = s_excl;
+
+        // width bytes of the tile's blocks
+        if (threadIdx.x < subs * kTileBlocks) {
+            const uint64_t k = t * subs * kTileBlocks + threadIdx.x;
+            if (k < nb) {
+                const uint8_t b = (uint8_t)sw[threadIdx.x];
+                const uint64_t pw = fq_off + 16u + 4u * nb + k;
+                if (pw + 1 <= bound) a.out[pw] = b;
+                if (a.m_out && 32u + 4u * nb + k + 1 <= bound2) a.m_out[32u + 4u * nb + k] = b;
+            }
+        }
+
+        // pass B: pack (ids re-read; they were read moments ago, so from L2)
+        const uint32_t per_warp = subs * kTileBlocks / kEncWarps;
+        for (uint32_t i = 0; i < per_warp; i++) {
+            const uint32_t lb = warp * per_warp + i;
+            const uint64_t k = t * subs * kTileBlocks + lb;
+            if (k >= nb) break;
+            const uint32_t b = sw[lb];
+            if (b == 0) continue;
+            uint32_t v[4], g[4];
+            load4_guard(a.ids, k * kBlock + 4u * lane, n, v);
+            unsigned long long dummy = ~0ull;
+            gaps_of(v, 0u, false, k, n, lane, g, &dummy);
+#pragma unroll
+            for (int j = 0; j < 4; j++) pk[warp][4 * lane + j] = 0u;
+            if (lane == 0) pk[warp][128] = 0u;
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (g[j] == 0u) continue;
+                const uint32_t pos = (4u * lane + j) * b;
+                const uint32_t w0 = pos >> 5, sh = pos & 31u;
+                atomicOr(&pk[warp][w0], g[j] << sh);
+                if (sh + b > 32u) atomicOr(&pk[warp][w0 + 1], g[j] >> (32u - sh));
+            }
+            __syncwarp();
+            const uint64_t rel = payload + 16u * (excl + spre[lb]);
+            if (lane < b) {
+                const uint4 q = make_uint4(pk[warp][4 * lane], pk[warp][4 * lane + 1], pk[warp][4 * lane + 2],
+                                           pk[warp][4 * lane + 3]);
+                const uint64_t p1 = fq_off + rel + 16u * lane;
+                if (p1 + 16 <= bound) *reinterpret_cast<uint4 *>(a.out + p1) = q;
+                if (a.m_out) {
+                    const uint64_t p2 = 16u + rel + 16u * lane;
+                    if (p2 + 16 <= bound2) *reinterpret_cast<uint4 *>(a.m_out + p2) = q;
+                }
+            }
+            __syncwarp();
+        }
+
+        if (t == ntiles - 1 && threadIdx.x == 0) enc_finalize(a, n, nb, excl + s_total);
+        __syncthreads();
     }
 }
 
-// FB raw container: copy the words (tail bits cleared) behind the 16-byte header.
-__global__ void fb_raw_kernel(EncArgs a)
+// Raw bodies (FQ raw ids, or FB raw words) for whichever output the finalisation chose them.
+__global__ void enc_fixup_kernel(EncArgs a)
 {
-    if (a.s.ctl->mode != kModeFbRaw) return;
-    const uint64_t nwords = dcdiv(a.nbits, 64);
-    uint64_t *dst = reinterpret_cast<uint64_t *>(a.out + 16);
-    const uint64_t padded = dcdiv(nwords, 2) * 2;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < padded; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t w = 0;
-        if (i < nwords) {
-            w = a.fb_words[i];
-            const uint32_t tail = (uint32_t)(a.nbits & 63u);
-            if (i == nwords - 1 && tail) w &= (1ull << tail) - 1ull;
+    const Ctl *c = a.s.ctl;
+    const uint32_t mode = c->mode, mode2 = a.m_out ? c->mode2 : kModeNone;
+    if (mode != kModeRaw && mode != kModeFbRaw && mode2 != kModeRaw && mode2 != kModeFbRaw) return;
+    const uint64_t n = c->n;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int which = 0; which < 2; which++) {
+        const uint32_t md = which == 0 ? mode : mode2;
+        uint8_t *base = which == 0 ? a.out : a.m_out;
+        if (md == kModeRaw) {
+            uint32_t *dst = reinterpret_cast<uint32_t *>(base + (which == 0 ? (a.fb ? 16u : 0u) : 16u) + 16u);
+            const uint64_t padded = dcdiv(n, 4) * 4;
+            for (uint64_t i = tid; i < padded; i += stride) dst[i] = i < n ? a.ids[i] : 0u;
+        } else if (md == kModeFbRaw) {
+            const uint64_t nbits = which == 0 ? a.nbits : a.m_nbits;
+            const uint64_t *src = which == 0 ? a.fb_words : a.m_words;
+            const uint64_t nwords = dcdiv(nbits, 64);
+            const uint64_t padded = dcdiv(nwords, 2) * 2;
+            const uint32_t tail = (uint32_t)(nbits & 63u);
+            uint64_t *dst = reinterpret_cast<uint64_t *>(base + 16);
+            for (uint64_t i = tid; i < padded; i += stride) {
+                uint64_t w = 0;
+                if (i < nwords) {
+                    w = src[i];
+                    if (i == nwords - 1 && tail) w &= (1ull << tail) - 1ull;
+                }
+                dst[i] = w;
+            }
         }
-        dst[i] = w;
     }
 }
 
@@ -472,119 +716,164 @@ __global__ void __launch_bounds__(kBitThreads) bits_extract_kernel(const uint64_
 
 // ---- decode ----
 
-// D1: one CTA -- validate the container and FQ header, scan widths into block offsets.
-__global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
+// ---- decode ----
+//
+// D0 (many CTAs): per tile of 64 blocks, the sum of the block widths (widths > 32 flagged).
+// D1 (one CTA):   header validation, scan of the tile sums into tile offsets, size checks.
+// D2 (many CTAs): per tile, block offsets from the tile offset + a local scan; one warp per block
+//                 unpacks, prefix-sums the gaps, validates and writes the ids (or bits).
+// Every check that bounds a read or a write happens before that access: no output is written
+// unless the header, the widths and the sizes are consistent with in_bytes and the capacity.
+
+struct FqHeader {
+    bool ok;          // container and FQ header readable and self-consistent (sizes not yet summed)
+    bool over;        // n above the output capacity
+    uint32_t mode;    // kModePacked / kModeRaw / kModeFbRaw
+    uint32_t fb_mode;
+    uint64_t fq_off, fq_bytes, n, nb, words;
+};
+
+__device__ FqHeader parse_header(const DecArgs &a, uint64_t in_bytes)
 {
-    __shared__ unsigned long long sm[33];
-    __shared__ int s_ok;
-    __shared__ uint32_t s_mode, s_fbmode;
-    __shared__ unsigned long long s_n, s_nb, s_words, s_fq_bytes, s_fq_off, s_bad;
-    __shared__ int s_over;
-    Ctl *c = a.s.ctl;
-    const uint64_t in_bytes = a.in_bytes_dev ? *a.in_bytes_dev : a.in_bytes_host;
+    FqHeader h{};
+    h.ok = true;
+    h.over = false;
+    h.mode = kModeNone;
+    h.fb_mode = kFbRaw;
+    h.fq_off = 0;
+    h.fq_bytes = in_bytes;
     const uint64_t limit = a.fb ? a.nbits : a.cap;
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        s_over = 0;
-        s_bad = ~0ull;
-        s_mode = kModeNone;
-        s_fbmode = kFbRaw;
-        s_fq_off = 0;
-        s_fq_bytes = in_bytes;
-        s_n = s_nb = s_words = 0;
-        if (a.fb) {
-            if (in_bytes < 16 || ld_u32(a.in) != kMagicBitmap ||
-                ((uint64_t)ld_u32(a.in + 8) | ((uint64_t)ld_u32(a.in + 12) << 32)) != a.nbits) {
-                s_ok = 0;
-            } else {
-                const uint32_t m = ld_u32(a.in + 4);
-                if (m == kFbRaw) {
-                    if (in_bytes != 16u + dpad16(8u * dcdiv(a.nbits, 64))) s_ok = 0;
-                    else s_mode = kModeFbRaw;
-                } else if (m == kFbSet || m == kFbClear) {
-                    s_fbmode = m;
-                    s_fq_off = 16;
-                    s_fq_bytes = in_bytes - 16u;
-                } else {
-                    s_ok = 0;
-                }
-            }
+    if (a.fb) {
+        if (in_bytes < 16 || ld_u32(a.in) != kMagicBitmap ||
+            ((uint64_t)ld_u32(a.in + 8) | ((uint64_t)ld_u32(a.in + 12) << 32)) != a.nbits) {
+            h.ok = false;
+            return h;
         }
-        if (s_ok && s_mode != kModeFbRaw) {
-            const uint8_t *fq = a.in + s_fq_off;
-            const uint64_t fqb = s_fq_bytes;
-            if (fqb < 16) {
-                s_ok = 0;
-            } else {
-                const uint32_t magic = ld_u32(fq);
-                const uint64_t n = ld_u32(fq + 4), nb = ld_u32(fq + 8), words = ld_u32(fq + 12);
-                s_n = n; s_nb = nb; s_words = words;
-                if (n > limit) {
-                    s_ok = 0;  // more ids than the output (or the scratch) holds: nothing is written
-                    s_over = 1;
-                } else if (magic == kMagicRaw) {
-                    if (nb != 0 || words != n || fqb != 16u + dpad16(4u * n)) s_ok = 0;
-                    else {
-                        for (uint64_t i = 16u + 4u * n; i < fqb; i++)
-                            if (fq[i]) s_ok = 0;
-                        s_mode = kModeRaw;
-                    }
-                } else if (magic == kMagicPacked) {
-                    if (nb != dcdiv(n, kBlock) || n == 0 || fqb < 16u + dpad16(5u * nb)) s_ok = 0;
-                    else {
-                        for (uint64_t i = 16u + 5u * nb; i < 16u + dpad16(5u * nb); i++)
-                            if (fq[i]) s_ok = 0;
-                        s_mode = kModePacked;
-                    }
-                } else {
-                    s_ok = 0;
-                }
-            }
+        const uint32_t m = ld_u32(a.in + 4);
+        if (m == kFbRaw) {
+            h.ok = in_bytes == 16u + dpad16(8u * dcdiv(a.nbits, 64));
+            h.mode = kModeFbRaw;
+            return h;
         }
+        if (m != kFbSet && m != kFbClear) {
+            h.ok = false;
+            return h;
+        }
+        h.fb_mode = m;
+        h.fq_off = 16;
+        h.fq_bytes = in_bytes - 16u;
     }
-    __syncthreads();
-    if (s_ok && s_mode == kModePacked) {
-        const uint8_t *fq = a.in + s_fq_off;
-        const uint64_t nb = s_nb;
-        const uint8_t *wd = fq + 16 + 4 * nb;
-        const uint64_t chunk = dcdiv(nb, kScanThreads);
-        const uint64_t k0 = (uint64_t)threadIdx.x * chunk, k1 = min(nb, k0 + chunk);
-        unsigned long long local = 0, total = 0;
-        for (uint64_t k = k0; k < k1; k++) {
-            const uint32_t b = wd[k];
-            if (b > 32u) atomicMin(&s_bad, (unsigned long long)(16 + 4 * nb + k));
-            local += b;
+    const uint8_t *fq = a.in + h.fq_off;
+    if (h.fq_bytes < 16) {
+        h.ok = false;
+        return h;
+    }
+    const uint32_t magic = ld_u32(fq);
+    h.n = ld_u32(fq + 4);
+    h.nb = ld_u32(fq + 8);
+    h.words = ld_u32(fq + 12);
+    if (h.n > limit) {  // more ids than the output (or the scratch) holds: nothing is written
+        h.ok = false;
+        h.over = true;
+        return h;
+    }
+    if (magic == kMagicRaw) {
+        h.mode = kModeRaw;
+        h.ok = h.nb == 0 && h.words == h.n && h.fq_bytes == 16u + dpad16(4u * h.n);
+    } else if (magic == kMagicPacked) {
+        h.mode = kModePacked;
+        h.ok = h.nb == dcdiv(h.n, kBlock) && h.n > 0 && h.fq_bytes >= 16u + dpad16(5u * h.nb);
+    } else {
+        h.ok = false;
+    }
+    return h;
+}
+
+__device__ __forceinline__ uint64_t dec_in_bytes(const DecArgs &a)
+{
+    return a.in_bytes_dev ? *a.in_bytes_dev : a.in_bytes_host;
+}
+
+// D0
+__global__ void __launch_bounds__(kEncThreads) dec_tiles_kernel(DecArgs a)
+{
+    __shared__ uint32_t ws[kEncWarps];
+    const FqHeader h = parse_header(a, dec_in_bytes(a));
+    if (!h.ok || h.mode != kModePacked) return;
+    const uint8_t *wd = a.in + h.fq_off + 16 + 4 * h.nb;
+    const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t b = 0;
+        if (threadIdx.x < kTileBlocks) {
+            const uint64_t k = t * kTileBlocks + threadIdx.x;
+            if (k < h.nb) {
+                b = wd[k];
+                if (b > 32u) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.fq_off + 16 + 4 * h.nb + k);
+            }
         }
-        unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
-        for (uint64_t k = k0; k < k1; k++) {
-            a.s.block_off[k] = (uint32_t)run;
-            run += wd[k];
-        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = b;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            if (s_bad != ~0ull || s_words != 4u * total || s_fq_bytes != 16u + dpad16(5u * nb) + 16u * total)
-                s_ok = 0;
+            uint32_t sum = 0;
+            for (uint32_t i = 0; i < kEncWarps; i++) sum += ws[i];
+            a.s.tile_sum[t] = sum;
         }
         __syncthreads();
     }
+}
+
+// D1
+__global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
+{
+    __shared__ unsigned long long sm[33];
+    Ctl *c = a.s.ctl;
+    const FqHeader h = parse_header(a, dec_in_bytes(a));
+    bool ok = h.ok;
+    if (ok && h.mode == kModeRaw && threadIdx.x == 0) {
+        const uint8_t *fq = a.in + h.fq_off;
+        for (uint64_t i = 16u + 4u * h.n; i < h.fq_bytes; i++)
+            if (fq[i]) ok = false;
+    }
+    if (ok && h.mode == kModePacked) {
+        const uint8_t *fq = a.in + h.fq_off;
+        const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
+        const uint64_t chunk = dcdiv(ntiles, kScanThreads);
+        const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
+        unsigned long long local = 0, total = 0;
+        for (uint64_t t = t0; t < t1; t++) local += a.s.tile_sum[t];
+        unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
+        for (uint64_t t = t0; t < t1; t++) {
+            a.s.tile_off[t] = (uint32_t)run;
+            run += a.s.tile_sum[t];
+        }
+        if (threadIdx.x == 0) {
+            c->total_b = total;
+            if (h.words != 4u * total || h.fq_bytes != 16u + dpad16(5u * h.nb) + 16u * total) ok = false;
+            for (uint64_t i = 16u + 5u * h.nb; i < 16u + dpad16(5u * h.nb); i++)
+                if (fq[i]) ok = false;
+        }
+    }
     if (threadIdx.x != 0) return;
-    c->fq_offset = s_fq_off;
-    c->fb_mode = s_fbmode;
-    c->n = s_n;
-    c->nb = s_nb;
-    if (s_over) {
-        set_error(c, a.fb ? FQ_ECORRUPT : FQ_ENOSPC, kWhereDecPlan, s_n);
+    c->fq_offset = h.fq_off;
+    c->fb_mode = h.fb_mode;
+    c->n = h.n;
+    c->nb = h.nb;
+    if (h.over) {
+        set_error(c, a.fb ? FQ_ECORRUPT : FQ_ENOSPC, kWhereDecPlan, h.n);
         c->mode = kModeNone;
-        if (a.n_out) *a.n_out = s_n;
+        if (a.n_out) *a.n_out = h.n;
         return;
     }
-    if (!s_ok) {
-        set_error(c, FQ_ECORRUPT, kWhereDecPlan, s_bad != ~0ull ? s_bad : 0ull);
+    if (!ok || c->code != FQ_OK) {  // D0 may have flagged a width > 32
+        set_error(c, FQ_ECORRUPT, kWhereDecPlan, 0ull);
         c->mode = kModeNone;
         if (a.n_out) *a.n_out = 0;
         return;
     }
-    c->mode = s_mode;
-    if (a.n_out) *a.n_out = s_n;
+    c->mode = h.mode;
+    if (a.n_out) *a.n_out = h.n;
 }
 
 // FB decode, before the scatter: clear (SET) or fill (CLEAR) the words, or copy raw words.
@@ -630,9 +919,17 @@ __device__ __forceinline__ void emit_id(const DecArgs &a, uint32_t clear_mode, u
     else atomicOr(&w32[v >> 5], 1u << (v & 31u));
 }
 
-// D2: one warp per block -- unpack, prefix-sum the gaps, validate, write ids (or bits).
-__global__ void __launch_bounds__(kEncThreads) dec_unpack_kernel(DecArgs a)
+constexpr uint32_t kDecStage = kTileBlocks * 32u * 16u + 16u;  // a tile's largest payload + one word of slack
+constexpr size_t kDecSmem = 2 * (size_t)kDecStage;
+
+// D2: tiles of 64 blocks, assigned round-robin.  A tile's payload is one contiguous range, so one
+// TMA bulk copy stages it into shared memory; the next tile's copy is in flight while this one
+// is decoded (one warp per block: extract, prefix-sum the gaps, validate, 128-bit stores).
+__global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
 {
+    extern __shared__ __align__(128) uint8_t dbuf[];  // [2][kDecStage]
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ uint32_t spre[kTileBlocks];
     const Ctl *c = a.s.ctl;
     const uint32_t mode = c->mode;
     if (mode != kModePacked && mode != kModeRaw) return;
@@ -652,75 +949,104 @@ __global__ void __launch_bounds__(kEncThreads) dec_unpack_kernel(DecArgs a)
         return;
     }
 
-    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
     const uint8_t *wd = fq + 16 + 4 * nb;
     const uint32_t *bases = reinterpret_cast<const uint32_t *>(fq + 16);
     const uint8_t *payload = fq + 16 + dpad16(5u * nb);
-    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t k = gwarp; k < nb; k += nwarps) {
-        const uint32_t b = wd[k];
-        const uint64_t base = bases[k];
-        if (lane < b) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(payload + 16u * ((uint64_t)a.s.block_off[k] + lane));
-            pk[warp][4 * lane] = q.x; pk[warp][4 * lane + 1] = q.y; pk[warp][4 * lane + 2] = q.z; pk[warp][4 * lane + 3] = q.w;
+    const uint64_t ntiles = dcdiv(nb, kTileBlocks);
+    const uint64_t total = c->total_b;
+    auto tile_bytes = [&](uint64_t t) -> uint32_t {
+        const uint64_t end = (t + 1 < ntiles) ? a.s.tile_off[t + 1] : total;
+        return (uint32_t)(16u * (end - a.s.tile_off[t]));
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+        const uint64_t t0 = blockIdx.x;
+        if (t0 < ntiles && tile_bytes(t0))
+            bulk_load(dbuf, payload + 16u * (uint64_t)a.s.tile_off[t0], tile_bytes(t0), &bars[0]);
+    }
+    __syncthreads();
+    uint32_t phase0 = 0u, phase1 = 0u;
+    for (uint64_t i = 0;; i++) {
+        const uint64_t t = blockIdx.x + i * gridDim.x;
+        if (t >= ntiles) break;
+        const uint32_t stage = (uint32_t)(i & 1u);
+        const uint64_t tn = t + gridDim.x;
+        if (threadIdx.x == 0 && tn < ntiles && tile_bytes(tn))
+            bulk_load(dbuf + (stage ^ 1u) * kDecStage, payload + 16u * (uint64_t)a.s.tile_off[tn], tile_bytes(tn),
+                      &bars[stage ^ 1u]);
+        if (warp == 0) {
+            const uint64_t k0 = t * kTileBlocks + 2 * lane;
+            const uint32_t x0 = k0 < nb ? wd[k0] : 0u, x1 = k0 + 1 < nb ? wd[k0 + 1] : 0u;
+            const uint32_t incl = warp_incl_scan(x0 + x1);
+            spre[2 * lane] = incl - x0 - x1;
+            spre[2 * lane + 1] = incl - x1;
         }
-        if (lane == 0) pk[warp][4 * b] = 0u;
-        __syncwarp();
-        const uint32_t mask = (b == 32u) ? 0xffffffffu : ((1u << b) - 1u);
-        unsigned long long inc[4];
-        unsigned long long lsum = 0;
-        bool bad = false;
+        if (tile_bytes(t)) {
+            if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(a.s.ctl, FQ_ETIMEOUT, kWhereDecUnpack, t);
+            if (stage) phase1 ^= 1u;
+            else phase0 ^= 1u;
+        }
+        __syncthreads();
+        const uint32_t *sp = reinterpret_cast<const uint32_t *>(dbuf + stage * kDecStage);
+        for (uint32_t bi = 0; bi < kBlocksPerWarp; bi++) {
+            const uint32_t local = warp * kBlocksPerWarp + bi;
+            const uint64_t k = t * kTileBlocks + local;
+            if (k >= nb) break;
+            const uint32_t b = wd[k];
+            const uint64_t base = bases[k];
+            const uint32_t *pk = sp + 4u * spre[local];
+            const uint32_t mask = (b == 32u) ? 0xffffffffu : ((1u << b) - 1u);
+            unsigned long long inc[4];
+            unsigned long long lsum = 0;
+            bool bad = false;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const uint32_t slot = 4u * lane + j;
-            uint32_t g = 0;
-            if (b) {
-                const uint32_t pos = slot * b, w0 = pos >> 5, sh = pos & 31u;
-                const uint64_t two = ((uint64_t)pk[warp][w0 + 1] << 32) | pk[warp][w0];
-                g = (uint32_t)(two >> sh) & mask;
+            for (int j = 0; j < 4; j++) {
+                const uint32_t slot = 4u * lane + j;
+                uint32_t g = 0;
+                if (b) {
+                    const uint32_t pos = slot * b, w0 = pos >> 5, sh = pos & 31u;
+                    const uint64_t two = ((uint64_t)pk[w0 + 1] << 32) | pk[w0];
+                    g = (uint32_t)(two >> sh) & mask;
+                }
+                const uint64_t idx = k * kBlock + slot;
+                if (slot == 0 || idx >= n) {
+                    if (g) bad = true;
+                    inc[j] = 0;
+                } else {
+                    inc[j] = (unsigned long long)g + 1ull;
+                }
+                lsum += inc[j];
             }
-            const uint64_t i = k * kBlock + slot;
-            if (slot == 0 || i >= n) {
-                if (g) bad = true;
-                inc[j] = 0;
+            const unsigned long long excl = warp_incl_scan64(lsum) - lsum;
+            unsigned long long v = base + excl;
+            const uint64_t i0 = k * kBlock + 4u * lane;
+            uint32_t out[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                v += inc[j];
+                out[j] = (uint32_t)v;
+                if (i0 + j < n && v > 0xffffffffull) bad = true;
+            }
+            // a full block (k + 1 < nb) ends in lane 31's last slot: it must stay below the next base
+            if (k + 1 < nb && lane == 31 && v >= (unsigned long long)bases[k + 1]) bad = true;
+            if (bad) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, k * kBlock);
+            if (!a.fb && i0 + 3 < n) {
+                *reinterpret_cast<uint4 *>(a.ids + i0) = make_uint4(out[0], out[1], out[2], out[3]);
             } else {
-                inc[j] = (unsigned long long)g + 1ull;
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (i0 + j < n) emit_id(a, clear_mode, i0 + j, out[j]);
             }
-            lsum += inc[j];
         }
-        const unsigned long long excl = warp_incl_scan64(lsum) - lsum;
-        unsigned long long v = base + excl;
-        const uint64_t i0 = k * kBlock + 4u * lane;
-        uint32_t out[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            v += inc[j];
-            out[j] = (uint32_t)v;
-            if (i0 + j < n && v > 0xffffffffull) bad = true;
-        }
-        // a full block (k + 1 < nb) ends in lane 31's last slot: it must stay below the next base
-        if (k + 1 < nb && lane == 31 && v >= (unsigned long long)bases[k + 1]) bad = true;
-        if (bad) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, k * kBlock);
-        if (!a.fb && i0 + 3 < n) {
-            *reinterpret_cast<uint4 *>(a.ids + i0) = make_uint4(out[0], out[1], out[2], out[3]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (i0 + j < n) emit_id(a, clear_mode, i0 + j, out[j]);
-        }
-        __syncwarp();
+        __syncthreads();  // the stage is free for the copy two tiles ahead
     }
 }
 
-__global__ void reset_status_kernel(Ctl *c)
+__global__ void reset_status_kernel(Scratch s, uint64_t ntiles)
 {
-    c->code = FQ_OK;
-    c->where = 0;
-    c->detail = ~0ull;
-    c->mode = kModeNone;
-    c->fb_mode = kFbRaw;
-    c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = 0;
+    reset_scratch_device(s, ntiles, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 uint32_t grid_for(uint64_t items, uint32_t per_cta, uint32_t max_ctas)
@@ -729,26 +1055,77 @@ uint32_t grid_for(uint64_t items, uint32_t per_cta, uint32_t max_ctas)
     return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(g, 1), max_ctas);
 }
 
+uint64_t enc_tiles(uint64_t n) { return cdiv(cdiv(n, kBlock), kTileBlocks); }
+
+// Kernels with more than 48 KB of dynamic shared memory must opt in, once per device.
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes, bool *done)
+{
+    int dev = 0;
+    FQ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+        FQ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t prepare_unpack()
+{
+    static bool done[64] = {false};
+    return allow_smem(dec_unpack_kernel, kDecSmem, done);
+}
+
+cudaError_t launch_encode(EncArgs a, uint64_t n_max, cudaStream_t st)
+{
+    // large inputs amortise each look-back over kSubs sub-tiles; smaller ones need every CTA busy
+    const uint64_t nsubs = std::max<uint64_t>(1, cdiv(cdiv(n_max, kBlock), kTileBlocks));
+    const uint32_t subs = nsubs >= (uint64_t)kSubs * 6 * num_sms() ? kSubs : 1u;
+    a.subs = subs;
+    const uint64_t tiles = cdiv(nsubs, subs);
+    static bool attr_set[64] = {false};
+    FQ_CUDA_TRY(allow_smem(enc_onepass_kernel, kOnepassSmem, attr_set));
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)3 * num_sms());
+    enc_onepass_kernel<<<grid, kEncThreads, kOnepassSmem, st>>>(a);
+    const uint64_t raw_words = std::max<uint64_t>(cdiv(n_max, 4) * 4, a.fb ? cdiv(a.nbits, 64) : 0);
+    enc_fixup_kernel<<<grid_for(std::max<uint64_t>(raw_words, a.m_out ? cdiv(a.m_nbits, 64) : 0), 256, 4 * num_sms()),
+                       256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ internal launches
 
-cudaError_t reset_status(const Scratch &s, cudaStream_t st)
+cudaError_t reset_status(const Scratch &s, uint64_t max_ids, cudaStream_t st)
 {
-    reset_status_kernel<<<1, 1, 0, st>>>(s.ctl);
+    const uint64_t ntiles = std::min<uint64_t>(std::max<uint64_t>(1, enc_tiles(max_ids)), s.etiles_cap);
+    reset_status_kernel<<<grid_for(ntiles, 256, 64), 256, 0, st>>>(s, ntiles);
     return cudaGetLastError();
 }
 
 cudaError_t encode_fq(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max, uint8_t *out,
                       uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
 {
-    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s};
-    const uint64_t nmax = n_dev ? n_max : n_host;
-    const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, cdiv(cdiv(nmax, kBlock), kTileBlocks));
-    enc_widths_kernel<<<tiles, kEncThreads, 0, st>>>(a);
-    enc_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
-    enc_pack_kernel<<<tiles, kEncThreads, 0, st>>>(a);
-    return cudaGetLastError();
+    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0, 1};
+    return launch_encode(a, n_dev ? n_max : n_host, st);
+}
+
+cudaError_t encode_fq_mirror(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max,
+                             uint8_t *out, uint64_t cap, uint64_t *out_bytes, const Mirror &m, const Scratch &s,
+                             cudaStream_t st)
+{
+    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words, m.nbits, 1};
+    return launch_encode(a, n_dev ? n_max : n_host, st);
+}
+
+cudaError_t encode_fb_positions(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap,
+                                uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
+{
+    EncArgs a{s.positions, 0, reinterpret_cast<const uint64_t *>(&s.ctl->n), out, cap, out_bytes, 1, nbits, words, s,
+              nullptr, 0, nullptr, nullptr, 0, 1};
+    return launch_encode(a, nbits / 2 + 1, st);
 }
 
 cudaError_t encode_fb(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap, uint64_t *out_bytes,
@@ -759,23 +1136,19 @@ cudaError_t encode_fb(const uint64_t *words, uint64_t nbits, uint8_t *out, uint6
     bits_count_kernel<<<btiles, kBitThreads, 0, st>>>(words, nbits, s.btile_cnt);
     fb_plan_kernel<<<1, kScanThreads, 0, st>>>(nbits, s);
     bits_extract_kernel<<<btiles, kBitThreads, 0, st>>>(words, nbits, s);
-    EncArgs a{s.positions, 0, reinterpret_cast<const uint64_t *>(&s.ctl->n), out, cap, out_bytes, 1, nbits, words, s};
-    const uint64_t nmax = nbits / 2 + 1;
-    const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, cdiv(cdiv(nmax, kBlock), kTileBlocks));
-    enc_widths_kernel<<<tiles, kEncThreads, 0, st>>>(a);
-    enc_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
-    enc_pack_kernel<<<tiles, kEncThreads, 0, st>>>(a);
-    fb_raw_kernel<<<grid_for(nwords, 256, 4 * num_sms()), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return encode_fb_positions(words, nbits, out, cap, out_bytes, s, st);
 }
 
 cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t *in_bytes_dev, uint32_t *ids,
                       uint64_t cap, uint64_t *n_out, const Scratch &s, cudaStream_t st)
 {
     DecArgs a{in, in_bytes_host, in_bytes_dev, ids, cap, n_out, 0, nullptr, 0, s};
+    const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(cap));
+    dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
     dec_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
-    const uint64_t nb = cdiv(cap, kBlock);
-    dec_unpack_kernel<<<grid_for(std::max(nb * 32, cap), kEncThreads, 8 * num_sms()), kEncThreads, 0, st>>>(a);
+    FQ_CUDA_TRY(prepare_unpack());
+    dec_unpack_kernel<<<grid_for(std::max(tiles * kEncThreads, cap), kEncThreads, 3 * num_sms()), kEncThreads, kDecSmem,
+                        st>>>(a);
     return cudaGetLastError();
 }
 
@@ -783,12 +1156,14 @@ cudaError_t decode_fb(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
                       uint64_t nbits, const Scratch &s, cudaStream_t st)
 {
     DecArgs a{in, in_bytes_host, in_bytes_dev, nullptr, nbits, nullptr, 1, words, nbits, s};
+    const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(nbits));
+    dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
     dec_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
     const uint64_t nwords = cdiv(nbits, 64);
     fb_init_kernel<<<grid_for(nwords, 256, 4 * num_sms()), 256, 0, st>>>(a);
-    const uint64_t nmax = nbits / 2 + 1;
-    dec_unpack_kernel<<<grid_for(std::max(cdiv(nmax, kBlock) * 32, nmax), kEncThreads, 8 * num_sms()), kEncThreads, 0,
-                        st>>>(a);
+    FQ_CUDA_TRY(prepare_unpack());
+    dec_unpack_kernel<<<grid_for(std::max(tiles * kEncThreads, nbits), kEncThreads, 3 * num_sms()), kEncThreads,
+                        kDecSmem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -846,7 +1221,7 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
     if (!workspace_fits(work_bytes, n, 0)) return FQ_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Scratch s = carve(d_work, n, 0);
-    cudaError_t e = reset_status(s, st);
+    cudaError_t e = reset_status(s, n, st);
     if (e == cudaSuccess) e = encode_fq(d_ids, n, nullptr, n, d_out, cap, d_out_bytes, s, st);
     return cuda_status(e);
 }
@@ -859,7 +1234,7 @@ fq_status fq_frontier_decode(const uint8_t *d_in, uint64_t in_bytes, uint32_t *d
     if (!workspace_fits(work_bytes, cap, 0)) return FQ_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Scratch s = carve(d_work, cap, 0);
-    cudaError_t e = reset_status(s, st);
+    cudaError_t e = reset_status(s, 0, st);
     if (e == cudaSuccess) e = decode_fq(d_in, in_bytes, nullptr, d_ids, cap, d_n, s, st);
     return cuda_status(e);
 }
@@ -872,7 +1247,7 @@ fq_status fq_bitmap_encode(const uint64_t *d_words, uint64_t nbits, uint8_t *d_o
     if (!workspace_fits(work_bytes, 0, nbits)) return FQ_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Scratch s = carve(d_work, 0, nbits);
-    cudaError_t e = reset_status(s, st);
+    cudaError_t e = reset_status(s, nbits / 2 + 1, st);
     if (e == cudaSuccess) e = encode_fb(d_words, nbits, d_out, cap, d_out_bytes, s, st);
     return cuda_status(e);
 }
@@ -885,7 +1260,7 @@ fq_status fq_bitmap_decode(const uint8_t *d_in, uint64_t in_bytes, uint64_t *d_w
     if (!workspace_fits(work_bytes, 0, nbits)) return FQ_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Scratch s = carve(d_work, 0, nbits);
-    cudaError_t e = reset_status(s, st);
+    cudaError_t e = reset_status(s, 0, st);
     if (e == cudaSuccess) e = decode_fb(d_in, in_bytes, nullptr, d_words, nbits, s, st);
     return cuda_status(e);
 }

@@ -54,7 +54,9 @@ struct Ctl {
     unsigned long long total_b;
     unsigned long long out_bytes;
     unsigned long long fq_offset;  // byte offset of the FQ stream inside the container
-    uint32_t pad[2];
+    uint32_t tile_ticket;          // single-pass encode: next tile to hand out
+    uint32_t mode2;                // mode of the mirrored FB stream (kMode*), kModeNone if absent
+    unsigned long long out2_bytes;
 };
 static_assert(sizeof(Ctl) <= 256, "control block must fit its slot");
 
@@ -69,6 +71,7 @@ struct Scratch {
     uint32_t *btile_cnt;  // [btiles_cap]
     uint32_t *btile_off;  // [btiles_cap]
     uint32_t *positions;  // [pos_cap]  bitmap positions (FB)
+    unsigned long long *tile_status;  // [etiles_cap] single-pass encode look-back words
     uint64_t ids_cap;     // largest id count an encode/decode may see
     uint64_t nbits_cap;
     uint64_t nb_cap, etiles_cap, btiles_cap, pos_cap;
@@ -97,8 +100,26 @@ cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
                       uint64_t cap, uint64_t *n_out, const Scratch &s, cudaStream_t st);
 cudaError_t decode_fb(const uint8_t *in, uint64_t in_bytes_host, const uint64_t *in_bytes_dev, uint64_t *words,
                       uint64_t nbits, const Scratch &s, cudaStream_t st);
-// Reset the status record to FQ_OK.
-cudaError_t reset_status(const Scratch &s, cudaStream_t st);
+// Reset the status record to FQ_OK and clear the look-back words of up to max_ids ids.
+cudaError_t reset_status(const Scratch &s, uint64_t max_ids, cudaStream_t st);
+
+// Optional mirror of an FQ encode: the same ids written a second time as an FB stream in SET
+// mode (header + the FQ stream, or the raw words when that is not smaller).  Valid when the
+// ids are exactly the set bits of `words` (nbits bits) and 2 * n <= nbits.
+struct Mirror {
+    uint8_t *out = nullptr;
+    uint64_t cap = 0;
+    uint64_t *out_bytes = nullptr;
+    const uint64_t *words = nullptr;
+    uint64_t nbits = 0;
+};
+cudaError_t encode_fq_mirror(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max,
+                             uint8_t *out, uint64_t cap, uint64_t *out_bytes, const Mirror &mirror,
+                             const Scratch &s, cudaStream_t st);
+// FB encode when the positions to code are already in s.positions with count and mode set in
+// s.ctl (n, fb_mode), e.g. by the BFS compaction.
+cudaError_t encode_fb_positions(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap,
+                                uint64_t *out_bytes, const Scratch &s, cudaStream_t st);
 
 // Bitmap -> sorted positions, shared with the BFS compaction: tile counts then extraction.
 int num_sms();
@@ -115,6 +136,24 @@ __device__ __forceinline__ void set_error(Ctl *c, int32_t code, uint32_t where, 
         if (prev == 0) c->where = where;
         atomicMin(&c->detail, detail);
     }
+}
+
+// Clear a Scratch's control block (status OK, no mode) and its first ntiles look-back words;
+// called by threads tid = 0 .. nthreads-1 of one kernel.
+__device__ __forceinline__ void reset_scratch_device(const Scratch &s, uint64_t ntiles, uint32_t tid, uint32_t nthreads)
+{
+    if (tid == 0) {
+        Ctl *c = s.ctl;
+        c->code = FQ_OK;
+        c->where = 0;
+        c->detail = ~0ull;
+        c->mode = kModeNone;
+        c->mode2 = kModeNone;
+        c->fb_mode = kFbRaw;
+        c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = 0;
+        c->tile_ticket = 0;
+    }
+    for (uint64_t i = tid; i < ntiles; i += nthreads) s.tile_status[i] = 0ull;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)

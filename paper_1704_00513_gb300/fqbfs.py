@@ -141,7 +141,7 @@ def workspace(max_ids: int, max_nbits: int, device="cuda") -> torch.Tensor:
 # ----------------------------------------------------------------------------- codec calls
 
 def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work: torch.Tensor | None = None,
-                       stream=None, sync: bool = True):
+                       stream=None, sync: bool = True, nbytes: torch.Tensor | None = None):
     """Encode sorted unique uint32 ids (an int32/uint32 CUDA tensor).  Returns (stream bytes, size)
     when sync, else (out buffer, device size tensor)."""
     n = ids.numel()
@@ -149,7 +149,8 @@ def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work:
         out = torch.empty(fq_queue_bound(n), dtype=torch.uint8, device=ids.device)
     if work is None:
         work = workspace(n, 0, ids.device)
-    nbytes = torch.zeros(1, dtype=torch.int64, device=ids.device)
+    if nbytes is None:
+        nbytes = torch.zeros(1, dtype=torch.int64, device=ids.device)
     _check(lib().fq_frontier_encode(_ptr(ids), n, _ptr(out), out.numel(), _ptr(nbytes), _ptr(work), work.numel(),
                                     _stream(stream)), "fq_frontier_encode")
     if not sync:
@@ -160,17 +161,21 @@ def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work:
 
 
 def fq_frontier_decode(stream_bytes: torch.Tensor, cap: int, out: torch.Tensor | None = None,
-                       work: torch.Tensor | None = None, stream=None, in_bytes: int | None = None):
-    """Decode an FQ stream (uint8 CUDA tensor) into at most cap ids; returns the int32 ids."""
+                       work: torch.Tensor | None = None, stream=None, in_bytes: int | None = None,
+                       sync: bool = True, n_out: torch.Tensor | None = None):
+    """Decode an FQ stream (uint8 CUDA tensor) into at most cap ids; returns the int32 ids
+    (when sync), else the output buffer (the count lands in n_out on the device)."""
     dev = stream_bytes.device
     if out is None:
         out = torch.empty(max(cap, 4), dtype=torch.int32, device=dev)
     if work is None:
         work = workspace(cap, 0, dev)
-    n = torch.zeros(1, dtype=torch.int64, device=dev)
+    n = torch.zeros(1, dtype=torch.int64, device=dev) if n_out is None else n_out
     nb = stream_bytes.numel() if in_bytes is None else in_bytes
     _check(lib().fq_frontier_decode(_ptr(stream_bytes), nb, _ptr(out), cap, _ptr(n), _ptr(work), work.numel(),
                                     _stream(stream)), "fq_frontier_decode")
+    if not sync:
+        return out
     _device_status(work, stream, "fq_frontier_decode")
     return out[: int(n.item())]
 
