@@ -105,6 +105,34 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
 fq_status fq_frontier_decode(const uint8_t *d_in, uint64_t in_bytes, uint32_t *d_ids, uint64_t cap,
                              uint64_t *d_n, void *d_work, uint64_t work_bytes, void *stream);
 
+/* ------------------------------------------------------------------ batched codec
+ * S independent frontier segments in a fixed number of launches (3 to encode, 4 to decode,
+ * whatever S is): the grouping of many small transfers into one that the thesis applies to its
+ * exchanges (sec. 6.5, data-transfer grouping), applied to the codec.  Stream s is byte-for-byte
+ * what fq_frontier_encode writes for segment s alone.
+ *
+ * Workspace: fq_batch_workspace_bytes(total_ids, S), 16-byte aligned; total_ids = seg_off[S]. */
+uint64_t fq_batch_workspace_bytes(uint64_t total_ids, uint32_t S);
+
+/* Segment s is d_ids[seg_off[s] .. seg_off[s+1]) (device u64 array of S+1 offsets, non-decreasing,
+ * each segment strictly increasing and shorter than 2^32).  Stream s is written at
+ * d_out + out_off[s] with capacity out_off[s+1] - out_off[s] (device u64 array of S+1 offsets,
+ * each a multiple of 16; fq_queue_bound(length) per segment always suffices); its size lands in
+ * d_out_bytes[s].  Device errors (status record of the workspace): FQ_EINVAL (bad segment table),
+ * FQ_EUNSORTED (detail = global index of the first bad id), FQ_ENOSPC (detail = segment).  On an
+ * error the contents of the affected streams are unspecified. */
+fq_status fq_frontier_encode_batch(const uint32_t *d_ids, const uint64_t *d_seg_off, uint32_t S, uint64_t total_ids,
+                                   uint8_t *d_out, const uint64_t *d_out_off, uint64_t *d_out_bytes, void *d_work,
+                                   uint64_t work_bytes, void *stream);
+
+/* Stream s is d_in[in_off[s] .. in_off[s] + in_bytes[s]) (in_off multiples of 16).  Its ids are
+ * written to d_ids + seg_off[s], at most seg_off[s+1] - seg_off[s] of them; their count lands in
+ * d_n[s].  Every stream is validated like fq_frontier_decode; a failure sets FQ_ECORRUPT (detail
+ * = segment) and that segment's count to 0, the others are still decoded. */
+fq_status fq_frontier_decode_batch(const uint8_t *d_in, const uint64_t *d_in_off, const uint64_t *d_in_bytes, uint32_t S,
+                                   uint32_t *d_ids, const uint64_t *d_seg_off, uint64_t total_ids, uint64_t *d_n,
+                                   void *d_work, uint64_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------ encode without a workspace
  * The thesis has no counterpart to this entry point.  It serves callers that cannot allocate
  * device memory -- code running inside another framework's memory pool, which must not see
@@ -163,6 +191,8 @@ fq_status fq_graph_destroy(fq_graph *g);
 #define FQ_BFS_FORCE_TOP_DOWN 0x2u /* ignore the switching rule: top-down at every level        */
 #define FQ_BFS_FORCE_BOTTOM_UP 0x4u/* bottom-up at every level after level 0                    */
 #define FQ_BFS_TIMING 0x8u         /* time every kernel class with CUDA events (fills stats)    */
+#define FQ_BFS_NO_CODEC 0x10u      /* skip the codec stage: expand the raw queue/bitmap (the plain
+                                      BFS the codec stage is measured against; no streams)      */
 
 typedef struct fq_bfs_opts {
     uint32_t alpha; /* top-down -> bottom-up when m_f * alpha > m_u   (0 selects 14) */
@@ -220,6 +250,23 @@ typedef struct fq_level_record {
 fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_parent, const fq_bfs_opts *opts,
                      fq_bfs_stats *h_stats, fq_level_record *h_levels, uint32_t max_levels, uint8_t *d_stream_log,
                      uint64_t stream_log_cap, void *stream);
+
+/* ------------------------------------------------------------------ multi-source BFS
+ * k <= 64 roots traversed together in one persistent cooperative kernel launch: each vertex holds
+ * a 64-bit mask of the roots that reached it, and a level ORs the frontier masks of the
+ * neighbours into the not-yet-seen bits (the thesis' SpMV frontier step, t = A (x) f masked by
+ * the visited list, Alg. "BFS based on replicated-CSR and SpVM", bit-sliced over the roots).
+ * d_depth[i * n + v] (k x n, row-major int32) = hop distance of v from h_roots[i], -1 if
+ * unreachable -- equal to fq_bfs_run's depth for that root.  The graph is the CSR of
+ * fq_graph_create.  Scratch: fq_msbfs_scratch_bytes(n) bytes (about 36 bytes per vertex).
+ * h_stats (may be NULL): levels, reached = sum over roots of reached vertices, reached_edges =
+ * sum over roots of undirected edges inside each root's component, edges_examined.  Synchronous.
+ * The level barriers wait with a bound; FQ_ETIMEOUT if one gives up.  The multi-source frontier
+ * has no codec stage. */
+uint64_t fq_msbfs_scratch_bytes(uint64_t n);
+fq_status fq_bfs_run_multi(const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, const uint32_t *h_roots,
+                           uint32_t k, int32_t *d_depth, void *d_scratch, uint64_t scratch_bytes,
+                           fq_bfs_stats *h_stats, void *stream);
 
 #ifdef __cplusplus
 }

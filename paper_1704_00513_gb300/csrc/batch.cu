@@ -1,0 +1,642 @@
+// batch.cu -- the frontier codec over many independent segments in a fixed number of launches
+// (fq_frontier_encode_batch / fq_frontier_decode_batch).
+//
+// The thesis groups many small transfers into one (custom MPI datatypes, sec. 6.5) and exchanges
+// one compressed frontier per processor pair; here S sorted id segments of any lengths become S
+// independent FQ streams (each exactly what fq_frontier_encode writes for that segment) through
+// one persistent kernel: tiles of 8192 ids of all segments are handed out in ticket order, each
+// tile's payload offset comes from a decoupled look-back over the earlier tiles of its own
+// segment, and the CTA holding a segment's last tile writes that stream's header.  Decoding runs
+// the inverse over all tiles of all streams.  Launch count: encode 3, decode 4, for any S.
+#include <algorithm>
+
+#include "codec_dev.cuh"
+#include "fq_common.cuh"
+
+namespace fq {
+namespace {
+
+constexpr uint32_t kBTileIds = kTileBlocks * kBlock;  // 8192 ids per tile
+constexpr size_t kBatchSmem = 2 * (size_t)kBTileIds * sizeof(uint32_t);
+constexpr uint32_t kDecStageB = kTileBlocks * 32u * 16u + 16u;
+constexpr size_t kBatchDecSmem = 2 * (size_t)kDecStageB;
+
+struct SegInfo {
+    unsigned long long n;       // ids in the segment (decode: announced by the stream header)
+    unsigned long long nb;      // 128-id blocks
+    unsigned long long total_b; // sum of widths
+    uint32_t mode;              // kMode* (kModeNone: nothing to write / invalid)
+    uint32_t ok;
+};
+
+struct BatchScratch {
+    Ctl *ctl;
+    unsigned long long *tile_base;  // [S + 1] first global tile of each segment
+    SegInfo *seg;                   // [S]
+    unsigned long long *status;     // [T] look-back words (encode)
+    uint32_t *tile_sum;             // [T] decode
+    uint32_t *tile_off;             // [T] decode: segment-local payload offset (16-byte units)
+    uint64_t tiles_cap;
+};
+
+uint64_t batch_tiles_cap(uint64_t total_ids, uint64_t S) { return total_ids / kBTileIds + S + 1; }
+
+uint64_t al256(uint64_t x) { return (x + 255u) / 256u * 256u; }
+
+uint64_t batch_layout(uint64_t total_ids, uint64_t S, BatchScratch *b, void *base)
+{
+    const uint64_t T = batch_tiles_cap(total_ids, S);
+    uint64_t o = 256;
+    const uint64_t o_tb = o; o = al256(o + 8 * (S + 1));
+    const uint64_t o_seg = o; o = al256(o + sizeof(SegInfo) * (S ? S : 1));
+    const uint64_t o_st = o; o = al256(o + 8 * T);
+    const uint64_t o_ts = o; o = al256(o + 4 * T);
+    const uint64_t o_to = o; o = al256(o + 4 * T);
+    if (b && base) {
+        uint8_t *p = static_cast<uint8_t *>(base);
+        b->ctl = reinterpret_cast<Ctl *>(p);
+        b->tile_base = reinterpret_cast<unsigned long long *>(p + o_tb);
+        b->seg = reinterpret_cast<SegInfo *>(p + o_seg);
+        b->status = reinterpret_cast<unsigned long long *>(p + o_st);
+        b->tile_sum = reinterpret_cast<uint32_t *>(p + o_ts);
+        b->tile_off = reinterpret_cast<uint32_t *>(p + o_to);
+        b->tiles_cap = T;
+    }
+    return o;
+}
+
+__device__ __forceinline__ uint32_t find_segment(const unsigned long long *tile_base, uint32_t S, uint64_t g)
+{
+    // largest s with tile_base[s] <= g (segments with no tile have equal bases; the last such wins)
+    uint32_t lo = 0, hi = S;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (tile_base[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void reset_ctl(Ctl *c)
+{
+    c->code = FQ_OK;
+    c->where = 0;
+    c->detail = ~0ull;
+    c->mode = c->mode2 = kModeNone;
+    c->fb_mode = kFbRaw;
+    c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = 0;
+    c->tile_ticket = 0;
+}
+
+struct BEnc {
+    const uint32_t *ids;
+    const uint64_t *seg_off;
+    uint32_t S;
+    uint8_t *out;
+    const uint64_t *out_off;
+    uint64_t *out_bytes;
+    BatchScratch b;
+};
+
+// ---- encode ----
+
+// One CTA: segment sizes, tiles per segment and their prefix, cleared look-back words, headers
+// of empty segments.
+__global__ void __launch_bounds__(kScanThreads) bat_plan_kernel(BEnc a)
+{
+    __shared__ unsigned long long sm[33];
+    if (threadIdx.x == 0) reset_ctl(a.b.ctl);
+    __syncthreads();
+    const uint64_t S = a.S;
+    const uint64_t chunk = dcdiv(S, kScanThreads);
+    const uint64_t s0 = (uint64_t)threadIdx.x * chunk, s1 = min(S, s0 + chunk);
+    unsigned long long local = 0, total = 0;
+    for (uint64_t s = s0; s < s1; s++) {
+        const uint64_t lo = a.seg_off[s], hi = a.seg_off[s + 1];
+        if (hi < lo || hi - lo > 0xffffffffull) {
+            set_error(a.b.ctl, FQ_EINVAL, kWhereEncPlan, s);
+            continue;
+        }
+        local += dcdiv(dcdiv(hi - lo, kBlock), kTileBlocks);
+    }
+    unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
+    for (uint64_t s = s0; s < s1; s++) {
+        a.b.tile_base[s] = run;
+        const uint64_t lo = a.seg_off[s], hi = a.seg_off[s + 1];
+        const uint64_t n = hi >= lo ? hi - lo : 0;
+        const uint64_t nt = dcdiv(dcdiv(n, kBlock), kTileBlocks);
+        run += hi >= lo && n <= 0xffffffffull ? nt : 0;
+        SegInfo si{};
+        si.n = n;
+        si.nb = dcdiv(n, kBlock);
+        si.mode = kModeNone;
+        a.b.seg[s] = si;
+        if (n == 0 && hi >= lo) {  // the empty stream is a bare raw header
+            const uint64_t cap = a.out_off[s + 1] - a.out_off[s];
+            if (cap < 16) {
+                set_error(a.b.ctl, FQ_ENOSPC, kWhereEncPlan, s);
+                a.out_bytes[s] = 16;
+            } else {
+                uint32_t *h = reinterpret_cast<uint32_t *>(a.out + a.out_off[s]);
+                h[0] = kMagicRaw; h[1] = 0; h[2] = 0; h[3] = 0;
+                a.out_bytes[s] = 16;
+            }
+        }
+    }
+    if (threadIdx.x == 0) a.b.tile_base[S] = total;
+    __syncthreads();
+    const uint64_t T = min((uint64_t)total, a.b.tiles_cap);
+    for (uint64_t t = threadIdx.x; t < T; t += kScanThreads) a.b.status[t] = 0ull;
+    if (threadIdx.x == 0 && total > a.b.tiles_cap) set_error(a.b.ctl, FQ_EINVAL, kWhereEncPlan, total);
+}
+
+// The stream decision for segment s once all its tiles are published.
+__device__ void bat_finalize(const BEnc &a, uint32_t s, uint64_t n, uint64_t nb, unsigned long long total)
+{
+    Ctl *c = a.b.ctl;
+    __threadfence();
+    uint8_t *out = a.out + a.out_off[s];
+    const uint64_t cap = a.out_off[s + 1] - a.out_off[s];
+    SegInfo si = a.b.seg[s];
+    si.total_b = total;
+    const uint64_t packed = 16u + dpad16(5u * nb) + 16u * total;
+    const uint64_t raw = 16u + dpad16(4u * n);
+    const bool is_packed = n > 0 && packed < raw;
+    const uint64_t size = is_packed ? packed : raw;
+    si.mode = is_packed ? kModePacked : kModeRaw;
+    if (size > cap) {
+        set_error(c, FQ_ENOSPC, kWhereEncPlan, s);
+        si.mode = kModeNone;
+        a.out_bytes[s] = size;
+        a.b.seg[s] = si;
+        return;
+    }
+    uint32_t *h = reinterpret_cast<uint32_t *>(out);
+    if (is_packed) {
+        h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
+        for (uint64_t p = 16u + 5u * nb; p < 16u + dpad16(5u * nb); p++) out[p] = 0;
+    } else {
+        h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
+    }
+    a.out_bytes[s] = size;
+    a.b.seg[s] = si;
+}
+
+__global__ void __launch_bounds__(kEncThreads, 3) bat_encode_kernel(BEnc a)
+{
+    extern __shared__ __align__(128) uint32_t sbuf[];  // [2][kBTileIds]
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ uint32_t s_tile, s_next;
+    __shared__ uint32_t sw[kTileBlocks], spre[kTileBlocks];
+    __shared__ unsigned long long s_excl, s_total;
+    __shared__ unsigned long long s_red[kEncWarps];
+    __shared__ uint32_t s_first;
+    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
+    __shared__ int s_abort;
+    Ctl *c = a.b.ctl;
+    if (threadIdx.x == 0) s_abort = c->code != FQ_OK;  // the plan rejected the segment table
+    __syncthreads();
+    if (s_abort) return;
+    const uint64_t T = a.b.tile_base[a.S];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (T == 0) return;
+
+    // tile g -> (segment, its ids, its length, local tile); bulk staging needs a full, aligned tile
+    auto locate = [&](uint64_t g, uint32_t &s, const uint32_t *&ids, uint64_t &n, uint64_t &t) {
+        s = find_segment(a.b.tile_base, a.S, g);
+        ids = a.ids + a.seg_off[s];
+        n = a.seg_off[s + 1] - a.seg_off[s];
+        t = g - a.b.tile_base[s];
+    };
+    auto bulk_ok = [&](const uint32_t *ids, uint64_t n, uint64_t t) {
+        return ((reinterpret_cast<uintptr_t>(ids + t * kBTileIds) & 15u) == 0) && (t + 1) * kBTileIds <= n;
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+        s_next = atomicAdd(&c->tile_ticket, 1u);
+        if (s_next < T) {
+            uint32_t s; const uint32_t *ids; uint64_t n, t;
+            locate(s_next, s, ids, n, t);
+            if (bulk_ok(ids, n, t)) bulk_load(sbuf, ids + t * kBTileIds, kBTileIds * 4u, &bars[0]);
+        }
+    }
+    __syncthreads();
+    uint32_t phase0 = 0u, phase1 = 0u;
+    for (uint32_t it = 0;; it++) {
+        if (threadIdx.x == 0) {
+            s_tile = s_next;
+            s_next = (s_next < T) ? atomicAdd(&c->tile_ticket, 1u) : (uint32_t)T;
+        }
+        __syncthreads();
+        const uint64_t g = s_tile, gn = s_next;
+        if (g >= T) break;
+        const uint32_t stage = it & 1u;
+        uint32_t *sb = sbuf + stage * kBTileIds;
+        uint32_t s; const uint32_t *ids; uint64_t n, t;
+        locate(g, s, ids, n, t);
+        if (threadIdx.x == 0 && gn < T) {  // the next ticket's ids into the other stage
+            uint32_t s2; const uint32_t *ids2; uint64_t n2, t2;
+            locate(gn, s2, ids2, n2, t2);
+            if (bulk_ok(ids2, n2, t2))
+                bulk_load(sbuf + (stage ^ 1u) * kBTileIds, ids2 + t2 * kBTileIds, kBTileIds * 4u, &bars[stage ^ 1u]);
+        }
+        if (bulk_ok(ids, n, t)) {
+            if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(c, FQ_ETIMEOUT, kWhereEncWidths, g);
+            if (stage) phase1 ^= 1u;
+            else phase0 ^= 1u;
+        } else {
+            for (uint32_t i = threadIdx.x; i < kBTileIds; i += kEncThreads) {
+                const uint64_t gi = t * kBTileIds + i;
+                sb[i] = gi < n ? ids[gi] : 0u;
+            }
+            __syncthreads();
+        }
+        const uint64_t nb = dcdiv(n, kBlock);
+        const uint64_t ntiles_s = dcdiv(nb, kTileBlocks);
+        uint8_t *out = a.out + a.out_off[s];
+        const uint64_t cap = a.out_off[s + 1] - a.out_off[s];
+        const uint64_t bound = min(cap, 16u + dpad16(4u * n));
+        const uint64_t payload = 16u + dpad16(5u * nb);
+        unsigned long long *status = a.b.status + a.b.tile_base[s];
+
+        // widths and bases
+        unsigned long long bad = ~0ull;
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+            const uint32_t lb = warp * kBlocksPerWarp + i;
+            const uint64_t k = t * kTileBlocks + lb;
+            uint32_t b = 0;
+            if (k < nb) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(sb + lb * kBlock + 4u * lane);
+                const uint32_t v[4] = {q.x, q.y, q.z, q.w};
+                uint32_t prevb = 0;
+                if (lane == 0 && k > 0) prevb = lb > 0 ? sb[lb * kBlock - 1] : ids[k * kBlock - 1];
+                uint32_t gg[4];
+                gaps_of(v, prevb, k > 0, k, n, lane, gg, &bad);
+                b = bitlen32(__reduce_max_sync(0xffffffffu, max(max(gg[0], gg[1]), max(gg[2], gg[3]))));
+                if (lane == 0 && 16u + 4u * k + 4 <= bound) *reinterpret_cast<uint32_t *>(out + 16u + 4u * k) = v[0];
+            }
+            if (lane == 0) sw[lb] = b;
+        }
+        if (bad != ~0ull) set_error(c, FQ_EUNSORTED, kWhereEncWidths, a.seg_off[s] + bad);
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t x0 = sw[2 * lane], x1 = sw[2 * lane + 1];
+            const uint32_t incl = warp_incl_scan(x0 + x1);
+            spre[2 * lane] = incl - x0 - x1;
+            spre[2 * lane + 1] = incl - x1;
+            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 0) {
+                publish(status, t, t == 0 ? kFlagPrefix : kFlagAgg, total);
+                s_total = total;
+            }
+        }
+        __syncthreads();
+        unsigned long long excl = 0;
+        if (t > 0) excl = lookback(status, t, c, s_red, &s_first);
+        if (threadIdx.x == 0) {
+            if (t > 0) publish(status, t, kFlagPrefix, excl + s_total);
+            s_excl = excl;
+        }
+        __syncthreads();
+        excl = s_excl;
+        if (threadIdx.x < kTileBlocks) {
+            const uint64_t k = t * kTileBlocks + threadIdx.x;
+            const uint64_t pw = 16u + 4u * nb + k;
+            if (k < nb && pw + 1 <= bound) out[pw] = (uint8_t)sw[threadIdx.x];
+        }
+        // pack from the staged ids
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+            const uint32_t lb = warp * kBlocksPerWarp + i;
+            const uint64_t k = t * kTileBlocks + lb;
+            const uint32_t b = sw[lb];
+            if (k >= nb || b == 0) continue;
+            const uint4 q = *reinterpret_cast<const uint4 *>(sb + lb * kBlock + 4u * lane);
+            const uint32_t v[4] = {q.x, q.y, q.z, q.w};
+            uint32_t gg[4];
+            unsigned long long dummy = ~0ull;
+            gaps_of(v, 0u, false, k, n, lane, gg, &dummy);
+            const uint4 w = pack_block(gg, b, pk[warp], lane);
+            const uint64_t p1 = payload + 16u * (excl + spre[lb] + lane);
+            if (lane < b && p1 + 16 <= bound) *reinterpret_cast<uint4 *>(out + p1) = w;
+        }
+        if (t == ntiles_s - 1 && threadIdx.x == 0) bat_finalize(a, s, n, nb, excl + s_total);
+        __syncthreads();
+    }
+}
+
+// Raw bodies of the segments whose stream is raw.
+__global__ void bat_fixup_kernel(BEnc a)
+{
+    for (uint64_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+        const SegInfo si = a.b.seg[s];
+        if (si.mode != kModeRaw) continue;
+        const uint32_t *ids = a.ids + a.seg_off[s];
+        uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + a.out_off[s] + 16);
+        const uint64_t padded = dcdiv(si.n, 4) * 4;
+        for (uint64_t i = threadIdx.x; i < padded; i += blockDim.x) dst[i] = i < si.n ? ids[i] : 0u;
+    }
+}
+
+// ---- decode ----
+
+struct BDec {
+    const uint8_t *in;
+    const uint64_t *in_off;
+    const uint64_t *in_bytes;
+    uint32_t S;
+    uint32_t *ids;
+    const uint64_t *seg_off;  // output positions; capacity of segment s = seg_off[s+1] - seg_off[s]
+    uint64_t *n_out;
+    BatchScratch b;
+};
+
+// One CTA: parse every stream header, tiles per stream and their prefix.
+__global__ void __launch_bounds__(kScanThreads) bat_dplan_kernel(BDec a)
+{
+    __shared__ unsigned long long sm[33];
+    if (threadIdx.x == 0) reset_ctl(a.b.ctl);
+    __syncthreads();
+    const uint64_t S = a.S;
+    const uint64_t chunk = dcdiv(S, kScanThreads);
+    const uint64_t s0 = (uint64_t)threadIdx.x * chunk, s1 = min(S, s0 + chunk);
+    unsigned long long local = 0, total = 0;
+    for (uint64_t s = s0; s < s1; s++) {
+        const uint8_t *fq = a.in + a.in_off[s];
+        const uint64_t bytes = a.in_bytes[s];
+        const uint64_t cap = a.seg_off[s + 1] - a.seg_off[s];
+        SegInfo si{};
+        si.mode = kModeNone;
+        si.ok = 0;
+        if (bytes >= 16 && (reinterpret_cast<uintptr_t>(fq) & 15u) == 0) {
+            const uint32_t magic = ld_u32(fq);
+            const uint64_t n = ld_u32(fq + 4), nb = ld_u32(fq + 8), words = ld_u32(fq + 12);
+            si.n = n;
+            si.nb = nb;
+            if (n > cap) {
+                set_error(a.b.ctl, FQ_ENOSPC, kWhereDecPlan, s);
+            } else if (magic == kMagicRaw && nb == 0 && words == n && bytes == 16u + dpad16(4u * n)) {
+                si.mode = kModeRaw;
+                si.ok = 1;
+                for (uint64_t i = 16u + 4u * n; i < bytes; i++)
+                    if (fq[i]) si.ok = 0;
+            } else if (magic == kMagicPacked && n > 0 && nb == dcdiv(n, kBlock) && bytes >= 16u + dpad16(5u * nb)) {
+                si.mode = kModePacked;
+                si.ok = 1;
+                for (uint64_t i = 16u + 5u * nb; i < 16u + dpad16(5u * nb); i++)
+                    if (fq[i]) si.ok = 0;
+            }
+        }
+        if (!si.ok) {
+            if (si.n <= cap) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecPlan, s);
+            si.mode = kModeNone;
+        }
+        a.b.seg[s] = si;
+        local += si.mode == kModePacked ? dcdiv(si.nb, kTileBlocks) : si.mode == kModeRaw ? dcdiv(si.n, kBTileIds) : 0;
+    }
+    unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
+    for (uint64_t s = s0; s < s1; s++) {
+        a.b.tile_base[s] = run;
+        const SegInfo si = a.b.seg[s];
+        run += si.mode == kModePacked ? dcdiv(si.nb, kTileBlocks) : si.mode == kModeRaw ? dcdiv(si.n, kBTileIds) : 0;
+        a.n_out[s] = si.mode == kModeNone ? 0 : si.n;
+    }
+    if (threadIdx.x == 0) {
+        a.b.tile_base[S] = total;
+        if (total > a.b.tiles_cap) set_error(a.b.ctl, FQ_EINVAL, kWhereDecPlan, total);
+    }
+}
+
+__global__ void __launch_bounds__(kEncThreads) bat_dtiles_kernel(BDec a)
+{
+    __shared__ uint32_t ws[kEncWarps];
+    const uint64_t T = min((uint64_t)a.b.tile_base[a.S], a.b.tiles_cap);
+    for (uint64_t g = blockIdx.x; g < T; g += gridDim.x) {
+        const uint32_t s = find_segment(a.b.tile_base, a.S, g);
+        const SegInfo si = a.b.seg[s];
+        if (si.mode != kModePacked) continue;  // uniform per CTA
+        const uint64_t t = g - a.b.tile_base[s];
+        const uint8_t *wd = a.in + a.in_off[s] + 16 + 4 * si.nb;
+        uint32_t b = 0;
+        if (threadIdx.x < kTileBlocks) {
+            const uint64_t k = t * kTileBlocks + threadIdx.x;
+            if (k < si.nb) {
+                b = wd[k];
+                if (b > 32u) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecPlan, s);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t sum = 0;
+            for (uint32_t i = 0; i < kEncWarps; i++) sum += ws[i];
+            a.b.tile_sum[g] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per stream (round robin): scan its tile sums, check its total against its header.
+__global__ void __launch_bounds__(kEncThreads) bat_dscan_kernel(BDec a)
+{
+    __shared__ unsigned long long sm[33];
+    for (uint64_t s = blockIdx.x; s < a.S; s += gridDim.x) {
+        SegInfo si = a.b.seg[s];
+        if (si.mode != kModePacked) continue;
+        const uint64_t base = a.b.tile_base[s];
+        const uint64_t nt = dcdiv(si.nb, kTileBlocks);
+        const uint64_t chunk = dcdiv(nt, kEncThreads);
+        const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(nt, t0 + chunk);
+        unsigned long long local = 0, total = 0;
+        for (uint64_t t = t0; t < t1; t++) local += a.b.tile_sum[base + t];
+        unsigned long long run = cta_excl_scan64<kEncThreads>(local, sm, &total);
+        for (uint64_t t = t0; t < t1; t++) {
+            a.b.tile_off[base + t] = (uint32_t)run;
+            run += a.b.tile_sum[base + t];
+        }
+        if (threadIdx.x == 0) {
+            const uint8_t *fq = a.in + a.in_off[s];
+            const uint64_t words = ld_u32(fq + 12);
+            si.total_b = total;
+            if (words != 4u * total || a.in_bytes[s] != 16u + dpad16(5u * si.nb) + 16u * total) {
+                set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecPlan, s);
+                si.mode = kModeNone;
+                a.n_out[s] = 0;
+            }
+            a.b.seg[s] = si;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
+{
+    extern __shared__ __align__(128) uint8_t dbuf[];  // [2][kDecStageB]
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ uint32_t spre[kTileBlocks];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = a.b.ctl->code == FQ_EINVAL;  // tile table larger than the workspace
+    __syncthreads();
+    if (s_abort) return;
+    const uint64_t T = min((uint64_t)a.b.tile_base[a.S], a.b.tiles_cap);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    // payload bytes of a packed tile, or 0 (raw tiles and empty tiles are read directly)
+    auto tile_bytes = [&](uint64_t g, uint32_t s, const SegInfo &si) -> uint32_t {
+        if (si.mode != kModePacked) return 0;
+        const uint64_t t = g - a.b.tile_base[s];
+        const uint64_t nt = dcdiv(si.nb, kTileBlocks);
+        const uint64_t end = (t + 1 < nt) ? a.b.tile_off[g + 1] : si.total_b;
+        return (uint32_t)(16u * (end - a.b.tile_off[g]));
+    };
+    auto payload_at = [&](uint64_t g, uint32_t s, const SegInfo &si) -> const uint8_t * {
+        return a.in + a.in_off[s] + 16 + dpad16(5u * si.nb) + 16u * (uint64_t)a.b.tile_off[g];
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+        const uint64_t g0 = blockIdx.x;
+        if (g0 < T) {
+            const uint32_t s = find_segment(a.b.tile_base, a.S, g0);
+            const SegInfo si = a.b.seg[s];
+            const uint32_t by = tile_bytes(g0, s, si);
+            if (by) bulk_load(dbuf, payload_at(g0, s, si), by, &bars[0]);
+        }
+    }
+    __syncthreads();
+    uint32_t phase0 = 0u, phase1 = 0u;
+    for (uint64_t i = 0;; i++) {
+        const uint64_t g = blockIdx.x + i * gridDim.x;
+        if (g >= T) break;
+        const uint32_t stage = (uint32_t)(i & 1u);
+        const uint32_t s = find_segment(a.b.tile_base, a.S, g);
+        const SegInfo si = a.b.seg[s];
+        const uint64_t gn = g + gridDim.x;
+        if (threadIdx.x == 0 && gn < T) {
+            const uint32_t s2 = find_segment(a.b.tile_base, a.S, gn);
+            const SegInfo si2 = a.b.seg[s2];
+            const uint32_t by = tile_bytes(gn, s2, si2);
+            if (by) bulk_load(dbuf + (stage ^ 1u) * kDecStageB, payload_at(gn, s2, si2), by, &bars[stage ^ 1u]);
+        }
+        const uint64_t t = g - a.b.tile_base[s];
+        const uint8_t *fq = a.in + a.in_off[s];
+        uint32_t *ids = a.ids + a.seg_off[s];
+        const bool vec_ok = (reinterpret_cast<uintptr_t>(ids) & 15u) == 0;
+        const uint32_t by = tile_bytes(g, s, si);
+        if (si.mode == kModeRaw) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(fq + 16);
+            const uint64_t i0 = t * kBTileIds, i1 = min((uint64_t)si.n, (uint64_t)(i0 + kBTileIds));
+            for (uint64_t j = i0 + threadIdx.x; j < i1; j += kEncThreads) {
+                const uint32_t v = src[j];
+                if (j > 0 && src[j - 1] >= v) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecUnpack, s);
+                ids[j] = v;
+            }
+        } else if (si.mode == kModePacked) {
+            const uint64_t nb = si.nb, n = si.n;
+            const uint8_t *wd = fq + 16 + 4 * nb;
+            const uint32_t *bases = reinterpret_cast<const uint32_t *>(fq + 16);
+            if (warp == 0) {
+                const uint64_t k0 = t * kTileBlocks + 2 * lane;
+                const uint32_t x0 = k0 < nb ? wd[k0] : 0u, x1 = k0 + 1 < nb ? wd[k0 + 1] : 0u;
+                const uint32_t incl = warp_incl_scan(x0 + x1);
+                spre[2 * lane] = incl - x0 - x1;
+                spre[2 * lane + 1] = incl - x1;
+            }
+            if (by) {
+                if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(a.b.ctl, FQ_ETIMEOUT, kWhereDecUnpack, g);
+                if (stage) phase1 ^= 1u;
+                else phase0 ^= 1u;
+            }
+            __syncthreads();
+            const uint32_t *sp = reinterpret_cast<const uint32_t *>(dbuf + stage * kDecStageB);
+            for (uint32_t bi = 0; bi < kBlocksPerWarp; bi++) {
+                const uint32_t local = warp * kBlocksPerWarp + bi;
+                const uint64_t k = t * kTileBlocks + local;
+                if (k >= nb) break;
+                uint32_t out[4];
+                unsigned long long last;
+                bool good = unpack_block(sp + 4u * spre[local], wd[k], bases[k], k, n, lane, out, &last);
+                if (k + 1 < nb && lane == 31 && last >= (unsigned long long)bases[k + 1]) good = false;
+                if (!good) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecUnpack, s);
+                const uint64_t i0 = k * kBlock + 4u * lane;
+                if (vec_ok && i0 + 3 < n) {
+                    *reinterpret_cast<uint4 *>(ids + i0) = make_uint4(out[0], out[1], out[2], out[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (i0 + j < n) ids[i0 + j] = out[j];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename K>
+cudaError_t allow_smem_b(K kernel, size_t bytes, bool *done)
+{
+    int dev = 0;
+    FQ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!done[dev]) {
+        FQ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace fq
+
+using namespace fq;
+
+extern "C" {
+
+uint64_t fq_batch_workspace_bytes(uint64_t total_ids, uint32_t S) { return batch_layout(total_ids, S, nullptr, nullptr); }
+
+fq_status fq_frontier_encode_batch(const uint32_t *d_ids, const uint64_t *d_seg_off, uint32_t S, uint64_t total_ids,
+                                   uint8_t *d_out, const uint64_t *d_out_off, uint64_t *d_out_bytes, void *d_work,
+                                   uint64_t work_bytes, void *stream)
+{
+    if (S == 0) return FQ_OK;
+    if (!d_seg_off || !d_out || !d_out_off || !d_out_bytes || !d_work || (total_ids && !d_ids)) return FQ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_out) & 15u) || (reinterpret_cast<uintptr_t>(d_work) & 15u)) return FQ_EINVAL;
+    if (work_bytes < fq_batch_workspace_bytes(total_ids, S)) return FQ_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BEnc a{d_ids, d_seg_off, S, d_out, d_out_off, d_out_bytes, {}};
+    batch_layout(total_ids, S, &a.b, d_work);
+    static bool done[64] = {false};
+    if (allow_smem_b(bat_encode_kernel, kBatchSmem, done) != cudaSuccess) return FQ_ECUDA;
+    bat_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)3 * num_sms());
+    bat_encode_kernel<<<grid, kEncThreads, kBatchSmem, st>>>(a);
+    bat_fixup_kernel<<<(uint32_t)std::min<uint64_t>(S, (uint64_t)8 * num_sms()), 256, 0, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? FQ_OK : FQ_ECUDA;
+}
+
+fq_status fq_frontier_decode_batch(const uint8_t *d_in, const uint64_t *d_in_off, const uint64_t *d_in_bytes, uint32_t S,
+                                   uint32_t *d_ids, const uint64_t *d_seg_off, uint64_t total_ids, uint64_t *d_n,
+                                   void *d_work, uint64_t work_bytes, void *stream)
+{
+    if (S == 0) return FQ_OK;
+    if (!d_in || !d_in_off || !d_in_bytes || !d_seg_off || !d_n || !d_work || (total_ids && !d_ids)) return FQ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_in) & 15u) || (reinterpret_cast<uintptr_t>(d_work) & 15u)) return FQ_EINVAL;
+    if (work_bytes < fq_batch_workspace_bytes(total_ids, S)) return FQ_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BDec a{d_in, d_in_off, d_in_bytes, S, d_ids, d_seg_off, d_n, {}};
+    batch_layout(total_ids, S, &a.b, d_work);
+    static bool done[64] = {false};
+    if (allow_smem_b(bat_dunpack_kernel, kBatchDecSmem, done) != cudaSuccess) return FQ_ECUDA;
+    bat_dplan_kernel<<<1, kScanThreads, 0, st>>>(a);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)8 * num_sms());
+    bat_dtiles_kernel<<<grid, kEncThreads, 0, st>>>(a);
+    bat_dscan_kernel<<<(uint32_t)std::min<uint64_t>(S, (uint64_t)8 * num_sms()), kEncThreads, 0, st>>>(a);
+    bat_dunpack_kernel<<<(uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)3 * num_sms()), kEncThreads,
+                         kBatchDecSmem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? FQ_OK : FQ_ECUDA;
+}
+
+}  // extern "C"

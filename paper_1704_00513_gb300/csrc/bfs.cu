@@ -576,7 +576,8 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     const uint32_t alpha = (opts && opts->alpha) ? opts->alpha : 14u;
     const uint32_t beta = (opts && opts->beta) ? opts->beta : 24u;
     const uint32_t flags = opts ? opts->flags : 0u;
-    const bool want_visited = flags & FQ_BFS_VISITED_STREAM;
+    const bool codec = !(flags & FQ_BFS_NO_CODEC);
+    const bool want_visited = codec && (flags & FQ_BFS_VISITED_STREAM);
     const uint64_t n = g->n, nwords = g->nwords;
     const int sms = num_sms();
     uint32_t *next32 = reinterpret_cast<uint32_t *>(g->next);
@@ -621,7 +622,9 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         // 1. encode F_d (Q_d and B_d), and V_d
         tm.begin(FQ_K_ENCODE);
         int enc_launches = 2;
-        if (2 * n_f <= n) {
+        if (!codec) {
+            enc_launches = 0;
+        } else if (2 * n_f <= n) {
             Mirror mb;
             mb.out = g->bs;
             mb.cap = g->bs_cap;
@@ -652,12 +655,14 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         // 3 + 4. decode the consumed form, expand
         if (dir == FQ_TOP_DOWN) {
             tm.begin(FQ_K_DECODE);
-            FQ_TRY(decode_fq(g->qs, 0, reinterpret_cast<const uint64_t *>(q_bytes), g->q2, n_f,
-                             reinterpret_cast<uint64_t *>(&g->ctr->dec_n), g->sq, st));
-            tm.end(FQ_K_DECODE, 2);
+            if (codec)
+                FQ_TRY(decode_fq(g->qs, 0, reinterpret_cast<const uint64_t *>(q_bytes), g->q2, n_f,
+                                 reinterpret_cast<uint64_t *>(&g->ctr->dec_n), g->sq, st));
+            tm.end(FQ_K_DECODE, codec ? 3 : 0);
+            const uint32_t *qin = codec ? g->q2 : g->q;
             tm.begin(FQ_K_TOP_DOWN);
             const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(std::max<uint64_t>(n_f, 1), kThreads), (uint64_t)sms * 8);
-            td_expand_kernel<<<grid, kThreads, 0, st>>>(g->q2, n_f, g->off, g->cols, vis32, next32, d_depth, d_parent,
+            td_expand_kernel<<<grid, kThreads, 0, st>>>(qin, n_f, g->off, g->cols, vis32, next32, d_depth, d_parent,
                                                         newdepth, g->items, &g->ctr->hub_items, g->items_cap, n,
                                                         g->sq.ctl, &g->ctr->m_f_next);
             td_hub_kernel<<<sms * 4, kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32,
@@ -666,13 +671,14 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             tm.end(FQ_K_TOP_DOWN, 2);
         } else {
             tm.begin(FQ_K_DECODE);
-            FQ_TRY(decode_fb(g->bs, 0, reinterpret_cast<const uint64_t *>(b_bytes), g->fbits2, n, g->sq, st));
-            tm.end(FQ_K_DECODE, 3);
+            if (codec) FQ_TRY(decode_fb(g->bs, 0, reinterpret_cast<const uint64_t *>(b_bytes), g->fbits2, n, g->sq, st));
+            tm.end(FQ_K_DECODE, codec ? 4 : 0);
+            const uint64_t *fin = codec ? g->fbits2 : g->fbits;
             tm.begin(FQ_K_BOTTOM_UP);
             const uint64_t words32 = cdiv(n, 32);
             const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16);
             bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
-                reinterpret_cast<const uint32_t *>(g->fbits2), vis32, g->iso32, next32, g->off, g->cols, d_depth,
+                reinterpret_cast<const uint32_t *>(fin), vis32, g->iso32, next32, g->off, g->cols, d_depth,
                 d_parent, newdepth, n, &g->ctr->examined, &g->ctr->m_f_next);
             FQ_TRY(cudaGetLastError());
             tm.end(FQ_K_BOTTOM_UP, 1);
@@ -697,25 +703,25 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         tm.collect(FQ_K_COMPACT);
         if (hc->r_err_q != FQ_OK) return hc->r_err_q;
         if (hc->r_err_v != FQ_OK) return hc->r_err_v;
-        if (dir == FQ_TOP_DOWN && hc->dec_n != n_f) return FQ_ECORRUPT;
+        if (codec && dir == FQ_TOP_DOWN && hc->dec_n != n_f) return FQ_ECORRUPT;
 
         const uint64_t examined = dir == FQ_TOP_DOWN ? m_f : hc->r_examined;
         const uint64_t nf_next = hc->n_f_next, mf_next = hc->r_m_f;
-        const uint64_t qb = hc->q_bytes, bb = hc->b_bytes, vb = want_visited ? hc->v_bytes : 0;
+        const uint64_t qb = codec ? hc->q_bytes : 0, bb = codec ? hc->b_bytes : 0, vb = want_visited ? hc->v_bytes : 0;
 
         // algorithmic bytes of this level (design model)
-        stats.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + (n + 7) / 8 + bb + (want_visited ? (n + 7) / 8 + vb : 0);
+        if (codec) stats.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + (n + 7) / 8 + bb + (want_visited ? (n + 7) / 8 + vb : 0);
         if (dir == FQ_TOP_DOWN) {
-            stats.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
+            if (codec) stats.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
             stats.kernel_bytes[FQ_K_TOP_DOWN] += 4 * examined + 20 * n_f + 8 * nf_next;
         } else {
-            stats.kernel_bytes[FQ_K_DECODE] += bb + (n + 7) / 8;
+            if (codec) stats.kernel_bytes[FQ_K_DECODE] += bb + (n + 7) / 8;
             stats.kernel_bytes[FQ_K_BOTTOM_UP] += 3 * ((n + 7) / 8) + 16 * (n - visited_count) + 4 * examined + 8 * nf_next;
         }
         stats.kernel_bytes[FQ_K_COMPACT] += 3 * ((n + 7) / 8) + 20 * nf_next;
 
         uint64_t log_off = ~0ull;
-        if (d_stream_log) {
+        if (d_stream_log && codec) {
             const uint64_t need = qb + bb + vb;
             if (log_used + need > stream_log_cap) {
                 result = FQ_ENOSPC;

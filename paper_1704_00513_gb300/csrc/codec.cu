@@ -16,6 +16,7 @@
 #include <cstdio>
 
 #include "fq_common.cuh"
+#include "codec_dev.cuh"
 
 namespace fq {
 
@@ -132,11 +133,6 @@ struct DecArgs {
 };
 
 __device__ __forceinline__ uint64_t enc_count(const EncArgs &a) { return a.n_dev ? *a.n_dev : a.n_host; }
-__device__ __forceinline__ uint64_t dpad16(uint64_t b) { return (b + 15u) & ~uint64_t(15); }
-__device__ __forceinline__ uint64_t dcdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
-
-__device__ __forceinline__ uint32_t ld_u32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
 // ---- single-pass encode ----
 //
 // One kernel computes widths, the payload offsets and the packed words in one read of the ids.
@@ -147,68 +143,6 @@ __device__ __forceinline__ uint32_t ld_u32(const uint8_t *p) { return *reinterpr
 // running; the waits are bounded anyway (kSpinLimit polls, then FQ_ETIMEOUT).  Packed words are
 // written only where they fit below the raw size: if the raw form wins, enc_fixup_kernel writes
 // it over them.  The CTA holding the last tile decides packed/raw and writes the headers.
-
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
-{
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
-
-__device__ __forceinline__ void publish(unsigned long long *status, uint64_t t, unsigned long long flag,
-                                        unsigned long long value)
-{
-    __threadfence();
-    atomicExch(status + t, flag | (value & kValueMask));
-}
-
-// CTA-wide: sum of the width sums of tiles 0 .. t-1 (t >= 1), by decoupled look-back.  Every
-// thread polls one predecessor, so one round covers kEncThreads tiles: the running prefix moves
-// that many tiles per L2 round trip.  All threads of the CTA must call it.
-__device__ unsigned long long lookback(unsigned long long *status, uint64_t t, Ctl *c, unsigned long long *red,
-                                       uint32_t *s_first)
-{
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    unsigned long long excl = 0;
-    long long base = (long long)t - 1;
-    for (;;) {
-        const long long idx = base - (long long)tid;
-        unsigned long long w = kFlagPrefix;  // before tile 0: an empty prefix
-        if (idx >= 0) {
-            uint32_t spins = 0;
-            w = ld_volatile_u64(status + idx);
-            while ((w >> 62) == 0ull) {
-                if (++spins > kSpinLimit) {
-                    set_error(c, FQ_ETIMEOUT, kWhereEncWidths, (unsigned long long)idx);
-                    w = kFlagPrefix;
-                    break;
-                }
-                __nanosleep(32);
-                w = ld_volatile_u64(status + idx);
-            }
-        }
-        __threadfence();
-        if (tid == 0) *s_first = kEncThreads;
-        __syncthreads();
-        if ((w >> 62) == 2ull) atomicMin(s_first, tid);  // nearest predecessor holding a full prefix
-        __syncthreads();
-        const uint32_t first = *s_first;
-        unsigned long long val = (tid <= first) ? (w & kValueMask) : 0ull;
-        val = warp_sum64(val);
-        if (lane == 0) red[warp] = val;
-        __syncthreads();
-        unsigned long long sum = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < kEncWarps; i++) sum += red[i];
-        __syncthreads();
-        excl += sum;
-        if (first < kEncThreads) return excl;
-        base -= kEncThreads;
-    }
-}
 
 __device__ __forceinline__ uint64_t fb_raw_size(uint64_t nbits) { return 16u + dpad16(8u * dcdiv(nbits, 64)); }
 
@@ -302,88 +236,11 @@ __device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned
     if (a.m_out) *a.m_out_bytes = size2;
 }
 
-// ---- TMA staging helpers (1-D bulk copies into shared memory, completion on an mbarrier) ----
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_fence()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Issue a bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) global -> shared,
-// arriving on `bar` with the byte count as its transaction.
-__device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, uint32_t bytes, unsigned long long *bar)
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(sdst)),
-                 "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// Wait until phase `parity` of `bar` completes; bounded: gives up after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
-{
-    for (uint32_t i = 0; i < kSpinLimit; i++) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
 constexpr uint32_t kSubIds = kTileBlocks * kBlock;    // 8192 ids = 32 KB per TMA stage
 constexpr uint32_t kSubs = 4;                         // sub-tiles per encode tile
 constexpr uint32_t kEncTileBlocks = kSubs * kTileBlocks;  // 256 blocks = 32768 ids per look-back
 constexpr size_t kOnepassSmem = 2 * kSubIds * sizeof(uint32_t);
 
-
-// Gaps of the four slots lane*4 .. lane*4+3 of block k from its four ids v; prev is the id
-// before the block (used only for the sortedness check of slot 0).
-__device__ __forceinline__ void gaps_of(const uint32_t v[4], uint32_t prev_block_last, bool has_prev_block, uint64_t k,
-                                        uint64_t n, uint32_t lane, uint32_t g[4], unsigned long long *bad)
-{
-    uint32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
-    bool has_prev = lane > 0;
-    if (lane == 0) {
-        prev = prev_block_last;
-        has_prev = has_prev_block;
-    }
-    const uint64_t i0 = k * kBlock + 4u * lane;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        g[j] = 0;
-        if (i0 + j >= n) continue;
-        const uint32_t p = (j == 0) ? prev : v[j - 1];
-        const bool hp = (j == 0) ? has_prev : true;
-        if (hp) {
-            if (v[j] <= p) *bad = min(*bad, (unsigned long long)(i0 + j));
-            else if (!(lane == 0 && j == 0)) g[j] = v[j] - p - 1u;
-        }
-    }
-}
-
-__device__ __forceinline__ void load4_guard(const uint32_t *ids, uint64_t i, uint64_t n, uint32_t v[4])
-{
-    if (i + 3 < n) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(ids + i);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; j++) v[j] = (i + j < n) ? ids[i + j] : 0u;
-    }
-}
 
 // Single pass over the ids: tiles of 256 blocks are handed out in ticket order.  Pass A streams
 // the tile's four 32 KB sub-tiles through two shared-memory stages filled by TMA bulk copies

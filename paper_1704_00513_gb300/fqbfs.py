@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfqbfs.so")
 
 FQ_OK, FQ_EINVAL, FQ_ENOMEM, FQ_ENOSPC, FQ_ECORRUPT, FQ_EUNSORTED, FQ_ETIMEOUT, FQ_ECUDA, FQ_EBUSY = range(9)
 FQ_TOP_DOWN, FQ_BOTTOM_UP = 0, 1
-FQ_BFS_VISITED_STREAM, FQ_BFS_FORCE_TOP_DOWN, FQ_BFS_FORCE_BOTTOM_UP, FQ_BFS_TIMING = 1, 2, 4, 8
+FQ_BFS_VISITED_STREAM, FQ_BFS_FORCE_TOP_DOWN, FQ_BFS_FORCE_BOTTOM_UP, FQ_BFS_TIMING, FQ_BFS_NO_CODEC = 1, 2, 4, 8, 16
 KCLASS = ("top_down", "bottom_up", "compact", "encode", "decode", "other")
 
 _u64, _u32, _i32, _vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
@@ -64,7 +64,13 @@ _SIGS = {
     "fq_frontier_decode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_encode_static": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fq_bitmap_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_batch_workspace_bytes": ([_u64, _u32], _u64),
+    "fq_frontier_encode_batch": ([_vp, _vp, _u32, _u64, _vp, _vp, _vp, _vp, _u64, _vp], _i32),
+    "fq_frontier_decode_batch": ([_vp, _vp, _vp, _u32, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_bitmap_decode": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp], _i32),
+    "fq_msbfs_scratch_bytes": ([_u64], _u64),
+    "fq_bfs_run_multi": ([_vp, _vp, _u64, ctypes.POINTER(_u32), _u32, _vp, _vp, _u64, ctypes.POINTER(fq_bfs_stats), _vp],
+                         _i32),
     "fq_graph_create": ([_vp, _vp, _u64, _u64, ctypes.POINTER(_vp)], _i32),
     "fq_graph_destroy": ([_vp], _i32),
     "fq_bfs_run": ([_vp, _u32, _vp, _vp, ctypes.POINTER(fq_bfs_opts), ctypes.POINTER(fq_bfs_stats),
@@ -212,6 +218,52 @@ def fq_bitmap_decode(stream_bytes: torch.Tensor, nbits: int, out: torch.Tensor |
     return out[: 2 * nwords64]
 
 
+# ----------------------------------------------------------------------------- batched codec
+
+def fq_batch_workspace_bytes(total_ids: int, S: int) -> int:
+    return int(lib().fq_batch_workspace_bytes(total_ids, S))
+
+
+class Batch:
+    """Buffers for batched encode/decode of S segments laid out by seg_off (int64 CUDA tensor,
+    S+1 offsets): stream capacities from fq_queue_bound, a workspace, size arrays."""
+
+    def __init__(self, seg_off: torch.Tensor):
+        assert seg_off.is_cuda and seg_off.dtype == torch.int64
+        self.seg_off = seg_off.contiguous()
+        self.S = seg_off.numel() - 1
+        lens = (seg_off[1:] - seg_off[:-1]).cpu()
+        caps = 16 + (4 * lens + 15) // 16 * 16
+        self.out_off = torch.zeros(self.S + 1, dtype=torch.int64)
+        self.out_off[1:] = torch.cumsum(caps, 0)
+        self.out_off = self.out_off.to(seg_off.device)
+        self.total_ids = int(seg_off[-1].item())
+        dev = seg_off.device
+        self.out = torch.empty(int(self.out_off[-1].item()), dtype=torch.uint8, device=dev)
+        self.out_bytes = torch.zeros(self.S, dtype=torch.int64, device=dev)
+        self.work = torch.empty(fq_batch_workspace_bytes(self.total_ids, self.S), dtype=torch.uint8, device=dev)
+        self.n = torch.zeros(self.S, dtype=torch.int64, device=dev)
+
+    def encode(self, ids: torch.Tensor, stream=None, check: bool = True):
+        _check(lib().fq_frontier_encode_batch(_ptr(ids), _ptr(self.seg_off), self.S, self.total_ids, _ptr(self.out),
+                                              _ptr(self.out_off), _ptr(self.out_bytes), _ptr(self.work),
+                                              self.work.numel(), _stream(stream)), "fq_frontier_encode_batch")
+        if check:
+            _device_status(self.work, stream, "fq_frontier_encode_batch")
+
+    def decode(self, ids_out: torch.Tensor, in_bytes: torch.Tensor | None = None, stream=None, check: bool = True):
+        nb = self.out_bytes if in_bytes is None else in_bytes
+        _check(lib().fq_frontier_decode_batch(_ptr(self.out), _ptr(self.out_off), _ptr(nb), self.S, _ptr(ids_out),
+                                              _ptr(self.seg_off), self.total_ids, _ptr(self.n), _ptr(self.work),
+                                              self.work.numel(), _stream(stream)), "fq_frontier_decode_batch")
+        if check:
+            _device_status(self.work, stream, "fq_frontier_decode_batch")
+
+    def stream(self, s: int) -> torch.Tensor:
+        o = int(self.out_off[s].item())
+        return self.out[o: o + int(self.out_bytes[s].item())]
+
+
 # ----------------------------------------------------------------------------- BFS
 
 @dataclass
@@ -257,6 +309,20 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+    def bfs_multi(self, roots, depth: torch.Tensor | None = None, scratch: torch.Tensor | None = None, stream=None):
+        """Multi-source BFS of up to 64 roots in one launch; returns (depth [k, n] int32, stats)."""
+        k = len(roots)
+        dev = self.offsets.device
+        if depth is None:
+            depth = torch.empty((k, self.n), dtype=torch.int32, device=dev)
+        if scratch is None:
+            scratch = torch.empty(int(lib().fq_msbfs_scratch_bytes(self.n)), dtype=torch.uint8, device=dev)
+        r = (_u32 * k)(*[int(x) for x in roots])
+        stats = fq_bfs_stats()
+        _check(lib().fq_bfs_run_multi(_ptr(self.offsets), _ptr(self.cols), self.n, r, k, _ptr(depth), _ptr(scratch),
+                                      scratch.numel(), ctypes.byref(stats), _stream(stream)), "fq_bfs_run_multi")
+        return depth, _stats_dict(stats)
 
     def bfs(self, root: int, depth: torch.Tensor | None = None, parent: torch.Tensor | None | bool = True,
             alpha: int = 14, beta: int = 24, flags: int = 0, record_streams: bool = False, max_levels: int = 4096,

@@ -158,3 +158,12 @@ def test_rmat24_full_size_sampled_roots():
                                      off.size - 1)
             assert np.array_equal(res.streams[d]["V"].cpu().numpy(), v)
     g.close()
+
+
+def test_rmat16_without_codec_stage_same_depths_and_schedule(rmat16):
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    for r in roots[:4]:
+        res = check_run(g, off, cols, r, flags=fqbfs.FQ_BFS_NO_CODEC, streams=False, visited=False)
+        assert res.stats["enc_queue_bytes"] == 0
+    g.close()
