@@ -62,6 +62,10 @@ typedef int32_t fq_status;
 /* Human-readable name of a status code (static storage). */
 const char *fq_status_string(fq_status s);
 
+/* The last cudaError_t value a call of this library saw fail in the calling thread (0 if none);
+ * *line (may be NULL) receives the library source line.  Explains an FQ_ECUDA return. */
+int fq_last_cuda_error(int *line);
+
 /* ------------------------------------------------------------------ sizes */
 
 /* Largest FQ stream for n ids: 16 + pad16(4n) bytes (the raw form; packed is chosen only when
@@ -267,6 +271,57 @@ uint64_t fq_msbfs_scratch_bytes(uint64_t n);
 fq_status fq_bfs_run_multi(const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, const uint32_t *h_roots,
                            uint32_t k, int32_t *d_depth, void *d_scratch, uint64_t scratch_bytes,
                            fq_bfs_stats *h_stats, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ * A continuous-batching server over resident graphs (the thesis has no serving layer; this is the
+ * serving form of its BFS + codec hot path).  `slots` worker threads each own a CUDA stream, a
+ * codec workspace and a BFS handle per resident graph.  Requests queue FIFO; the head request is
+ * admitted when a slot is idle and its device footprint fits in the HBM budget next to the resident
+ * graphs and the running requests.  An admitted request allocates its device buffers stream-ordered,
+ * copies its host input in, runs, copies its result to the host buffers and frees -- so requests
+ * that arrive while others are on the GPU start as slots and memory free up, and their copies and
+ * kernels overlap.  Each request's result is the one the plain calls give alone. */
+#define FQ_REQ_BFS 1     /* h_out: int32 depth[n] (out_cap >= 4n); h_out2 (optional): parent[n]   */
+#define FQ_REQ_ENCODE 2  /* h_in: uint32 ids[in_count]; h_out: FQ stream (out_cap bytes)            */
+#define FQ_REQ_DECODE 3  /* h_in: FQ stream of in_count bytes (multiple of 16); h_out: ids (out_cap) */
+
+typedef struct fq_request {
+    uint32_t kind;       /* FQ_REQ_*                                                             */
+    uint32_t graph;      /* BFS: id from fq_server_add_graph                                     */
+    uint32_t root;       /* BFS: source vertex                                                   */
+    uint32_t flags;      /* BFS: fq_bfs_opts.flags                                               */
+    const void *h_in;    /* host input (kept valid until done)                                   */
+    uint64_t in_count;   /* ENCODE: ids; DECODE: bytes                                           */
+    void *h_out;         /* host output                                                          */
+    uint64_t out_cap;    /* bytes at h_out                                                       */
+    void *h_out2;        /* BFS: parent output or NULL                                           */
+    uint64_t out2_cap;
+    uint64_t out_count;  /* result: BFS reached vertices; ENCODE stream bytes; DECODE ids        */
+    uint64_t aux;        /* result: BFS undirected edges in the reached component                */
+    fq_status status;    /* result                                                               */
+    int32_t done;        /* set to 1 when the result is in place                                */
+    double t_submit, t_start, t_end; /* fq_server_clock() seconds                                 */
+} fq_request;
+
+typedef struct fq_server fq_server;
+
+/* max_codec_ids bounds the ids of one codec request (workspace size).  Starts the slot threads on
+ * the current device. */
+fq_status fq_server_create(uint64_t hbm_budget_bytes, uint32_t slots, uint64_t max_codec_ids, fq_server **out);
+/* Finishes the queued requests, joins the workers, frees everything. */
+fq_status fq_server_destroy(fq_server *s);
+/* Make a CSR graph (device arrays, borrowed) resident; creates one BFS handle per slot. FQ_EBUSY
+ * while requests run. */
+fq_status fq_server_add_graph(fq_server *s, const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, uint64_t m,
+                              uint32_t *graph_id);
+/* Queue a request (the struct stays owned by the caller and valid until done).  FQ_ENOMEM if it can
+ * never fit in the budget. */
+fq_status fq_server_submit(fq_server *s, fq_request *r);
+/* Wait up to timeout_s seconds for r; returns its status, or FQ_ETIMEOUT. */
+fq_status fq_server_wait(fq_server *s, fq_request *r, double timeout_s);
+fq_status fq_server_info(fq_server *s, uint64_t *resident, uint64_t *in_use, uint64_t *queued, uint64_t *completed);
+/* The server's clock (seconds, monotonic) used for the request timestamps. */
+double fq_server_clock(void);
 
 #ifdef __cplusplus
 }

@@ -589,7 +589,11 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
 
 #define FQ_TRY(expr)                                  \
     do {                                              \
-        if ((expr) != cudaSuccess) return FQ_ECUDA;   \
+        const cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) {                      \
+            note_cuda_error(_e, __LINE__);            \
+            return FQ_ECUDA;                          \
+        }                                             \
     } while (0)
 
     // ---- level 0 set-up

@@ -81,6 +81,17 @@ Scratch carve(void *base, uint64_t max_ids, uint64_t max_nbits)
     return s;
 }
 
+namespace {
+thread_local int g_last_cuda_error = 0;
+thread_local int g_last_cuda_line = 0;
+}  // namespace
+
+void note_cuda_error(cudaError_t e, int line)
+{
+    g_last_cuda_error = (int)e;
+    g_last_cuda_line = line;
+}
+
 int num_sms()
 {
     static int cached[64] = {0};
@@ -1032,7 +1043,12 @@ using namespace fq;
 
 namespace {
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-fq_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FQ_OK : FQ_ECUDA; }
+fq_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return FQ_OK;
+    note_cuda_error(e, __LINE__);
+    return FQ_ECUDA;
+}
 }  // namespace
 
 extern "C" {
@@ -1051,6 +1067,12 @@ const char *fq_status_string(fq_status s)
     case FQ_EBUSY: return "FQ_EBUSY";
     default: return "FQ_UNKNOWN";
     }
+}
+
+int fq_last_cuda_error(int *line)
+{
+    if (line) *line = g_last_cuda_line;
+    return g_last_cuda_error;
 }
 
 uint64_t fq_queue_bound(uint64_t n) { return 16u + pad16(4u * n); }

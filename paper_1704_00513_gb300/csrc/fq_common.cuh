@@ -217,8 +217,16 @@ __device__ __forceinline__ unsigned long long cta_excl_scan64(unsigned long long
 
 }  // namespace fq
 
-#define FQ_CUDA_TRY(expr)                         \
-    do {                                          \
-        cudaError_t _e = (expr);                  \
-        if (_e != cudaSuccess) return _e;         \
+namespace fq {
+// The last CUDA error the library saw in this thread (reported by fq_last_cuda_error()).
+void note_cuda_error(cudaError_t e, int line);
+}
+
+#define FQ_CUDA_TRY(expr)                                \
+    do {                                                 \
+        cudaError_t _e = (expr);                         \
+        if (_e != cudaSuccess) {                         \
+            fq::note_cuda_error(_e, __LINE__);           \
+            return _e;                                   \
+        }                                                \
     } while (0)

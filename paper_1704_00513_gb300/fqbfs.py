@@ -56,6 +56,7 @@ _lib = None
 
 _SIGS = {
     "fq_status_string": ([_i32], ctypes.c_char_p),
+    "fq_last_cuda_error": ([ctypes.POINTER(_i32)], _i32),
     "fq_queue_bound": ([_u64], _u64),
     "fq_bitmap_bound": ([_u64], _u64),
     "fq_workspace_bytes": ([_u64, _u64], _u64),
@@ -111,7 +112,11 @@ def _stream(stream=None) -> int:
 
 def _check(status: int, what: str):
     if status != FQ_OK:
-        raise FqError(status, what)
+        detail = 0
+        if status == FQ_ECUDA:
+            line = _i32(0)
+            detail = (int(lib().fq_last_cuda_error(ctypes.byref(line))) << 32) | line.value
+        raise FqError(status, what, detail)
 
 
 def _ptr(t: torch.Tensor | None):

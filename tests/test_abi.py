@@ -10,6 +10,7 @@ import pytest
 import oracle
 from paper_1704_00513_gb300 import build as fqbuild
 from paper_1704_00513_gb300 import fqbfs
+from paper_1704_00513_gb300 import serve
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fqbfs.h")
 
@@ -30,7 +31,9 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["fq_frontier_encode", "fq_frontier_decode", "fq_bitmap_encode", "fq_bitmap_decode",
-                     "fq_graph_create", "fq_graph_destroy", "fq_bfs_run", "fq_workspace_bytes", "fq_work_status"]:
+                     "fq_graph_create", "fq_graph_destroy", "fq_bfs_run", "fq_workspace_bytes", "fq_work_status",
+                     "fq_frontier_encode_batch", "fq_frontier_decode_batch", "fq_bfs_run_multi",
+                     "fq_server_create", "fq_server_submit", "fq_server_wait"]:
         assert required in names
 
 
@@ -40,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
     for name in names:
         assert hasattr(lib, name), name
         assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
-    assert set(names) <= set(fqbfs.exported_symbols())
+    assert set(names) <= set(fqbfs.exported_symbols()) | set(serve.exported_symbols())
 
 
 def test_host_size_functions_match_stream_definitions(lib):
