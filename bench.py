@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-codec", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--codec-only", action="store_true",
                    help="only the standalone codec points (sorted sets, geometric gaps); prints them as JSON")
     return p.parse_args()
@@ -326,6 +329,13 @@ def run_fqbfs(args, world, rank, local):
 
     if not args.no_codec:
         codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = {"codec_4096_segments": batched_codec(dev, peaks["hbm_gbs"]),
+                   "msbfs_scale22_64_roots": batched_msbfs(dev)}
+    served = None
+    if not args.no_serving and rank == 0:
+        served = serving(dev, (off, cols, roots), seconds=args.serve_seconds)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, off, cols, my_roots[args.warmup:], world)
@@ -346,7 +356,8 @@ def run_fqbfs(args, world, rank, local):
                            "roots_per_rank": args.steps, "streams": "Q_d, B_d, V_d encoded every level",
                            "l2": "no flush: the 2.2 GB CSR exceeds L2", "levels_mean": statistics.mean(levels),
                            "parallelism": f"replicas{world}"},
-                "roofline": roofline, "codec": codec, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "codec": codec, "batched": batched, "serving": served,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -397,6 +408,217 @@ def codec_points(dev, peak_gbs, points=((26, 1.0), (26, 16.0), (24, 256.0), (28,
                     "roundtrip_ok": ok})
         del ids, out, work, dec
         torch.cuda.empty_cache()
+    return res
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def batched_codec(dev, peak_gbs, S=4096, lo=16, hi=1 << 20, mean_gap=16.0, seed=SEED, reps=3):
+    """4,096 sorted segments (lengths log-uniform in [16, 2^20], multiples of 4 ids so every segment
+    starts 16-byte aligned; gaps geometric with mean 16): one batched encode + decode against the
+    same work as 4,096 per-segment calls.  Both forms are also timed as captured CUDA graphs, so the
+    comparison is not one of Python launch overhead."""
+    from paper_1704_00513_gb300 import fqbfs, inputs
+    rng = np.random.default_rng(seed)
+    lens = np.exp(rng.uniform(np.log(lo), np.log(hi), S)).astype(np.int64) // 4 * 4
+    lens = np.maximum(lens, 4)
+    off_h = np.zeros(S + 1, np.int64)
+    off_h[1:] = np.cumsum(lens)
+    total = int(off_h[-1])
+    r = inputs.uniform32(seed, 6, 0, total, device=dev)
+    u01 = (r.to(torch.float64) + 0.5) / 2.0**32
+    gaps = torch.floor(torch.log(u01) / np.log1p(-1.0 / mean_gap)).to(torch.int64) + 1
+    del r, u01
+    seg_off = torch.from_numpy(off_h).to(dev)
+    starts = torch.repeat_interleave(seg_off[:-1], torch.from_numpy(lens).to(dev))
+    cs = torch.cumsum(gaps, 0)
+    first = torch.repeat_interleave(cs[seg_off[:-1]] - gaps[seg_off[:-1]], torch.from_numpy(lens).to(dev))
+    ids = (cs - first - 1).to(torch.int32)  # per-segment values from 0: strictly increasing
+    del gaps, cs, first, starts
+    b = fqbfs.Batch(seg_off)
+    out_ids = torch.empty_like(ids)
+    stream = torch.cuda.current_stream()
+    # batched form
+    b.encode(ids)
+    b.decode(out_ids)
+    ok = bool(torch.equal(out_ids, ids))
+    enc_bytes = int(b.out_bytes.sum().item())
+    alg = 4 * total + enc_bytes
+    e0, e1 = _events()
+    e0.record(stream)
+    for _ in range(reps):
+        b.encode(ids, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_be = e0.elapsed_time(e1) / reps / 1e3
+    e0.record(stream)
+    for _ in range(reps):
+        b.decode(out_ids, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_bd = e0.elapsed_time(e1) / reps / 1e3
+    g_batch = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_batch):
+        b.encode(ids, check=False)
+        b.decode(out_ids, check=False)
+    g_batch.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        g_batch.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_bg = e0.elapsed_time(e1) / reps / 1e3
+    # plain form: one fq_frontier_encode + fq_frontier_decode per segment
+    L = fqbfs.lib()
+    maxlen = int(lens.max())
+    work = fqbfs.workspace(maxlen, 0, dev)
+    nbytes = torch.zeros(S, dtype=torch.int64, device=dev)
+    ndec = torch.zeros(S, dtype=torch.int64, device=dev)
+    sizes = b.out_bytes.cpu().numpy()
+    oo = b.out_off.cpu().numpy()
+    base_ids, base_out, base_dec = ids.data_ptr(), b.out.data_ptr(), out_ids.data_ptr()
+    pw, pnb, pnd = work.data_ptr(), nbytes.data_ptr(), ndec.data_ptr()
+
+    def plain_calls():
+        st = torch.cuda.current_stream().cuda_stream
+        for i in range(S):
+            n = int(lens[i])
+            L.fq_frontier_encode(base_ids + 4 * int(off_h[i]), n, base_out + int(oo[i]), int(oo[i + 1] - oo[i]),
+                                 pnb + 8 * i, pw, work.numel(), st)
+        for i in range(S):
+            n = int(lens[i])
+            L.fq_frontier_decode(base_out + int(oo[i]), int(sizes[i]), base_dec + 4 * int(off_h[i]), n, pnd + 8 * i,
+                                 pw, work.numel(), st)
+
+    plain_calls()
+    torch.cuda.synchronize()
+    ok_plain = bool(torch.equal(out_ids, ids)) and bool(torch.equal(nbytes, b.out_bytes))
+    e0.record(stream)
+    plain_calls()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_p = e0.elapsed_time(e1) / 1e3
+    g_plain = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_plain):
+        plain_calls()
+    g_plain.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g_plain.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pg = e0.elapsed_time(e1) / 1e3
+    res = {"segments": S, "ids": total, "stream_bytes": enc_bytes, "ratio": 4 * total / enc_bytes,
+           "batched_encode_GBps": alg / t_be / 1e9, "batched_decode_GBps": alg / t_bd / 1e9,
+           "batched_graph_GBps": 2 * alg / t_bg / 1e9, "batched_graph_frac": 2 * alg / t_bg / 1e9 / peak_gbs,
+           "plain_calls_GBps": 2 * alg / t_p / 1e9, "plain_graph_GBps": 2 * alg / t_pg / 1e9,
+           "batched_over_plain_graph": t_pg / t_bg, "batched_over_plain_calls": t_p / t_bg,
+           "launches_batched": 7, "launches_plain": 7 * S, "roundtrip_ok": ok and ok_plain}
+    del b, ids, out_ids, work
+    torch.cuda.empty_cache()
+    return res
+
+
+def batched_msbfs(dev, scale=22, k=64):
+    """64-root multi-source BFS in one launch against 64 single-root runs of the same graph."""
+    from paper_1704_00513_gb300 import fqbfs
+    off, cols, roots = make_graph(scale, 16, dev)
+    roots = roots[:k]
+    g = fqbfs.Graph(off, cols)
+    scratch = torch.empty(int(fqbfs.lib().fq_msbfs_scratch_bytes(off.numel() - 1)), dtype=torch.uint8, device=dev)
+    depth = torch.empty((k, off.numel() - 1), dtype=torch.int32, device=dev)
+    g.bfs_multi(roots, depth=depth, scratch=scratch)
+    stream = torch.cuda.current_stream()
+    e0, e1 = _events()
+    e0.record(stream)
+    _, st = g.bfs_multi(roots, depth=depth, scratch=scratch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_multi = e0.elapsed_time(e1) / 1e3
+    edges = st["reached_edges"]
+    res = {"scale": scale, "roots": k, "multi_GTEPS": edges / t_multi / 1e9, "multi_ms": t_multi * 1e3,
+           "levels": st["levels"], "edges_examined": st["edges_examined"]}
+    for name, flags in (("plain_nocodec", fqbfs.FQ_BFS_NO_CODEC), ("plain_codec", fqbfs.FQ_BFS_VISITED_STREAM)):
+        d1 = torch.empty(off.numel() - 1, dtype=torch.int32, device=dev)
+        p1 = torch.empty_like(d1)
+        g.bfs(roots[0], depth=d1, parent=p1, flags=flags)
+        e0.record(stream)
+        edges_p = 0
+        same = True
+        for i, r in enumerate(roots):
+            rr = g.bfs(r, depth=d1, parent=p1, flags=flags)
+            edges_p += rr.stats["reached_edges"]
+            if i in (0, k - 1):
+                same = same and bool(torch.equal(d1, depth[i]))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        res[name + "_GTEPS"] = edges_p / t / 1e9
+        res[name + "_ms"] = t * 1e3
+        res[name + "_same_depths"] = same
+    res["multi_over_plain_nocodec"] = res["plain_nocodec_ms"] / res["multi_ms"]
+    g.close()
+    del g, depth, scratch
+    torch.cuda.empty_cache()
+    return res
+
+
+def serving(dev, graph24, seconds=4.0, rate=2000.0, budget=100 << 30, seed=SEED):
+    """Poisson request stream over resident R-MAT graphs of scales 18, 20, 22, 24: half single-root
+    BFS queries (random graph, random root), half codec requests on sorted sets of 2^10 .. 2^24 ids
+    (log-uniform, mean gap 16; half encode, half decode), admitted by an HBM budget.  Continuous
+    batching (8 slots) against the same stream served one request at a time."""
+    from paper_1704_00513_gb300 import fqbfs, inputs, serve
+    graphs = []
+    for sc in (18, 20, 22):
+        off, cols = inputs.rmat_csr(sc, 16, seed=seed, device=dev)
+        graphs.append((off, cols, inputs.pick_roots(off, 256, seed=seed)))
+    off24, cols24, roots24 = graph24
+    graphs.append((off24, cols24, roots24))
+    rng = np.random.default_rng(seed)
+    # a pool of codec inputs and their streams (pinned host memory), reused across requests
+    pool = []
+    for i in range(24):
+        n = int(np.exp(rng.uniform(np.log(1 << 10), np.log(1 << 24))))
+        v = inputs.geometric_set(n, 16.0, seed=seed + i, device=dev)
+        ids = v.to(torch.int32)
+        enc, size = fqbfs.fq_frontier_encode(ids)
+        pool.append((ids.cpu().pin_memory(), enc.cpu().pin_memory(), n))
+    n_max = max(p[2] for p in pool)
+    outs_codec = [torch.empty(fqbfs.fq_queue_bound(n_max), dtype=torch.uint8).pin_memory() for _ in range(16)]
+    outs_bfs = [[torch.empty(g[0].numel() - 1, dtype=torch.int32).pin_memory() for _ in range(8)] for g in graphs]
+
+    def make(server, gids):
+        def mk(i, r):
+            if r.random() < 0.5:
+                gi = int(r.integers(len(graphs)))
+                root = graphs[gi][2][int(r.integers(len(graphs[gi][2])))]
+                buf = outs_bfs[gi][i % 8]
+                return serve.Request(serve.FQ_REQ_BFS, graph=gids[gi], root=root, h_out=buf.data_ptr(),
+                                     out_cap=4 * buf.numel())
+            ids, enc, n = pool[int(r.integers(len(pool)))]
+            out = outs_codec[i % 16]
+            if r.random() < 0.5:
+                return serve.Request(serve.FQ_REQ_ENCODE, h_in=ids.data_ptr(), in_count=n, h_out=out.data_ptr(),
+                                     out_cap=out.numel())
+            return serve.Request(serve.FQ_REQ_DECODE, h_in=enc.data_ptr(), in_count=enc.numel(), h_out=out.data_ptr(),
+                                 out_cap=4 * n)
+        return mk
+
+    res = {"rate_rps": rate, "seconds": seconds, "budget_GB": budget / 2**30, "graphs": [18, 20, 22, 24]}
+    for name, slots in (("continuous", 8), ("one_at_a_time", 1)):
+        server = serve.Server(budget, slots, n_max)
+        gids = [server.add_graph(g[0], g[1]) for g in graphs]
+        warm = serve.run_poisson(server, make(server, gids), rate, 0.3, seed + 1)
+        lr = serve.run_poisson(server, make(server, gids), rate, seconds, seed)
+        res[name] = {"slots": slots, "requests": lr.requests, "throughput_rps": lr.throughput,
+                     "p50_ms": lr.p50_ms, "p99_ms": lr.p99_ms, "bfs_p50_ms": lr.bfs_p50_ms,
+                     "codec_p50_ms": lr.codec_p50_ms, "errors": lr.errors + warm.errors}
+        server.close()
+    res["throughput_gain"] = res["continuous"]["throughput_rps"] / max(res["one_at_a_time"]["throughput_rps"], 1e-9)
     return res
 
 
