@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_encode_kernel(BEnc a)
                 if (lane == 0 && k > 0) prevb = lb > 0 ? sb[lb * kBlock - 1] : ids[k * kBlock - 1];
                 uint32_t gg[4];
                 gaps_of(v, prevb, k > 0, k, n, lane, gg, &bad);
-                b = bitlen32(__reduce_max_sync(0xffffffffu, max(max(gg[0], gg[1]), max(gg[2], gg[3]))));
+                b = bitlen32(__reduce_or_sync(0xffffffffu, gg[0] | gg[1] | gg[2] | gg[3]));
                 if (lane == 0 && 16u + 4u * k + 4 <= bound) *reinterpret_cast<uint32_t *>(out + 16u + 4u * k) = v[0];
             }
             if (lane == 0) sw[lb] = b;
@@ -317,9 +317,10 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_encode_kernel(BEnc a)
             uint32_t gg[4];
             unsigned long long dummy = ~0ull;
             gaps_of(v, 0u, false, k, n, lane, gg, &dummy);
-            const uint4 w = pack_block(gg, b, pk[warp], lane);
-            const uint64_t p1 = payload + 16u * (excl + spre[lb] + lane);
-            if (lane < b && p1 + 16 <= bound) *reinterpret_cast<uint4 *>(out + p1) = w;
+            uint32_t w4[4];
+            pack_block_words(gg, b, pk[warp], lane, w4);
+            const uint64_t rel = payload + 16u * (excl + spre[lb]);
+            store_block_words(out + rel, w4, b, lane, rel, bound);
         }
         if (t == ntiles_s - 1 && threadIdx.x == 0) bat_finalize(a, s, n, nb, excl + s_total);
         __syncthreads();
@@ -557,9 +558,17 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
                 const uint64_t k = t * kTileBlocks + local;
                 if (k >= nb) break;
                 uint32_t out[4];
-                unsigned long long last;
-                bool good = unpack_block(sp + 4u * spre[local], wd[k], bases[k], k, n, lane, out, &last);
-                if (k + 1 < nb && lane == 31 && last >= (unsigned long long)bases[k + 1]) good = false;
+                const uint32_t b = wd[k];
+                bool good;
+                if (k + 1 < nb && b <= 16u) {  // full narrow block: the lean 32-bit path
+                    uint32_t last;
+                    good = unpack_full_narrow(sp + 4u * spre[local], b, bases[k], lane, out, &last);
+                    if (lane == 31 && last >= bases[k + 1]) good = false;
+                } else {
+                    unsigned long long last;
+                    good = unpack_block(sp + 4u * spre[local], b, bases[k], k, n, lane, out, &last);
+                    if (k + 1 < nb && lane == 31 && last >= (unsigned long long)bases[k + 1]) good = false;
+                }
                 if (!good) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecUnpack, s);
                 const uint64_t i0 = k * kBlock + 4u * lane;
                 if (vec_ok && i0 + 3 < n) {

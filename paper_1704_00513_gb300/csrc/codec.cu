@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kEncThreads, 3) enc_onepass_kernel(EncArgs a)
                         if (lane == 0 && k > 0) prevb = lb > 0 ? s[lb * kBlock - 1] : a.ids[k * kBlock - 1];
                         uint32_t g[4];
                         gaps_of(v, prevb, k > 0, k, n, lane, g, &bad);
-                        b = bitlen32(__reduce_max_sync(0xffffffffu, max(max(g[0], g[1]), max(g[2], g[3]))));
+                        b = bitlen32(__reduce_or_sync(0xffffffffu, g[0] | g[1] | g[2] | g[3]));
                         if (lane == 0) {
                             const uint64_t pb = fq_off + 16u + 4u * k;
                             if (pb + 4 <= bound) *reinterpret_cast<uint32_t *>(a.out + pb) = v[0];
@@ -424,35 +424,131 @@ __global__ void __launch_bounds__(kEncThreads, 3) enc_onepass_kernel(EncArgs a)
             load4_guard(a.ids, k * kBlock + 4u * lane, n, v);
             unsigned long long dummy = ~0ull;
             gaps_of(v, 0u, false, k, n, lane, g, &dummy);
-#pragma unroll
-            for (int j = 0; j < 4; j++) pk[warp][4 * lane + j] = 0u;
-            if (lane == 0) pk[warp][128] = 0u;
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (g[j] == 0u) continue;
-                const uint32_t pos = (4u * lane + j) * b;
-                const uint32_t w0 = pos >> 5, sh = pos & 31u;
-                atomicOr(&pk[warp][w0], g[j] << sh);
-                if (sh + b > 32u) atomicOr(&pk[warp][w0 + 1], g[j] >> (32u - sh));
-            }
-            __syncwarp();
+            uint32_t w4[4];
+            pack_block_words(g, b, pk[warp], lane, w4);
             const uint64_t rel = payload + 16u * (excl + spre[lb]);
-            if (lane < b) {
-                const uint4 q = make_uint4(pk[warp][4 * lane], pk[warp][4 * lane + 1], pk[warp][4 * lane + 2],
-                                           pk[warp][4 * lane + 3]);
-                const uint64_t p1 = fq_off + rel + 16u * lane;
-                if (p1 + 16 <= bound) *reinterpret_cast<uint4 *>(a.out + p1) = q;
-                if (a.m_out) {
-                    const uint64_t p2 = 16u + rel + 16u * lane;
-                    if (p2 + 16 <= bound2) *reinterpret_cast<uint4 *>(a.m_out + p2) = q;
-                }
-            }
-            __syncwarp();
+            store_block_words(a.out + fq_off + rel, w4, b, lane, fq_off + rel, bound);
+            if (a.m_out) store_block_words(a.m_out + 16u + rel, w4, b, lane, 16u + rel, bound2);
         }
 
         if (t == ntiles - 1 && threadIdx.x == 0) enc_finalize(a, n, nb, excl + s_total);
         __syncthreads();
+    }
+}
+
+// ---- streaming encode for large inputs: widths pass, one-CTA plan, pack pass ----
+//
+// When the input is far larger than L2 the single pass cannot keep its tiles on chip between
+// measuring and packing anyway, so three high-occupancy streaming kernels do better: every warp
+// issues the loads of its eight blocks before using any of them, and nothing waits on another CTA.
+
+__device__ __forceinline__ void load_blocks8(const uint32_t *ids, uint64_t k0, uint64_t n, uint32_t lane,
+                                             uint32_t v[kBlocksPerWarp][4])
+{
+#pragma unroll
+    for (uint32_t i = 0; i < kBlocksPerWarp; i++) load4_guard(ids, (k0 + i) * kBlock + 4u * lane, n, v[i]);
+}
+
+__global__ void __launch_bounds__(kEncThreads, 4) enc_s_widths_kernel(EncArgs a)
+{
+    __shared__ uint32_t ws[kEncWarps];
+    const uint64_t n = a.n_host, nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t k0 = t * kTileBlocks + warp * kBlocksPerWarp;
+        uint32_t v[kBlocksPerWarp][4];
+        load_blocks8(a.ids, k0, n, lane, v);
+        const uint32_t before = (lane == 0 && k0 > 0 && k0 < nb) ? a.ids[k0 * kBlock - 1] : 0u;
+        unsigned long long bad = ~0ull;
+        uint32_t sum = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+            const uint64_t k = k0 + i;
+            const uint32_t prev_last = __shfl_sync(0xffffffffu, i > 0 ? v[i > 0 ? i - 1 : 0][3] : 0u, 31);
+            if (k >= nb) continue;
+            uint32_t g[4];
+            gaps_of(v[i], i > 0 ? prev_last : before, k > 0, k, n, lane, g, &bad);
+            const uint32_t b = bitlen32(__reduce_or_sync(0xffffffffu, g[0] | g[1] | g[2] | g[3]));
+            if (lane == 0) {
+                a.s.widths[k] = (uint8_t)b;
+                a.s.bases[k] = v[i][0];
+            }
+            sum += b;
+        }
+        if (bad != ~0ull) set_error(a.s.ctl, FQ_EUNSORTED, kWhereEncWidths, bad);
+        if (lane == 0) ws[warp] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tsum = 0;
+            for (uint32_t w = 0; w < kEncWarps; w++) tsum += ws[w];
+            a.s.tile_sum[t] = tsum;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) enc_s_plan_kernel(EncArgs a)
+{
+    __shared__ unsigned long long sm[33];
+    const uint64_t n = a.n_host, nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    const uint64_t chunk = dcdiv(ntiles, kScanThreads);
+    const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
+    unsigned long long local = 0, total = 0;
+    for (uint64_t t = t0; t < t1; t++) local += a.s.tile_sum[t];
+    unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
+    for (uint64_t t = t0; t < t1; t++) {
+        a.s.tile_off[t] = (uint32_t)run;
+        run += a.s.tile_sum[t];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) enc_finalize(a, n, nb, total);
+}
+
+// One warp per group of kBlocksPerWarp consecutive blocks (groups never straddle a tile), with no
+// CTA barrier: each warp forms its own offsets from the tile's width bytes (two per lane, one warp
+// scan) and the tile's payload offset, and copies its blocks' bases and widths into the header.
+__global__ void __launch_bounds__(kEncThreads) enc_s_pack_kernel(EncArgs a)
+{
+    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
+    const Ctl *c = a.s.ctl;
+    if (c->mode != kModePacked) return;  // raw bodies come from enc_fixup_kernel
+    const uint64_t n = a.n_host, nb = dcdiv(n, kBlock);
+    const uint64_t ngroups = dcdiv(nb, kBlocksPerWarp);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint64_t payload = 16u + dpad16(5u * nb);
+    constexpr uint32_t kGroupsPerTile = kTileBlocks / kBlocksPerWarp;
+    for (uint64_t grp = (uint64_t)blockIdx.x * kEncWarps + warp; grp < ngroups; grp += (uint64_t)gridDim.x * kEncWarps) {
+        const uint64_t k0 = grp * kBlocksPerWarp, t = grp / kGroupsPerTile;
+        const uint32_t git = (uint32_t)(grp % kGroupsPerTile);  // group inside the tile
+        uint32_t v[kBlocksPerWarp][4];
+        load_blocks8(a.ids, k0, n, lane, v);
+        const uint64_t kk = t * kTileBlocks + 2 * lane;
+        const uint32_t x0 = kk < nb ? a.s.widths[kk] : 0u, x1 = kk + 1 < nb ? a.s.widths[kk + 1] : 0u;
+        const uint32_t tile_base = a.s.tile_off[t];
+        const uint32_t my_base = (lane < kBlocksPerWarp && k0 + lane < nb) ? a.s.bases[k0 + lane] : 0u;
+        const uint32_t incl = warp_incl_scan(x0 + x1);
+        // lane l describes blocks 2l and 2l+1 of the tile: exclusive width prefix | b(2l) << 16 | b(2l+1) << 24
+        const uint32_t info = (incl - x0 - x1) | (x0 << 16) | (x1 << 24);
+        const uint32_t mine = __shfl_sync(0xffffffffu, info, (git * kBlocksPerWarp + (lane & 7u)) >> 1);
+        if (lane < kBlocksPerWarp && k0 + lane < nb) {
+            reinterpret_cast<uint32_t *>(a.out + 16)[k0 + lane] = my_base;
+            a.out[16 + 4 * nb + k0 + lane] = (uint8_t)((lane & 1u) ? (mine >> 24) : ((mine >> 16) & 0xffu));
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+            const uint64_t k = k0 + i;
+            const uint32_t in = __shfl_sync(0xffffffffu, info, (git * kBlocksPerWarp + i) >> 1);
+            const uint32_t b = (i & 1u) ? (in >> 24) : ((in >> 16) & 0xffu);
+            const uint32_t pre = (in & 0xffffu) + ((i & 1u) ? ((in >> 16) & 0xffu) : 0u);
+            if (k >= nb || b == 0) continue;
+            uint32_t g[4];
+            unsigned long long dummy = ~0ull;
+            gaps_of(v[i], 0u, false, k, n, lane, g, &dummy);
+            uint32_t w4[4];
+            pack_block_words(g, b, pk[warp], lane, w4);
+            const uint64_t rel = payload + 16u * ((uint64_t)tile_base + pre);
+            store_block_words(a.out + rel, w4, b, lane, rel, ~0ull);
+        }
     }
 }
 
@@ -797,7 +893,7 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
 {
     extern __shared__ __align__(128) uint8_t dbuf[];  // [2][kDecStage]
     __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t spre[kTileBlocks];
+    __shared__ uint32_t spre[kTileBlocks], swid[kTileBlocks], sbase[kTileBlocks + 1];
     const Ctl *c = a.s.ctl;
     const uint32_t mode = c->mode;
     if (mode != kModePacked && mode != kModeRaw) return;
@@ -850,6 +946,13 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
             const uint32_t incl = warp_incl_scan(x0 + x1);
             spre[2 * lane] = incl - x0 - x1;
             spre[2 * lane + 1] = incl - x1;
+            swid[2 * lane] = x0;
+            swid[2 * lane + 1] = x1;
+        } else if (warp == 1 || warp == 2) {  // the tile's bases and the next tile's first base
+            const uint32_t j = (warp - 1) * 32u + lane;
+            const uint64_t k = t * kTileBlocks + j;
+            sbase[j] = k < nb ? bases[k] : 0u;
+            if (j == 0) sbase[kTileBlocks] = (t + 1) * kTileBlocks < nb ? bases[(t + 1) * kTileBlocks] : 0u;
         }
         if (tile_bytes(t)) {
             if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(a.s.ctl, FQ_ETIMEOUT, kWhereDecUnpack, t);
@@ -862,44 +965,22 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
             const uint32_t local = warp * kBlocksPerWarp + bi;
             const uint64_t k = t * kTileBlocks + local;
             if (k >= nb) break;
-            const uint32_t b = wd[k];
-            const uint64_t base = bases[k];
+            const uint32_t b = swid[local];
             const uint32_t *pk = sp + 4u * spre[local];
-            const uint32_t mask = (b == 32u) ? 0xffffffffu : ((1u << b) - 1u);
-            unsigned long long inc[4];
-            unsigned long long lsum = 0;
-            bool bad = false;
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t slot = 4u * lane + j;
-                uint32_t g = 0;
-                if (b) {
-                    const uint32_t pos = slot * b, w0 = pos >> 5, sh = pos & 31u;
-                    const uint64_t two = ((uint64_t)pk[w0 + 1] << 32) | pk[w0];
-                    g = (uint32_t)(two >> sh) & mask;
-                }
-                const uint64_t idx = k * kBlock + slot;
-                if (slot == 0 || idx >= n) {
-                    if (g) bad = true;
-                    inc[j] = 0;
-                } else {
-                    inc[j] = (unsigned long long)g + 1ull;
-                }
-                lsum += inc[j];
-            }
-            const unsigned long long excl = warp_incl_scan64(lsum) - lsum;
-            unsigned long long v = base + excl;
             const uint64_t i0 = k * kBlock + 4u * lane;
             uint32_t out[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                v += inc[j];
-                out[j] = (uint32_t)v;
-                if (i0 + j < n && v > 0xffffffffull) bad = true;
+            bool good;
+            if (k + 1 < nb && b <= 16u) {  // full narrow block: the lean 32-bit path
+                uint32_t lastv;
+                good = unpack_full_narrow(pk, b, sbase[local], lane, out, &lastv);
+                if (lane == 31 && lastv >= sbase[local + 1]) good = false;
+            } else {
+                unsigned long long lastv;
+                good = unpack_block(pk, b, sbase[local], k, n, lane, out, &lastv);
+                // a full block (k + 1 < nb) ends in lane 31's last slot: it must stay below the next base
+                if (k + 1 < nb && lane == 31 && lastv >= (unsigned long long)sbase[local + 1]) good = false;
             }
-            // a full block (k + 1 < nb) ends in lane 31's last slot: it must stay below the next base
-            if (k + 1 < nb && lane == 31 && v >= (unsigned long long)bases[k + 1]) bad = true;
-            if (bad) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, k * kBlock);
+            if (!good) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, k * kBlock);
             if (!a.fb && i0 + 3 < n) {
                 *reinterpret_cast<uint4 *>(a.ids + i0) = make_uint4(out[0], out[1], out[2], out[3]);
             } else {
@@ -924,6 +1005,23 @@ uint32_t grid_for(uint64_t items, uint32_t per_cta, uint32_t max_ctas)
 }
 
 uint64_t enc_tiles(uint64_t n) { return cdiv(cdiv(n, kBlock), kTileBlocks); }
+
+// CTAs of `kernel` (static shared memory only) resident on the whole GPU at once, cached per device
+// in `cache`: a grid-stride kernel launched with exactly this many CTAs runs in a single wave.
+template <typename K>
+uint64_t resident_grid(K kernel, int threads, int *cache)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return (uint64_t)num_sms();
+    if (!cache[dev]) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0)
+            per_sm = 1;
+        cache[dev] = per_sm;
+    }
+    return (uint64_t)cache[dev] * num_sms();
+}
+constexpr uint64_t kStreamingIds = 1ull << 22;  // 16 MB of ids: beyond this the streaming encoder is used
 
 // Kernels with more than 48 KB of dynamic shared memory must opt in, once per device.
 template <typename K>
@@ -977,6 +1075,19 @@ cudaError_t encode_fq(const uint32_t *ids, uint64_t n_host, const uint64_t *n_de
                       uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
 {
     EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0, 1};
+    if (!n_dev && n_host >= kStreamingIds && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0) {
+        // far larger than L2: three streaming kernels (widths, plan, pack) + the raw fix-up
+        static int occ_widths[64], occ_pack[64];
+        const uint64_t tiles = enc_tiles(n_host);
+        const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_s_widths_kernel, kEncThreads, occ_widths));
+        const uint32_t gp = (uint32_t)std::min<uint64_t>(tiles * (kTileBlocks / kBlocksPerWarp) / kEncWarps + 1,
+                                                         resident_grid(enc_s_pack_kernel, kEncThreads, occ_pack));
+        enc_s_widths_kernel<<<gw, kEncThreads, 0, st>>>(a);
+        enc_s_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
+        enc_s_pack_kernel<<<gp, kEncThreads, 0, st>>>(a);
+        enc_fixup_kernel<<<grid_for(cdiv(n_host, 4) * 4, 256, 4 * num_sms()), 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     return launch_encode(a, n_dev ? n_max : n_host, st);
 }
 

@@ -129,6 +129,14 @@ __device__ __forceinline__ void gaps_of(const uint32_t v[4], uint32_t prev_block
         prev = prev_block_last;
         has_prev = has_prev_block;
     }
+    if ((k + 1) * kBlock <= n) {  // full block: 32-bit gaps and one sortedness test per lane
+        g[0] = lane ? v[0] - prev - 1u : 0u;
+        g[1] = v[1] - v[0] - 1u;
+        g[2] = v[2] - v[1] - 1u;
+        g[3] = v[3] - v[2] - 1u;
+        const bool unsorted = (has_prev && v[0] <= prev) | (v[1] <= v[0]) | (v[2] <= v[1]) | (v[3] <= v[2]);
+        if (!unsorted) return;  // otherwise the general path below finds the first bad index
+    }
     const uint64_t i0 = k * kBlock + 4u * lane;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -155,11 +163,63 @@ __device__ __forceinline__ void load4_guard(const uint32_t *ids, uint64_t i, uin
 }
 
 
+// floor(x / b) == (x * kRecip16[b]) >> 16 for 1 <= b <= 32 and 0 <= x < 2048 (kRecip16[b] is
+// ceil(2^16 / b)); used where a width divides a small bit count, instead of an integer division.
+static __constant__ uint32_t kRecip16[33] = {
+    0u,     65536u, 32768u, 21846u, 16384u, 13108u, 10923u, 9363u, 8192u, 7282u, 6554u,
+    5958u,  5462u,  5042u,  4682u,  4370u,  4096u,  3856u,  3641u, 3450u, 3277u, 3121u,
+    2979u,  2850u,  2731u,  2622u,  2521u,  2428u,  2341u,  2260u, 2185u, 2115u, 2048u};
+
 // Pack the 128 gaps of one block (4 per lane, slot 4*lane + j at bits [slot*b, slot*b + b)) into
-// 4*b words staged in row (129+ words of shared memory), then return lane's 4 output words
-// (meaningful for lane < b).  All 32 lanes must call it.
-__device__ __forceinline__ uint4 pack_block(const uint32_t g[4], uint32_t b, uint32_t *row, uint32_t lane)
+// its 4*b payload words.  Lane L returns words L, L+32, L+64, L+96 in w[0..3] (those below 4*b are
+// meaningful).  For b <= 16 each lane first forms its 4*b-bit segment; while segments are shorter
+// than a word, pairs of neighbouring segments are merged by shuffles (after k merges the segment of
+// lane 2^k * i covers S = 4*b*2^k bits, 32 <= S < 64), so that each output word overlaps at most two
+// segments and takes three shuffles.  Wider blocks OR the slots into a shared-memory row (129+
+// words).  All 32 lanes must call it.
+__device__ __forceinline__ void pack_block_words(const uint32_t g[4], uint32_t b, uint32_t *row, uint32_t lane,
+                                                 uint32_t w[4])
 {
+    w[0] = w[1] = w[2] = w[3] = 0u;
+    if (b == 0u) return;  // no payload words
+    if (b <= 16u) {
+        uint32_t lo = g[0] | (g[1] << b), hi = 0u;  // 2b <= 32: slot 1 never spills
+        const uint32_t s2 = 2u * b, s3 = 3u * b;
+        if (s2 < 32u) {
+            lo |= g[2] << s2;
+            hi |= __funnelshift_l(g[2], 0u, s2);
+        } else {
+            hi |= g[2] << (s2 - 32u);
+        }
+        if (s3 < 32u) {
+            lo |= g[3] << s3;
+            hi |= __funnelshift_l(g[3], 0u, s3);
+        } else {
+            hi |= g[3] << (s3 - 32u);
+        }
+        uint32_t S = 4u * b, k = 0;
+        while (S < 32u) {  // segments here fit in S < 32 bits, so hi is still 0
+            const uint32_t p = __shfl_down_sync(0xffffffffu, lo, 1u << k);
+            hi = __funnelshift_l(p, 0u, S);
+            lo |= p << S;
+            S <<= 1;
+            k++;
+        }
+        const uint32_t m = kRecip16[b];
+        const uint32_t nw = b <= 8u ? 1u : 2u;
+        for (uint32_t i = 0; i < nw; i++) {
+            const uint32_t word = lane + 32u * i;
+            const uint32_t first = ((8u * word * m) >> 16) >> k;  // segment holding the word's first bit
+            const uint32_t sL = __shfl_sync(0xffffffffu, lo, min(first << k, 31u));
+            const uint32_t sH = __shfl_sync(0xffffffffu, hi, min(first << k, 31u));
+            const uint32_t nL = __shfl_sync(0xffffffffu, lo, min((first + 1u) << k, 31u));
+            const uint32_t r = 32u * word - first * S;  // bit of that segment where the word starts
+            uint32_t v = r < 32u ? __funnelshift_r(sL, sH, r) : (sH >> (r - 32u));
+            if (S - r < 32u) v |= nL << (S - r);
+            if (word < 4u * b) w[i] = v;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < 4; j++) row[4 * lane + j] = 0u;
     if (lane == 0) row[128] = 0u;
@@ -173,46 +233,120 @@ __device__ __forceinline__ uint4 pack_block(const uint32_t g[4], uint32_t b, uin
         if (sh + b > 32u) atomicOr(&row[w0 + 1], g[j] >> (32u - sh));
     }
     __syncwarp();
+#pragma unroll
+    for (uint32_t i = 0; i < 4; i++) w[i] = row[lane + 32u * i];
+    __syncwarp();
+}
+
+// Store the words of pack_block_words at dst (the block's payload, 16-byte aligned), keeping only
+// those below `limit` bytes of dst's buffer position `pos0` (speculative writes stop at the bound).
+__device__ __forceinline__ void store_block_words(uint8_t *dst, const uint32_t w[4], uint32_t b, uint32_t lane,
+                                                  uint64_t pos0, uint64_t limit)
+{
+    const uint64_t room = limit > pos0 ? limit - pos0 : 0ull;
+    const uint32_t room32 = room > 0xffffffffull ? 0xffffffffu : (uint32_t)room;
+    const uint32_t nwords = min(4u * b, room32 >> 2);
+#pragma unroll
+    for (uint32_t i = 0; i < 4; i++) {
+        const uint32_t word = lane + 32u * i;
+        if (word < nwords) reinterpret_cast<uint32_t *>(dst)[word] = w[i];
+    }
+}
+
+// Pack the 128 gaps of one block into 4*b words staged in row, then return lane's 4 consecutive
+// output words as one 128-bit value (meaningful for lane < b).  All 32 lanes must call it.
+__device__ __forceinline__ uint4 pack_block(const uint32_t g[4], uint32_t b, uint32_t *row, uint32_t lane)
+{
+    uint32_t w[4];
+    pack_block_words(g, b, row, lane, w);
+    __syncwarp();
+#pragma unroll
+    for (uint32_t i = 0; i < 4; i++) row[lane + 32u * i] = w[i];
+    __syncwarp();
     uint4 q = make_uint4(0u, 0u, 0u, 0u);
     if (lane < b) q = make_uint4(row[4 * lane], row[4 * lane + 1], row[4 * lane + 2], row[4 * lane + 3]);
     __syncwarp();
     return q;
 }
 
-// Unpack one block of width b whose payload words start at pk (readable one word past the block),
+// Unpack a FULL block (all 128 slots hold ids) of width 0 <= b <= 16 with 32-bit arithmetic only:
+// a lane's four slots are the 4*b bits at 4*lane*b, read as a funnel-shifted 64-bit window of
+// three staged words; a 32-bit warp scan of the slot increments (a block's increments sum to at
+// most 128 * 2^16) gives the ids.  The only checks a full block needs: slot 0 holds 0, and the
+// last id does not pass 2^32 - 1 (lane 31 tests it in 64 bits).  Returns false if either fails.
+__device__ __forceinline__ bool unpack_full_narrow(const uint32_t *pk, uint32_t b, uint32_t base, uint32_t lane,
+                                                   uint32_t out[4], uint32_t *last)
+{
+    const uint32_t bit0 = 4u * lane * b, ws = bit0 >> 5, sh = bit0 & 31u;
+    const uint32_t w0 = pk[ws], w1 = pk[ws + 1], w2 = pk[ws + 2];
+    const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+    const uint32_t mask = (1u << b) - 1u;
+    uint32_t g[4];
+    g[0] = lo & mask;
+    g[1] = __funnelshift_r(lo, hi, b) & mask;  // b < 32
+    const uint32_t s2 = 2u * b, s3 = 3u * b;
+    g[2] = (s2 < 32u ? __funnelshift_r(lo, hi, s2) : (hi >> (s2 - 32u))) & mask;
+    g[3] = (s3 < 32u ? __funnelshift_r(lo, hi, s3) : (hi >> (s3 - 32u))) & mask;
+    const uint32_t first = (lane == 0) ? 0u : g[0] + 1u;  // slot 0 of the block is the base itself
+    const uint32_t lsum = first + g[1] + g[2] + g[3] + 3u;
+    const uint32_t excl = warp_incl_scan(lsum) - lsum;
+    uint32_t v = base + excl + first;
+    out[0] = v;
+    v += g[1] + 1u;
+    out[1] = v;
+    v += g[2] + 1u;
+    out[2] = v;
+    v += g[3] + 1u;
+    out[3] = v;
+    *last = v;
+    bool ok = !(lane == 0 && g[0] != 0u);
+    if (lane == 31) ok = ok && ((unsigned long long)base + excl + lsum <= 0xffffffffull);
+    return ok;
+}
+
+// Unpack one block of width b whose payload words start at pk (readable two words past the block),
 // base = the block's first id.  Writes lane's four ids to out[] and returns false if the block is
 // inconsistent (non-zero slot 0 or padding slot, u32 overflow); `last` receives lane's last value.
 __device__ __forceinline__ bool unpack_block(const uint32_t *pk, uint32_t b, uint64_t base, uint64_t k, uint64_t n,
                                              uint32_t lane, uint32_t out[4], unsigned long long *last)
 {
     const uint32_t mask = (b == 32u) ? 0xffffffffu : ((1u << b) - 1u);
-    unsigned long long inc[4];
-    unsigned long long lsum = 0;
-    bool bad = false;
+    uint32_t g[4];
+    if (b <= 16u) {  // the lane's four slots lie in one 3-word window
+        const uint32_t bit0 = 4u * lane * b, ws = bit0 >> 5, sh = bit0 & 31u;
+        const unsigned long long x = ((unsigned long long)pk[ws + 1] << 32) | pk[ws];
+        unsigned long long seg = x >> sh;
+        if (sh) seg |= (unsigned long long)pk[ws + 2] << (64u - sh);
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const uint32_t slot = 4u * lane + j;
-        uint32_t g = 0;
-        if (b) {
-            const uint32_t pos = slot * b, w0 = pos >> 5, sh = pos & 31u;
-            const uint64_t two = ((uint64_t)pk[w0 + 1] << 32) | pk[w0];
-            g = (uint32_t)(two >> sh) & mask;
+        for (int j = 0; j < 4; j++) g[j] = b ? (uint32_t)(seg >> (j * b)) & mask : 0u;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t pos = (4u * lane + j) * b, w0 = pos >> 5, sh = pos & 31u;
+            const unsigned long long two = ((unsigned long long)pk[w0 + 1] << 32) | pk[w0];
+            g[j] = (uint32_t)(two >> sh) & mask;
         }
-        const uint64_t idx = k * kBlock + slot;
-        if (slot == 0 || idx >= n) {
-            if (g) bad = true;
-            inc[j] = 0;
-        } else {
-            inc[j] = (unsigned long long)g + 1ull;
-        }
-        lsum += inc[j];
     }
-    const unsigned long long excl = warp_incl_scan64(lsum) - lsum;
-    unsigned long long v = base + excl;
     const uint64_t i0 = k * kBlock + 4u * lane;
+    bool bad = false;
+    unsigned long long lsum64 = 0;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        v += inc[j];
+        const bool pad = (lane == 0 && j == 0) || i0 + j >= n;
+        if (pad && g[j]) bad = true;
+        lsum64 += pad ? 0ull : (unsigned long long)g[j] + 1ull;
+    }
+    unsigned long long v;
+    if (b <= 16u) {  // every prefix of a block fits in 32 bits: 128 * 2^16
+        const uint32_t lsum = (uint32_t)lsum64;
+        const uint32_t excl = warp_incl_scan(lsum) - lsum;
+        v = base + excl;
+    } else {
+        v = base + (warp_incl_scan64(lsum64) - lsum64);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        v += (i0 + j >= n || (lane == 0 && j == 0)) ? 0ull : (unsigned long long)g[j] + 1ull;
         out[j] = (uint32_t)v;
         if (i0 + j < n && v > 0xffffffffull) bad = true;
     }
