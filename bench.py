@@ -269,12 +269,15 @@ def run_fqbfs(args, world, rank, local):
     g = fqbfs.Graph(off, cols)
     depth = torch.empty(n, dtype=torch.int32, device=dev)
     parent = torch.empty(n, dtype=torch.int32, device=dev)
-    flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_TIMING
+    # timed: the device-driven level loop (one graph launch per search, no host round trip per
+    # level); profiled: the same roots through the host-driven loop with per-class event timing
+    flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP
+    prof_flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_TIMING
     my_roots = shard_roots(roots, world, rank, args.warmup + args.steps)
     stream = torch.cuda.current_stream()
 
     for r in my_roots[: args.warmup]:
-        g.bfs(r, depth=depth, parent=parent, flags=flags)
+        g.bfs(r, depth=depth, parent=parent, flags=flags, max_levels=64)
     torch.cuda.synchronize()
 
     kms = {k: 0.0 for k in fqbfs.KCLASS}
@@ -290,15 +293,13 @@ def run_fqbfs(args, world, rank, local):
         stop = torch.cuda.Event(enable_timing=True)
         start.record(stream)
         for r in my_roots[args.warmup:]:
-            res = g.bfs(r, depth=depth, parent=parent, flags=flags)
+            res = g.bfs(r, depth=depth, parent=parent, flags=flags, max_levels=64)
             s = res.stats
             edges += s["reached_edges"]
             qraw += s["raw_queue_bytes"]; qenc += s["enc_queue_bytes"]
             braw += s["raw_bitmap_bytes"]; benc += s["enc_bitmap_bytes"]; venc += s["enc_visited_bytes"]
             levels.append(s["levels"])
             for k in fqbfs.KCLASS:
-                kms[k] += s["kernel_ms"][k]
-                kbytes[k] += s["kernel_bytes"][k]
                 klaunch[k] += s["kernel_launches"][k]
         stop.record(stream)
         torch.cuda.synchronize()
@@ -309,12 +310,27 @@ def run_fqbfs(args, world, rank, local):
     edges_all = sum_over_ranks(float(edges), world)
     value = edges_all / (t_max / 1e3) / 1e9
 
+    # per-class kernel time of the same searches (host-driven loop, events around each class)
+    prof_klaunch = {k: 0 for k in fqbfs.KCLASS}
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for r in my_roots[args.warmup:]:
+        s = g.bfs(r, depth=depth, parent=parent, flags=prof_flags, max_levels=64).stats
+        for k in fqbfs.KCLASS:
+            kms[k] += s["kernel_ms"][k]
+            kbytes[k] += s["kernel_bytes"][k]
+            prof_klaunch[k] += s["kernel_launches"][k]
+    p1.record(stream)
+    torch.cuda.synchronize()
+    host_loop_ms = p0.elapsed_time(p1)
+
     # dominant kernel class and its roofline (algorithmic bytes / event-timed duration)
     peaks, peak_kind = measured_peaks()
     dom = max(("top_down", "bottom_up", "compact", "encode", "decode"), key=lambda k: kms[k])
     achieved = kbytes[dom] / (kms[dom] / 1e3) / 1e9 if kms[dom] > 0 else 0.0
     traffic = kernel_traffic(dom)
-    launches = klaunch[dom]
+    launches = prof_klaunch[dom]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": dom, "peak_source": peak_kind,
@@ -355,6 +371,8 @@ def run_fqbfs(args, world, rank, local):
                            "edgefactor": args.edgefactor, "vertices": n, "directed_edges": int(cols.numel()),
                            "roots_per_rank": args.steps, "streams": "Q_d, B_d, V_d encoded every level",
                            "l2": "no flush: the 2.2 GB CSR exceeds L2", "levels_mean": statistics.mean(levels),
+                           "level_loop": "device (one CUDA graph per search)",
+                           "host_loop_ms_per_step": host_loop_ms / args.steps,
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "codec": codec, "batched": batched, "serving": served,
                 "cpu_baseline": cpu, "e2e": e2e,
@@ -640,9 +658,12 @@ def run_e2e(args, off, cols, roots, world):
     off_d = off_h.to(dev, non_blocking=True)
     cols_d = cols_h.to(dev, non_blocking=True)
     g = fqbfs.Graph(off_d, cols_d)
+    depth_d = torch.empty(n, dtype=torch.int32, device=dev)
+    parent_d = torch.empty(n, dtype=torch.int32, device=dev)
     edges = 0
     for r in roots:
-        res = g.bfs(r, flags=fqbfs.FQ_BFS_VISITED_STREAM)
+        res = g.bfs(r, depth=depth_d, parent=parent_d, flags=fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP,
+                    max_levels=64)
         depth_h.copy_(res.depth, non_blocking=True)
         parent_h.copy_(res.parent, non_blocking=True)
         edges += res.stats["reached_edges"]

@@ -197,6 +197,14 @@ fq_status fq_graph_destroy(fq_graph *g);
 #define FQ_BFS_TIMING 0x8u         /* time every kernel class with CUDA events (fills stats)    */
 #define FQ_BFS_NO_CODEC 0x10u      /* skip the codec stage: expand the raw queue/bitmap (the plain
                                       BFS the codec stage is measured against; no streams)      */
+#define FQ_BFS_DEVICE_LOOP 0x20u   /* run the level loop on the device: one CUDA graph (built on
+                                      the first call per handle, output buffers and stream-log
+                                      buffer, then reused) whose while node repeats the level and
+                                      whose if/else nodes pick the encode form and the direction,
+                                      so no level waits on the host.  Same results, records and
+                                      streams as the host-driven loop; FQ_BFS_TIMING is ignored
+                                      (kernel_ms stay 0).  Needs a driver with conditional graph
+                                      nodes (CUDA 12.4 or later).                                */
 
 typedef struct fq_bfs_opts {
     uint32_t alpha; /* top-down -> bottom-up when m_f * alpha > m_u   (0 selects 14) */
@@ -250,7 +258,9 @@ typedef struct fq_level_record {
  * h_stats (may be NULL) and h_levels[0..max_levels) (may be NULL) receive the per-run and
  * per-level records.  If d_stream_log is not NULL every level's Q_d, B_d [, V_d] are copied
  * there back to back (fails with FQ_ENOSPC when stream_log_cap is exceeded).
- * Synchronous (the level loop reads two counters per level).  Not thread-safe per handle. */
+ * Synchronous.  The host-driven loop reads one counter record per level; with
+ * FQ_BFS_DEVICE_LOOP the host only starts the graph and reads the records at the end.  At most
+ * 4096 level records are kept in device-loop mode.  Not thread-safe per handle. */
 fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_parent, const fq_bfs_opts *opts,
                      fq_bfs_stats *h_stats, fq_level_record *h_levels, uint32_t max_levels, uint8_t *d_stream_log,
                      uint64_t stream_log_cap, void *stream);

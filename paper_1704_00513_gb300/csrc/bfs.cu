@@ -55,6 +55,23 @@ struct Counters {
 };
 static_assert(sizeof(Counters) == 256, "counter block is 256 bytes");
 
+// State of the device-driven level loop (FQ_BFS_DEVICE_LOOP).  The host writes the parameters
+// before each run; loop_init_kernel sets the rest; loop_end_kernel advances it once per level.
+struct LoopParams {
+    uint32_t root, alpha, beta, flags;
+    uint32_t max_levels, pad;
+    unsigned long long log_cap;
+};
+struct LoopState {
+    LoopParams p;
+    unsigned long long n_f, m_f, m_u, visited;  // the level about to run
+    unsigned long long log_used;
+    uint32_t d, dir;
+    int32_t status, soft_status;  // a hard error stops the loop; ENOSPC of the log does not
+    fq_bfs_stats stats;
+};
+constexpr uint32_t kMaxDeviceRecords = 4096;
+
 // Top-down visit of edge (src, w): the thread whose atomicOr sets w's bit in the next-frontier
 // bitmap discovers w, writes depth and parent, and returns deg(w) for the next level's m_f.
 __device__ __forceinline__ unsigned long long td_visit(uint32_t w, uint32_t src, const uint32_t *__restrict__ visited32,
@@ -74,8 +91,9 @@ __device__ __forceinline__ unsigned long long td_visit(uint32_t w, uint32_t src,
 // Level 0: the root, V_0's single position, cleared codec scratch.
 __global__ void bfs_init_kernel(const int64_t *off, uint32_t root, uint64_t n, int32_t *depth, uint32_t *parent,
                                 uint32_t *q, uint64_t *fbits, uint64_t *visited, uint32_t *vis_cnt, Counters *ctr,
-                                Scratch sq, Scratch sv)
+                                Scratch sq, Scratch sv, const LoopState *ls)
 {
+    if (ls) root = ls->p.root;  // device-driven loop: the root is a run parameter
     reset_scratch_device(sq, 1, threadIdx.x, blockDim.x);
     reset_scratch_device(sv, 1, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -127,8 +145,12 @@ __global__ void __launch_bounds__(kThreads) td_expand_kernel(const uint32_t *__r
                                                              int32_t *depth, uint32_t *parent, int32_t newdepth,
                                                              HubItem *items, unsigned long long *nitems,
                                                              unsigned long long items_cap, uint64_t n, Ctl *err,
-                                                             unsigned long long *m_f_next)
+                                                             unsigned long long *m_f_next, const LoopState *ls)
 {
+    if (ls) {  // device-driven loop: the level's size and depth come from the loop state
+        nf = ls->n_f;
+        newdepth = (int32_t)ls->d + 1;
+    }
     const uint32_t lane = threadIdx.x & 31u;
     unsigned long long degsum = 0;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -187,8 +209,10 @@ __global__ void __launch_bounds__(kThreads) td_hub_kernel(const HubItem *__restr
                                                           const uint32_t *__restrict__ cols,
                                                           const uint32_t *__restrict__ visited32, uint32_t *next32,
                                                           int32_t *depth, uint32_t *parent, int32_t newdepth,
-                                                          const int64_t *__restrict__ off, unsigned long long *m_f_next)
+                                                          const int64_t *__restrict__ off, unsigned long long *m_f_next,
+                                                          const LoopState *ls)
 {
+    if (ls) newdepth = (int32_t)ls->d + 1;
     const unsigned long long total = min(*nitems, items_cap);
     unsigned long long degsum = 0;
     for (unsigned long long it = blockIdx.x; it < total; it += gridDim.x) {
@@ -212,8 +236,10 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_kernel(const uint32_t *__re
                                                             const int64_t *__restrict__ off,
                                                             const uint32_t *__restrict__ cols, int32_t *depth,
                                                             uint32_t *parent, int32_t newdepth, uint64_t n,
-                                                            unsigned long long *examined, unsigned long long *m_f_next)
+                                                            unsigned long long *examined, unsigned long long *m_f_next,
+                                                            const LoopState *ls)
 {
+    if (ls) newdepth = (int32_t)ls->d + 1;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -417,6 +443,160 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
     }
 }
 
+// ---- the device-driven level loop (FQ_BFS_DEVICE_LOOP) ----
+// The same level as the host-driven loop, with the host's per-level decisions taken by two
+// one-thread kernels: loop_begin_kernel before the level (encode form, direction) and
+// loop_end_kernel after it (records, statistics, termination), which set the graph's
+// conditional handles.
+
+__global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m)
+{
+    ls->n_f = ctr->n_f_next;
+    ls->m_f = ctr->r_m_f;
+    ls->visited = ls->n_f;
+    ls->m_u = m - ls->m_f;
+    ls->log_used = 0;
+    ls->d = 0;
+    ls->dir = FQ_TOP_DOWN;
+    ls->status = FQ_OK;
+    ls->soft_status = FQ_OK;
+    memset(&ls->stats, 0, sizeof(ls->stats));
+    ls->stats.kernel_launches[FQ_K_OTHER] = 2;  // bfs_init_kernel, loop_init_kernel
+}
+
+// Direction rule of the host loop: m_f*alpha > m_u  <=>  m_f > floor(m_u/alpha), and
+// n_f*beta < n  <=>  n_f < ceil(n/beta), so no product can overflow.
+__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int has_dense, cudaGraphConditionalHandle h_dense,
+                                  cudaGraphConditionalHandle h_dir)
+{
+    const uint32_t flags = ls->p.flags;
+    const unsigned long long alpha = ls->p.alpha, beta = ls->p.beta;
+    uint32_t dir = ls->dir;
+    if (flags & FQ_BFS_FORCE_TOP_DOWN) dir = FQ_TOP_DOWN;
+    else if (flags & FQ_BFS_FORCE_BOTTOM_UP) dir = FQ_BOTTOM_UP;
+    else if (dir == FQ_TOP_DOWN && ls->m_f > ls->m_u / alpha) dir = FQ_BOTTOM_UP;
+    else if (dir == FQ_BOTTOM_UP && ls->n_f < (n + beta - 1) / beta) dir = FQ_TOP_DOWN;
+    ls->dir = dir;
+    if (has_dense) cudaGraphSetConditional(h_dense, 2ull * ls->n_f > n ? 1u : 0u);
+    cudaGraphSetConditional(h_dir, dir == FQ_TOP_DOWN ? 1u : 0u);
+}
+
+// Appends the level's Q_d, B_d [, V_d] to the stream log when they fit (the test loop_end_kernel
+// repeats to advance the log).
+__global__ void log_append_kernel(const LoopState *ls, const Counters *ctr, const uint8_t *qs, const uint8_t *bs,
+                                  const uint8_t *vs, uint8_t *log, int want_v)
+{
+    const unsigned long long qb = ctr->q_bytes, bb = ctr->b_bytes, vb = want_v ? ctr->v_bytes : 0ull;
+    const unsigned long long used = ls->log_used;
+    if (used + qb + bb + vb > ls->p.log_cap) return;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint8_t *src[3] = {qs, bs, vs};
+    const unsigned long long len[3] = {qb, bb, vb};
+    unsigned long long at = used;
+    for (int k = 0; k < 3; k++) {
+        uint8_t *dst = log + at;
+        const bool vec = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src[k]) | len[k]) & 15u) == 0;
+        if (vec) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src[k]);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (uint64_t i = tid; i < len[k] / 16; i += stride) d4[i] = s4[i];
+        } else {
+            for (uint64_t i = tid; i < len[k]; i += stride) dst[i] = src[k][i];
+        }
+        at += len[k];
+    }
+}
+
+__global__ void loop_end_kernel(LoopState *ls, const Counters *ctr, fq_level_record *recs, uint64_t n, int codec,
+                                int want_v, int has_log, cudaGraphConditionalHandle h_while)
+{
+    uint32_t go = 0;
+    const uint32_t d = ls->d, dir = ls->dir;
+    const unsigned long long n_f = ls->n_f, m_f = ls->m_f;
+    fq_bfs_stats &st = ls->stats;
+    if (ctr->r_err_q != FQ_OK) ls->status = ctr->r_err_q;
+    else if (ctr->r_err_v != FQ_OK) ls->status = ctr->r_err_v;
+    else if (codec && dir == FQ_TOP_DOWN && ctr->dec_n != n_f) ls->status = FQ_ECORRUPT;
+    if (ls->status != FQ_OK) {
+        cudaGraphSetConditional(h_while, 0u);
+        return;
+    }
+    const unsigned long long examined = dir == FQ_TOP_DOWN ? m_f : ctr->r_examined;
+    const unsigned long long nf_next = ctr->n_f_next, mf_next = ctr->r_m_f;
+    const unsigned long long qb = codec ? ctr->q_bytes : 0, bb = codec ? ctr->b_bytes : 0;
+    const unsigned long long vb = want_v ? ctr->v_bytes : 0;
+    const unsigned long long nbytes = (n + 7) / 8;
+    const bool dense = 2ull * n_f > n;
+
+    if (codec) {
+        st.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + nbytes + bb + (want_v ? nbytes + vb : 0);
+        st.kernel_launches[FQ_K_ENCODE] += (dense ? 8 : 2) + (want_v ? 2 : 0);
+    }
+    if (dir == FQ_TOP_DOWN) {
+        if (codec) {
+            st.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
+            st.kernel_launches[FQ_K_DECODE] += 3;
+        }
+        st.kernel_bytes[FQ_K_TOP_DOWN] += 4 * examined + 20 * n_f + 8 * nf_next;
+        st.kernel_launches[FQ_K_TOP_DOWN] += 2;
+    } else {
+        if (codec) {
+            st.kernel_bytes[FQ_K_DECODE] += bb + nbytes;
+            st.kernel_launches[FQ_K_DECODE] += 4;
+        }
+        st.kernel_bytes[FQ_K_BOTTOM_UP] += 3 * nbytes + 16 * (n - ls->visited) + 4 * examined + 8 * nf_next;
+        st.kernel_launches[FQ_K_BOTTOM_UP] += 1;
+    }
+    st.kernel_bytes[FQ_K_COMPACT] += 3 * nbytes + 20 * nf_next;
+    st.kernel_launches[FQ_K_COMPACT] += 3;
+    st.kernel_launches[FQ_K_OTHER] += 2 + (has_log ? 1 : 0);  // loop_begin, loop_end [, log_append]
+
+    unsigned long long log_off = ~0ull;
+    if (has_log && codec) {
+        const unsigned long long need = qb + bb + vb;
+        if (ls->log_used + need > ls->p.log_cap) {
+            ls->soft_status = FQ_ENOSPC;
+        } else {
+            log_off = ls->log_used;
+            ls->log_used += need;
+        }
+    }
+    if (d < ls->p.max_levels) {
+        fq_level_record &r = recs[d];
+        r.level = d;
+        r.direction = dir;
+        r.n_f = n_f;
+        r.m_f = m_f;
+        r.m_u = ls->m_u;
+        r.examined = examined;
+        r.q_bytes = qb;
+        r.b_bytes = bb;
+        r.v_bytes = vb;
+        r.log_offset = log_off;
+    }
+    st.levels = d + 1;
+    if (dir == FQ_BOTTOM_UP && d < 32) st.directions |= 1u << d;
+    st.reached += n_f;
+    st.reached_edges += m_f;
+    st.edges_examined += examined;
+    st.raw_queue_bytes += 4 * n_f;
+    st.enc_queue_bytes += qb;
+    st.raw_bitmap_bytes += nbytes;
+    st.enc_bitmap_bytes += bb;
+    st.enc_visited_bytes += vb;
+
+    if (nf_next != 0) {
+        ls->n_f = nf_next;
+        ls->m_f = mf_next;
+        ls->visited += nf_next;
+        ls->m_u -= mf_next;
+        ls->d = d + 1;
+        if ((uint64_t)d + 1 >= n || ls->visited > n) ls->status = FQ_ECORRUPT;  // at most n levels, n vertices
+        else go = 1;
+    }
+    cudaGraphSetConditional(h_while, go);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ graph handle
@@ -438,13 +618,24 @@ struct fq_graph {
     uint64_t items_cap;
     uint32_t *tile_cnt, *tile_off, *vis_cnt, *vtile_off;
     uint64_t cmp_tiles;
-    uint8_t *host;  // pinned copy of Counters
+    uint8_t *host;  // pinned: Counters copy, then LoopState and level records (device-driven loop)
     cudaEvent_t ev[2 * FQ_NUM_KCLASS];
+    // device-driven level loop: state, records and the cached executable graph with its key
+    LoopState *ls;
+    fq_level_record *recs;
+    cudaGraph_t dl_graph;
+    cudaGraphExec_t dl_exec;
+    cudaStream_t dl_stream;
+    const int32_t *dl_depth;
+    const uint32_t *dl_parent;
+    const uint8_t *dl_log;
+    uint32_t dl_mode;
 };
 
 namespace {
 
 uint64_t al256(uint64_t x) { return (x + 255u) / 256u * 256u; }
+constexpr uint64_t kHostLs = 256;  // offset of the LoopState copy in the pinned host block
 
 struct Timer {
     fq_graph *g;
@@ -468,6 +659,308 @@ struct Timer {
         if (cudaEventElapsedTime(&t, g->ev[2 * k], g->ev[2 * k + 1]) == cudaSuccess) ms[k] += t;
     }
 };
+
+#define FQ_CU(expr)                                   \
+    do {                                              \
+        const cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) {                      \
+            note_cuda_error(_e, __LINE__);            \
+            return _e;                                \
+        }                                             \
+    } while (0)
+
+// The steps of one level, shared by the host-driven loop (sizes from the host, ls == nullptr)
+// and the device-driven one (sizes from the loop state: ls != nullptr, grids sized for the
+// largest case).
+
+// Level 0: cleared outputs and bitmaps, the root, V_0.
+cudaError_t step_init(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_parent, const LoopState *ls,
+                      cudaStream_t st)
+{
+    const uint64_t n = g->n, nwords = g->nwords;
+    FQ_CU(cudaMemsetAsync(d_depth, 0xff, 4 * n, st));
+    if (d_parent) FQ_CU(cudaMemsetAsync(d_parent, 0xff, 4 * n, st));
+    FQ_CU(cudaMemsetAsync(g->fbits, 0, 8 * (nwords + 2), st));
+    FQ_CU(cudaMemsetAsync(g->next, 0, 8 * (nwords + 2), st));
+    FQ_CU(cudaMemsetAsync(g->visited, 0, 8 * (nwords + 2), st));
+    FQ_CU(cudaMemsetAsync(g->vis_cnt, 0, 4 * g->cmp_tiles, st));
+    FQ_CU(cudaMemsetAsync(g->ctr, 0, sizeof(Counters), st));
+    bfs_init_kernel<<<1, 256, 0, st>>>(g->off, root, n, d_depth, d_parent, g->q, g->fbits, g->visited, g->vis_cnt,
+                                       g->ctr, g->sq, g->sv, ls);
+    return cudaGetLastError();
+}
+
+// Step 1: Q_d, and B_d (mirrored from the queue when 2 n_f <= n, else from the bitmap).
+cudaError_t step_encode_q(fq_graph *g, bool dense, uint64_t n_f, const LoopState *ls, cudaStream_t st)
+{
+    const uint64_t n = g->n;
+    const uint64_t *n_dev = ls ? reinterpret_cast<const uint64_t *>(&ls->n_f) : nullptr;
+    const uint64_t n_max = ls ? n : n_f;
+    uint64_t *q_bytes = reinterpret_cast<uint64_t *>(&g->ctr->q_bytes);
+    uint64_t *b_bytes = reinterpret_cast<uint64_t *>(&g->ctr->b_bytes);
+    if (!dense) {
+        Mirror mb;
+        mb.out = g->bs;
+        mb.cap = g->bs_cap;
+        mb.out_bytes = b_bytes;
+        mb.words = g->fbits;
+        mb.nbits = n;
+        FQ_CU(encode_fq_mirror(g->q, n_f, n_dev, n_max, g->qs, g->qs_cap, q_bytes, mb, g->sq, st));
+    } else {  // a frontier denser than half the vertices: its bitmap codes the clear positions
+        FQ_CU(encode_fq(g->q, n_f, n_dev, n_max, g->qs, g->qs_cap, q_bytes, g->sq, st));
+        FQ_CU(reset_status(g->sq, n / 2 + 1, st));
+        FQ_CU(encode_fb(g->fbits, n, g->bs, g->bs_cap, b_bytes, g->sq, st));
+    }
+    return cudaSuccess;
+}
+
+// Step 1 (V_d): the visited bitmap's positions, extracted by the previous compaction.
+cudaError_t step_encode_v(fq_graph *g, cudaStream_t st)
+{
+    return encode_fb_positions(g->visited, g->n, g->vs, g->bs_cap, reinterpret_cast<uint64_t *>(&g->ctr->v_bytes),
+                               g->sv, st);
+}
+
+// Step 3, top-down: decode Q_d.
+cudaError_t step_decode_q(fq_graph *g, uint64_t n_f, const LoopState *ls, cudaStream_t st)
+{
+    return decode_fq(g->qs, 0, reinterpret_cast<const uint64_t *>(&g->ctr->q_bytes), g->q2, ls ? g->n : n_f,
+                     reinterpret_cast<uint64_t *>(&g->ctr->dec_n), g->sq, st);
+}
+
+// Step 4, top-down: expand the (decoded) queue.
+cudaError_t step_top_down(fq_graph *g, bool codec, uint64_t n_f, int32_t newdepth, int32_t *d_depth,
+                          uint32_t *d_parent, const LoopState *ls, cudaStream_t st)
+{
+    const int sms = num_sms();
+    const uint32_t *qin = codec ? g->q2 : g->q;
+    const uint32_t grid =
+        ls ? (uint32_t)sms * 8 : (uint32_t)std::min<uint64_t>(cdiv(std::max<uint64_t>(n_f, 1), kThreads), (uint64_t)sms * 8);
+    uint32_t *next32 = reinterpret_cast<uint32_t *>(g->next);
+    const uint32_t *vis32 = reinterpret_cast<const uint32_t *>(g->visited);
+    td_expand_kernel<<<grid, kThreads, 0, st>>>(qin, n_f, g->off, g->cols, vis32, next32, d_depth, d_parent, newdepth,
+                                                g->items, &g->ctr->hub_items, g->items_cap, g->n, g->sq.ctl,
+                                                &g->ctr->m_f_next, ls);
+    td_hub_kernel<<<sms * 4, kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32, next32,
+                                                d_depth, d_parent, newdepth, g->off, &g->ctr->m_f_next, ls);
+    return cudaGetLastError();
+}
+
+// Step 3, bottom-up: decode B_d.
+cudaError_t step_decode_b(fq_graph *g, cudaStream_t st)
+{
+    return decode_fb(g->bs, 0, reinterpret_cast<const uint64_t *>(&g->ctr->b_bytes), g->fbits2, g->n, g->sq, st);
+}
+
+// Step 4, bottom-up: sweep the unvisited vertices against the (decoded) frontier bitmap.
+cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d_depth, uint32_t *d_parent,
+                           const LoopState *ls, cudaStream_t st)
+{
+    const int sms = num_sms();
+    const uint64_t *fin = codec ? g->fbits2 : g->fbits;
+    const uint64_t words32 = cdiv(g->n, 32);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16);
+    bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
+        reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
+        reinterpret_cast<uint32_t *>(g->next), g->off, g->cols, d_depth, d_parent, newdepth, g->n, &g->ctr->examined,
+        &g->ctr->m_f_next, ls);
+    return cudaGetLastError();
+}
+
+// Step 5: compaction (+ V_{d+1} positions, cleared scratch for the next level).
+cudaError_t step_compact(fq_graph *g, cudaStream_t st)
+{
+    const uint32_t ct = (uint32_t)g->cmp_tiles;
+    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt);
+    cmp_scan_kernel<<<1, kScanThreads, 0, st>>>(g->tile_cnt, g->tile_off, g->vis_cnt, g->vtile_off, g->cmp_tiles, g->n,
+                                                g->ctr, g->sq, g->sv);
+    cmp_extract_kernel<<<ct, kThreads, 0, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
+                                                g->vtile_off, g->q, g->sv);
+    return cudaGetLastError();
+}
+
+cudaError_t capture_segment(cudaStream_t cs, cudaGraph_t *out, cudaError_t (*fn)(void *), void *ctx)
+{
+    *out = nullptr;
+    FQ_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    const cudaError_t e = fn(ctx);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        note_cuda_error(e != cudaSuccess ? e : e2, __LINE__);
+        return e != cudaSuccess ? e : e2;
+    }
+    *out = gr;
+    return cudaSuccess;
+}
+
+struct LoopBuild {
+    fq_graph *g;
+    int32_t *depth;
+    uint32_t *parent;
+    uint8_t *log;
+    bool codec, want_v;
+};
+
+cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGraphNode_t *dep, void *func,
+                            void **args)
+{
+    cudaKernelNodeParams kp = {};
+    kp.func = func;
+    kp.gridDim = dim3(1, 1, 1);
+    kp.blockDim = dim3(1, 1, 1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphAddKernelNode(node, gr, dep, dep ? 1 : 0, &kp);
+}
+
+// A conditional node after `dep` in `gr` on handle h (type, size bodies); returns the bodies.
+cudaError_t add_conditional(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGraphNode_t *dep,
+                            cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, unsigned size,
+                            cudaGraph_t *bodies)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    FQ_CU(cudaGraphAddNode(node, gr, dep, nullptr, dep ? 1 : 0, &p));
+    for (unsigned i = 0; i < size; i++) bodies[i] = p.conditional.phGraph_out[i];
+    return cudaSuccess;
+}
+
+// Segments of the loop body, each captured from one stream into its own graph.
+cudaError_t seg_init(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    const cudaError_t r = step_init(c.g, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
+    if (r != cudaSuccess) return r;
+    loop_init_kernel<<<1, 1, 0, c.g->dl_stream>>>(c.g->ls, c.g->ctr, c.g->m);
+    return cudaGetLastError();
+}
+cudaError_t seg_dense(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    return step_encode_q(c.g, true, 0, c.g->ls, c.g->dl_stream);
+}
+cudaError_t seg_sparse(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    return step_encode_q(c.g, false, 0, c.g->ls, c.g->dl_stream);
+}
+cudaError_t seg_visited(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    return step_encode_v(c.g, c.g->dl_stream);
+}
+cudaError_t seg_top_down(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    if (c.codec) {
+        const cudaError_t r = step_decode_q(c.g, 0, c.g->ls, c.g->dl_stream);
+        if (r != cudaSuccess) return r;
+    }
+    return step_top_down(c.g, c.codec, 0, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
+}
+cudaError_t seg_bottom_up(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    if (c.codec) {
+        const cudaError_t r = step_decode_b(c.g, c.g->dl_stream);
+        if (r != cudaSuccess) return r;
+    }
+    return step_bottom_up(c.g, c.codec, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
+}
+cudaError_t seg_compact(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    const cudaError_t r = step_compact(c.g, c.g->dl_stream);
+    if (r != cudaSuccess || !c.log) return r;
+    log_append_kernel<<<4 * num_sms(), 256, 0, c.g->dl_stream>>>(c.g->ls, c.g->ctr, c.g->qs, c.g->bs, c.g->vs, c.log,
+                                                                 c.want_v ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Build the device-driven loop for these buffers and mode:
+//   init -> while(h_while) { begin -> [if h_dense: Q+B from bitmap | Q+B mirrored] -> [V] ->
+//                            [if h_dir: top-down | bottom-up] -> compact [-> log] -> end }
+cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
+{
+    fq_graph *g = b.g;
+    cudaStream_t cs = g->dl_stream;
+    cudaGraph_t sg_init = nullptr, sg_dense = nullptr, sg_sparse = nullptr, sg_v = nullptr, sg_td = nullptr,
+                sg_bu = nullptr, sg_cmp = nullptr, top = nullptr;
+    LoopBuild ctx = b;
+    cudaError_t e = capture_segment(cs, &sg_init, seg_init, &ctx);
+    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_dense, seg_dense, &ctx);
+    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_sparse, seg_sparse, &ctx);
+    if (e == cudaSuccess && b.want_v) e = capture_segment(cs, &sg_v, seg_visited, &ctx);
+    if (e == cudaSuccess) e = capture_segment(cs, &sg_td, seg_top_down, &ctx);
+    if (e == cudaSuccess) e = capture_segment(cs, &sg_bu, seg_bottom_up, &ctx);
+    if (e == cudaSuccess) e = capture_segment(cs, &sg_cmp, seg_compact, &ctx);
+    if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
+    if (e != cudaSuccess) goto done;
+    {
+        cudaGraphNode_t n_init, n_while, n_begin, n_last, tmp;
+        cudaGraph_t body, enc[2], dir[2];
+        cudaGraphConditionalHandle h_while, h_dense = 0, h_dir;
+        if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, sg_init)) != cudaSuccess) goto done;
+        if ((e = cudaGraphConditionalHandleCreate(&h_while, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) goto done;
+        if ((e = add_conditional(&n_while, top, &n_init, h_while, cudaGraphCondTypeWhile, 1, &body)) != cudaSuccess)
+            goto done;
+        if (b.codec && (e = cudaGraphConditionalHandleCreate(&h_dense, body, 0, 0)) != cudaSuccess) goto done;
+        if ((e = cudaGraphConditionalHandleCreate(&h_dir, body, 0, 0)) != cudaSuccess) goto done;
+        {
+            LoopState *ls = g->ls;
+            uint64_t n = g->n;
+            int has_dense = b.codec ? 1 : 0;
+            void *args[] = {&ls, &n, &has_dense, &h_dense, &h_dir};
+            if ((e = add_kernel_node(&n_begin, body, nullptr, (void *)loop_begin_kernel, args)) != cudaSuccess) goto done;
+        }
+        n_last = n_begin;
+        if (b.codec) {
+            if ((e = add_conditional(&tmp, body, &n_last, h_dense, cudaGraphCondTypeIf, 2, enc)) != cudaSuccess) goto done;
+            n_last = tmp;
+            cudaGraphNode_t c0, c1;
+            if ((e = cudaGraphAddChildGraphNode(&c0, enc[0], nullptr, 0, sg_dense)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c1, enc[1], nullptr, 0, sg_sparse)) != cudaSuccess) goto done;
+        }
+        if (b.want_v) {
+            if ((e = cudaGraphAddChildGraphNode(&tmp, body, &n_last, 1, sg_v)) != cudaSuccess) goto done;
+            n_last = tmp;
+        }
+        if ((e = add_conditional(&tmp, body, &n_last, h_dir, cudaGraphCondTypeIf, 2, dir)) != cudaSuccess) goto done;
+        n_last = tmp;
+        {
+            cudaGraphNode_t c0, c1;
+            if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, sg_td)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, sg_bu)) != cudaSuccess) goto done;
+        }
+        if ((e = cudaGraphAddChildGraphNode(&tmp, body, &n_last, 1, sg_cmp)) != cudaSuccess) goto done;
+        n_last = tmp;
+        {
+            LoopState *ls = g->ls;
+            const Counters *ctr = g->ctr;
+            fq_level_record *recs = g->recs;
+            uint64_t n = g->n;
+            int codec = b.codec ? 1 : 0, want_v = b.want_v ? 1 : 0, has_log = b.log ? 1 : 0;
+            void *args[] = {&ls, &ctr, &recs, &n, &codec, &want_v, &has_log, &h_while};
+            if ((e = add_kernel_node(&tmp, body, &n_last, (void *)loop_end_kernel, args)) != cudaSuccess) goto done;
+        }
+    }
+done:
+    for (cudaGraph_t *gp : {&sg_init, &sg_dense, &sg_sparse, &sg_v, &sg_td, &sg_bu, &sg_cmp})
+        if (*gp) cudaGraphDestroy(*gp);  // child-graph nodes hold their own copies
+    if (e != cudaSuccess) {
+        note_cuda_error(e, __LINE__);
+        if (top) cudaGraphDestroy(top);
+        return e;
+    }
+    *out = top;
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -512,12 +1005,15 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     const uint64_t o_to = o; o = al256(o + 4 * g->cmp_tiles);
     const uint64_t o_vc = o; o = al256(o + 4 * g->cmp_tiles);
     const uint64_t o_vo = o; o = al256(o + 4 * g->cmp_tiles);
+    const uint64_t o_ls = o; o = al256(o + sizeof(LoopState));
+    const uint64_t o_recs = o; o = al256(o + sizeof(fq_level_record) * kMaxDeviceRecords);
     if (cudaMalloc(&g->mem, o) != cudaSuccess) {
         cudaGetLastError();
         delete g;
         return FQ_ENOMEM;
     }
-    if (cudaMallocHost(&g->host, 512) != cudaSuccess) {
+    if (cudaMallocHost(&g->host, kHostLs + al256(sizeof(LoopState)) + sizeof(fq_level_record) * kMaxDeviceRecords) !=
+        cudaSuccess) {
         cudaGetLastError();
         cudaFree(g->mem);
         delete g;
@@ -541,6 +1037,8 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     g->tile_off = reinterpret_cast<uint32_t *>(g->mem + o_to);
     g->vis_cnt = reinterpret_cast<uint32_t *>(g->mem + o_vc);
     g->vtile_off = reinterpret_cast<uint32_t *>(g->mem + o_vo);
+    g->ls = reinterpret_cast<LoopState *>(g->mem + o_ls);
+    g->recs = reinterpret_cast<fq_level_record *>(g->mem + o_recs);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++) cudaEventCreate(&g->ev[i]);
     if (cudaMemset(g->mem, 0, o) != cudaSuccess) {
         fq_graph_destroy(g);
@@ -559,6 +1057,9 @@ fq_status fq_graph_destroy(fq_graph *g)
 {
     if (!g) return FQ_EINVAL;
     cudaDeviceSynchronize();
+    if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
+    if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
+    if (g->dl_stream) cudaStreamDestroy(g->dl_stream);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     if (g->host) cudaFreeHost(g->host);
@@ -578,14 +1079,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     const uint32_t flags = opts ? opts->flags : 0u;
     const bool codec = !(flags & FQ_BFS_NO_CODEC);
     const bool want_visited = codec && (flags & FQ_BFS_VISITED_STREAM);
-    const uint64_t n = g->n, nwords = g->nwords;
-    const int sms = num_sms();
-    uint32_t *next32 = reinterpret_cast<uint32_t *>(g->next);
-    const uint32_t *vis32 = reinterpret_cast<const uint32_t *>(g->visited);
-
-    fq_bfs_stats stats;
-    memset(&stats, 0, sizeof(stats));
-    Timer tm{g, st, (flags & FQ_BFS_TIMING) != 0, stats.kernel_ms, stats.kernel_launches};
+    const uint64_t n = g->n;
 
 #define FQ_TRY(expr)                                  \
     do {                                              \
@@ -596,18 +1090,62 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         }                                             \
     } while (0)
 
+    if (flags & FQ_BFS_DEVICE_LOOP) {
+        // the whole search is one graph launch; the host reads the records once at the end
+        const uint32_t mode = (codec ? 0u : FQ_BFS_NO_CODEC) | (want_visited ? FQ_BFS_VISITED_STREAM : 0u);
+        if (!g->dl_exec || g->dl_depth != d_depth || g->dl_parent != d_parent || g->dl_log != d_stream_log ||
+            g->dl_mode != mode) {
+            if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
+            if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
+            g->dl_exec = nullptr;
+            g->dl_graph = nullptr;
+            if (!g->dl_stream) FQ_TRY(cudaStreamCreateWithFlags(&g->dl_stream, cudaStreamNonBlocking));
+            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited};
+            FQ_TRY(build_device_loop(b, &g->dl_graph));
+            FQ_TRY(cudaGraphInstantiate(&g->dl_exec, g->dl_graph, 0));
+            g->dl_depth = d_depth;
+            g->dl_parent = d_parent;
+            g->dl_log = d_stream_log;
+            g->dl_mode = mode;
+        }
+        LoopState *hls = reinterpret_cast<LoopState *>(g->host + kHostLs);
+        fq_level_record *hrec = reinterpret_cast<fq_level_record *>(g->host + kHostLs + al256(sizeof(LoopState)));
+        LoopParams prm{};
+        prm.root = root;
+        prm.alpha = alpha;
+        prm.beta = beta;
+        prm.flags = flags;
+        prm.max_levels = h_levels ? std::min<uint32_t>(max_levels, kMaxDeviceRecords) : 0u;
+        prm.log_cap = d_stream_log ? stream_log_cap : 0ull;
+        hls->p = prm;
+        FQ_TRY(cudaMemcpyAsync(&g->ls->p, &hls->p, sizeof(LoopParams), cudaMemcpyHostToDevice, st));
+        FQ_TRY(cudaGraphLaunch(g->dl_exec, st));
+        FQ_TRY(cudaMemcpyAsync(hls, g->ls, sizeof(LoopState), cudaMemcpyDeviceToHost, st));
+        const uint32_t first = std::min<uint32_t>(prm.max_levels, 64u);  // most searches have fewer levels
+        if (first) FQ_TRY(cudaMemcpyAsync(hrec, g->recs, sizeof(fq_level_record) * first, cudaMemcpyDeviceToHost, st));
+        FQ_TRY(cudaStreamSynchronize(st));
+        if (hls->status != FQ_OK) return (fq_status)hls->status;
+        const uint32_t kept = std::min<uint32_t>(prm.max_levels, hls->stats.levels);
+        if (kept > first) {
+            FQ_TRY(cudaMemcpyAsync(hrec + first, g->recs + first, sizeof(fq_level_record) * (kept - first),
+                                   cudaMemcpyDeviceToHost, st));
+            FQ_TRY(cudaStreamSynchronize(st));
+        }
+        if (h_levels)
+            for (uint32_t d = 0; d < kept; d++) h_levels[d] = hrec[d];
+        fq_bfs_stats stats = hls->stats;
+        stats.reached_edges /= 2;
+        if (h_stats) *h_stats = stats;
+        return (fq_status)hls->soft_status;
+    }
+
+    fq_bfs_stats stats;
+    memset(&stats, 0, sizeof(stats));
+    Timer tm{g, st, (flags & FQ_BFS_TIMING) != 0, stats.kernel_ms, stats.kernel_launches};
+
     // ---- level 0 set-up
     tm.begin(FQ_K_OTHER);
-    FQ_TRY(cudaMemsetAsync(d_depth, 0xff, 4 * n, st));
-    if (d_parent) FQ_TRY(cudaMemsetAsync(d_parent, 0xff, 4 * n, st));
-    FQ_TRY(cudaMemsetAsync(g->fbits, 0, 8 * (nwords + 2), st));
-    FQ_TRY(cudaMemsetAsync(g->next, 0, 8 * (nwords + 2), st));
-    FQ_TRY(cudaMemsetAsync(g->visited, 0, 8 * (nwords + 2), st));
-    FQ_TRY(cudaMemsetAsync(g->vis_cnt, 0, 4 * g->cmp_tiles, st));
-    FQ_TRY(cudaMemsetAsync(g->ctr, 0, sizeof(Counters), st));
-    bfs_init_kernel<<<1, 256, 0, st>>>(g->off, root, n, d_depth, d_parent, g->q, g->fbits, g->visited, g->vis_cnt,
-                                       g->ctr, g->sq, g->sv);
-    FQ_TRY(cudaGetLastError());
+    FQ_TRY(step_init(g, root, d_depth, d_parent, nullptr, st));
     tm.end(FQ_K_OTHER, 1);
     FQ_TRY(cudaMemcpyAsync(g->host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     FQ_TRY(cudaStreamSynchronize(st));
@@ -620,31 +1158,18 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     int dir = FQ_TOP_DOWN;
     uint64_t log_used = 0;
     fq_status result = FQ_OK;
-    unsigned long long *q_bytes = &g->ctr->q_bytes, *b_bytes = &g->ctr->b_bytes, *v_bytes = &g->ctr->v_bytes;
 
     for (uint32_t d = 0;; d++) {
         // 1. encode F_d (Q_d and B_d), and V_d
         tm.begin(FQ_K_ENCODE);
-        int enc_launches = 2;
-        if (!codec) {
-            enc_launches = 0;
-        } else if (2 * n_f <= n) {
-            Mirror mb;
-            mb.out = g->bs;
-            mb.cap = g->bs_cap;
-            mb.out_bytes = reinterpret_cast<uint64_t *>(b_bytes);
-            mb.words = g->fbits;
-            mb.nbits = n;
-            FQ_TRY(encode_fq_mirror(g->q, n_f, nullptr, n_f, g->qs, g->qs_cap, reinterpret_cast<uint64_t *>(q_bytes),
-                                    mb, g->sq, st));
-        } else {  // a frontier denser than half the vertices: its bitmap codes the clear positions
-            FQ_TRY(encode_fq(g->q, n_f, nullptr, n_f, g->qs, g->qs_cap, reinterpret_cast<uint64_t *>(q_bytes), g->sq, st));
-            FQ_TRY(reset_status(g->sq, n / 2 + 1, st));
-            FQ_TRY(encode_fb(g->fbits, n, g->bs, g->bs_cap, reinterpret_cast<uint64_t *>(b_bytes), g->sq, st));
-            enc_launches += 6;
+        int enc_launches = 0;
+        if (codec) {
+            const bool dense = 2 * n_f > n;
+            FQ_TRY(step_encode_q(g, dense, n_f, nullptr, st));
+            enc_launches = dense ? 8 : 2;
         }
         if (want_visited) {
-            FQ_TRY(encode_fb_positions(g->visited, n, g->vs, g->bs_cap, reinterpret_cast<uint64_t *>(v_bytes), g->sv, st));
+            FQ_TRY(step_encode_v(g, st));
             enc_launches += 2;
         }
         tm.end(FQ_K_ENCODE, enc_launches);
@@ -657,46 +1182,23 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         const int32_t newdepth = (int32_t)d + 1;
 
         // 3 + 4. decode the consumed form, expand
+        tm.begin(FQ_K_DECODE);
+        if (codec && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, st));
+        if (codec && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, st));
+        tm.end(FQ_K_DECODE, codec ? (dir == FQ_TOP_DOWN ? 3 : 4) : 0);
         if (dir == FQ_TOP_DOWN) {
-            tm.begin(FQ_K_DECODE);
-            if (codec)
-                FQ_TRY(decode_fq(g->qs, 0, reinterpret_cast<const uint64_t *>(q_bytes), g->q2, n_f,
-                                 reinterpret_cast<uint64_t *>(&g->ctr->dec_n), g->sq, st));
-            tm.end(FQ_K_DECODE, codec ? 3 : 0);
-            const uint32_t *qin = codec ? g->q2 : g->q;
             tm.begin(FQ_K_TOP_DOWN);
-            const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(std::max<uint64_t>(n_f, 1), kThreads), (uint64_t)sms * 8);
-            td_expand_kernel<<<grid, kThreads, 0, st>>>(qin, n_f, g->off, g->cols, vis32, next32, d_depth, d_parent,
-                                                        newdepth, g->items, &g->ctr->hub_items, g->items_cap, n,
-                                                        g->sq.ctl, &g->ctr->m_f_next);
-            td_hub_kernel<<<sms * 4, kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32,
-                                                        next32, d_depth, d_parent, newdepth, g->off, &g->ctr->m_f_next);
-            FQ_TRY(cudaGetLastError());
+            FQ_TRY(step_top_down(g, codec, n_f, newdepth, d_depth, d_parent, nullptr, st));
             tm.end(FQ_K_TOP_DOWN, 2);
         } else {
-            tm.begin(FQ_K_DECODE);
-            if (codec) FQ_TRY(decode_fb(g->bs, 0, reinterpret_cast<const uint64_t *>(b_bytes), g->fbits2, n, g->sq, st));
-            tm.end(FQ_K_DECODE, codec ? 4 : 0);
-            const uint64_t *fin = codec ? g->fbits2 : g->fbits;
             tm.begin(FQ_K_BOTTOM_UP);
-            const uint64_t words32 = cdiv(n, 32);
-            const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16);
-            bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
-                reinterpret_cast<const uint32_t *>(fin), vis32, g->iso32, next32, g->off, g->cols, d_depth,
-                d_parent, newdepth, n, &g->ctr->examined, &g->ctr->m_f_next);
-            FQ_TRY(cudaGetLastError());
+            FQ_TRY(step_bottom_up(g, codec, newdepth, d_depth, d_parent, nullptr, st));
             tm.end(FQ_K_BOTTOM_UP, 1);
         }
 
         // 5. compaction (+ V_{d+1} positions, cleared scratch for the next level)
         tm.begin(FQ_K_COMPACT);
-        const uint32_t ct = (uint32_t)g->cmp_tiles;
-        cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, nwords, g->tile_cnt, g->vis_cnt);
-        cmp_scan_kernel<<<1, kScanThreads, 0, st>>>(g->tile_cnt, g->tile_off, g->vis_cnt, g->vtile_off, g->cmp_tiles, n,
-                                                    g->ctr, g->sq, g->sv);
-        cmp_extract_kernel<<<ct, kThreads, 0, st>>>(g->next, g->fbits, g->visited, nwords, n, g->tile_off, g->vtile_off,
-                                                    g->q, g->sv);
-        FQ_TRY(cudaGetLastError());
+        FQ_TRY(step_compact(g, st));
         tm.end(FQ_K_COMPACT, 3);
 
         FQ_TRY(cudaMemcpyAsync(g->host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));

@@ -491,15 +491,7 @@ __global__ void __launch_bounds__(kScanThreads) enc_s_plan_kernel(EncArgs a)
 {
     __shared__ unsigned long long sm[33];
     const uint64_t n = a.n_host, nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
-    const uint64_t chunk = dcdiv(ntiles, kScanThreads);
-    const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
-    unsigned long long local = 0, total = 0;
-    for (uint64_t t = t0; t < t1; t++) local += a.s.tile_sum[t];
-    unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
-    for (uint64_t t = t0; t < t1; t++) {
-        a.s.tile_off[t] = (uint32_t)run;
-        run += a.s.tile_sum[t];
-    }
+    const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
     __syncthreads();
     if (threadIdx.x == 0) enc_finalize(a, n, nb, total);
 }
@@ -803,15 +795,7 @@ __global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
     if (ok && h.mode == kModePacked) {
         const uint8_t *fq = a.in + h.fq_off;
         const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
-        const uint64_t chunk = dcdiv(ntiles, kScanThreads);
-        const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
-        unsigned long long local = 0, total = 0;
-        for (uint64_t t = t0; t < t1; t++) local += a.s.tile_sum[t];
-        unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
-        for (uint64_t t = t0; t < t1; t++) {
-            a.s.tile_off[t] = (uint32_t)run;
-            run += a.s.tile_sum[t];
-        }
+        const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
         if (threadIdx.x == 0) {
             c->total_b = total;
             if (h.words != 4u * total || h.fq_bytes != 16u + dpad16(5u * h.nb) + 16u * total) ok = false;
@@ -883,17 +867,49 @@ __device__ __forceinline__ void emit_id(const DecArgs &a, uint32_t clear_mode, u
     else atomicOr(&w32[v >> 5], 1u << (v & 31u));
 }
 
-constexpr uint32_t kDecStage = kTileBlocks * 32u * 16u + 16u;  // a tile's largest payload + one word of slack
-constexpr size_t kDecSmem = 2 * (size_t)kDecStage;
+// A group's largest payload (kBlocksPerWarp blocks of width 32) + slack for the 3-word windows.
+constexpr uint32_t kDecStage = kBlocksPerWarp * 32u * 16u + 16u;
+constexpr size_t kDecSmem = (size_t)kEncWarps * 2 * kDecStage;
 
-// D2: tiles of 64 blocks, assigned round-robin.  A tile's payload is one contiguous range, so one
-// TMA bulk copy stages it into shared memory; the next tile's copy is in flight while this one
-// is decoded (one warp per block: extract, prefix-sum the gaps, validate, 128-bit stores).
+// Where one group of kBlocksPerWarp blocks (never straddling a tile) sits: lane l describes tile
+// blocks 2l, 2l+1 in `info` (exclusive width prefix | b(2l) << 16 | b(2l+1) << 24), lane i <= 8
+// holds the base of the group's block i in `base` (i = 8: the next group's first, for the bound
+// check), and the payload range is [off, off + bytes) of the payload area.
+struct GroupMeta {
+    uint32_t info, base, pre;
+    uint64_t off;
+    uint32_t bytes;
+};
+
+__device__ __forceinline__ GroupMeta group_meta(const DecArgs &a, const uint8_t *wd, const uint32_t *bases,
+                                                uint64_t nb, uint64_t grp, uint32_t lane)
+{
+    constexpr uint32_t kGroupsPerTile = kTileBlocks / kBlocksPerWarp;
+    const uint64_t t = grp / kGroupsPerTile, k0 = grp * kBlocksPerWarp;
+    const uint32_t git = (uint32_t)(grp % kGroupsPerTile);
+    const uint64_t kk = t * kTileBlocks + 2 * lane;
+    const uint32_t x0 = kk < nb ? wd[kk] : 0u, x1 = kk + 1 < nb ? wd[kk + 1] : 0u;
+    const uint32_t tile_base = a.s.tile_off[t];
+    GroupMeta m;
+    m.base = (lane <= kBlocksPerWarp && k0 + lane < nb) ? bases[k0 + lane] : 0u;
+    const uint32_t incl = warp_incl_scan(x0 + x1);
+    m.info = (incl - x0 - x1) | (x0 << 16) | (x1 << 24);
+    const uint32_t lead = git * (kBlocksPerWarp / 2);  // the lane describing the group's first block
+    m.pre = __shfl_sync(0xffffffffu, incl - x0 - x1, lead);
+    const uint32_t end = __shfl_sync(0xffffffffu, incl, lead + kBlocksPerWarp / 2 - 1);
+    m.off = 16ull * ((uint64_t)tile_base + m.pre);
+    m.bytes = 16u * (end - m.pre);
+    return m;
+}
+
+// D2: one warp per group of kBlocksPerWarp blocks, groups assigned round-robin over all warps, no
+// CTA barrier.  A group's payload is one contiguous range: lane 0 stages it into the warp's own
+// shared-memory buffer with one TMA bulk copy while the warp decodes the previous group from the
+// other buffer (extract, prefix-sum the gaps, validate, 128-bit stores).
 __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
 {
-    extern __shared__ __align__(128) uint8_t dbuf[];  // [2][kDecStage]
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t spre[kTileBlocks], swid[kTileBlocks], sbase[kTileBlocks + 1];
+    extern __shared__ __align__(128) uint8_t dbuf[];  // [kEncWarps][2][kDecStage]
+    __shared__ __align__(8) unsigned long long bars[kEncWarps][2];
     const Ctl *c = a.s.ctl;
     const uint32_t mode = c->mode;
     if (mode != kModePacked && mode != kModeRaw) return;
@@ -916,69 +932,59 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
     const uint8_t *wd = fq + 16 + 4 * nb;
     const uint32_t *bases = reinterpret_cast<const uint32_t *>(fq + 16);
     const uint8_t *payload = fq + 16 + dpad16(5u * nb);
-    const uint64_t ntiles = dcdiv(nb, kTileBlocks);
-    const uint64_t total = c->total_b;
-    auto tile_bytes = [&](uint64_t t) -> uint32_t {
-        const uint64_t end = (t + 1 < ntiles) ? a.s.tile_off[t + 1] : total;
-        return (uint32_t)(16u * (end - a.s.tile_off[t]));
-    };
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+    const uint64_t ngroups = dcdiv(nb, kBlocksPerWarp);
+    const uint64_t nwarps = (uint64_t)gridDim.x * kEncWarps;
+    uint64_t grp = (uint64_t)blockIdx.x * kEncWarps + warp;
+    if (grp >= ngroups) return;
+    uint8_t *buf = dbuf + (size_t)warp * 2 * kDecStage;
+    unsigned long long *bar = bars[warp];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         mbar_init_fence();
-        const uint64_t t0 = blockIdx.x;
-        if (t0 < ntiles && tile_bytes(t0))
-            bulk_load(dbuf, payload + 16u * (uint64_t)a.s.tile_off[t0], tile_bytes(t0), &bars[0]);
     }
-    __syncthreads();
+    __syncwarp();
+    GroupMeta cur = group_meta(a, wd, bases, nb, grp, lane);
+    if (lane == 0 && cur.bytes) bulk_load(buf, payload + cur.off, cur.bytes, &bar[0]);
     uint32_t phase0 = 0u, phase1 = 0u;
-    for (uint64_t i = 0;; i++) {
-        const uint64_t t = blockIdx.x + i * gridDim.x;
-        if (t >= ntiles) break;
-        const uint32_t stage = (uint32_t)(i & 1u);
-        const uint64_t tn = t + gridDim.x;
-        if (threadIdx.x == 0 && tn < ntiles && tile_bytes(tn))
-            bulk_load(dbuf + (stage ^ 1u) * kDecStage, payload + 16u * (uint64_t)a.s.tile_off[tn], tile_bytes(tn),
-                      &bars[stage ^ 1u]);
-        if (warp == 0) {
-            const uint64_t k0 = t * kTileBlocks + 2 * lane;
-            const uint32_t x0 = k0 < nb ? wd[k0] : 0u, x1 = k0 + 1 < nb ? wd[k0 + 1] : 0u;
-            const uint32_t incl = warp_incl_scan(x0 + x1);
-            spre[2 * lane] = incl - x0 - x1;
-            spre[2 * lane + 1] = incl - x1;
-            swid[2 * lane] = x0;
-            swid[2 * lane + 1] = x1;
-        } else if (warp == 1 || warp == 2) {  // the tile's bases and the next tile's first base
-            const uint32_t j = (warp - 1) * 32u + lane;
-            const uint64_t k = t * kTileBlocks + j;
-            sbase[j] = k < nb ? bases[k] : 0u;
-            if (j == 0) sbase[kTileBlocks] = (t + 1) * kTileBlocks < nb ? bases[(t + 1) * kTileBlocks] : 0u;
-        }
-        if (tile_bytes(t)) {
-            if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(a.s.ctl, FQ_ETIMEOUT, kWhereDecUnpack, t);
+    for (uint32_t it = 0;; it++) {
+        const uint32_t stage = it & 1u;
+        const uint64_t gn = grp + nwarps;
+        GroupMeta nxt{};
+        if (gn < ngroups) nxt = group_meta(a, wd, bases, nb, gn, lane);
+        __syncwarp();  // every lane is done with the other buffer (read in the previous iteration)
+        if (gn < ngroups && lane == 0 && nxt.bytes)
+            bulk_load(buf + (stage ^ 1u) * kDecStage, payload + nxt.off, nxt.bytes, &bar[stage ^ 1u]);
+        if (cur.bytes) {
+            if (!mbar_wait(&bar[stage], stage ? phase1 : phase0)) set_error(a.s.ctl, FQ_ETIMEOUT, kWhereDecUnpack, grp);
             if (stage) phase1 ^= 1u;
             else phase0 ^= 1u;
         }
-        __syncthreads();
-        const uint32_t *sp = reinterpret_cast<const uint32_t *>(dbuf + stage * kDecStage);
-        for (uint32_t bi = 0; bi < kBlocksPerWarp; bi++) {
-            const uint32_t local = warp * kBlocksPerWarp + bi;
-            const uint64_t k = t * kTileBlocks + local;
+        const uint32_t *sp = reinterpret_cast<const uint32_t *>(buf + stage * kDecStage);
+        const uint32_t git = (uint32_t)(grp % (kTileBlocks / kBlocksPerWarp));
+        const uint64_t k0 = grp * kBlocksPerWarp;
+#pragma unroll 2
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+            const uint64_t k = k0 + i;
+            const uint32_t in = __shfl_sync(0xffffffffu, cur.info, git * (kBlocksPerWarp / 2) + (i >> 1));
+            const uint32_t base = __shfl_sync(0xffffffffu, cur.base, i);
+            const uint32_t next = __shfl_sync(0xffffffffu, cur.base, i + 1);
             if (k >= nb) break;
-            const uint32_t b = swid[local];
-            const uint32_t *pk = sp + 4u * spre[local];
+            const uint32_t b = (i & 1u) ? (in >> 24) : ((in >> 16) & 0xffu);
+            const uint32_t pre = (in & 0xffffu) + ((i & 1u) ? ((in >> 16) & 0xffu) : 0u) - cur.pre;
+            const uint32_t *pk = sp + 4u * pre;
             const uint64_t i0 = k * kBlock + 4u * lane;
             uint32_t out[4];
             bool good;
             if (k + 1 < nb && b <= 16u) {  // full narrow block: the lean 32-bit path
                 uint32_t lastv;
-                good = unpack_full_narrow(pk, b, sbase[local], lane, out, &lastv);
-                if (lane == 31 && lastv >= sbase[local + 1]) good = false;
+                good = unpack_full_narrow(pk, b, base, lane, out, &lastv);
+                if (lane == 31 && lastv >= next) good = false;
             } else {
                 unsigned long long lastv;
-                good = unpack_block(pk, b, sbase[local], k, n, lane, out, &lastv);
+                good = unpack_block(pk, b, base, k, n, lane, out, &lastv);
                 // a full block (k + 1 < nb) ends in lane 31's last slot: it must stay below the next base
-                if (k + 1 < nb && lane == 31 && lastv >= (unsigned long long)sbase[local + 1]) good = false;
+                if (k + 1 < nb && lane == 31 && lastv >= (unsigned long long)next) good = false;
             }
             if (!good) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, k * kBlock);
             if (!a.fb && i0 + 3 < n) {
@@ -989,7 +995,9 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
                     if (i0 + j < n) emit_id(a, clear_mode, i0 + j, out[j]);
             }
         }
-        __syncthreads();  // the stage is free for the copy two tiles ahead
+        if (gn >= ngroups) break;
+        grp = gn;
+        cur = nxt;
     }
 }
 

@@ -215,6 +215,39 @@ __device__ __forceinline__ unsigned long long cta_excl_scan64(unsigned long long
     return r;
 }
 
+// Exclusive scan (from 0) of the u32 values in[0..count) into out[0..count) by one CTA of NT
+// threads; out may equal in.  Returns the 64-bit total to every thread.  Thread i owns a
+// contiguous chunk and reads it kScanWin values at a time with all of a window's loads issued
+// before any is used, so a chunk of a few dozen values costs one memory latency, not one each.
+constexpr uint32_t kScanWin = 16;
+template <uint32_t NT>
+__device__ unsigned long long cta_chunk_scan_u32(const uint32_t *in, uint32_t *out, uint64_t count,
+                                                 unsigned long long *sm)
+{
+    const uint64_t chunk = (count + NT - 1) / NT;
+    const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = t0 + chunk < count ? t0 + chunk : count;
+    unsigned long long local = 0, total = 0;
+    for (uint64_t w = t0; w < t1; w += kScanWin) {
+        uint32_t x[kScanWin];
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) x[i] = (w + i < t1) ? in[w + i] : 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) local += x[i];
+    }
+    unsigned long long run = cta_excl_scan64<NT>(local, sm, &total);
+    for (uint64_t w = t0; w < t1; w += kScanWin) {
+        uint32_t x[kScanWin];
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) x[i] = (w + i < t1) ? in[w + i] : 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) {
+            if (w + i < t1) out[w + i] = (uint32_t)run;
+            run += x[i];
+        }
+    }
+    return total;
+}
+
 }  // namespace fq
 
 namespace fq {

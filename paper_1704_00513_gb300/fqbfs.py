@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfqbfs.so")
 FQ_OK, FQ_EINVAL, FQ_ENOMEM, FQ_ENOSPC, FQ_ECORRUPT, FQ_EUNSORTED, FQ_ETIMEOUT, FQ_ECUDA, FQ_EBUSY = range(9)
 FQ_TOP_DOWN, FQ_BOTTOM_UP = 0, 1
 FQ_BFS_VISITED_STREAM, FQ_BFS_FORCE_TOP_DOWN, FQ_BFS_FORCE_BOTTOM_UP, FQ_BFS_TIMING, FQ_BFS_NO_CODEC = 1, 2, 4, 8, 16
+FQ_BFS_DEVICE_LOOP = 32
 KCLASS = ("top_down", "bottom_up", "compact", "encode", "decode", "other")
 
 _u64, _u32, _i32, _vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
@@ -303,6 +304,7 @@ class Graph:
             _check(lib().fq_graph_create(_ptr(self.offsets), _ptr(self.cols), self.n, self.m, ctypes.byref(h)),
                    "fq_graph_create")
         self._h = h
+        self._levels = {}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -341,7 +343,9 @@ class Graph:
             parent = None
         opts = fq_bfs_opts(alpha, beta, flags, 0)
         stats = fq_bfs_stats()
-        levels = (fq_level_record * max_levels)()
+        levels = self._levels.get(max_levels)
+        if levels is None:  # reused across calls: only the first stats.levels entries are read
+            levels = self._levels[max_levels] = (fq_level_record * max_levels)()
         log = None
         log_cap = 0
         if record_streams:

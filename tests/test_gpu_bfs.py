@@ -1,6 +1,7 @@
 """CUDA BFS parity: depths bit-identical to the oracle's FIFO BFS, parents a valid BFS tree,
 per-level records (n_f, m_f, m_u, direction, edges examined) equal to the oracle's schedule,
-and every level's encoded streams Q_d, B_d, V_d byte-identical to the oracle's."""
+and every level's encoded streams Q_d, B_d, V_d byte-identical to the oracle's -- for the
+host-driven level loop and for the device-driven one (FQ_BFS_DEVICE_LOOP, one CUDA graph)."""
 import numpy as np
 import pytest
 import torch
@@ -12,6 +13,9 @@ from paper_1704_00513_gb300 import fqbfs
 from paper_1704_00513_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+# the two level-loop drivers: host-driven (0) and one CUDA graph with a device-side while loop
+LOOPS = pytest.mark.parametrize("loop", [0, fqbfs.FQ_BFS_DEVICE_LOOP], ids=["host_loop", "device_loop"])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,20 +68,22 @@ def rmat16():
     return off.numpy(), cols.numpy().view(np.uint32), roots
 
 
-def test_rmat16_eight_roots_streams_and_schedule(rmat16):
+@LOOPS
+def test_rmat16_eight_roots_streams_and_schedule(rmat16, loop):
     off, cols, roots = rmat16
     g = fqbfs.Graph(*to_dev(off, cols))
     for r in roots:
-        check_run(g, off, cols, r)
+        check_run(g, off, cols, r, flags=loop)
     g.close()
 
 
+@LOOPS
 @pytest.mark.parametrize("flags", [fqbfs.FQ_BFS_FORCE_TOP_DOWN, fqbfs.FQ_BFS_FORCE_BOTTOM_UP])
-def test_rmat16_forced_directions(rmat16, flags):
+def test_rmat16_forced_directions(rmat16, flags, loop):
     off, cols, roots = rmat16
     g = fqbfs.Graph(*to_dev(off, cols))
     for r in roots[:3]:
-        check_run(g, off, cols, r, flags=flags)
+        check_run(g, off, cols, r, flags=flags | loop)
     g.close()
 
 
@@ -91,8 +97,9 @@ def test_timing_flag_fills_kernel_classes(rmat16):
     g.close()
 
 
+@LOOPS
 @pytest.mark.parametrize("case", ["path", "star", "complete", "two_components", "isolated_root", "grid"])
-def test_small_graph_shapes(case):
+def test_small_graph_shapes(case, loop):
     if case == "path":
         n = 3000
         edges = [(i, i + 1) for i in range(n - 1)]
@@ -121,9 +128,9 @@ def test_small_graph_shapes(case):
         root = 35 * c + 45
     off, cols = csr_from_edges(n, edges)
     g = fqbfs.Graph(*to_dev(off, cols))
-    check_run(g, off, cols, root)
+    check_run(g, off, cols, root, flags=loop)
     for fl in (fqbfs.FQ_BFS_FORCE_TOP_DOWN, fqbfs.FQ_BFS_FORCE_BOTTOM_UP):
-        check_run(g, off, cols, root, flags=fl, streams=False, visited=False)
+        check_run(g, off, cols, root, flags=fl | loop, streams=False, visited=False)
     g.close()
 
 
@@ -160,10 +167,84 @@ def test_rmat24_full_size_sampled_roots():
     g.close()
 
 
-def test_rmat16_without_codec_stage_same_depths_and_schedule(rmat16):
+@LOOPS
+def test_rmat16_without_codec_stage_same_depths_and_schedule(rmat16, loop):
     off, cols, roots = rmat16
     g = fqbfs.Graph(*to_dev(off, cols))
     for r in roots[:4]:
-        res = check_run(g, off, cols, r, flags=fqbfs.FQ_BFS_NO_CODEC, streams=False, visited=False)
+        res = check_run(g, off, cols, r, flags=fqbfs.FQ_BFS_NO_CODEC | loop, streams=False, visited=False)
         assert res.stats["enc_queue_bytes"] == 0
+    g.close()
+
+
+def test_device_loop_matches_host_loop_records_streams_and_stats(rmat16):
+    """The device-driven loop takes the host loop's decisions on the device: identical level
+    records, statistics (but the event timings it does not take) and stream logs."""
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    for r in roots[:4]:
+        for extra in (fqbfs.FQ_BFS_VISITED_STREAM, 0):
+            a = g.bfs(r, flags=extra, record_streams=True)
+            da, pa = a.depth.clone(), a.parent.clone()
+            b = g.bfs(r, flags=extra | fqbfs.FQ_BFS_DEVICE_LOOP, record_streams=True)
+            assert torch.equal(da, b.depth)
+            assert a.levels == b.levels
+            for k in ("levels", "directions", "reached", "reached_edges", "edges_examined", "raw_queue_bytes",
+                      "enc_queue_bytes", "raw_bitmap_bytes", "enc_bitmap_bytes", "enc_visited_bytes", "kernel_bytes"):
+                assert a.stats[k] == b.stats[k], k
+            for k in ("top_down", "bottom_up", "compact", "encode", "decode"):
+                assert a.stats["kernel_launches"][k] == b.stats["kernel_launches"][k], k
+            for sa, sb in zip(a.streams, b.streams):
+                for key in ("Q", "B", "V"):
+                    assert torch.equal(sa[key], sb[key]), (sa["level"], key)
+            # both parent arrays are valid BFS trees of the same depths
+            assert oracle.validate(off, cols, r, da.cpu().numpy(), pa.cpu().numpy().view(np.uint32)) == 0
+    g.close()
+
+
+def test_device_loop_graph_reuse_and_rebuild(rmat16):
+    """One graph serves every root with the same buffers; new output buffers (or a parent-less run)
+    rebuild it; results stay exact throughout."""
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    n = off.size - 1
+    d1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    p1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    for i, r in enumerate(roots):
+        depth = d1 if i % 3 else torch.empty(n, dtype=torch.int32, device="cuda")
+        parent = p1 if i % 2 else None
+        res = g.bfs(r, depth=depth, parent=parent if parent is not None else False,
+                    flags=fqbfs.FQ_BFS_DEVICE_LOOP | fqbfs.FQ_BFS_VISITED_STREAM)
+        ref_depth, _ = oracle.bfs(off, cols, r)
+        assert np.array_equal(res.depth.cpu().numpy(), ref_depth)
+        if parent is not None:
+            assert oracle.validate(off, cols, r, ref_depth, res.parent.cpu().numpy().view(np.uint32)) == 0
+    g.close()
+
+
+def test_device_loop_log_overflow_reports_enospc(rmat16):
+    """A stream log too small for every level: FQ_ENOSPC, with the search itself complete and the
+    levels that did fit logged exactly as the host loop logs them."""
+    import ctypes
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    n = off.size - 1
+    r = roots[1]
+    full = g.bfs(r, flags=fqbfs.FQ_BFS_VISITED_STREAM, record_streams=True)
+    cap = (full.levels[0]["q_bytes"] + full.levels[0]["b_bytes"] + full.levels[0]["v_bytes"]) + 16
+    outs = []
+    for loop in (0, fqbfs.FQ_BFS_DEVICE_LOOP):
+        depth = torch.empty(n, dtype=torch.int32, device="cuda")
+        log = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+        opts = fqbfs.fq_bfs_opts(14, 24, fqbfs.FQ_BFS_VISITED_STREAM | loop, 0)
+        stats = fqbfs.fq_bfs_stats()
+        levels = (fqbfs.fq_level_record * 64)()
+        st = fqbfs.lib().fq_bfs_run(g._h, int(r), depth.data_ptr(), None, ctypes.byref(opts), ctypes.byref(stats),
+                                    levels, 64, log.data_ptr(), cap, None)
+        torch.cuda.synchronize()
+        assert st == fqbfs.FQ_ENOSPC
+        assert torch.equal(depth, full.depth)
+        outs.append((log.cpu(), [levels[i].log_offset for i in range(stats.levels)]))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
     g.close()
