@@ -393,54 +393,70 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
     }
 }
 
+// Positions of the set bits of the warp's 32 words (lane L holds word wbase + L) written to
+// out[pos ...] in increasing order.  Only nonzero words are visited: each is broadcast to the
+// warp, lane L takes its bits L and L + 32, and two ballots give every set bit its output slot,
+// so each store instruction writes one contiguous run (the writes are coalesced).
+__device__ __forceinline__ void expand_words(uint64_t x, uint64_t wbase, unsigned long long pos, uint32_t *out,
+                                             uint32_t lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t nz = __ballot_sync(0xffffffffu, x != 0ull);
+    while (nz) {
+        const uint32_t src = __ffs(nz) - 1u;
+        nz &= nz - 1u;
+        const uint64_t xw = __shfl_sync(0xffffffffu, x, src);
+        const uint32_t lo = (uint32_t)xw, hi = (uint32_t)(xw >> 32);
+        const uint32_t pos0 = (uint32_t)((wbase + src) * 64u);
+        const bool b0 = (lo >> lane) & 1u, b1 = (hi >> lane) & 1u;
+        const uint32_t n0 = __popc(lo);
+        if (b0) out[pos + __popc(lo & lt)] = pos0 + lane;
+        if (b1) out[pos + n0 + __popc(hi & lt)] = pos0 + 32u + lane;
+        pos += n0 + __popc(hi);
+    }
+}
+
+// The next frontier F_{d+1} as a sorted queue (and as the bitmap the next level's B encode reads),
+// next cleared, and -- when V_{d+1} is coded -- the positions V_{d+1} codes.  One word per thread;
+// the CTA's tile offset comes from cmp_scan_kernel, each warp's from a CTA prefix of warp counts.
 __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restrict__ next, uint64_t *__restrict__ fbits,
                                                                const uint64_t *__restrict__ visited, uint64_t nwords,
                                                                uint64_t n, const uint32_t *__restrict__ tile_off,
                                                                const uint32_t *__restrict__ vtile_off, uint32_t *q,
-                                                               Scratch sv)
+                                                               Scratch sv, int want_v)
 {
-    __shared__ unsigned long long sm[33];
-    const uint64_t w0 = (uint64_t)blockIdx.x * kCmpWords + (uint64_t)threadIdx.x * kCmpWordsPerThread;
-    const bool v_clear = sv.ctl->fb_mode == kFbClear;
-    uint64_t x[kCmpWordsPerThread], y[kCmpWordsPerThread];
-    uint32_t cnt = 0, vcnt = 0;
-#pragma unroll
-    for (uint32_t j = 0; j < kCmpWordsPerThread; j++) {
-        const uint64_t w = w0 + j;
-        x[j] = 0;
-        y[j] = 0;
-        if (w < nwords) {
-            x[j] = next[w];
-            fbits[w] = x[j];  // F_{d+1} as a bitmap for the next level's B encode
-            if (x[j]) next[w] = 0;
-            uint64_t vis = visited[w];
-            if (v_clear) {
+    static_assert(kCmpWordsPerThread == 1, "one word per thread");
+    __shared__ uint32_t wq[kThreads / 32], wv[kThreads / 32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t w = (uint64_t)blockIdx.x * kCmpWords + threadIdx.x;
+    uint64_t x = 0, y = 0;
+    if (w < nwords) {
+        x = next[w];
+        fbits[w] = x;  // F_{d+1} as a bitmap for the next level's B encode
+        if (x) next[w] = 0;
+        if (want_v) {
+            y = visited[w];
+            if (sv.ctl->fb_mode == kFbClear) {
                 const uint64_t nb = bits_in_word(w, nwords, n);
-                vis = ~vis & (nb == 64 ? ~0ull : ((1ull << nb) - 1ull));
+                y = ~y & (nb == 64 ? ~0ull : ((1ull << nb) - 1ull));
             }
-            y[j] = vis;
-        }
-        cnt += __popcll(x[j]);
-        vcnt += __popcll(y[j]);
-    }
-    unsigned long long total;
-    unsigned long long pos = cta_excl_scan64<kThreads>(cnt, sm, &total) + tile_off[blockIdx.x];
-    unsigned long long vpos = cta_excl_scan64<kThreads>(vcnt, sm, &total) + vtile_off[blockIdx.x];
-#pragma unroll
-    for (uint32_t j = 0; j < kCmpWordsPerThread; j++) {
-        uint64_t a = x[j];
-        while (a) {
-            const uint32_t bit = __ffsll((long long)a) - 1;
-            q[pos++] = (uint32_t)((w0 + j) * 64u + bit);
-            a &= a - 1;
-        }
-        uint64_t b = y[j];
-        while (b) {
-            const uint32_t bit = __ffsll((long long)b) - 1;
-            sv.positions[vpos++] = (uint32_t)((w0 + j) * 64u + bit);
-            b &= b - 1;
         }
     }
+    const uint32_t cq = __reduce_add_sync(0xffffffffu, (uint32_t)__popcll(x));
+    const uint32_t cv = __reduce_add_sync(0xffffffffu, (uint32_t)__popcll(y));
+    if (lane == 0) {
+        wq[warp] = cq;
+        wv[warp] = cv;
+    }
+    __syncthreads();
+    unsigned long long oq = tile_off[blockIdx.x], ov = want_v ? vtile_off[blockIdx.x] : 0ull;
+    for (uint32_t i = 0; i < warp; i++) {
+        oq += wq[i];
+        ov += wv[i];
+    }
+    const uint64_t wbase = (uint64_t)blockIdx.x * kCmpWords + warp * 32u;
+    expand_words(x, wbase, oq, q, lane);
+    if (want_v) expand_words(y, wbase, ov, sv.positions, lane);
 }
 
 // ---- the device-driven level loop (FQ_BFS_DEVICE_LOOP) ----
@@ -768,14 +784,14 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
 }
 
 // Step 5: compaction (+ V_{d+1} positions, cleared scratch for the next level).
-cudaError_t step_compact(fq_graph *g, cudaStream_t st)
+cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
 {
     const uint32_t ct = (uint32_t)g->cmp_tiles;
     cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt);
     cmp_scan_kernel<<<1, kScanThreads, 0, st>>>(g->tile_cnt, g->tile_off, g->vis_cnt, g->vtile_off, g->cmp_tiles, g->n,
                                                 g->ctr, g->sq, g->sv);
     cmp_extract_kernel<<<ct, kThreads, 0, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
-                                                g->vtile_off, g->q, g->sv);
+                                                g->vtile_off, g->q, g->sv, want_v ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -876,7 +892,7 @@ cudaError_t seg_bottom_up(void *p)
 cudaError_t seg_compact(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    const cudaError_t r = step_compact(c.g, c.g->dl_stream);
+    const cudaError_t r = step_compact(c.g, c.want_v, c.g->dl_stream);
     if (r != cudaSuccess || !c.log) return r;
     log_append_kernel<<<4 * num_sms(), 256, 0, c.g->dl_stream>>>(c.g->ls, c.g->ctr, c.g->qs, c.g->bs, c.g->vs, c.log,
                                                                  c.want_v ? 1 : 0);
@@ -1198,7 +1214,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
 
         // 5. compaction (+ V_{d+1} positions, cleared scratch for the next level)
         tm.begin(FQ_K_COMPACT);
-        FQ_TRY(step_compact(g, st));
+        FQ_TRY(step_compact(g, want_visited, st));
         tm.end(FQ_K_COMPACT, 3);
 
         FQ_TRY(cudaMemcpyAsync(g->host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));

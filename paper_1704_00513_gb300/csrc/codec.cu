@@ -6,12 +6,12 @@
 // every block's payload is 16*b_k bytes, so it starts on a 16-byte boundary and a warp moves
 // it with b_k 128-bit accesses.
 //
-// Encode = 3 launches: widths (one warp per 128-id block: gaps, max, bit length, sortedness),
-// plan (one CTA: scan of per-tile width sums, packed/raw choice, headers), pack (one warp per
-// block: bits OR-ed into a shared-memory staging row, then b_k vector stores).
-// Decode = 2 launches: plan (one CTA: header and size validation, scan of widths into per-block
-// payload offsets), unpack (one warp per block: b_k vector loads, slot extraction, warp prefix
-// sum of the gaps, 128-bit stores).
+// Encode = 2 launches: widths (one warp per 8 blocks: gaps, widths, bases, sortedness, per-tile
+// width sums) and pack (packed/raw decision, headers, offsets, bits assembled with warp shuffles,
+// vector stores -- or the raw body).  Decode = 3 launches: per-tile width sums, plan (one CTA:
+// header and size validation, scan of the tile sums), unpack (one warp per 8 blocks: the group's
+// payload staged in shared memory by one TMA bulk copy, slot extraction, warp prefix sum of the
+// gaps, 128-bit stores).
 #include <algorithm>
 #include <cstdio>
 
@@ -127,7 +127,6 @@ struct EncArgs {
     uint64_t *m_out_bytes;
     const uint64_t *m_words;
     uint64_t m_nbits;
-    uint32_t subs;          // 32 KB sub-tiles per look-back tile (1 for small inputs, kSubs for large)
 };
 
 struct DecArgs {
@@ -144,82 +143,97 @@ struct DecArgs {
 };
 
 __device__ __forceinline__ uint64_t enc_count(const EncArgs &a) { return a.n_dev ? *a.n_dev : a.n_host; }
-// ---- single-pass encode ----
+// ---- encode: widths kernel + pack kernel ----
 //
-// One kernel computes widths, the payload offsets and the packed words in one read of the ids.
-// Tiles of 64 blocks (8192 ids) are handed out in order through a ticket counter; each CTA keeps
-// its tile's ids in registers (8 blocks x 4 ids per lane), publishes the tile's width sum, finds
-// the sum over all earlier tiles by a decoupled look-back over their published words, then packs.
-// Tiles are taken in ticket order, so every tile a CTA waits for is held by a CTA that is already
-// running; the waits are bounded anyway (kSpinLimit polls, then FQ_ETIMEOUT).  Packed words are
-// written only where they fit below the raw size: if the raw form wins, enc_fixup_kernel writes
-// it over them.  The CTA holding the last tile decides packed/raw and writes the headers.
+// W (one warp per group of 8 blocks, one CTA per 64-block tile): gaps, block widths and bases,
+// the sortedness check, per-tile width sums, and the grand width sum (one atomic per tile).
+// P: every CTA takes the packed/raw decision from the grand sum on its own (the same pure
+// function the header writer uses), then packs the tiles it owns -- a tile's payload offset is
+// the sum of the earlier tiles' width sums, added up incrementally by the CTA -- or copies the
+// raw body.  The id count may live in device memory (n_dev), so the launches need no host sync.
 
 __device__ __forceinline__ uint64_t fb_raw_size(uint64_t nbits) { return 16u + dpad16(8u * dcdiv(nbits, 64)); }
 
-// Decide the modes, write headers and sizes.  Called by one thread after every tile published.
-__device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total)
+// Modes and sizes of the output (and of its mirror) from the id count and the width sum.  A pure
+// function of its inputs, so every CTA of the pack kernel takes the same decision on its own.
+struct EncPlan {
+    uint32_t mode, mode2;
+    uint64_t size, size2;
+    int32_t err;          // FQ_OK, or the error the header writer records
+    uint64_t err_detail;
+    bool fatal;           // the main output is not written at all
+};
+
+__device__ EncPlan enc_decide(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total, int32_t code)
 {
-    Ctl *c = a.s.ctl;
-    __threadfence();
-    c->n = n;
-    c->nb = nb;
-    c->total_b = total;
-    c->fq_offset = a.fb ? 16u : 0u;
-    const int32_t code = *reinterpret_cast<volatile int32_t *>(&c->code);
+    EncPlan p{kModeNone, kModeNone, 0, 0, FQ_OK, 0, false};
     if (code != FQ_OK) {
-        c->mode = kModeNone;
-        c->mode2 = kModeNone;
-        *a.out_bytes = 0;
-        if (a.m_out) *a.m_out_bytes = 0;
-        return;
+        p.fatal = true;
+        return p;
     }
     const uint64_t packed = 16u + dpad16(5u * nb) + 16u * total;
     const uint64_t raw = 16u + dpad16(4u * n);
     const bool is_packed = n > 0 && packed < raw;
     const uint64_t fq_size = is_packed ? packed : raw;
     const uint32_t fq_mode = is_packed ? kModePacked : kModeRaw;
-    uint32_t mode = fq_mode;
-    uint64_t size = fq_size;
+    p.mode = fq_mode;
+    p.size = fq_size;
     if (a.fb) {
         const uint64_t fbr = fb_raw_size(a.nbits);
         if (16u + fq_size >= fbr) {
-            mode = kModeFbRaw;
-            size = fbr;
+            p.mode = kModeFbRaw;
+            p.size = fbr;
         } else {
-            size = 16u + fq_size;
+            p.size = 16u + fq_size;
         }
     }
-    uint32_t mode2 = kModeNone;
-    uint64_t size2 = 0;
     if (a.m_out) {
         const uint64_t fbr = fb_raw_size(a.m_nbits);
         if (2u * n > a.m_nbits) {
-            set_error(c, FQ_EINVAL, kWhereEncPlan, n);  // the mirror is only defined for SET mode
+            p.err = FQ_EINVAL;  // the mirror is only defined for SET mode
+            p.err_detail = n;
         } else if (16u + fq_size >= fbr) {
-            mode2 = kModeFbRaw;
-            size2 = fbr;
+            p.mode2 = kModeFbRaw;
+            p.size2 = fbr;
         } else {
-            mode2 = fq_mode;
-            size2 = 16u + fq_size;
+            p.mode2 = fq_mode;
+            p.size2 = 16u + fq_size;
         }
-        if (size2 > a.m_cap) {
-            set_error(c, FQ_ENOSPC, kWhereEncPlan, size2);
-            mode2 = kModeNone;
+        if (p.size2 > a.m_cap) {
+            p.err = FQ_ENOSPC;
+            p.err_detail = p.size2;
+            p.mode2 = kModeNone;
         }
     }
-    if (size > a.cap) {
-        set_error(c, FQ_ENOSPC, kWhereEncPlan, size);
+    if (p.size > a.cap) {
+        p.err = FQ_ENOSPC;
+        p.err_detail = p.size;
+        p.mode = p.mode2 = kModeNone;
+        p.fatal = true;
+    }
+    return p;
+}
+
+// Record the decision, write the headers and sizes.  One thread, after every widths-kernel write.
+__device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total, const EncPlan &p)
+{
+    Ctl *c = a.s.ctl;
+    c->n = n;
+    c->nb = nb;
+    c->total_b = total;
+    c->fq_offset = a.fb ? 16u : 0u;
+    if (p.err != FQ_OK) set_error(c, p.err, kWhereEncPlan, p.err_detail);
+    if (p.fatal) {
         c->mode = kModeNone;
         c->mode2 = kModeNone;
-        *a.out_bytes = size;
+        *a.out_bytes = p.err == FQ_ENOSPC ? p.size : 0;
         if (a.m_out) *a.m_out_bytes = 0;
         return;
     }
     // headers (+ the zero pad between the width bytes and the payload of a packed stream)
     for (int which = 0; which < 2; which++) {
         uint8_t *base = which == 0 ? a.out : a.m_out;
-        const uint32_t md = which == 0 ? mode : mode2;
+        const uint32_t md = which == 0 ? p.mode : p.mode2;
         if (!base || md == kModeNone) continue;
         uint32_t *h = reinterpret_cast<uint32_t *>(base);
         const bool fbc = which == 1 || a.fb;
@@ -234,213 +248,18 @@ __device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned
         if (md == kModePacked) {
             h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
             uint8_t *fq = reinterpret_cast<uint8_t *>(h);
-            for (uint64_t p = 16u + 5u * nb; p < 16u + dpad16(5u * nb); p++) fq[p] = 0;
+            for (uint64_t q = 16u + 5u * nb; q < 16u + dpad16(5u * nb); q++) fq[q] = 0;
         } else if (md == kModeRaw) {
             h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
         }
     }
-    c->mode = mode;
-    c->mode2 = mode2;
-    c->out_bytes = size;
-    c->out2_bytes = size2;
-    *a.out_bytes = size;
-    if (a.m_out) *a.m_out_bytes = size2;
+    c->mode = p.mode;
+    c->mode2 = p.mode2;
+    c->out_bytes = p.size;
+    c->out2_bytes = p.size2;
+    *a.out_bytes = p.size;
+    if (a.m_out) *a.m_out_bytes = p.size2;
 }
-
-constexpr uint32_t kSubIds = kTileBlocks * kBlock;    // 8192 ids = 32 KB per TMA stage
-constexpr uint32_t kSubs = 4;                         // sub-tiles per encode tile
-constexpr uint32_t kEncTileBlocks = kSubs * kTileBlocks;  // 256 blocks = 32768 ids per look-back
-constexpr size_t kOnepassSmem = 2 * kSubIds * sizeof(uint32_t);
-
-
-// Single pass over the ids: tiles of 256 blocks are handed out in ticket order.  Pass A streams
-// the tile's four 32 KB sub-tiles through two shared-memory stages filled by TMA bulk copies
-// (the next sub-tile is in flight while one is measured) and records every block's width and
-// base; one decoupled look-back per tile gives the payload offset; pass B re-reads the tile's
-// ids (L2-resident by then) and packs.  The CTA holding the last tile decides packed/raw.
-__global__ void __launch_bounds__(kEncThreads, 3) enc_onepass_kernel(EncArgs a)
-{
-    extern __shared__ __align__(128) uint32_t sbuf[];  // [2][kSubIds]
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t s_tile, s_next;
-    __shared__ uint32_t sw[kEncTileBlocks];     // widths of the tile's blocks
-    __shared__ uint32_t spre[kEncTileBlocks];   // exclusive prefix of the widths inside the tile
-    __shared__ unsigned long long s_excl, s_total;
-    __shared__ unsigned long long s_red[kEncWarps];
-    __shared__ uint32_t s_first;
-    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
-    Ctl *c = a.s.ctl;
-    const uint64_t n = enc_count(a);
-    const uint64_t nb = dcdiv(n, kBlock);
-    const uint32_t subs = a.subs;
-    const uint64_t nsubs = dcdiv(nb, kTileBlocks);
-    const uint64_t ntiles = dcdiv(nsubs, subs);
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint64_t fq_off = a.fb ? 16u : 0u;
-    const uint64_t payload = 16u + dpad16(5u * nb);
-    // bytes of each output that may be written before the mode is known: anything beyond is only
-    // needed by a packed stream that is not smaller than the raw form, which is never kept
-    uint64_t bound = min(a.cap, fq_off + 16u + dpad16(4u * n));
-    if (a.fb) bound = min(bound, fb_raw_size(a.nbits));
-    uint64_t bound2 = 0;
-    if (a.m_out) bound2 = min(a.m_cap, min(16u + 16u + dpad16(4u * n), fb_raw_size(a.m_nbits)));
-
-    if (ntiles == 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, 0ull);
-        return;
-    }
-    const bool aligned = (reinterpret_cast<uintptr_t>(a.ids) & 15u) == 0;
-    auto bulk_sub = [&](uint64_t sub) { return aligned && (sub + 1) * kSubIds <= n; };
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init_fence();
-        s_next = atomicAdd(&c->tile_ticket, 1u);
-    }
-    __syncthreads();
-    uint32_t phase0 = 0u, phase1 = 0u;  // completed-phase parity of each stage's barrier
-    // Sub-tiles are consumed in the sequence: tile t's subs, then tile tn's subs, ...; element i
-    // is staged in stage i & 1.  Starting on element i issues the copy of element i + 1 into the
-    // other stage, whose previous element was consumed before the last barrier.
-    uint32_t seq = 0;
-    if (threadIdx.x == 0 && s_next < ntiles) {
-        const uint64_t sub = (uint64_t)s_next * subs;
-        if (sub < nsubs && bulk_sub(sub)) bulk_load(sbuf, a.ids + sub * kSubIds, kSubIds * 4u, &bars[0]);
-    }
-
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = s_next;
-            s_next = (s_next < ntiles) ? atomicAdd(&c->tile_ticket, 1u) : (uint32_t)ntiles;
-        }
-        __syncthreads();
-        const uint64_t t = s_tile, tn = s_next;
-        if (t >= ntiles) break;
-
-        // pass A: widths and bases, sub-tile by sub-tile
-        unsigned long long bad = ~0ull;
-        for (uint32_t j = 0; j < subs; j++, seq++) {
-            const uint64_t sub = t * subs + j;
-            const uint32_t stage = seq & 1u;
-            uint32_t *s = sbuf + stage * kSubIds;
-            if (threadIdx.x == 0) {
-                const uint64_t nxt = (j + 1 < subs) ? sub + 1 : (tn < ntiles ? (uint64_t)tn * subs : nsubs);
-                if (nxt < nsubs && bulk_sub(nxt))
-                    bulk_load(sbuf + (stage ^ 1u) * kSubIds, a.ids + nxt * kSubIds, kSubIds * 4u, &bars[stage ^ 1u]);
-            }
-            if (sub < nsubs) {
-                if (bulk_sub(sub)) {
-                    if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(c, FQ_ETIMEOUT, kWhereEncWidths, sub);
-                    if (stage) phase1 ^= 1u;
-                    else phase0 ^= 1u;
-                } else {  // ragged end (or unaligned ids): plain loads, zero past n
-                    for (uint32_t i = threadIdx.x; i < kSubIds; i += kEncThreads) {
-                        const uint64_t gi = sub * kSubIds + i;
-                        s[i] = gi < n ? a.ids[gi] : 0u;
-                    }
-                    __syncthreads();
-                }
-#pragma unroll 4
-                for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
-                    const uint32_t lb = warp * kBlocksPerWarp + i;  // block inside the sub-tile
-                    const uint64_t k = sub * kTileBlocks + lb;
-                    uint32_t b = 0;
-                    if (k < nb) {
-                        const uint4 q = *reinterpret_cast<const uint4 *>(s + lb * kBlock + 4u * lane);
-                        const uint32_t v[4] = {q.x, q.y, q.z, q.w};
-                        uint32_t prevb = 0;
-                        if (lane == 0 && k > 0) prevb = lb > 0 ? s[lb * kBlock - 1] : a.ids[k * kBlock - 1];
-                        uint32_t g[4];
-                        gaps_of(v, prevb, k > 0, k, n, lane, g, &bad);
-                        b = bitlen32(__reduce_or_sync(0xffffffffu, g[0] | g[1] | g[2] | g[3]));
-                        if (lane == 0) {
-                            const uint64_t pb = fq_off + 16u + 4u * k;
-                            if (pb + 4 <= bound) *reinterpret_cast<uint32_t *>(a.out + pb) = v[0];
-                            if (a.m_out && 32u + 4u * k + 4 <= bound2) *reinterpret_cast<uint32_t *>(a.m_out + 32u + 4u * k) = v[0];
-                        }
-                    }
-                    if (lane == 0) sw[j * kTileBlocks + lb] = b;
-                }
-            } else {
-                if (threadIdx.x < kTileBlocks) sw[j * kTileBlocks + threadIdx.x] = 0;
-            }
-            __syncthreads();  // stage consumed: it may be refilled from the next element on
-        }
-        if (bad != ~0ull) set_error(c, FQ_EUNSORTED, kWhereEncWidths, bad);
-        if (subs < kSubs && threadIdx.x >= subs * kTileBlocks) sw[threadIdx.x] = 0;  // unused width slots
-        __syncthreads();
-
-        // tile prefix over its 256 widths (warp 0: 8 per lane), publication, look-back
-        if (warp == 0) {
-            uint32_t x[8], sum = 0;
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                x[i] = sw[8 * lane + i];
-                sum += x[i];
-            }
-            const uint32_t incl = warp_incl_scan(sum);
-            uint32_t run = incl - sum;
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                spre[8 * lane + i] = run;
-                run += x[i];
-            }
-            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane == 0) {
-                publish(a.s.tile_status, t, t == 0 ? kFlagPrefix : kFlagAgg, total);
-                s_total = total;
-            }
-        }
-        __syncthreads();
-        unsigned long long excl = 0;
-        if (t > 0) excl = lookback(a.s.tile_status, t, c, s_red, &s_first);
-        if (threadIdx.x == 0) {
-            if (t > 0) publish(a.s.tile_status, t, kFlagPrefix, excl + s_total);
-            s_excl = excl;
-        }
-        __syncthreads();
-        excl = s_excl;
-
-        // width bytes of the tile's blocks
-        if (threadIdx.x < subs * kTileBlocks) {
-            const uint64_t k = t * subs * kTileBlocks + threadIdx.x;
-            if (k < nb) {
-                const uint8_t b = (uint8_t)sw[threadIdx.x];
-                const uint64_t pw = fq_off + 16u + 4u * nb + k;
-                if (pw + 1 <= bound) a.out[pw] = b;
-                if (a.m_out && 32u + 4u * nb + k + 1 <= bound2) a.m_out[32u + 4u * nb + k] = b;
-            }
-        }
-
-        // pass B: pack (ids re-read; they were read moments ago, so from L2)
-        const uint32_t per_warp = subs * kTileBlocks / kEncWarps;
-        for (uint32_t i = 0; i < per_warp; i++) {
-            const uint32_t lb = warp * per_warp + i;
-            const uint64_t k = t * subs * kTileBlocks + lb;
-            if (k >= nb) break;
-            const uint32_t b = sw[lb];
-            if (b == 0) continue;
-            uint32_t v[4], g[4];
-            load4_guard(a.ids, k * kBlock + 4u * lane, n, v);
-            unsigned long long dummy = ~0ull;
-            gaps_of(v, 0u, false, k, n, lane, g, &dummy);
-            uint32_t w4[4];
-            pack_block_words(g, b, pk[warp], lane, w4);
-            const uint64_t rel = payload + 16u * (excl + spre[lb]);
-            store_block_words(a.out + fq_off + rel, w4, b, lane, fq_off + rel, bound);
-            if (a.m_out) store_block_words(a.m_out + 16u + rel, w4, b, lane, 16u + rel, bound2);
-        }
-
-        if (t == ntiles - 1 && threadIdx.x == 0) enc_finalize(a, n, nb, excl + s_total);
-        __syncthreads();
-    }
-}
-
-// ---- streaming encode for large inputs: widths pass, one-CTA plan, pack pass ----
-//
-// When the input is far larger than L2 the single pass cannot keep its tiles on chip between
-// measuring and packing anyway, so three high-occupancy streaming kernels do better: every warp
-// issues the loads of its eight blocks before using any of them, and nothing waits on another CTA.
 
 __device__ __forceinline__ void load_blocks8(const uint32_t *ids, uint64_t k0, uint64_t n, uint32_t lane,
                                              uint32_t v[kBlocksPerWarp][4])
@@ -449,10 +268,11 @@ __device__ __forceinline__ void load_blocks8(const uint32_t *ids, uint64_t k0, u
     for (uint32_t i = 0; i < kBlocksPerWarp; i++) load4_guard(ids, (k0 + i) * kBlock + 4u * lane, n, v[i]);
 }
 
-__global__ void __launch_bounds__(kEncThreads, 4) enc_s_widths_kernel(EncArgs a)
+// W: every warp issues the loads of its eight blocks before using any of them.
+__global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
 {
     __shared__ uint32_t ws[kEncWarps];
-    const uint64_t n = a.n_host, nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint64_t k0 = t * kTileBlocks + warp * kBlocksPerWarp;
@@ -482,79 +302,18 @@ __global__ void __launch_bounds__(kEncThreads, 4) enc_s_widths_kernel(EncArgs a)
             uint32_t tsum = 0;
             for (uint32_t w = 0; w < kEncWarps; w++) tsum += ws[w];
             a.s.tile_sum[t] = tsum;
+            if (tsum) atomicAdd(&a.s.ctl->total_b, (unsigned long long)tsum);
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) enc_s_plan_kernel(EncArgs a)
+// Raw bodies (FQ raw ids, or FB raw words) for whichever output the decision chose them; every
+// thread of the grid takes a strided share.
+__device__ void enc_raw_bodies(const EncArgs &a, const EncPlan &p, uint64_t n, uint64_t tid, uint64_t stride)
 {
-    __shared__ unsigned long long sm[33];
-    const uint64_t n = a.n_host, nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
-    const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
-    __syncthreads();
-    if (threadIdx.x == 0) enc_finalize(a, n, nb, total);
-}
-
-// One warp per group of kBlocksPerWarp consecutive blocks (groups never straddle a tile), with no
-// CTA barrier: each warp forms its own offsets from the tile's width bytes (two per lane, one warp
-// scan) and the tile's payload offset, and copies its blocks' bases and widths into the header.
-__global__ void __launch_bounds__(kEncThreads) enc_s_pack_kernel(EncArgs a)
-{
-    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
-    const Ctl *c = a.s.ctl;
-    if (c->mode != kModePacked) return;  // raw bodies come from enc_fixup_kernel
-    const uint64_t n = a.n_host, nb = dcdiv(n, kBlock);
-    const uint64_t ngroups = dcdiv(nb, kBlocksPerWarp);
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint64_t payload = 16u + dpad16(5u * nb);
-    constexpr uint32_t kGroupsPerTile = kTileBlocks / kBlocksPerWarp;
-    for (uint64_t grp = (uint64_t)blockIdx.x * kEncWarps + warp; grp < ngroups; grp += (uint64_t)gridDim.x * kEncWarps) {
-        const uint64_t k0 = grp * kBlocksPerWarp, t = grp / kGroupsPerTile;
-        const uint32_t git = (uint32_t)(grp % kGroupsPerTile);  // group inside the tile
-        uint32_t v[kBlocksPerWarp][4];
-        load_blocks8(a.ids, k0, n, lane, v);
-        const uint64_t kk = t * kTileBlocks + 2 * lane;
-        const uint32_t x0 = kk < nb ? a.s.widths[kk] : 0u, x1 = kk + 1 < nb ? a.s.widths[kk + 1] : 0u;
-        const uint32_t tile_base = a.s.tile_off[t];
-        const uint32_t my_base = (lane < kBlocksPerWarp && k0 + lane < nb) ? a.s.bases[k0 + lane] : 0u;
-        const uint32_t incl = warp_incl_scan(x0 + x1);
-        // lane l describes blocks 2l and 2l+1 of the tile: exclusive width prefix | b(2l) << 16 | b(2l+1) << 24
-        const uint32_t info = (incl - x0 - x1) | (x0 << 16) | (x1 << 24);
-        const uint32_t mine = __shfl_sync(0xffffffffu, info, (git * kBlocksPerWarp + (lane & 7u)) >> 1);
-        if (lane < kBlocksPerWarp && k0 + lane < nb) {
-            reinterpret_cast<uint32_t *>(a.out + 16)[k0 + lane] = my_base;
-            a.out[16 + 4 * nb + k0 + lane] = (uint8_t)((lane & 1u) ? (mine >> 24) : ((mine >> 16) & 0xffu));
-        }
-#pragma unroll
-        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
-            const uint64_t k = k0 + i;
-            const uint32_t in = __shfl_sync(0xffffffffu, info, (git * kBlocksPerWarp + i) >> 1);
-            const uint32_t b = (i & 1u) ? (in >> 24) : ((in >> 16) & 0xffu);
-            const uint32_t pre = (in & 0xffffu) + ((i & 1u) ? ((in >> 16) & 0xffu) : 0u);
-            if (k >= nb || b == 0) continue;
-            uint32_t g[4];
-            unsigned long long dummy = ~0ull;
-            gaps_of(v[i], 0u, false, k, n, lane, g, &dummy);
-            uint32_t w4[4];
-            pack_block_words(g, b, pk[warp], lane, w4);
-            const uint64_t rel = payload + 16u * ((uint64_t)tile_base + pre);
-            store_block_words(a.out + rel, w4, b, lane, rel, ~0ull);
-        }
-    }
-}
-
-// Raw bodies (FQ raw ids, or FB raw words) for whichever output the finalisation chose them.
-__global__ void enc_fixup_kernel(EncArgs a)
-{
-    const Ctl *c = a.s.ctl;
-    const uint32_t mode = c->mode, mode2 = a.m_out ? c->mode2 : kModeNone;
-    if (mode != kModeRaw && mode != kModeFbRaw && mode2 != kModeRaw && mode2 != kModeFbRaw) return;
-    const uint64_t n = c->n;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int which = 0; which < 2; which++) {
-        const uint32_t md = which == 0 ? mode : mode2;
+        const uint32_t md = which == 0 ? p.mode : p.mode2;
         uint8_t *base = which == 0 ? a.out : a.m_out;
         if (md == kModeRaw) {
             uint32_t *dst = reinterpret_cast<uint32_t *>(base + (which == 0 ? (a.fb ? 16u : 0u) : 16u) + 16u);
@@ -575,6 +334,78 @@ __global__ void enc_fixup_kernel(EncArgs a)
                 }
                 dst[i] = w;
             }
+        }
+    }
+}
+
+// P: decision, headers (CTA 0), then the packed body tile by tile -- one warp per group of
+// kBlocksPerWarp blocks, offsets from the tile's width bytes (two per lane, one warp scan) -- or
+// the raw bodies.  Packed words go to the output and, identical, to the mirror's inner stream.
+__global__ void __launch_bounds__(kEncThreads) enc_pack_kernel(EncArgs a)
+{
+    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
+    __shared__ unsigned long long s_part[kEncWarps];
+    const Ctl *c = a.s.ctl;
+    const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    const unsigned long long total = c->total_b;
+    const EncPlan p = enc_decide(a, n, nb, total, *reinterpret_cast<const volatile int32_t *>(&c->code));
+    if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, total, p);
+    if (p.fatal) return;
+    enc_raw_bodies(a, p, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+    const bool pk1 = p.mode == kModePacked, pk2 = p.mode2 == kModePacked;
+    if (!pk1 && !pk2) return;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint64_t off1 = a.fb ? 16u : 0u, off2 = 16u;  // where each output's FQ stream starts
+    const uint64_t payload = 16u + dpad16(5u * nb);
+    unsigned long long prefix = 0;  // width sum of tiles [0, done)
+    uint64_t done = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // add the width sums of tiles [done, t)
+        unsigned long long part = 0;
+        for (uint64_t i = done + threadIdx.x; i < t; i += blockDim.x) part += a.s.tile_sum[i];
+        part = warp_sum64(part);
+        if (lane == 0) s_part[warp] = part;
+        __syncthreads();
+        for (uint32_t w = 0; w < kEncWarps; w++) prefix += s_part[w];
+        __syncthreads();
+        done = t;
+        const uint64_t k0 = t * kTileBlocks + warp * kBlocksPerWarp;
+        if (k0 >= nb) continue;
+        uint32_t v[kBlocksPerWarp][4];
+        load_blocks8(a.ids, k0, n, lane, v);
+        const uint64_t kk = t * kTileBlocks + 2 * lane;
+        const uint32_t x0 = kk < nb ? a.s.widths[kk] : 0u, x1 = kk + 1 < nb ? a.s.widths[kk + 1] : 0u;
+        const uint32_t my_base = (lane < kBlocksPerWarp && k0 + lane < nb) ? a.s.bases[k0 + lane] : 0u;
+        const uint32_t incl = warp_incl_scan(x0 + x1);
+        // lane l describes blocks 2l and 2l+1 of the tile: exclusive width prefix | b(2l) << 16 | b(2l+1) << 24
+        const uint32_t info = (incl - x0 - x1) | (x0 << 16) | (x1 << 24);
+        const uint32_t mine = __shfl_sync(0xffffffffu, info, (warp * kBlocksPerWarp + (lane & 7u)) >> 1);
+        if (lane < kBlocksPerWarp && k0 + lane < nb) {
+            const uint8_t wb = (uint8_t)((lane & 1u) ? (mine >> 24) : ((mine >> 16) & 0xffu));
+            if (pk1) {
+                reinterpret_cast<uint32_t *>(a.out + off1 + 16)[k0 + lane] = my_base;
+                a.out[off1 + 16 + 4 * nb + k0 + lane] = wb;
+            }
+            if (pk2) {
+                reinterpret_cast<uint32_t *>(a.m_out + off2 + 16)[k0 + lane] = my_base;
+                a.m_out[off2 + 16 + 4 * nb + k0 + lane] = wb;
+            }
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+            const uint64_t k = k0 + i;
+            const uint32_t in = __shfl_sync(0xffffffffu, info, (warp * kBlocksPerWarp + i) >> 1);
+            const uint32_t b = (i & 1u) ? (in >> 24) : ((in >> 16) & 0xffu);
+            const uint32_t pre = (in & 0xffffu) + ((i & 1u) ? ((in >> 16) & 0xffu) : 0u);
+            if (k >= nb || b == 0) continue;
+            uint32_t g[4];
+            unsigned long long dummy = ~0ull;
+            gaps_of(v[i], 0u, false, k, n, lane, g, &dummy);
+            uint32_t w4[4];
+            pack_block_words(g, b, pk[warp], lane, w4);
+            const uint64_t rel = payload + 16u * (prefix + pre);
+            if (pk1) store_block_words(a.out + off1 + rel, w4, b, lane, 0, ~0ull);
+            if (pk2) store_block_words(a.m_out + off2 + rel, w4, b, lane, 0, ~0ull);
         }
     }
 }
@@ -1029,7 +860,6 @@ uint64_t resident_grid(K kernel, int threads, int *cache)
     }
     return (uint64_t)cache[dev] * num_sms();
 }
-constexpr uint64_t kStreamingIds = 1ull << 22;  // 16 MB of ids: beyond this the streaming encoder is used
 
 // Kernels with more than 48 KB of dynamic shared memory must opt in, once per device.
 template <typename K>
@@ -1051,20 +881,19 @@ cudaError_t prepare_unpack()
     return allow_smem(dec_unpack_kernel, kDecSmem, done);
 }
 
+// W then P, with grids of at most one resident wave (both kernels stride over their tiles).
 cudaError_t launch_encode(EncArgs a, uint64_t n_max, cudaStream_t st)
 {
-    // large inputs amortise each look-back over kSubs sub-tiles; smaller ones need every CTA busy
-    const uint64_t nsubs = std::max<uint64_t>(1, cdiv(cdiv(n_max, kBlock), kTileBlocks));
-    const uint32_t subs = nsubs >= (uint64_t)kSubs * 6 * num_sms() ? kSubs : 1u;
-    a.subs = subs;
-    const uint64_t tiles = cdiv(nsubs, subs);
-    static bool attr_set[64] = {false};
-    FQ_CUDA_TRY(allow_smem(enc_onepass_kernel, kOnepassSmem, attr_set));
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(tiles, (uint64_t)3 * num_sms());
-    enc_onepass_kernel<<<grid, kEncThreads, kOnepassSmem, st>>>(a);
-    const uint64_t raw_words = std::max<uint64_t>(cdiv(n_max, 4) * 4, a.fb ? cdiv(a.nbits, 64) : 0);
-    enc_fixup_kernel<<<grid_for(std::max<uint64_t>(raw_words, a.m_out ? cdiv(a.m_nbits, 64) : 0), 256, 4 * num_sms()),
-                       256, 0, st>>>(a);
+    static int occ_w[64], occ_p[64];
+    const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(n_max));
+    uint64_t raw_items = cdiv(n_max, 4) * 4;  // the raw bodies P may have to copy instead
+    if (a.fb) raw_items = std::max<uint64_t>(raw_items, cdiv(a.nbits, 64));
+    if (a.m_out) raw_items = std::max<uint64_t>(raw_items, cdiv(a.m_nbits, 64));
+    const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_widths_kernel, kEncThreads, occ_w));
+    const uint32_t gp = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads)),
+                                                     resident_grid(enc_pack_kernel, kEncThreads, occ_p));
+    enc_widths_kernel<<<gw, kEncThreads, 0, st>>>(a);
+    enc_pack_kernel<<<gp, kEncThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1082,20 +911,7 @@ cudaError_t reset_status(const Scratch &s, uint64_t max_ids, cudaStream_t st)
 cudaError_t encode_fq(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max, uint8_t *out,
                       uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
 {
-    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0, 1};
-    if (!n_dev && n_host >= kStreamingIds && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0) {
-        // far larger than L2: three streaming kernels (widths, plan, pack) + the raw fix-up
-        static int occ_widths[64], occ_pack[64];
-        const uint64_t tiles = enc_tiles(n_host);
-        const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_s_widths_kernel, kEncThreads, occ_widths));
-        const uint32_t gp = (uint32_t)std::min<uint64_t>(tiles * (kTileBlocks / kBlocksPerWarp) / kEncWarps + 1,
-                                                         resident_grid(enc_s_pack_kernel, kEncThreads, occ_pack));
-        enc_s_widths_kernel<<<gw, kEncThreads, 0, st>>>(a);
-        enc_s_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
-        enc_s_pack_kernel<<<gp, kEncThreads, 0, st>>>(a);
-        enc_fixup_kernel<<<grid_for(cdiv(n_host, 4) * 4, 256, 4 * num_sms()), 256, 0, st>>>(a);
-        return cudaGetLastError();
-    }
+    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0};
     return launch_encode(a, n_dev ? n_max : n_host, st);
 }
 
@@ -1103,7 +919,7 @@ cudaError_t encode_fq_mirror(const uint32_t *ids, uint64_t n_host, const uint64_
                              uint8_t *out, uint64_t cap, uint64_t *out_bytes, const Mirror &m, const Scratch &s,
                              cudaStream_t st)
 {
-    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words, m.nbits, 1};
+    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words, m.nbits};
     return launch_encode(a, n_dev ? n_max : n_host, st);
 }
 
@@ -1111,7 +927,7 @@ cudaError_t encode_fb_positions(const uint64_t *words, uint64_t nbits, uint8_t *
                                 uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
 {
     EncArgs a{s.positions, 0, reinterpret_cast<const uint64_t *>(&s.ctl->n), out, cap, out_bytes, 1, nbits, words, s,
-              nullptr, 0, nullptr, nullptr, 0, 1};
+              nullptr, 0, nullptr, nullptr, 0};
     return launch_encode(a, nbits / 2 + 1, st);
 }
 
