@@ -94,10 +94,9 @@ __global__ void bfs_init_kernel(const int64_t *off, uint32_t root, uint64_t n, i
                                 Scratch sq, Scratch sv, const LoopState *ls)
 {
     if (ls) root = ls->p.root;  // device-driven loop: the root is a run parameter
-    reset_scratch_device(sq, 1, threadIdx.x, blockDim.x);
-    reset_scratch_device(sv, 1, threadIdx.x, blockDim.x);
-    __syncthreads();
     if (threadIdx.x != 0) return;
+    reset_scratch_device(sq);
+    reset_scratch_device(sv);
     depth[root] = 0;
     if (parent) parent[root] = root;
     q[0] = root;
@@ -382,12 +381,9 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
         ctr->r_detail_v = sv.ctl->detail;
     }
     __syncthreads();
-    const uint64_t qtiles = min((uint64_t)sq.etiles_cap, (uint64_t)((s_nf + 8191) / 8192 + 1));
-    const uint64_t vtiles = min((uint64_t)sv.etiles_cap, (uint64_t)((vcount + 8191) / 8192 + 1));
-    reset_scratch_device(sq, qtiles, threadIdx.x, blockDim.x);
-    reset_scratch_device(sv, vtiles, threadIdx.x, blockDim.x);
-    __syncthreads();
     if (threadIdx.x == 0) {
+        reset_scratch_device(sq);
+        reset_scratch_device(sv);
         sv.ctl->n = vcount;
         sv.ctl->fb_mode = set_mode ? kFbSet : kFbClear;
     }

@@ -24,7 +24,7 @@ namespace fq {
 
 namespace {
 struct Layout {
-    uint64_t widths, bases, block_off, tile_sum, tile_off, btile_cnt, btile_off, positions, tile_status, total;
+    uint64_t widths, bases, block_off, tile_sum, tile_off, btile_cnt, btile_off, positions, total;
     uint64_t ids_cap, nb_cap, etiles_cap, btiles_cap, pos_cap;
 };
 
@@ -47,7 +47,6 @@ Layout layout(uint64_t max_ids, uint64_t max_nbits)
     L.btile_cnt = o; o = align256(o + 4 * L.btiles_cap);
     L.btile_off = o; o = align256(o + 4 * L.btiles_cap);
     L.positions = o; o = align256(o + 4 * L.pos_cap);
-    L.tile_status = o; o = align256(o + 8 * L.etiles_cap);
     L.total = o;
     return L;
 }
@@ -71,7 +70,6 @@ Scratch carve(void *base, uint64_t max_ids, uint64_t max_nbits)
     s.btile_cnt = reinterpret_cast<uint32_t *>(b + L.btile_cnt);
     s.btile_off = reinterpret_cast<uint32_t *>(b + L.btile_off);
     s.positions = reinterpret_cast<uint32_t *>(b + L.positions);
-    s.tile_status = reinterpret_cast<unsigned long long *>(b + L.tile_status);
     s.ids_cap = L.ids_cap;
     s.nbits_cap = max_nbits;
     s.nb_cap = L.nb_cap;
@@ -341,7 +339,7 @@ __device__ void enc_raw_bodies(const EncArgs &a, const EncPlan &p, uint64_t n, u
 // P: decision, headers (CTA 0), then the packed body tile by tile -- one warp per group of
 // kBlocksPerWarp blocks, offsets from the tile's width bytes (two per lane, one warp scan) -- or
 // the raw bodies.  Packed words go to the output and, identical, to the mirror's inner stream.
-__global__ void __launch_bounds__(kEncThreads) enc_pack_kernel(EncArgs a)
+__global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
 {
     __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
     __shared__ unsigned long long s_part[kEncWarps];
@@ -832,10 +830,7 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
     }
 }
 
-__global__ void reset_status_kernel(Scratch s, uint64_t ntiles)
-{
-    reset_scratch_device(s, ntiles, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
+__global__ void reset_status_kernel(Scratch s) { reset_scratch_device(s); }
 
 uint32_t grid_for(uint64_t items, uint32_t per_cta, uint32_t max_ctas)
 {
@@ -903,8 +898,8 @@ cudaError_t launch_encode(EncArgs a, uint64_t n_max, cudaStream_t st)
 
 cudaError_t reset_status(const Scratch &s, uint64_t max_ids, cudaStream_t st)
 {
-    const uint64_t ntiles = std::min<uint64_t>(std::max<uint64_t>(1, enc_tiles(max_ids)), s.etiles_cap);
-    reset_status_kernel<<<grid_for(ntiles, 256, 64), 256, 0, st>>>(s, ntiles);
+    (void)max_ids;
+    reset_status_kernel<<<1, 1, 0, st>>>(s);
     return cudaGetLastError();
 }
 

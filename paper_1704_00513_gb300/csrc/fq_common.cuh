@@ -71,7 +71,6 @@ struct Scratch {
     uint32_t *btile_cnt;  // [btiles_cap]
     uint32_t *btile_off;  // [btiles_cap]
     uint32_t *positions;  // [pos_cap]  bitmap positions (FB)
-    unsigned long long *tile_status;  // [etiles_cap] single-pass encode look-back words
     uint64_t ids_cap;     // largest id count an encode/decode may see
     uint64_t nbits_cap;
     uint64_t nb_cap, etiles_cap, btiles_cap, pos_cap;
@@ -140,20 +139,17 @@ __device__ __forceinline__ void set_error(Ctl *c, int32_t code, uint32_t where, 
 
 // Clear a Scratch's control block (status OK, no mode) and its first ntiles look-back words;
 // called by threads tid = 0 .. nthreads-1 of one kernel.
-__device__ __forceinline__ void reset_scratch_device(const Scratch &s, uint64_t ntiles, uint32_t tid, uint32_t nthreads)
+__device__ __forceinline__ void reset_scratch_device(const Scratch &s)
 {
-    if (tid == 0) {
-        Ctl *c = s.ctl;
-        c->code = FQ_OK;
-        c->where = 0;
-        c->detail = ~0ull;
-        c->mode = kModeNone;
-        c->mode2 = kModeNone;
-        c->fb_mode = kFbRaw;
-        c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = 0;
-        c->tile_ticket = 0;
-    }
-    for (uint64_t i = tid; i < ntiles; i += nthreads) s.tile_status[i] = 0ull;
+    Ctl *c = s.ctl;
+    c->code = FQ_OK;
+    c->where = 0;
+    c->detail = ~0ull;
+    c->mode = kModeNone;
+    c->mode2 = kModeNone;
+    c->fb_mode = kFbRaw;
+    c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = 0;
+    c->tile_ticket = 0;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
