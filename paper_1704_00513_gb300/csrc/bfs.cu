@@ -332,35 +332,49 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
                                                                 Scratch sq, Scratch sv)
 {
     __shared__ unsigned long long sm[33];
-    __shared__ unsigned long long s_nf, s_vis;
     const uint64_t chunk = (ntiles + kScanThreads - 1) / kScanThreads;
-    const uint64_t t0 = (uint64_t)threadIdx.x * chunk, t1 = min(ntiles, t0 + chunk);
+    const uint64_t t0 = min(ntiles, (uint64_t)threadIdx.x * chunk), t1 = min(ntiles, t0 + chunk);
     const uint64_t tile_bits = 64ull * kCmpWords;
-    unsigned long long local = 0, total = 0;
-    for (uint64_t t = t0; t < t1; t++) local += tile_cnt[t];
-    unsigned long long run = cta_excl_scan64<kScanThreads>(local, sm, &total);
-    for (uint64_t t = t0; t < t1; t++) {
-        tile_off[t] = (uint32_t)run;
-        run += tile_cnt[t];
+    // one read of both count arrays (kScanWin at a time, every load of a window issued first)
+    unsigned long long lq = 0, lv = 0;
+    for (uint64_t w = t0; w < t1; w += kScanWin) {
+        uint32_t x[kScanWin], y[kScanWin];
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) {
+            x[i] = w + i < t1 ? tile_cnt[w + i] : 0u;
+            y[i] = w + i < t1 ? vis_cnt[w + i] : 0u;
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) {
+            lq += x[i];
+            lv += y[i];
+        }
     }
-    if (threadIdx.x == 0) s_nf = total;
-    local = 0;
-    for (uint64_t t = t0; t < t1; t++) local += vis_cnt[t];
-    cta_excl_scan64<kScanThreads>(local, sm, &total);
-    if (threadIdx.x == 0) s_vis = total;
-    __syncthreads();
-    const bool set_mode = 2ull * s_vis <= n;
-    local = 0;
-    for (uint64_t t = t0; t < t1; t++) {
-        const uint64_t bits = min(n, (t + 1) * tile_bits) - t * tile_bits;
-        local += set_mode ? vis_cnt[t] : bits - vis_cnt[t];
+    const unsigned long long lb = t1 > t0 ? min(n, t1 * tile_bits) - t0 * tile_bits : 0ull;  // bits in the chunk
+    unsigned long long nf_total = 0, vis_total = 0, total = 0;
+    unsigned long long run = cta_excl_scan64<kScanThreads>(lq, sm, &nf_total);
+    cta_excl_scan64<kScanThreads>(lv, sm, &vis_total);
+    const bool set_mode = 2ull * vis_total <= n;
+    unsigned long long vrun = cta_excl_scan64<kScanThreads>(set_mode ? lv : lb - lv, sm, &total);
+    for (uint64_t w = t0; w < t1; w += kScanWin) {
+        uint32_t x[kScanWin], y[kScanWin];
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) {
+            x[i] = w + i < t1 ? tile_cnt[w + i] : 0u;
+            y[i] = w + i < t1 ? vis_cnt[w + i] : 0u;
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kScanWin; i++) {
+            if (w + i >= t1) break;
+            const uint64_t t = w + i;
+            tile_off[t] = (uint32_t)run;
+            vtile_off[t] = (uint32_t)vrun;
+            run += x[i];
+            const uint64_t bits = min(n, (t + 1) * tile_bits) - t * tile_bits;
+            vrun += set_mode ? y[i] : bits - y[i];
+        }
     }
-    run = cta_excl_scan64<kScanThreads>(local, sm, &total);
-    for (uint64_t t = t0; t < t1; t++) {
-        vtile_off[t] = (uint32_t)run;
-        const uint64_t bits = min(n, (t + 1) * tile_bits) - t * tile_bits;
-        run += set_mode ? vis_cnt[t] : bits - vis_cnt[t];
-    }
+    const unsigned long long s_nf = nf_total, s_vis = vis_total;
     const unsigned long long vcount = total;
     // snapshot the level's live counters and codec status, then clear for the next level
     if (threadIdx.x == 0) {
@@ -379,9 +393,6 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
         ctr->r_err_v = sv.ctl->code;
         ctr->r_where_v = sv.ctl->where;
         ctr->r_detail_v = sv.ctl->detail;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
         reset_scratch_device(sq);
         reset_scratch_device(sv);
         sv.ctl->n = vcount;
