@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="fqbfs", choices=["fqbfs", "reference"])
     p.add_argument("--scale", type=int, default=24)
+    p.add_argument("--level-loop", default="device", choices=["device", "host"],
+                   help="BFS level loop driver for the timed pass: one CUDA graph per search (device) or the "
+                        "host loop (host); ncu sees kernels of graphs with conditional nodes only in host mode")
     p.add_argument("--edgefactor", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -290,7 +293,7 @@ def run_fqbfs(args, world, rank, local):
     parent = torch.empty(n, dtype=torch.int32, device=dev)
     # timed: the device-driven level loop (one graph launch per search, no host round trip per
     # level); profiled: the same roots through the host-driven loop with per-class event timing
-    flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP
+    flags = fqbfs.FQ_BFS_VISITED_STREAM | (fqbfs.FQ_BFS_DEVICE_LOOP if args.level_loop == "device" else 0)
     prof_flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_TIMING
     warm_roots, timed_roots = warm_and_timed(roots, world, rank, args.warmup, args.steps)
     stream = torch.cuda.current_stream()
@@ -400,7 +403,8 @@ def run_fqbfs(args, world, rank, local):
                            "edgefactor": args.edgefactor, "vertices": n, "directed_edges": int(cols.numel()),
                            "roots_per_rank": args.steps, "streams": "Q_d, B_d, V_d encoded every level",
                            "l2": "no flush: the 2.2 GB CSR exceeds L2", "levels_mean": statistics.mean(levels),
-                           "level_loop": "device (one CUDA graph per search)",
+                           "level_loop": ("device (one CUDA graph per search)" if args.level_loop == "device"
+                                          else "host (one counter read per level)"),
                            "gteps_hmean": hmean, "edges_examined": examined,
                            "host_loop_ms_per_step": host_loop_ms / args.steps,
                            "parallelism": f"replicas{world}"},

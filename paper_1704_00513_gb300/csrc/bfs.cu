@@ -184,19 +184,31 @@ __global__ void __launch_bounds__(kThreads) td_expand_kernel(const uint32_t *__r
         const uint32_t incl = warp_incl_scan(deg);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t p = incl - deg;
-        for (uint32_t c = 0; c < total; c += 32u) {
-            const uint32_t idx = c + lane;
-            uint32_t lo = 0;
+        constexpr uint32_t kU = 4;  // edge slots per lane per round: their loads are all in flight at once
+        for (uint32_t c = 0; c < total; c += 32u * kU) {
+            uint32_t src[kU], w[kU];
 #pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1) {
-                const uint32_t cand = lo + step;
-                const uint32_t pc = __shfl_sync(0xffffffffu, p, cand);
-                if (pc <= idx) lo = cand;
+            for (uint32_t r = 0; r < kU; r++) {
+                const uint32_t idx = c + 32u * r + lane;
+                uint32_t lo = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1) {
+                    const uint32_t cand = lo + step;
+                    const uint32_t pc = __shfl_sync(0xffffffffu, p, cand);
+                    if (pc <= idx) lo = cand;
+                }
+                src[r] = __shfl_sync(0xffffffffu, v, lo);
+                const long long ss = __shfl_sync(0xffffffffu, s, lo);
+                const uint32_t ps = __shfl_sync(0xffffffffu, p, lo);
+                w[r] = idx < total ? cols[ss + (idx - ps)] : 0xffffffffu;
             }
-            const uint32_t src = __shfl_sync(0xffffffffu, v, lo);
-            const long long ss = __shfl_sync(0xffffffffu, s, lo);
-            const uint32_t ps = __shfl_sync(0xffffffffu, p, lo);
-            if (idx < total) degsum += td_visit(cols[ss + (idx - ps)], src, visited32, next32, depth, parent, newdepth, off);
+            bool seen[kU];
+#pragma unroll
+            for (uint32_t r = 0; r < kU; r++)
+                seen[r] = w[r] == 0xffffffffu || ((visited32[w[r] >> 5] >> (w[r] & 31u)) & 1u);
+#pragma unroll
+            for (uint32_t r = 0; r < kU; r++)
+                if (!seen[r]) degsum += td_visit(w[r], src[r], visited32, next32, depth, parent, newdepth, off);
         }
     }
     degsum = warp_sum64(degsum);
@@ -214,10 +226,22 @@ __global__ void __launch_bounds__(kThreads) td_hub_kernel(const HubItem *__restr
     if (ls) newdepth = (int32_t)ls->d + 1;
     const unsigned long long total = min(*nitems, items_cap);
     unsigned long long degsum = 0;
+    constexpr uint32_t kPer = kHubChunk / kThreads;  // entries per thread per item
     for (unsigned long long it = blockIdx.x; it < total; it += gridDim.x) {
         const HubItem h = items[it];
-        for (uint32_t j = threadIdx.x; j < h.count; j += blockDim.x)
-            degsum += td_visit(cols[h.start + j], h.v, visited32, next32, depth, parent, newdepth, off);
+        uint32_t w[kPer];
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; c++) {  // the item's columns first, all loads in flight ...
+            const uint32_t j = threadIdx.x + c * kThreads;
+            w[c] = j < h.count ? cols[h.start + j] : 0xffffffffu;
+        }
+        bool seen[kPer];
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; c++)  // ... then their visited bits ...
+            seen[c] = w[c] == 0xffffffffu || ((visited32[w[c] >> 5] >> (w[c] & 31u)) & 1u);
+#pragma unroll
+        for (uint32_t c = 0; c < kPer; c++)  // ... then the claims
+            if (!seen[c]) degsum += td_visit(w[c], h.v, visited32, next32, depth, parent, newdepth, off);
     }
     degsum = warp_sum64(degsum);
     if ((threadIdx.x & 31u) == 0 && degsum) atomicAdd(m_f_next, degsum);
@@ -335,20 +359,11 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
     const uint64_t chunk = (ntiles + kScanThreads - 1) / kScanThreads;
     const uint64_t t0 = min(ntiles, (uint64_t)threadIdx.x * chunk), t1 = min(ntiles, t0 + chunk);
     const uint64_t tile_bits = 64ull * kCmpWords;
-    // one read of both count arrays (kScanWin at a time, every load of a window issued first)
+    // each thread sums its chunk of both count arrays (one tile per thread up to 2^24 vertices)
     unsigned long long lq = 0, lv = 0;
-    for (uint64_t w = t0; w < t1; w += kScanWin) {
-        uint32_t x[kScanWin], y[kScanWin];
-#pragma unroll
-        for (uint32_t i = 0; i < kScanWin; i++) {
-            x[i] = w + i < t1 ? tile_cnt[w + i] : 0u;
-            y[i] = w + i < t1 ? vis_cnt[w + i] : 0u;
-        }
-#pragma unroll
-        for (uint32_t i = 0; i < kScanWin; i++) {
-            lq += x[i];
-            lv += y[i];
-        }
+    for (uint64_t t = t0; t < t1; t++) {
+        lq += tile_cnt[t];
+        lv += vis_cnt[t];
     }
     const unsigned long long lb = t1 > t0 ? min(n, t1 * tile_bits) - t0 * tile_bits : 0ull;  // bits in the chunk
     unsigned long long nf_total = 0, vis_total = 0, total = 0;
@@ -356,43 +371,44 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
     cta_excl_scan64<kScanThreads>(lv, sm, &vis_total);
     const bool set_mode = 2ull * vis_total <= n;
     unsigned long long vrun = cta_excl_scan64<kScanThreads>(set_mode ? lv : lb - lv, sm, &total);
-    for (uint64_t w = t0; w < t1; w += kScanWin) {
-        uint32_t x[kScanWin], y[kScanWin];
-#pragma unroll
-        for (uint32_t i = 0; i < kScanWin; i++) {
-            x[i] = w + i < t1 ? tile_cnt[w + i] : 0u;
-            y[i] = w + i < t1 ? vis_cnt[w + i] : 0u;
-        }
-#pragma unroll
-        for (uint32_t i = 0; i < kScanWin; i++) {
-            if (w + i >= t1) break;
-            const uint64_t t = w + i;
+    if (t1 == t0 + 1) {  // the common case: nothing to re-read
+        tile_off[t0] = (uint32_t)run;
+        vtile_off[t0] = (uint32_t)vrun;
+    } else {
+        for (uint64_t t = t0; t < t1; t++) {
             tile_off[t] = (uint32_t)run;
             vtile_off[t] = (uint32_t)vrun;
-            run += x[i];
+            const uint32_t x = tile_cnt[t], y = vis_cnt[t];
+            run += x;
             const uint64_t bits = min(n, (t + 1) * tile_bits) - t * tile_bits;
-            vrun += set_mode ? y[i] : bits - y[i];
+            vrun += set_mode ? y : bits - y;
         }
     }
     const unsigned long long s_nf = nf_total, s_vis = vis_total;
     const unsigned long long vcount = total;
-    // snapshot the level's live counters and codec status, then clear for the next level
+    // snapshot the level's live counters and codec status, then clear for the next level (every
+    // load first: the stores below could alias them, and one thread's dependent round trips are
+    // this kernel's critical path)
     if (threadIdx.x == 0) {
+        const unsigned long long m_f = ctr->m_f_next, ex = ctr->examined, hub = ctr->hub_items;
+        const int32_t cq = sq.ctl->code, cv = sv.ctl->code;
+        const uint32_t wq = sq.ctl->where, wv = sv.ctl->where;
+        const unsigned long long dq = sq.ctl->detail, dv = sv.ctl->detail;
         ctr->n_f_next = s_nf;
-        ctr->r_m_f = ctr->m_f_next;  // summed by the expansion kernels
+        ctr->r_m_f = m_f;  // summed by the expansion kernels
         ctr->m_f_next = 0;
         ctr->vis_count = s_vis;
         ctr->v_count = vcount;
-        ctr->r_examined = ctr->examined;
+        ctr->r_examined = ex;
         ctr->examined = 0;
-        ctr->r_hub_items = ctr->hub_items;
+        ctr->r_hub_items = hub;
         ctr->hub_items = 0;
-        ctr->r_err_q = sq.ctl->code;
-        ctr->r_where_q = sq.ctl->where;
-        ctr->r_detail_q = sq.ctl->detail;
-        ctr->r_err_v = sv.ctl->code;
-        ctr->r_where_v = sv.ctl->where;
-        ctr->r_detail_v = sv.ctl->detail;
+        ctr->r_err_q = cq;
+        ctr->r_where_q = wq;
+        ctr->r_detail_q = dq;
+        ctr->r_err_v = cv;
+        ctr->r_where_v = wv;
+        ctr->r_detail_v = dv;
         reset_scratch_device(sq);
         reset_scratch_device(sv);
         sv.ctl->n = vcount;
@@ -401,27 +417,29 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
 }
 
 // Positions of the set bits of the warp's 32 words (lane L holds word wbase + L) written to
-// out[pos ...] in increasing order.  Only nonzero words are visited: each is broadcast to the
-// warp, lane L takes its bits L and L + 32, and two ballots give every set bit its output slot,
-// so each store instruction writes one contiguous run (the writes are coalesced).
-__device__ __forceinline__ void expand_words(uint64_t x, uint64_t wbase, unsigned long long pos, uint32_t *out,
-                                             uint32_t lane)
+// out[pos ...] in increasing order: each lane writes its word's positions into the warp's
+// shared-memory stage at its prefix offset, then the warp copies the stage out with coalesced
+// stores (2,048 positions at most: 32 words x 64 bits).
+__device__ __forceinline__ void extract_words(uint64_t x, uint64_t wbase, unsigned long long pos, uint32_t *out,
+                                              uint32_t lane, uint32_t *stage)
 {
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t nz = __ballot_sync(0xffffffffu, x != 0ull);
-    while (nz) {
-        const uint32_t src = __ffs(nz) - 1u;
-        nz &= nz - 1u;
-        const uint64_t xw = __shfl_sync(0xffffffffu, x, src);
-        const uint32_t lo = (uint32_t)xw, hi = (uint32_t)(xw >> 32);
-        const uint32_t pos0 = (uint32_t)((wbase + src) * 64u);
-        const bool b0 = (lo >> lane) & 1u, b1 = (hi >> lane) & 1u;
-        const uint32_t n0 = __popc(lo);
-        if (b0) out[pos + __popc(lo & lt)] = pos0 + lane;
-        if (b1) out[pos + n0 + __popc(hi & lt)] = pos0 + 32u + lane;
-        pos += n0 + __popc(hi);
+    const uint32_t c = (uint32_t)__popcll(x);
+    const uint32_t incl = warp_incl_scan(c);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    uint32_t o = incl - c;
+    const uint32_t p0 = (uint32_t)((wbase + lane) * 64u);
+    while (x) {
+        stage[o++] = p0 + (uint32_t)(__ffsll((long long)x) - 1);
+        x &= x - 1ull;
     }
+    __syncwarp();
+    for (uint32_t i = lane; i < total; i += 32u) out[pos + i] = stage[i];
+    __syncwarp();
 }
+
+constexpr size_t kCmpStage = 2048 * sizeof(uint32_t);               // one warp's stage
+constexpr size_t kCmpSmem = (kThreads / 32) * kCmpStage;            // 64 KB per CTA
 
 // The next frontier F_{d+1} as a sorted queue (and as the bitmap the next level's B encode reads),
 // next cleared, and -- when V_{d+1} is coded -- the positions V_{d+1} codes.  One word per thread;
@@ -433,6 +451,7 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
                                                                Scratch sv, int want_v)
 {
     static_assert(kCmpWordsPerThread == 1, "one word per thread");
+    extern __shared__ __align__(16) uint32_t cstage[];  // [warps][2048]
     __shared__ uint32_t wq[kThreads / 32], wv[kThreads / 32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * kCmpWords + threadIdx.x;
@@ -462,8 +481,9 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
         ov += wv[i];
     }
     const uint64_t wbase = (uint64_t)blockIdx.x * kCmpWords + warp * 32u;
-    expand_words(x, wbase, oq, q, lane);
-    if (want_v) expand_words(y, wbase, ov, sv.positions, lane);
+    uint32_t *stage = cstage + warp * 2048u;
+    extract_words(x, wbase, oq, q, lane, stage);
+    if (want_v) extract_words(y, wbase, ov, sv.positions, lane, stage);
 }
 
 // ---- the device-driven level loop (FQ_BFS_DEVICE_LOOP) ----
@@ -530,9 +550,14 @@ __global__ void log_append_kernel(const LoopState *ls, const Counters *ctr, cons
     }
 }
 
-__global__ void loop_end_kernel(LoopState *ls, const Counters *ctr, fq_level_record *recs, uint64_t n, int codec,
-                                int want_v, int has_log, cudaGraphConditionalHandle h_while)
+__global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_level_record *recs, uint64_t n,
+                                int codec, int want_v, int has_log, cudaGraphConditionalHandle h_while)
 {
+    // local copies: every load is issued up front, the state is written back once at the end
+    LoopState lsv = *ls_out;
+    const Counters cv = *ctr_in;
+    LoopState *ls = &lsv;
+    const Counters *ctr = &cv;
     uint32_t go = 0;
     const uint32_t d = ls->d, dir = ls->dir;
     const unsigned long long n_f = ls->n_f, m_f = ls->m_f;
@@ -541,6 +566,7 @@ __global__ void loop_end_kernel(LoopState *ls, const Counters *ctr, fq_level_rec
     else if (ctr->r_err_v != FQ_OK) ls->status = ctr->r_err_v;
     else if (codec && dir == FQ_TOP_DOWN && ctr->dec_n != n_f) ls->status = FQ_ECORRUPT;
     if (ls->status != FQ_OK) {
+        ls_out->status = ls->status;
         cudaGraphSetConditional(h_while, 0u);
         return;
     }
@@ -617,6 +643,7 @@ __global__ void loop_end_kernel(LoopState *ls, const Counters *ctr, fq_level_rec
         if ((uint64_t)d + 1 >= n || ls->visited > n) ls->status = FQ_ECORRUPT;  // at most n levels, n vertices
         else go = 1;
     }
+    *ls_out = lsv;
     cudaGraphSetConditional(h_while, go);
 }
 
@@ -797,8 +824,15 @@ cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
     cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt);
     cmp_scan_kernel<<<1, kScanThreads, 0, st>>>(g->tile_cnt, g->tile_off, g->vis_cnt, g->vtile_off, g->cmp_tiles, g->n,
                                                 g->ctr, g->sq, g->sv);
-    cmp_extract_kernel<<<ct, kThreads, 0, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
-                                                g->vtile_off, g->q, g->sv, want_v ? 1 : 0);
+    static bool smem_set[64];
+    int dev = 0;
+    FQ_CU(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+        FQ_CU(cudaFuncSetAttribute(cmp_extract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCmpSmem));
+        smem_set[dev] = true;
+    }
+    cmp_extract_kernel<<<ct, kThreads, kCmpSmem, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
+                                                       g->vtile_off, g->q, g->sv, want_v ? 1 : 0);
     return cudaGetLastError();
 }
 
