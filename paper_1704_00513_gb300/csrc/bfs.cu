@@ -154,12 +154,17 @@ __global__ void __launch_bounds__(kThreads) td_expand_kernel(const uint32_t *__r
     unsigned long long degsum = 0;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t base = gw * 32u; base < nf; base += nw * 32u) {
+    // frontier vertices per warp: 32 when the frontier fills the grid, fewer (down to one) when it
+    // is small, so that a short frontier with long lists still spreads over every warp
+    uint32_t vpw = 32;
+    while (vpw > 1 && (uint64_t)(vpw / 2) * nw >= nf) vpw /= 2;
+    for (uint64_t base = gw * vpw; base < nf; base += nw * vpw) {
         const uint64_t i = base + lane;
+        const bool mine = lane < vpw && i < nf;
         uint32_t v = 0, deg = 0;
         long long s = 0;
-        if (i < nf && q[i] >= n) set_error(err, FQ_ECORRUPT, kWhereBfs, i);  // defensive: ids come from our decoder
-        if (i < nf && q[i] < n) {
+        if (mine && q[i] >= n) set_error(err, FQ_ECORRUPT, kWhereBfs, i);  // defensive: ids come from our decoder
+        if (mine && q[i] < n) {
             v = q[i];
             s = off[v];
             const long long d = off[v + 1] - s;
@@ -785,13 +790,13 @@ cudaError_t step_top_down(fq_graph *g, bool codec, uint64_t n_f, int32_t newdept
     const int sms = num_sms();
     const uint32_t *qin = codec ? g->q2 : g->q;
     const uint32_t grid =
-        ls ? (uint32_t)sms * 8 : (uint32_t)std::min<uint64_t>(cdiv(std::max<uint64_t>(n_f, 1), kThreads), (uint64_t)sms * 8);
+        ls ? (uint32_t)sms * 8 : (uint32_t)std::min<uint64_t>(cdiv(std::max<uint64_t>(n_f, 1), kThreads / 32), (uint64_t)sms * 8);
     uint32_t *next32 = reinterpret_cast<uint32_t *>(g->next);
     const uint32_t *vis32 = reinterpret_cast<const uint32_t *>(g->visited);
     td_expand_kernel<<<grid, kThreads, 0, st>>>(qin, n_f, g->off, g->cols, vis32, next32, d_depth, d_parent, newdepth,
                                                 g->items, &g->ctr->hub_items, g->items_cap, g->n, g->sq.ctl,
                                                 &g->ctr->m_f_next, ls);
-    td_hub_kernel<<<sms * 4, kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32, next32,
+    td_hub_kernel<<<sms * 6, kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32, next32,
                                                 d_depth, d_parent, newdepth, g->off, &g->ctr->m_f_next, ls);
     return cudaGetLastError();
 }
