@@ -196,10 +196,21 @@ def kernel_traffic(kclass: str):
     if not ent:
         return None
     src = os.path.join(ROOT, "paper_1704_00513_gb300", "csrc", ent["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != ent.get("source_sha256_16"):
+    if kernel_source_hash(src, ent["kernel"]) != ent.get("kernel_sha256_16"):
         return None
     return ent.get("dram_bytes_per_launch_fullsize")
+
+
+def kernel_source_hash(path: str, kernel: str):
+    """sha256 (16 hex digits) of one __global__ function's text, signature to closing brace, so
+    that the recorded counters stay valid until that kernel itself changes."""
+    text = open(path).read()
+    at = text.find(f" {kernel}(")
+    if at < 0:
+        return None
+    start = text.rfind("__global__", 0, at)
+    end = text.find("\n}\n", at)
+    return hashlib.sha256(text[start:end].encode()).hexdigest()[:16]
 
 
 def make_graph(scale, edgefactor, device):
