@@ -64,6 +64,9 @@ def _load():
             lib.orc_fb_raw_size.argtypes, lib.orc_fb_raw_size.restype = [u64], u64
             lib.orc_fq_encode.argtypes, lib.orc_fq_encode.restype = [u32p, u64, u8p, u64, u64p], ctypes.c_int
             lib.orc_fq_decode.argtypes, lib.orc_fq_decode.restype = [u8p, u64, u32p, u64, u64p], ctypes.c_int
+            lib.orc_px_size.argtypes, lib.orc_px_size.restype = [u64, u64, u64], u64
+            lib.orc_px_encode.argtypes, lib.orc_px_encode.restype = [u32p, u64, u8p, u64, u64p], ctypes.c_int
+            lib.orc_px_decode.argtypes, lib.orc_px_decode.restype = [u8p, u64, u32p, u64, u64p], ctypes.c_int
             lib.orc_fb_encode.argtypes, lib.orc_fb_encode.restype = [u64p, u64, u8p, u64, u64p], ctypes.c_int
             lib.orc_fb_decode.argtypes, lib.orc_fb_decode.restype = [u8p, u64, u64p, u64], ctypes.c_int
             lib.orc_bfs.argtypes, lib.orc_bfs.restype = [u64, i64p, u32p, ctypes.c_uint32, i32p, u32p], ctypes.c_int
@@ -125,6 +128,38 @@ def fq_decode(stream, cap: int | None = None):
     out = np.zeros(max(int(cap), 1), dtype=np.uint32)
     n = ctypes.c_uint64(0)
     st = _load().orc_fq_decode(_ptr(s, ctypes.c_uint8), s.size, _ptr(out, ctypes.c_uint32), int(cap), ctypes.byref(n))
+    if st != OK:
+        return st, np.zeros(0, np.uint32)
+    return st, out[: n.value].copy()
+
+
+def px_size(nb: int, sum_b: int, e_total: int) -> int:
+    """Bytes of a packed PX (patched) stream with these block count, width sum and exceptions."""
+    return int(_load().orc_px_size(nb, sum_b, e_total))
+
+
+def px_encode(ids, cap: int | None = None):
+    """Patched-exceptions encode of a strictly increasing uint32 sequence (PX stream, or the raw
+    FQ form when that is not larger); returns (status, stream bytes as uint8)."""
+    v = _as(ids, np.uint32)
+    n = v.size
+    cap = fq_raw_size(n) if cap is None else int(cap)
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    nbytes = ctypes.c_uint64(0)
+    st = _load().orc_px_encode(_ptr(v, ctypes.c_uint32), n, _ptr(out, ctypes.c_uint8), cap, ctypes.byref(nbytes))
+    if st != OK:
+        return st, np.zeros(0, np.uint8)
+    return st, out[: nbytes.value].copy()
+
+
+def px_decode(stream, cap: int | None = None):
+    """Decode a PX stream (or a raw FQ one); returns (status, uint32 ids)."""
+    s = _as(stream, np.uint8)
+    if cap is None:
+        cap = int(s[4:8].view(np.uint32)[0]) if s.size >= 16 else 0
+    out = np.zeros(max(int(cap), 1), dtype=np.uint32)
+    n = ctypes.c_uint64(0)
+    st = _load().orc_px_decode(_ptr(s, ctypes.c_uint8), s.size, _ptr(out, ctypes.c_uint32), int(cap), ctypes.byref(n))
     if st != OK:
         return st, np.zeros(0, np.uint32)
     return st, out[: n.value].copy()

@@ -15,6 +15,9 @@
  *   orc_fq_encode/decode  delta + frame-of-reference binary packing in blocks of 128
  *                      ("Binary packing", "Delta compression" in sec. 5.2; S4-BP128 in sec. 5.3;
  *                      width formula Eq. 6/7), written bit by bit
+ *   orc_px_encode/decode  binary packing with patched exceptions ("Patched coding and
+ *                      Exceptions", sec. 5.2, Eq. 8-9; the PFOR family in sec. 5.3): per block
+ *                      the width b that minimises the block's bytes, gaps >= 2^b stored apart
  *   orc_fb_encode/decode  frontier/visited bitmap codec: positions of the minority bit value,
  *                      coded with the queue codec, or the raw words (bitmap frontiers, sec. 3.3
  *                      "Sparse vector with pop counting"; lossless requirement, sec. 5.2)
@@ -42,6 +45,7 @@ enum {
 #define ORC_MAGIC_PACKED ((uint32_t)'F' | ((uint32_t)'Q' << 8) | ((uint32_t)'P' << 16) | ((uint32_t)'1' << 24))
 #define ORC_MAGIC_RAW    ((uint32_t)'F' | ((uint32_t)'Q' << 8) | ((uint32_t)'R' << 16) | ((uint32_t)'1' << 24))
 #define ORC_MAGIC_BITMAP ((uint32_t)'F' | ((uint32_t)'B' << 8) | ((uint32_t)'M' << 16) | ((uint32_t)'1' << 24))
+#define ORC_MAGIC_PATCHED ((uint32_t)'F' | ((uint32_t)'Q' << 8) | ((uint32_t)'X' << 16) | ((uint32_t)'1' << 24))
 
 #define ORC_BLOCK 128u /* B, the block length of binary packing (sec. 5.2, S4-BP128 in sec. 5.3) */
 
@@ -262,6 +266,237 @@ int orc_fq_decode(const uint8_t *in, uint64_t in_bytes, uint32_t *out, uint64_t 
                 continue;
             }
             value = value + gap + 1u;
+            if (value > 0xFFFFFFFFu)
+                return ORC_ECORRUPT;
+            out[i] = (uint32_t)value;
+        }
+        bit0 += 128u * bk;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ patched codec "PX"
+ *
+ * Binary packing with exceptions (sec. 5.2 "Patched coding and Exceptions": a value that does
+ * not fit in the block's b bits -- a gap >= 2^b, Eq. 8-9 -- is stored apart; PFOR family,
+ * sec. 5.3).  Same gaps, blocks and raw fallback as FQ.  Per block k the width b_k is the b in
+ * 0..32 that minimises the block's bytes 16*b + 5*e_b, e_b = number of gaps >= 2^b (each
+ * exception costs a u8 slot position and a u32 high part); ties go to the larger b.  Layout
+ * (all u32 little-endian, every section starting on a 16-byte boundary):
+ *   header 32 B : "FQX1", n, nb, payload_words = 4*sum(b), E = sum(e), 0, 0, 0
+ *   u32 base[nb], u8 b[nb], u8 e[nb], zero pad to 16
+ *   payload     : per block 4*b_k words, slot j's low b_k gap bits at [j*b_k, (j+1)*b_k)
+ *   u8 pos[E]   : per block in order, its exception slots (1..127, increasing), zero pad to 16
+ *   u32 high[E] : gap >> b_k of each exception, zero pad to 16
+ * The packed form is used only if strictly smaller than the raw FQ form (which it then is).
+ */
+
+uint64_t orc_px_size(uint64_t nb, uint64_t sum_b, uint64_t e_total)
+{
+    return 32u + pad16(6u * nb) + 16u * sum_b + pad16(e_total) + pad16(4u * e_total);
+}
+
+/* the width and exception count of one block of gaps g[0..cnt) (slot 0 included, always 0) */
+static void px_choose(const uint64_t *g, uint64_t cnt, uint32_t *b_out, uint32_t *e_out)
+{
+    uint32_t b, best_b = 32;
+    uint64_t best_cost = 16u * 32u, j;
+    for (b = 0; b <= 32u; b++) {
+        uint64_t e = 0, cost;
+        for (j = 0; j < cnt; j++)
+            if (b < 32u && (g[j] >> b) != 0u)
+                e++;
+        cost = 16u * b + 5u * e;
+        if (cost <= best_cost) { /* <=: a tie moves to the larger b */
+            best_cost = cost;
+            best_b = b;
+        }
+    }
+    *b_out = best_b;
+    *e_out = 0;
+    for (j = 0; j < cnt; j++)
+        if (best_b < 32u && (g[j] >> best_b) != 0u)
+            (*e_out)++;
+}
+
+int orc_px_encode(const uint32_t *v, uint64_t n, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
+{
+    uint64_t nb, k, j, t, i, sum_b = 0, e_total = 0, size, packed_size, raw_size, payload, bit0, xpos, xhigh, x;
+    uint8_t *b, *e;
+    uint64_t g[ORC_BLOCK];
+    int packed;
+
+    *out_bytes = 0;
+    if (n > 0xFFFFFFFFu)
+        return ORC_EINVAL;
+    for (i = 1; i < n; i++)
+        if (v[i] <= v[i - 1])
+            return ORC_EUNSORTED;
+    nb = (n + ORC_BLOCK - 1u) / ORC_BLOCK;
+    b = (uint8_t *)calloc(nb ? nb : 1u, 1);
+    e = (uint8_t *)calloc(nb ? nb : 1u, 1);
+    if (!b || !e) {
+        free(b);
+        free(e);
+        return ORC_ENOMEM;
+    }
+    for (k = 0; k < nb; k++) {
+        uint32_t bk, ek;
+        uint64_t cnt = 0;
+        for (j = 0; j < ORC_BLOCK; j++) {
+            i = k * ORC_BLOCK + j;
+            if (i >= n)
+                break;
+            g[cnt++] = j == 0 ? 0u : (uint64_t)v[i] - (uint64_t)v[i - 1] - 1u;
+        }
+        px_choose(g, cnt, &bk, &ek);
+        b[k] = (uint8_t)bk;
+        e[k] = (uint8_t)ek;
+        sum_b += bk;
+        e_total += ek;
+    }
+    packed_size = orc_px_size(nb, sum_b, e_total);
+    raw_size = orc_fq_raw_size(n);
+    packed = (n > 0) && (packed_size < raw_size);
+    size = packed ? packed_size : raw_size;
+    *out_bytes = size;
+    if (size > cap) {
+        free(b);
+        free(e);
+        return ORC_ENOSPC;
+    }
+    memset(out, 0, size);
+    if (!packed) { /* the raw FQ form */
+        put_u32(out + 0, ORC_MAGIC_RAW);
+        put_u32(out + 4, (uint32_t)n);
+        put_u32(out + 8, 0u);
+        put_u32(out + 12, (uint32_t)n);
+        for (i = 0; i < n; i++)
+            put_u32(out + 16u + 4u * i, v[i]);
+        free(b);
+        free(e);
+        return ORC_OK;
+    }
+    put_u32(out + 0, ORC_MAGIC_PATCHED);
+    put_u32(out + 4, (uint32_t)n);
+    put_u32(out + 8, (uint32_t)nb);
+    put_u32(out + 12, (uint32_t)(4u * sum_b));
+    put_u32(out + 16, (uint32_t)e_total);
+    for (k = 0; k < nb; k++) {
+        put_u32(out + 32u + 4u * k, v[k * ORC_BLOCK]);
+        out[32u + 4u * nb + k] = b[k];
+        out[32u + 5u * nb + k] = e[k];
+    }
+    payload = 32u + pad16(6u * nb);
+    xpos = payload + 16u * sum_b;
+    xhigh = xpos + pad16(e_total);
+    bit0 = 8u * payload;
+    x = 0; /* exceptions written so far */
+    for (k = 0; k < nb; k++) {
+        for (j = 0; j < ORC_BLOCK; j++) {
+            uint64_t gap = 0;
+            i = k * ORC_BLOCK + j;
+            if (j > 0 && i < n)
+                gap = (uint64_t)v[i] - (uint64_t)v[i - 1] - 1u;
+            for (t = 0; t < b[k]; t++)
+                if ((gap >> t) & 1u)
+                    set_bit(out, bit0 + j * b[k] + t);
+            if (b[k] < 32u && (gap >> b[k]) != 0u) { /* an exception: slot and high part */
+                out[xpos + x] = (uint8_t)j;
+                put_u32(out + xhigh + 4u * x, (uint32_t)(gap >> b[k]));
+                x++;
+            }
+        }
+        bit0 += 128u * b[k];
+    }
+    free(b);
+    free(e);
+    return ORC_OK;
+}
+
+/* Inverse of orc_px_encode (and of the raw FQ form).  Rejects (ORC_ECORRUPT): unknown magic,
+ * nb != ceil(n/128), nonzero reserved header words, a width > 32, more than 127 exceptions in a
+ * block or any with width 32, payload_words != 4*sum(b), E != sum(e), in_bytes != the layout's
+ * size, nonzero pads, exception slots that are not increasing within 1..127 or that fall past
+ * n, a zero high part or one that does not fit above the width, a nonzero slot 0 or padding
+ * slot, and values that overflow u32.  n > cap gives ORC_ENOSPC with *n_out = n. */
+int orc_px_decode(const uint8_t *in, uint64_t in_bytes, uint32_t *out, uint64_t cap, uint64_t *n_out)
+{
+    uint64_t n, nb, words, e_total, k, j, t, i, sum_b = 0, sum_e = 0, payload, xpos, xhigh, bit0, x;
+    uint64_t g[ORC_BLOCK];
+
+    *n_out = 0;
+    if (in_bytes < 16u)
+        return ORC_ECORRUPT;
+    if (get_u32(in) == ORC_MAGIC_RAW)
+        return orc_fq_decode(in, in_bytes, out, cap, n_out);
+    if (get_u32(in) != ORC_MAGIC_PATCHED || in_bytes < 32u)
+        return ORC_ECORRUPT;
+    n = get_u32(in + 4);
+    nb = get_u32(in + 8);
+    words = get_u32(in + 12);
+    e_total = get_u32(in + 16);
+    if (get_u32(in + 20) || get_u32(in + 24) || get_u32(in + 28))
+        return ORC_ECORRUPT;
+    if (nb != (n + ORC_BLOCK - 1u) / ORC_BLOCK || in_bytes < 32u + pad16(6u * nb))
+        return ORC_ECORRUPT;
+    for (k = 0; k < nb; k++) {
+        uint32_t bk = in[32u + 4u * nb + k], ek = in[32u + 5u * nb + k];
+        if (bk > 32u || ek > 127u || (bk == 32u && ek != 0u))
+            return ORC_ECORRUPT;
+        sum_b += bk;
+        sum_e += ek;
+    }
+    payload = 32u + pad16(6u * nb);
+    if (words != 4u * sum_b || e_total != sum_e || in_bytes != orc_px_size(nb, sum_b, sum_e))
+        return ORC_ECORRUPT;
+    xpos = payload + 16u * sum_b;
+    xhigh = xpos + pad16(sum_e);
+    for (i = 32u + 6u * nb; i < payload; i++)
+        if (in[i] != 0u)
+            return ORC_ECORRUPT;
+    for (i = xpos + sum_e; i < xhigh; i++)
+        if (in[i] != 0u)
+            return ORC_ECORRUPT;
+    for (i = xhigh + 4u * sum_e; i < in_bytes; i++)
+        if (in[i] != 0u)
+            return ORC_ECORRUPT;
+    *n_out = n;
+    if (n > cap)
+        return ORC_ENOSPC;
+
+    bit0 = 8u * payload;
+    x = 0;
+    for (k = 0; k < nb; k++) {
+        uint32_t bk = in[32u + 4u * nb + k], ek = in[32u + 5u * nb + k], q;
+        uint64_t value = get_u32(in + 32u + 4u * k), last = 0;
+        for (j = 0; j < ORC_BLOCK; j++) { /* the low bits of every slot */
+            g[j] = 0;
+            for (t = 0; t < bk; t++)
+                g[j] |= (uint64_t)get_bit(in, bit0 + j * bk + t) << t;
+        }
+        for (q = 0; q < ek; q++, x++) { /* patch the exceptions */
+            uint64_t slot = in[xpos + x], high = get_u32(in + xhigh + 4u * x);
+            if (slot == 0u || slot <= last || k * ORC_BLOCK + slot >= n)
+                return ORC_ECORRUPT;
+            if (high == 0u || (high >> (32u - bk)) != 0u)
+                return ORC_ECORRUPT;
+            last = slot;
+            g[slot] |= high << bk;
+        }
+        for (j = 0; j < ORC_BLOCK; j++) {
+            i = k * ORC_BLOCK + j;
+            if (j == 0 || i >= n) {
+                if (g[j] != 0u)
+                    return ORC_ECORRUPT;
+                if (j == 0) {
+                    if (k > 0 && value <= out[i - 1u])
+                        return ORC_ECORRUPT;
+                    out[i] = (uint32_t)value;
+                }
+                continue;
+            }
+            value = value + g[j] + 1u;
             if (value > 0xFFFFFFFFu)
                 return ORC_ECORRUPT;
             out[i] = (uint32_t)value;
