@@ -426,15 +426,24 @@ def run_fqbfs(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def codec_points(dev, peak_gbs, points=((26, 1.0), (26, 16.0), (24, 256.0), (28, 4.0), (28, 15.0)), reps=5):
+CODEC_POINTS = ((26, 1.0, None), (26, 16.0, None), (24, 128.0, None), (28, 4.0, None), (28, 15.0, None),
+                (25, 16.0, (0.01, 256, 16384)), (24, 4.0, (0.002, 4096, 65536)))
+
+
+def codec_points(dev, peak_gbs, points=CODEC_POINTS, reps=5):
     """Standalone frontier codec throughput on sorted sets with geometric gaps (the codec sweep's
-    shape): algorithmic bytes (4n + stream) / event-timed seconds, and the compression ratio."""
+    shape), plus two sets with rare large gaps (outliers: fraction, range): algorithmic bytes
+    (4n + stream) / event-timed seconds and the compression ratio, for the FQ codec and for the
+    FQX (patched exceptions) codec on the same ids."""
     from paper_1704_00513_gb300 import fqbfs, inputs
     res = []
     stream = torch.cuda.current_stream()
-    for logn, mu in points:
+    for logn, mu, outl in points:
         n = 1 << logn
-        v = inputs.geometric_set(n, mu, seed=logn * 1000 + int(mu), device=dev)
+        if outl is None:
+            v = inputs.geometric_set(n, mu, seed=logn * 1000 + int(mu), device=dev)
+        else:
+            v = inputs.outlier_set(n, mu, outl[0], outl[1], outl[2], seed=logn * 1000 + int(mu) + 7, device=dev)
         if int(v[-1]) >= 2**32:
             continue
         ids = torch.where(v >= 2**31, v - 2**32, v).to(torch.int32)
@@ -465,10 +474,36 @@ def codec_points(dev, peak_gbs, points=((26, 1.0), (26, 16.0), (24, 256.0), (28,
         t_dec = s0.elapsed_time(s1) / reps / 1e3
         ok = bool(torch.equal(dec, ids))
         alg = 4 * n + size
-        res.append({"n": n, "mean_gap": mu, "bytes": size, "ratio": 4 * n / size, "bits_per_id": 8 * size / n,
-                    "encode_GBps": alg / t_enc / 1e9, "decode_GBps": alg / t_dec / 1e9,
-                    "encode_frac": alg / t_enc / 1e9 / peak_gbs, "decode_frac": alg / t_dec / 1e9 / peak_gbs,
-                    "roundtrip_ok": ok})
+        pt = {"n": n, "mean_gap": mu, "outliers": list(outl) if outl else None, "bytes": size, "ratio": 4 * n / size,
+              "bits_per_id": 8 * size / n,
+              "encode_GBps": alg / t_enc / 1e9, "decode_GBps": alg / t_dec / 1e9,
+              "encode_frac": alg / t_enc / 1e9 / peak_gbs, "decode_frac": alg / t_dec / 1e9 / peak_gbs,
+              "roundtrip_ok": ok}
+        # the same ids through the patched-exceptions codec
+        for _ in range(3):
+            fqbfs.fq_frontier_encode(ids, out=out, work=work, sync=False, nbytes=nbytes, px=True)
+        torch.cuda.synchronize()
+        psize = int(nbytes.item())
+        s0.record(stream)
+        for _ in range(reps):
+            fqbfs.fq_frontier_encode(ids, out=out, work=work, sync=False, nbytes=nbytes, px=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        t_penc = s0.elapsed_time(s1) / reps / 1e3
+        for _ in range(3):
+            fqbfs.fq_frontier_decode(out, cap=n, out=dec, work=work, in_bytes=psize, sync=False, n_out=ndec)
+        s0.record(stream)
+        for _ in range(reps):
+            fqbfs.fq_frontier_decode(out, cap=n, out=dec, work=work, in_bytes=psize, sync=False, n_out=ndec)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        t_pdec = s0.elapsed_time(s1) / reps / 1e3
+        palg = 4 * n + psize
+        pt["px"] = {"bytes": psize, "ratio": 4 * n / psize, "bits_per_id": 8 * psize / n,
+                    "encode_GBps": palg / t_penc / 1e9, "decode_GBps": palg / t_pdec / 1e9,
+                    "encode_frac": palg / t_penc / 1e9 / peak_gbs, "decode_frac": palg / t_pdec / 1e9 / peak_gbs,
+                    "roundtrip_ok": bool(torch.equal(dec, ids))}
+        res.append(pt)
         del ids, out, work, dec
         torch.cuda.empty_cache()
     return res

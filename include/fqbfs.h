@@ -33,6 +33,14 @@
  *    raw     {u32 'FQR1', n, 0, n}, u32 v[n], zeros to 16 B.
  *    The packed form is written only when strictly smaller than the raw one (sec. 5.2
  *    "Lossless": the encoding must be smaller than the input; sec. 5.4.2 thresholds).
+ *  FQX, the same sequence with patched exceptions (sec. 5.2 "Patched coding and Exceptions",
+ *    Eq. 8-9; the PFOR family of sec. 5.3), written by fq_frontier_encode_px:
+ *    {u32 'FQX1', n, nb, payload_words, E, 0, 0, 0}, u32 base[nb], u8 b[nb], u8 e[nb], zeros to
+ *    16 B, the blocks' low b_k bits of every slot as in FQ, u8 slot[E] (each block's exception
+ *    slots, increasing, 1..127), zeros to 16 B, u32 high[E] (slot value >> b_k), zeros to 16 B.
+ *    Per block b_k minimises the block's bytes 16*b + 5*e_b, e_b = slots >= 2^b (ties to the
+ *    larger b).  Written only when strictly smaller than the raw FQ form, which it writes
+ *    otherwise.
  *  FB, a bitmap of N bits in uint64 words (bit i = bit i%64 of word i/64):
  *    {u32 'FBM1', u32 mode, u64 N} then either an FQ stream of the set positions (mode 1, when
  *    2*popcount <= N) or of the clear positions below N (mode 2), or -- when that is not
@@ -100,9 +108,17 @@ fq_status fq_work_status(const void *d_work, void *stream, uint64_t *h_detail);
 fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
                              uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
 
-/* Decode the FQ stream d_in[0..in_bytes) into d_ids (room for cap ids); the number of ids is
+/* The same as fq_frontier_encode with the FQX (patched exceptions) format: a block whose largest
+ * gaps are rare outliers keeps a small width and stores the outliers apart.  Same arguments,
+ * workspace, bound (fq_queue_bound) and errors.  "Patched coding and Exceptions", sec. 5.2. */
+fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
+                                uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
+
+/* Decode the FQ (or FQX) stream d_in[0..in_bytes) into d_ids (room for cap ids); the number of ids is
  * written to the device u64 *d_n.  The stream is validated (magic, nb, widths <= 32, sizes
- * against in_bytes, zero padding and slots, strictly increasing values without u32 overflow);
+ * against in_bytes, zero padding and slots, strictly increasing values without u32 overflow;
+ * FQX also exception counts <= 127, none at width 32, exception slots increasing within the id
+ * range, nonzero high parts that fit above the width);
  * a failure sets FQ_ECORRUPT.  Header-level faults are caught before any output is written;
  * value-level faults may leave d_ids partly written.  Never writes more than cap ids
  * (FQ_ENOSPC if the stream holds more).  The decompress step of the same algorithm. */

@@ -24,7 +24,7 @@ namespace fq {
 
 namespace {
 struct Layout {
-    uint64_t widths, bases, block_off, tile_sum, tile_off, btile_cnt, btile_off, positions, total;
+    uint64_t widths, bases, block_off, tile_sum, tile_off, btile_cnt, btile_off, positions, ex, tile_ex, tile_exoff, total;
     uint64_t ids_cap, nb_cap, etiles_cap, btiles_cap, pos_cap;
 };
 
@@ -47,6 +47,9 @@ Layout layout(uint64_t max_ids, uint64_t max_nbits)
     L.btile_cnt = o; o = align256(o + 4 * L.btiles_cap);
     L.btile_off = o; o = align256(o + 4 * L.btiles_cap);
     L.positions = o; o = align256(o + 4 * L.pos_cap);
+    L.ex = o;        o = align256(o + L.nb_cap);
+    L.tile_ex = o;   o = align256(o + 4 * L.etiles_cap);
+    L.tile_exoff = o; o = align256(o + 4 * L.etiles_cap);
     L.total = o;
     return L;
 }
@@ -70,6 +73,9 @@ Scratch carve(void *base, uint64_t max_ids, uint64_t max_nbits)
     s.btile_cnt = reinterpret_cast<uint32_t *>(b + L.btile_cnt);
     s.btile_off = reinterpret_cast<uint32_t *>(b + L.btile_off);
     s.positions = reinterpret_cast<uint32_t *>(b + L.positions);
+    s.ex = b + L.ex;
+    s.tile_ex = reinterpret_cast<uint32_t *>(b + L.tile_ex);
+    s.tile_exoff = reinterpret_cast<uint32_t *>(b + L.tile_exoff);
     s.ids_cap = L.ids_cap;
     s.nbits_cap = max_nbits;
     s.nb_cap = L.nb_cap;
@@ -125,6 +131,7 @@ struct EncArgs {
     uint64_t *m_out_bytes;
     const uint64_t *m_words;
     uint64_t m_nbits;
+    int px;                 // patched codec (exceptions); plain FQ containers only
 };
 
 struct DecArgs {
@@ -162,18 +169,26 @@ struct EncPlan {
     bool fatal;           // the main output is not written at all
 };
 
-__device__ EncPlan enc_decide(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total, int32_t code)
+// Bytes of a packed patched stream: header, u32 bases + u8 widths + u8 exception counts, payload,
+// u8 exception slots, u32 high parts, every section padded to 16.
+__device__ __forceinline__ uint64_t px_bytes(uint64_t nb, uint64_t sum_b, uint64_t e)
+{
+    return kPxHeader + dpad16(6u * nb) + 16u * sum_b + dpad16(e) + dpad16(4u * e);
+}
+
+__device__ EncPlan enc_decide(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total,
+                              unsigned long long total_e, int32_t code)
 {
     EncPlan p{kModeNone, kModeNone, 0, 0, FQ_OK, 0, false};
     if (code != FQ_OK) {
         p.fatal = true;
         return p;
     }
-    const uint64_t packed = 16u + dpad16(5u * nb) + 16u * total;
+    const uint64_t packed = a.px ? px_bytes(nb, total, total_e) : 16u + dpad16(5u * nb) + 16u * total;
     const uint64_t raw = 16u + dpad16(4u * n);
     const bool is_packed = n > 0 && packed < raw;
     const uint64_t fq_size = is_packed ? packed : raw;
-    const uint32_t fq_mode = is_packed ? kModePacked : kModeRaw;
+    const uint32_t fq_mode = is_packed ? (a.px ? kModePatched : kModePacked) : kModeRaw;
     p.mode = fq_mode;
     p.size = fq_size;
     if (a.fb) {
@@ -213,7 +228,8 @@ __device__ EncPlan enc_decide(const EncArgs &a, uint64_t n, uint64_t nb, unsigne
 }
 
 // Record the decision, write the headers and sizes.  One thread, after every widths-kernel write.
-__device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total, const EncPlan &p)
+__device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned long long total,
+                             unsigned long long total_e, const EncPlan &p)
 {
     Ctl *c = a.s.ctl;
     c->n = n;
@@ -247,6 +263,15 @@ __device__ void enc_finalize(const EncArgs &a, uint64_t n, uint64_t nb, unsigned
             h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
             uint8_t *fq = reinterpret_cast<uint8_t *>(h);
             for (uint64_t q = 16u + 5u * nb; q < 16u + dpad16(5u * nb); q++) fq[q] = 0;
+        } else if (md == kModePatched) {
+            h[0] = kMagicPatched; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
+            h[4] = (uint32_t)total_e; h[5] = h[6] = h[7] = 0u;
+            uint8_t *fq = reinterpret_cast<uint8_t *>(h);
+            const uint64_t meta = kPxHeader + dpad16(6u * nb), xpos = meta + 16u * total;
+            const uint64_t xhigh = xpos + dpad16(total_e), end = xhigh + dpad16(4u * total_e);
+            for (uint64_t q = kPxHeader + 6u * nb; q < meta; q++) fq[q] = 0;  // the zero pads
+            for (uint64_t q = xpos + total_e; q < xhigh; q++) fq[q] = 0;
+            for (uint64_t q = xhigh + 4u * total_e; q < end; q++) fq[q] = 0;
         } else if (md == kModeRaw) {
             h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
         }
@@ -266,10 +291,38 @@ __device__ __forceinline__ void load_blocks8(const uint32_t *ids, uint64_t k0, u
     for (uint32_t i = 0; i < kBlocksPerWarp; i++) load4_guard(ids, (k0 + i) * kBlock + 4u * lane, n, v[i]);
 }
 
+// Patched codec: width and exception count of one block -- the b in 0..32 minimising the block's
+// bytes 16*b + 5*e_b, e_b = number of gaps >= 2^b, ties to the larger b.  A per-warp histogram of
+// the gaps' bit lengths gives every e_b at once: lane b sums the bins above b.  All 32 lanes call it.
+__device__ __forceinline__ void px_width(const uint32_t g[4], uint32_t lane, uint32_t *hist, uint32_t *b_out,
+                                         uint32_t *e_out)
+{
+    hist[lane] = 0u;
+    if (lane == 0) hist[32] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; j++) atomicAdd(&hist[bitlen32(g[j])], 1u);
+    __syncwarp();
+    uint32_t e = hist[lane + 1];  // gaps of bit length lane + 1
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {  // suffix sum: e = gaps of bit length > lane
+        const uint32_t y = __shfl_down_sync(0xffffffffu, e, o);
+        if (lane + o < 32u) e += y;
+    }
+    const uint32_t key = ((16u * lane + 5u * e) << 6) | (63u - lane);  // min cost, then max b
+    const uint32_t best = min(__reduce_min_sync(0xffffffffu, key), ((16u * 32u) << 6) | (63u - 32u));
+    const uint32_t b = 63u - (best & 63u);
+    *b_out = b;
+    *e_out = b == 32u ? 0u : __shfl_sync(0xffffffffu, e, b & 31u);
+    __syncwarp();  // the histogram is reused for the next block
+}
+
 // W: every warp issues the loads of its eight blocks before using any of them.
+template <bool kPx>
 __global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
 {
-    __shared__ uint32_t ws[kEncWarps];
+    __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
+    __shared__ uint32_t hist[kPx ? kEncWarps : 1][33];
     const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -278,7 +331,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
         load_blocks8(a.ids, k0, n, lane, v);
         const uint32_t before = (lane == 0 && k0 > 0 && k0 < nb) ? a.ids[k0 * kBlock - 1] : 0u;
         unsigned long long bad = ~0ull;
-        uint32_t sum = 0;
+        uint32_t sum = 0, sum_e = 0;
 #pragma unroll
         for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
             const uint64_t k = k0 + i;
@@ -286,21 +339,35 @@ __global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
             if (k >= nb) continue;
             uint32_t g[4];
             gaps_of(v[i], i > 0 ? prev_last : before, k > 0, k, n, lane, g, &bad);
-            const uint32_t b = bitlen32(__reduce_or_sync(0xffffffffu, g[0] | g[1] | g[2] | g[3]));
+            uint32_t b, e = 0;
+            if (kPx) px_width(g, lane, hist[kPx ? warp : 0], &b, &e);
+            else b = bitlen32(__reduce_or_sync(0xffffffffu, g[0] | g[1] | g[2] | g[3]));
             if (lane == 0) {
                 a.s.widths[k] = (uint8_t)b;
                 a.s.bases[k] = v[i][0];
+                if (kPx) a.s.ex[k] = (uint8_t)e;
             }
             sum += b;
+            sum_e += e;
         }
         if (bad != ~0ull) set_error(a.s.ctl, FQ_EUNSORTED, kWhereEncWidths, bad);
-        if (lane == 0) ws[warp] = sum;
+        if (lane == 0) {
+            ws[warp] = sum;
+            we[warp] = sum_e;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t tsum = 0;
-            for (uint32_t w = 0; w < kEncWarps; w++) tsum += ws[w];
+            uint32_t tsum = 0, tex = 0;
+            for (uint32_t w = 0; w < kEncWarps; w++) {
+                tsum += ws[w];
+                tex += we[w];
+            }
             a.s.tile_sum[t] = tsum;
             if (tsum) atomicAdd(&a.s.ctl->total_b, (unsigned long long)tsum);
+            if (kPx) {
+                a.s.tile_ex[t] = tex;
+                if (tex) atomicAdd(&a.s.ctl->total_e, (unsigned long long)tex);
+            }
         }
         __syncthreads();
     }
@@ -339,32 +406,46 @@ __device__ void enc_raw_bodies(const EncArgs &a, const EncPlan &p, uint64_t n, u
 // P: decision, headers (CTA 0), then the packed body tile by tile -- one warp per group of
 // kBlocksPerWarp blocks, offsets from the tile's width bytes (two per lane, one warp scan) -- or
 // the raw bodies.  Packed words go to the output and, identical, to the mirror's inner stream.
+template <bool kPx>
 __global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
 {
     __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
-    __shared__ unsigned long long s_part[kEncWarps];
+    __shared__ unsigned long long s_part[kEncWarps], s_parte[kEncWarps];
     const Ctl *c = a.s.ctl;
     const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
-    const unsigned long long total = c->total_b;
-    const EncPlan p = enc_decide(a, n, nb, total, *reinterpret_cast<const volatile int32_t *>(&c->code));
-    if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, total, p);
+    const unsigned long long total = c->total_b, total_e = kPx ? c->total_e : 0ull;
+    const EncPlan p = enc_decide(a, n, nb, total, total_e, *reinterpret_cast<const volatile int32_t *>(&c->code));
+    if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, total, total_e, p);
     if (p.fatal) return;
     enc_raw_bodies(a, p, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
-    const bool pk1 = p.mode == kModePacked, pk2 = p.mode2 == kModePacked;
+    const uint32_t packed_mode = kPx ? kModePatched : kModePacked;
+    const bool pk1 = p.mode == packed_mode, pk2 = p.mode2 == packed_mode;
     if (!pk1 && !pk2) return;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint64_t off1 = a.fb ? 16u : 0u, off2 = 16u;  // where each output's FQ stream starts
-    const uint64_t payload = 16u + dpad16(5u * nb);
-    unsigned long long prefix = 0;  // width sum of tiles [0, done)
+    const uint64_t hdr = kPx ? kPxHeader : 16u;
+    const uint64_t payload = hdr + dpad16((kPx ? 6u : 5u) * nb);
+    const uint64_t xpos = payload + 16u * total, xhigh = xpos + dpad16(total_e);  // patched: exception areas
+    unsigned long long prefix = 0, prefix_e = 0;  // width and exception sums of tiles [0, done)
     uint64_t done = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        // add the width sums of tiles [done, t)
-        unsigned long long part = 0;
-        for (uint64_t i = done + threadIdx.x; i < t; i += blockDim.x) part += a.s.tile_sum[i];
+        // add the width (and exception) sums of tiles [done, t)
+        unsigned long long part = 0, parte = 0;
+        for (uint64_t i = done + threadIdx.x; i < t; i += blockDim.x) {
+            part += a.s.tile_sum[i];
+            if (kPx) parte += a.s.tile_ex[i];
+        }
         part = warp_sum64(part);
-        if (lane == 0) s_part[warp] = part;
+        if (kPx) parte = warp_sum64(parte);
+        if (lane == 0) {
+            s_part[warp] = part;
+            s_parte[warp] = parte;
+        }
         __syncthreads();
-        for (uint32_t w = 0; w < kEncWarps; w++) prefix += s_part[w];
+        for (uint32_t w = 0; w < kEncWarps; w++) {
+            prefix += s_part[w];
+            if (kPx) prefix_e += s_parte[w];
+        }
         __syncthreads();
         done = t;
         const uint64_t k0 = t * kTileBlocks + warp * kBlocksPerWarp;
@@ -377,16 +458,25 @@ __global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
         const uint32_t incl = warp_incl_scan(x0 + x1);
         // lane l describes blocks 2l and 2l+1 of the tile: exclusive width prefix | b(2l) << 16 | b(2l+1) << 24
         const uint32_t info = (incl - x0 - x1) | (x0 << 16) | (x1 << 24);
-        const uint32_t mine = __shfl_sync(0xffffffffu, info, (warp * kBlocksPerWarp + (lane & 7u)) >> 1);
+        uint32_t infoe = 0;  // the same for exception counts (a tile holds at most 64 * 127 exceptions)
+        if (kPx) {
+            const uint32_t e0 = kk < nb ? a.s.ex[kk] : 0u, e1 = kk + 1 < nb ? a.s.ex[kk + 1] : 0u;
+            const uint32_t ie = warp_incl_scan(e0 + e1);
+            infoe = (ie - e0 - e1) | (e0 << 16) | (e1 << 24);
+        }
+        const uint32_t src = (warp * kBlocksPerWarp + (lane & 7u)) >> 1;
+        const uint32_t mine = __shfl_sync(0xffffffffu, info, src);
+        const uint32_t mine_e = __shfl_sync(0xffffffffu, infoe, src);
         if (lane < kBlocksPerWarp && k0 + lane < nb) {
             const uint8_t wb = (uint8_t)((lane & 1u) ? (mine >> 24) : ((mine >> 16) & 0xffu));
             if (pk1) {
-                reinterpret_cast<uint32_t *>(a.out + off1 + 16)[k0 + lane] = my_base;
-                a.out[off1 + 16 + 4 * nb + k0 + lane] = wb;
+                reinterpret_cast<uint32_t *>(a.out + off1 + hdr)[k0 + lane] = my_base;
+                a.out[off1 + hdr + 4 * nb + k0 + lane] = wb;
+                if (kPx) a.out[off1 + hdr + 5 * nb + k0 + lane] = (uint8_t)((lane & 1u) ? (mine_e >> 24) : ((mine_e >> 16) & 0xffu));
             }
             if (pk2) {
-                reinterpret_cast<uint32_t *>(a.m_out + off2 + 16)[k0 + lane] = my_base;
-                a.m_out[off2 + 16 + 4 * nb + k0 + lane] = wb;
+                reinterpret_cast<uint32_t *>(a.m_out + off2 + hdr)[k0 + lane] = my_base;
+                a.m_out[off2 + hdr + 4 * nb + k0 + lane] = wb;
             }
         }
 #pragma unroll
@@ -395,10 +485,36 @@ __global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
             const uint32_t in = __shfl_sync(0xffffffffu, info, (warp * kBlocksPerWarp + i) >> 1);
             const uint32_t b = (i & 1u) ? (in >> 24) : ((in >> 16) & 0xffu);
             const uint32_t pre = (in & 0xffffu) + ((i & 1u) ? ((in >> 16) & 0xffu) : 0u);
-            if (k >= nb || b == 0) continue;
+            if (k >= nb) continue;
+            uint32_t e = 0;
             uint32_t g[4];
             unsigned long long dummy = ~0ull;
             gaps_of(v[i], 0u, false, k, n, lane, g, &dummy);
+            if (kPx) {
+                const uint32_t ine = __shfl_sync(0xffffffffu, infoe, (warp * kBlocksPerWarp + i) >> 1);
+                e = (i & 1u) ? (ine >> 24) : ((ine >> 16) & 0xffu);
+                if (e) {  // exceptions: slot numbers and high parts, in slot order
+                    const uint32_t pre_e = (ine & 0xffffu) + ((i & 1u) ? ((ine >> 16) & 0xffu) : 0u);
+                    uint32_t cnt = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; j++) cnt += (b < 32u && (g[j] >> b) != 0u) ? 1u : 0u;
+                    const uint32_t ex_incl = warp_incl_scan(cnt);
+                    uint64_t x = prefix_e + pre_e + (ex_incl - cnt);
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        if (b < 32u && (g[j] >> b) != 0u) {
+                            a.out[off1 + xpos + x] = (uint8_t)(4u * lane + j);
+                            reinterpret_cast<uint32_t *>(a.out + off1 + xhigh)[x] = g[j] >> b;
+                            x++;
+                        }
+                    }
+                }
+            }
+            if (b == 0) continue;
+            if (kPx && e) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) g[j] &= (b < 32u) ? ((1u << b) - 1u) : 0xffffffffu;  // low bits only
+            }
             uint32_t w4[4];
             pack_block_words(g, b, pk[warp], lane, w4);
             const uint64_t rel = payload + 16u * (prefix + pre);
@@ -516,6 +632,8 @@ struct FqHeader {
     uint32_t mode;    // kModePacked / kModeRaw / kModeFbRaw
     uint32_t fb_mode;
     uint64_t fq_off, fq_bytes, n, nb, words;
+    uint64_t hdr, meta;  // packed forms: header bytes (16, patched 32) and metadata bytes per block (5, 6)
+    uint64_t e_total;    // patched: exceptions announced by the header
 };
 
 __device__ FqHeader parse_header(const DecArgs &a, uint64_t in_bytes)
@@ -562,12 +680,22 @@ __device__ FqHeader parse_header(const DecArgs &a, uint64_t in_bytes)
         h.over = true;
         return h;
     }
+    h.hdr = 16;
+    h.meta = 5;
+    h.e_total = 0;
     if (magic == kMagicRaw) {
         h.mode = kModeRaw;
         h.ok = h.nb == 0 && h.words == h.n && h.fq_bytes == 16u + dpad16(4u * h.n);
     } else if (magic == kMagicPacked) {
         h.mode = kModePacked;
         h.ok = h.nb == dcdiv(h.n, kBlock) && h.n > 0 && h.fq_bytes >= 16u + dpad16(5u * h.nb);
+    } else if (magic == kMagicPatched && !a.fb && h.fq_bytes >= kPxHeader) {
+        h.mode = kModePatched;
+        h.hdr = kPxHeader;
+        h.meta = 6;
+        h.e_total = ld_u32(fq + 16);
+        h.ok = h.nb == dcdiv(h.n, kBlock) && h.n > 0 && h.fq_bytes >= kPxHeader + dpad16(6u * h.nb) &&
+               ld_u32(fq + 20) == 0u && ld_u32(fq + 24) == 0u && ld_u32(fq + 28) == 0u;
     } else {
         h.ok = false;
     }
@@ -582,28 +710,43 @@ __device__ __forceinline__ uint64_t dec_in_bytes(const DecArgs &a)
 // D0
 __global__ void __launch_bounds__(kEncThreads) dec_tiles_kernel(DecArgs a)
 {
-    __shared__ uint32_t ws[kEncWarps];
+    __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
     const FqHeader h = parse_header(a, dec_in_bytes(a));
-    if (!h.ok || h.mode != kModePacked) return;
-    const uint8_t *wd = a.in + h.fq_off + 16 + 4 * h.nb;
+    if (!h.ok || (h.mode != kModePacked && h.mode != kModePatched)) return;
+    const bool px = h.mode == kModePatched;
+    const uint8_t *wd = a.in + h.fq_off + h.hdr + 4 * h.nb;
     const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        uint32_t b = 0;
+        uint32_t b = 0, e = 0;
         if (threadIdx.x < kTileBlocks) {
             const uint64_t k = t * kTileBlocks + threadIdx.x;
             if (k < h.nb) {
                 b = wd[k];
-                if (b > 32u) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.fq_off + 16 + 4 * h.nb + k);
+                if (b > 32u) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.fq_off + h.hdr + 4 * h.nb + k);
+                if (px) {  // exception count: at most 127 (slot 0 never), none at width 32
+                    e = wd[h.nb + k];
+                    if (e > 127u || (b == 32u && e)) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.hdr + 5 * h.nb + k);
+                }
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-        if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = b;
+        for (int o = 16; o > 0; o >>= 1) {
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+        }
+        if ((threadIdx.x & 31u) == 0) {
+            ws[threadIdx.x >> 5] = b;
+            we[threadIdx.x >> 5] = e;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t sum = 0;
-            for (uint32_t i = 0; i < kEncWarps; i++) sum += ws[i];
+            uint32_t sum = 0, sume = 0;
+            for (uint32_t i = 0; i < kEncWarps; i++) {
+                sum += ws[i];
+                sume += we[i];
+            }
             a.s.tile_sum[t] = sum;
+            if (px) a.s.tile_ex[t] = sume;
         }
         __syncthreads();
     }
@@ -629,6 +772,25 @@ __global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
             c->total_b = total;
             if (h.words != 4u * total || h.fq_bytes != 16u + dpad16(5u * h.nb) + 16u * total) ok = false;
             for (uint64_t i = 16u + 5u * h.nb; i < 16u + dpad16(5u * h.nb); i++)
+                if (fq[i]) ok = false;
+        }
+    }
+    if (ok && h.mode == kModePatched) {
+        const uint8_t *fq = a.in + h.fq_off;
+        const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
+        const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
+        const unsigned long long tex = cta_chunk_scan_u32<kScanThreads>(a.s.tile_ex, a.s.tile_exoff, ntiles, sm);
+        if (threadIdx.x == 0) {
+            c->total_b = total;
+            c->total_e = tex;
+            const uint64_t meta = kPxHeader + dpad16(6u * h.nb), xpos = meta + 16u * total;
+            const uint64_t xhigh = xpos + dpad16(tex), end = xhigh + dpad16(4u * tex);
+            if (h.words != 4u * total || h.e_total != tex || h.fq_bytes != end) ok = false;
+            for (uint64_t i = kPxHeader + 6u * h.nb; ok && i < meta; i++)  // the zero pads
+                if (fq[i]) ok = false;
+            for (uint64_t i = xpos + tex; ok && i < xhigh; i++)
+                if (fq[i]) ok = false;
+            for (uint64_t i = xhigh + 4u * tex; ok && i < end; i++)
                 if (fq[i]) ok = false;
         }
     }
@@ -708,10 +870,12 @@ struct GroupMeta {
     uint32_t info, base, pre;
     uint64_t off;
     uint32_t bytes;
+    uint32_t infoe;  // patched: like info, for the exception counts (in-tile prefix | e(2l) << 16 | e(2l+1) << 24)
+    uint64_t exoff;  // patched: the tile's first exception
 };
 
 __device__ __forceinline__ GroupMeta group_meta(const DecArgs &a, const uint8_t *wd, const uint32_t *bases,
-                                                uint64_t nb, uint64_t grp, uint32_t lane)
+                                                const uint8_t *exn, uint64_t nb, uint64_t grp, uint32_t lane)
 {
     constexpr uint32_t kGroupsPerTile = kTileBlocks / kBlocksPerWarp;
     const uint64_t t = grp / kGroupsPerTile, k0 = grp * kBlocksPerWarp;
@@ -728,6 +892,14 @@ __device__ __forceinline__ GroupMeta group_meta(const DecArgs &a, const uint8_t 
     const uint32_t end = __shfl_sync(0xffffffffu, incl, lead + kBlocksPerWarp / 2 - 1);
     m.off = 16ull * ((uint64_t)tile_base + m.pre);
     m.bytes = 16u * (end - m.pre);
+    m.infoe = 0;
+    m.exoff = 0;
+    if (exn) {
+        const uint32_t e0 = kk < nb ? exn[kk] : 0u, e1 = kk + 1 < nb ? exn[kk + 1] : 0u;
+        const uint32_t ie = warp_incl_scan(e0 + e1);
+        m.infoe = (ie - e0 - e1) | (e0 << 16) | (e1 << 24);
+        m.exoff = a.s.tile_exoff[t];
+    }
     return m;
 }
 
@@ -739,9 +911,10 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
 {
     extern __shared__ __align__(128) uint8_t dbuf[];  // [kEncWarps][2][kDecStage]
     __shared__ __align__(8) unsigned long long bars[kEncWarps][2];
+    __shared__ uint32_t patch[kEncWarps][kBlock];  // patched: one block's high parts by slot
     const Ctl *c = a.s.ctl;
     const uint32_t mode = c->mode;
-    if (mode != kModePacked && mode != kModeRaw) return;
+    if (mode != kModePacked && mode != kModeRaw && mode != kModePatched) return;
     const uint64_t n = c->n, nb = c->nb;
     const uint8_t *fq = a.in + c->fq_offset;
     const uint32_t clear_mode = (a.fb && c->fb_mode == kFbClear) ? 1u : 0u;
@@ -758,9 +931,14 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
         return;
     }
 
-    const uint8_t *wd = fq + 16 + 4 * nb;
-    const uint32_t *bases = reinterpret_cast<const uint32_t *>(fq + 16);
-    const uint8_t *payload = fq + 16 + dpad16(5u * nb);
+    const bool px = mode == kModePatched;
+    const uint64_t hdr = px ? kPxHeader : 16u;
+    const uint8_t *wd = fq + hdr + 4 * nb;
+    const uint32_t *bases = reinterpret_cast<const uint32_t *>(fq + hdr);
+    const uint8_t *exn = px ? fq + hdr + 5 * nb : nullptr;  // patched: exceptions per block
+    const uint8_t *payload = fq + hdr + dpad16((px ? 6u : 5u) * nb);
+    const uint8_t *xslot = payload + 16u * c->total_b;    // patched: exception slots, then high parts
+    const uint32_t *xhigh = reinterpret_cast<const uint32_t *>(xslot + dpad16(c->total_e));
     const uint64_t ngroups = dcdiv(nb, kBlocksPerWarp);
     const uint64_t nwarps = (uint64_t)gridDim.x * kEncWarps;
     uint64_t grp = (uint64_t)blockIdx.x * kEncWarps + warp;
@@ -773,14 +951,14 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
         mbar_init_fence();
     }
     __syncwarp();
-    GroupMeta cur = group_meta(a, wd, bases, nb, grp, lane);
+    GroupMeta cur = group_meta(a, wd, bases, exn, nb, grp, lane);
     if (lane == 0 && cur.bytes) bulk_load(buf, payload + cur.off, cur.bytes, &bar[0]);
     uint32_t phase0 = 0u, phase1 = 0u;
     for (uint32_t it = 0;; it++) {
         const uint32_t stage = it & 1u;
         const uint64_t gn = grp + nwarps;
         GroupMeta nxt{};
-        if (gn < ngroups) nxt = group_meta(a, wd, bases, nb, gn, lane);
+        if (gn < ngroups) nxt = group_meta(a, wd, bases, exn, nb, gn, lane);
         __syncwarp();  // every lane is done with the other buffer (read in the previous iteration)
         if (gn < ngroups && lane == 0 && nxt.bytes)
             bulk_load(buf + (stage ^ 1u) * kDecStage, payload + nxt.off, nxt.bytes, &bar[stage ^ 1u]);
@@ -805,7 +983,38 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
             const uint64_t i0 = k * kBlock + 4u * lane;
             uint32_t out[4];
             bool good;
-            if (k + 1 < nb && b <= 16u) {  // full narrow block: the lean 32-bit path
+            uint32_t e = 0, pre_e = 0;
+            if (px) {
+                const uint32_t ine = __shfl_sync(0xffffffffu, cur.infoe, git * (kBlocksPerWarp / 2) + (i >> 1));
+                e = (i & 1u) ? (ine >> 24) : ((ine >> 16) & 0xffu);
+                pre_e = (ine & 0xffffu) + ((i & 1u) ? ((ine >> 16) & 0xffu) : 0u);
+            }
+            if (e) {  // patched block: low bits, plus each exception's high part above them
+                uint32_t g[4];
+                extract_slots(pk, b, lane, g);
+                uint32_t *pt = patch[warp];
+#pragma unroll
+                for (int j = 0; j < 4; j++) pt[4 * lane + j] = 0u;
+                __syncwarp();
+                const uint64_t x0 = cur.exoff + pre_e;
+                bool okx = true;
+                for (uint32_t q = lane; q < e; q += 32u) {
+                    const uint32_t slot = xslot[x0 + q], prev = q ? xslot[x0 + q - 1] : 0u, high = xhigh[x0 + q];
+                    // slots 1..127, increasing, inside the id range; a nonzero high part that fits above b
+                    if (slot == 0u || slot >= kBlock || slot <= prev || k * kBlock + slot >= n || high == 0u ||
+                        ((uint64_t)high >> (32u - b)) != 0ull)
+                        okx = false;
+                    else
+                        pt[slot] = high;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 4; j++) g[j] |= pt[4 * lane + j] << b;  // b < 32: width 32 has no exceptions
+                __syncwarp();
+                unsigned long long lastv;
+                good = okx && scan_slots(g, base, k, n, lane, out, &lastv);
+                if (k + 1 < nb && lane == 31 && lastv >= (unsigned long long)next) good = false;
+            } else if (k + 1 < nb && b <= 16u) {  // full narrow block: the lean 32-bit path
                 uint32_t lastv;
                 good = unpack_full_narrow(pk, b, base, lane, out, &lastv);
                 if (lane == 31 && lastv >= next) good = false;
@@ -884,11 +1093,20 @@ cudaError_t launch_encode(EncArgs a, uint64_t n_max, cudaStream_t st)
     uint64_t raw_items = cdiv(n_max, 4) * 4;  // the raw bodies P may have to copy instead
     if (a.fb) raw_items = std::max<uint64_t>(raw_items, cdiv(a.nbits, 64));
     if (a.m_out) raw_items = std::max<uint64_t>(raw_items, cdiv(a.m_nbits, 64));
-    const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_widths_kernel, kEncThreads, occ_w));
+    static int occ_wx[64], occ_px[64];
+    if (a.px) {
+        const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_widths_kernel<true>, kEncThreads, occ_wx));
+        const uint32_t gp = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads)),
+                                                         resident_grid(enc_pack_kernel<true>, kEncThreads, occ_px));
+        enc_widths_kernel<true><<<gw, kEncThreads, 0, st>>>(a);
+        enc_pack_kernel<true><<<gp, kEncThreads, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_widths_kernel<false>, kEncThreads, occ_w));
     const uint32_t gp = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads)),
-                                                     resident_grid(enc_pack_kernel, kEncThreads, occ_p));
-    enc_widths_kernel<<<gw, kEncThreads, 0, st>>>(a);
-    enc_pack_kernel<<<gp, kEncThreads, 0, st>>>(a);
+                                                     resident_grid(enc_pack_kernel<false>, kEncThreads, occ_p));
+    enc_widths_kernel<false><<<gw, kEncThreads, 0, st>>>(a);
+    enc_pack_kernel<false><<<gp, kEncThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1032,6 +1250,20 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
     Scratch s = carve(d_work, n, 0);
     cudaError_t e = reset_status(s, n, st);
     if (e == cudaSuccess) e = encode_fq(d_ids, n, nullptr, n, d_out, cap, d_out_bytes, s, st);
+    return cuda_status(e);
+}
+
+fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
+                                uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream)
+{
+    if ((n && !d_ids) || !d_out || !d_out_bytes || !d_work) return FQ_EINVAL;
+    if (n > 0xffffffffull || !aligned16(d_ids) || !aligned16(d_out) || !aligned16(d_work)) return FQ_EINVAL;
+    if (!workspace_fits(work_bytes, n, 0)) return FQ_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch s = carve(d_work, n, 0);
+    EncArgs a{d_ids, n, nullptr, d_out, cap, d_out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0, 1};
+    cudaError_t e = reset_status(s, n, st);
+    if (e == cudaSuccess) e = launch_encode(a, n, st);
     return cuda_status(e);
 }
 

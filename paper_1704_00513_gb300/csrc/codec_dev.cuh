@@ -304,14 +304,11 @@ __device__ __forceinline__ bool unpack_full_narrow(const uint32_t *pk, uint32_t 
     return ok;
 }
 
-// Unpack one block of width b whose payload words start at pk (readable two words past the block),
-// base = the block's first id.  Writes lane's four ids to out[] and returns false if the block is
-// inconsistent (non-zero slot 0 or padding slot, u32 overflow); `last` receives lane's last value.
-__device__ __forceinline__ bool unpack_block(const uint32_t *pk, uint32_t b, uint64_t base, uint64_t k, uint64_t n,
-                                             uint32_t lane, uint32_t out[4], unsigned long long *last)
+// The b-bit slot values of one block whose payload words start at pk (readable two words past
+// the block): lane's slots 4*lane .. 4*lane+3 in g[].
+__device__ __forceinline__ void extract_slots(const uint32_t *pk, uint32_t b, uint32_t lane, uint32_t g[4])
 {
     const uint32_t mask = (b == 32u) ? 0xffffffffu : ((1u << b) - 1u);
-    uint32_t g[4];
     if (b <= 16u) {  // the lane's four slots lie in one 3-word window
         const uint32_t bit0 = 4u * lane * b, ws = bit0 >> 5, sh = bit0 & 31u;
         const unsigned long long x = ((unsigned long long)pk[ws + 1] << 32) | pk[ws];
@@ -327,6 +324,14 @@ __device__ __forceinline__ bool unpack_block(const uint32_t *pk, uint32_t b, uin
             g[j] = (uint32_t)(two >> sh) & mask;
         }
     }
+}
+
+// Ids of block k from its gaps g[] (lane's slots) and base: a 64-bit warp prefix sum of gap + 1.
+// Returns false if the block is inconsistent (non-zero slot 0 or padding slot, u32 overflow);
+// `last` receives lane's last value.
+__device__ __forceinline__ bool scan_slots(const uint32_t g[4], uint64_t base, uint64_t k, uint64_t n,
+                                           uint32_t lane, uint32_t out[4], unsigned long long *last)
+{
     const uint64_t i0 = k * kBlock + 4u * lane;
     bool bad = false;
     unsigned long long lsum64 = 0;
@@ -336,14 +341,7 @@ __device__ __forceinline__ bool unpack_block(const uint32_t *pk, uint32_t b, uin
         if (pad && g[j]) bad = true;
         lsum64 += pad ? 0ull : (unsigned long long)g[j] + 1ull;
     }
-    unsigned long long v;
-    if (b <= 16u) {  // every prefix of a block fits in 32 bits: 128 * 2^16
-        const uint32_t lsum = (uint32_t)lsum64;
-        const uint32_t excl = warp_incl_scan(lsum) - lsum;
-        v = base + excl;
-    } else {
-        v = base + (warp_incl_scan64(lsum64) - lsum64);
-    }
+    unsigned long long v = base + (warp_incl_scan64(lsum64) - lsum64);
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         v += (i0 + j >= n || (lane == 0 && j == 0)) ? 0ull : (unsigned long long)g[j] + 1ull;
@@ -352,6 +350,15 @@ __device__ __forceinline__ bool unpack_block(const uint32_t *pk, uint32_t b, uin
     }
     *last = v;
     return !bad;
+}
+
+// Unpack one block of width b (payload at pk, base = the block's first id): lane's four ids.
+__device__ __forceinline__ bool unpack_block(const uint32_t *pk, uint32_t b, uint64_t base, uint64_t k, uint64_t n,
+                                             uint32_t lane, uint32_t out[4], unsigned long long *last)
+{
+    uint32_t g[4];
+    extract_slots(pk, b, lane, g);
+    return scan_slots(g, base, k, n, lane, out, last);
 }
 
 }  // namespace fq

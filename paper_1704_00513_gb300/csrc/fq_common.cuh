@@ -23,6 +23,8 @@ constexpr uint32_t kScanThreads = 1024;   // single-CTA plan/scan kernels
 constexpr uint32_t kMagicPacked = 0x31505146u;  // "FQP1"
 constexpr uint32_t kMagicRaw = 0x31525146u;     // "FQR1"
 constexpr uint32_t kMagicBitmap = 0x314D4246u;  // "FBM1"
+constexpr uint32_t kMagicPatched = 0x31585146u; // "FQX1": binary packing with exceptions
+constexpr uint32_t kPxHeader = 32;              // bytes of the patched stream's header
 
 enum : uint32_t { kFbRaw = 0, kFbSet = 1, kFbClear = 2 };
 
@@ -32,6 +34,7 @@ enum : uint32_t {
     kModePacked = 1,    // FQ packed
     kModeRaw = 2,       // FQ raw
     kModeFbRaw = 3,     // FB raw words
+    kModePatched = 4,   // FQX packed (exceptions)
 };
 
 // internal stage ids recorded in fq_device_status.where
@@ -57,6 +60,7 @@ struct Ctl {
     uint32_t tile_ticket;          // single-pass encode: next tile to hand out
     uint32_t mode2;                // mode of the mirrored FB stream (kMode*), kModeNone if absent
     unsigned long long out2_bytes;
+    unsigned long long total_e;    // patched codec: exceptions over all blocks
 };
 static_assert(sizeof(Ctl) <= 256, "control block must fit its slot");
 
@@ -71,6 +75,9 @@ struct Scratch {
     uint32_t *btile_cnt;  // [btiles_cap]
     uint32_t *btile_off;  // [btiles_cap]
     uint32_t *positions;  // [pos_cap]  bitmap positions (FB)
+    uint8_t *ex;          // [nb_cap] patched codec: exceptions per block
+    uint32_t *tile_ex;    // [etiles_cap] patched codec: exceptions per tile
+    uint32_t *tile_exoff; // [etiles_cap] patched codec: exception offset of each tile
     uint64_t ids_cap;     // largest id count an encode/decode may see
     uint64_t nbits_cap;
     uint64_t nb_cap, etiles_cap, btiles_cap, pos_cap;
@@ -148,7 +155,7 @@ __device__ __forceinline__ void reset_scratch_device(const Scratch &s)
     c->mode = kModeNone;
     c->mode2 = kModeNone;
     c->fb_mode = kFbRaw;
-    c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = 0;
+    c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = c->total_e = 0;
     c->tile_ticket = 0;
 }
 

@@ -63,6 +63,7 @@ _SIGS = {
     "fq_workspace_bytes": ([_u64, _u64], _u64),
     "fq_work_status": ([_vp, _vp, ctypes.POINTER(_u64)], _i32),
     "fq_frontier_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_frontier_encode_px": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_decode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_encode_static": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fq_bitmap_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
@@ -153,9 +154,11 @@ def workspace(max_ids: int, max_nbits: int, device="cuda") -> torch.Tensor:
 # ----------------------------------------------------------------------------- codec calls
 
 def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work: torch.Tensor | None = None,
-                       stream=None, sync: bool = True, nbytes: torch.Tensor | None = None):
-    """Encode sorted unique uint32 ids (an int32/uint32 CUDA tensor).  Returns (stream bytes, size)
-    when sync, else (out buffer, device size tensor)."""
+                       stream=None, sync: bool = True, nbytes: torch.Tensor | None = None, px: bool = False):
+    """Encode sorted unique uint32 ids (an int32/uint32 CUDA tensor) as an FQ stream, or with
+    px=True as an FQX (patched exceptions) stream.  Returns (stream bytes, size) when sync, else
+    (out buffer, device size tensor)."""
+    name = "fq_frontier_encode_px" if px else "fq_frontier_encode"
     n = ids.numel()
     if out is None:
         out = torch.empty(fq_queue_bound(n), dtype=torch.uint8, device=ids.device)
@@ -163,11 +166,11 @@ def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work:
         work = workspace(n, 0, ids.device)
     if nbytes is None:
         nbytes = torch.zeros(1, dtype=torch.int64, device=ids.device)
-    _check(lib().fq_frontier_encode(_ptr(ids), n, _ptr(out), out.numel(), _ptr(nbytes), _ptr(work), work.numel(),
-                                    _stream(stream)), "fq_frontier_encode")
+    _check(getattr(lib(), name)(_ptr(ids), n, _ptr(out), out.numel(), _ptr(nbytes), _ptr(work), work.numel(),
+                                _stream(stream)), name)
     if not sync:
         return out, nbytes
-    _device_status(work, stream, "fq_frontier_encode")
+    _device_status(work, stream, name)
     size = int(nbytes.item())
     return out[:size], size
 

@@ -174,6 +174,20 @@ def geometric_set(n: int, mean_gap: float, seed: int, device="cpu") -> torch.Ten
     return torch.cumsum(steps, 0)
 
 
+def outlier_set(n: int, mean_gap: float, frac: float, lo: int, hi: int, seed: int, device="cpu") -> torch.Tensor:
+    """geometric_set's ids with a fraction `frac` of the gaps widened by a uniform draw in [lo, hi):
+    mostly small gaps with rare large jumps, the shape patched exceptions are for."""
+    if n == 0:
+        return torch.zeros(0, dtype=torch.int64, device=device)
+    v = geometric_set(n, mean_gap, seed, device=device)
+    steps = torch.diff(v, prepend=torch.zeros(1, dtype=torch.int64, device=device))
+    pick = uniform32(seed, 6, 0, n, device=device)
+    extra = uniform32(seed, 7, 0, n, device=device)
+    hit = pick < round(frac * 2**32)
+    steps = steps + torch.where(hit, lo + extra % max(1, hi - lo), torch.zeros_like(extra))
+    return torch.cumsum(steps, 0)
+
+
 def bernoulli_bitmap(nbits: int, density: float, seed: int, device="cpu") -> torch.Tensor:
     """Bitmap of nbits i.i.d. Bernoulli(density) bits as int32 words (little-endian halves of the
     uint64 words: bit i is bit i%32 of int32 word i/32); bits past nbits are zero."""
