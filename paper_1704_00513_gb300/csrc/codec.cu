@@ -991,29 +991,52 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
             }
             if (e) {  // patched block: low bits, plus each exception's high part above them
                 uint32_t g[4];
-                extract_slots(pk, b, lane, g);
+                if (b <= 16u) extract_narrow(pk, b, lane, g);
+                else extract_slots(pk, b, lane, g);
                 uint32_t *pt = patch[warp];
-#pragma unroll
-                for (int j = 0; j < 4; j++) pt[4 * lane + j] = 0u;
-                __syncwarp();
                 const uint64_t x0 = cur.exoff + pre_e;
                 bool okx = true;
-                for (uint32_t q = lane; q < e; q += 32u) {
-                    const uint32_t slot = xslot[x0 + q], prev = q ? xslot[x0 + q - 1] : 0u, high = xhigh[x0 + q];
-                    // slots 1..127, increasing, inside the id range; a nonzero high part that fits above b
-                    if (slot == 0u || slot >= kBlock || slot <= prev || k * kBlock + slot >= n || high == 0u ||
-                        ((uint64_t)high >> (32u - b)) != 0ull)
-                        okx = false;
-                    else
-                        pt[slot] = high;
+                uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, hor = 0;  // 128-bit mask of exception slots
+                for (uint32_t q0 = 0; q0 < e; q0 += 32u) {
+                    const uint32_t q = q0 + lane;
+                    uint32_t slot = 0, bit = 0;
+                    if (q < e) {
+                        slot = xslot[x0 + q];
+                        const uint32_t prev = q ? xslot[x0 + q - 1] : 0u, high = xhigh[x0 + q];
+                        // slots 1..127, increasing, inside the id range; a nonzero high part that fits above b
+                        if (slot == 0u || slot >= kBlock || slot <= prev || k * kBlock + slot >= n || high == 0u ||
+                            ((uint64_t)high >> (32u - b)) != 0ull) {
+                            okx = false;
+                        } else {
+                            pt[slot] = high;
+                            bit = 1u << (slot & 31u);
+                            hor |= high;
+                        }
+                    }
+                    m0 |= __reduce_or_sync(0xffffffffu, (slot >> 5) == 0u ? bit : 0u);
+                    m1 |= __reduce_or_sync(0xffffffffu, (slot >> 5) == 1u ? bit : 0u);
+                    m2 |= __reduce_or_sync(0xffffffffu, (slot >> 5) == 2u ? bit : 0u);
+                    m3 |= __reduce_or_sync(0xffffffffu, (slot >> 5) == 3u ? bit : 0u);
                 }
                 __syncwarp();
+                const uint32_t mw = (lane < 8u) ? m0 : (lane < 16u) ? m1 : (lane < 24u) ? m2 : m3;
+                const uint32_t mine4 = (mw >> ((4u * lane) & 31u)) & 0xfu;  // my four slots
 #pragma unroll
-                for (int j = 0; j < 4; j++) g[j] |= pt[4 * lane + j] << b;  // b < 32: width 32 has no exceptions
-                __syncwarp();
-                unsigned long long lastv;
-                good = okx && scan_slots(g, base, k, n, lane, out, &lastv);
-                if (k + 1 < nb && lane == 31 && lastv >= (unsigned long long)next) good = false;
+                for (int j = 0; j < 4; j++)
+                    if ((mine4 >> j) & 1u) g[j] |= pt[4 * lane + j] << b;  // b < 32: width 32 has no exceptions
+                __syncwarp();  // the stage is rewritten by the next patched block
+                const uint32_t widest = b + bitlen32(__reduce_or_sync(0xffffffffu, hor));
+                // every lane runs the scan (it shuffles across the warp); then the exception checks count
+                if (k + 1 < nb && widest <= 16u) {  // increments still sum below 2^32: the 32-bit scan
+                    uint32_t lastv;
+                    good = scan_full32(g, base, lane, out, &lastv);
+                    if (lane == 31 && lastv >= next) good = false;
+                } else {
+                    unsigned long long lastv;
+                    good = scan_slots(g, base, k, n, lane, out, &lastv);
+                    if (k + 1 < nb && lane == 31 && lastv >= (unsigned long long)next) good = false;
+                }
+                good = good && okx;
             } else if (k + 1 < nb && b <= 16u) {  // full narrow block: the lean 32-bit path
                 uint32_t lastv;
                 good = unpack_full_narrow(pk, b, base, lane, out, &lastv);

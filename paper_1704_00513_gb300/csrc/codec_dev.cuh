@@ -269,24 +269,28 @@ __device__ __forceinline__ uint4 pack_block(const uint32_t g[4], uint32_t b, uin
     return q;
 }
 
-// Unpack a FULL block (all 128 slots hold ids) of width 0 <= b <= 16 with 32-bit arithmetic only:
-// a lane's four slots are the 4*b bits at 4*lane*b, read as a funnel-shifted 64-bit window of
-// three staged words; a 32-bit warp scan of the slot increments (a block's increments sum to at
-// most 128 * 2^16) gives the ids.  The only checks a full block needs: slot 0 holds 0, and the
-// last id does not pass 2^32 - 1 (lane 31 tests it in 64 bits).  Returns false if either fails.
-__device__ __forceinline__ bool unpack_full_narrow(const uint32_t *pk, uint32_t b, uint32_t base, uint32_t lane,
-                                                   uint32_t out[4], uint32_t *last)
+// The slots of a block of width 0 <= b <= 16 with 32-bit arithmetic only: a lane's four slots are
+// the 4*b bits at 4*lane*b, read as a funnel-shifted 64-bit window of three staged words.
+__device__ __forceinline__ void extract_narrow(const uint32_t *pk, uint32_t b, uint32_t lane, uint32_t g[4])
 {
     const uint32_t bit0 = 4u * lane * b, ws = bit0 >> 5, sh = bit0 & 31u;
     const uint32_t w0 = pk[ws], w1 = pk[ws + 1], w2 = pk[ws + 2];
     const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
     const uint32_t mask = (1u << b) - 1u;
-    uint32_t g[4];
     g[0] = lo & mask;
     g[1] = __funnelshift_r(lo, hi, b) & mask;  // b < 32
     const uint32_t s2 = 2u * b, s3 = 3u * b;
     g[2] = (s2 < 32u ? __funnelshift_r(lo, hi, s2) : (hi >> (s2 - 32u))) & mask;
     g[3] = (s3 < 32u ? __funnelshift_r(lo, hi, s3) : (hi >> (s3 - 32u))) & mask;
+}
+
+// Ids of a FULL block (all 128 slots hold ids) whose increments g + 1 sum to less than 2^32 (true
+// for any block of width <= 16: at most 128 * 2^16): a 32-bit warp scan.  The only checks a full
+// block needs: slot 0 holds 0, and the last id does not pass 2^32 - 1 (lane 31 tests it in 64
+// bits).  Returns false if either fails.
+__device__ __forceinline__ bool scan_full32(const uint32_t g[4], uint32_t base, uint32_t lane, uint32_t out[4],
+                                            uint32_t *last)
+{
     const uint32_t first = (lane == 0) ? 0u : g[0] + 1u;  // slot 0 of the block is the base itself
     const uint32_t lsum = first + g[1] + g[2] + g[3] + 3u;
     const uint32_t excl = warp_incl_scan(lsum) - lsum;
@@ -302,6 +306,15 @@ __device__ __forceinline__ bool unpack_full_narrow(const uint32_t *pk, uint32_t 
     bool ok = !(lane == 0 && g[0] != 0u);
     if (lane == 31) ok = ok && ((unsigned long long)base + excl + lsum <= 0xffffffffull);
     return ok;
+}
+
+// Unpack a FULL block of width 0 <= b <= 16 with 32-bit arithmetic only.
+__device__ __forceinline__ bool unpack_full_narrow(const uint32_t *pk, uint32_t b, uint32_t base, uint32_t lane,
+                                                   uint32_t out[4], uint32_t *last)
+{
+    uint32_t g[4];
+    extract_narrow(pk, b, lane, g);
+    return scan_full32(g, base, lane, out, last);
 }
 
 // The b-bit slot values of one block whose payload words start at pk (readable two words past
