@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-codec", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep the built-in launch grids (no autotuning)")
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--codec-only", action="store_true",
                    help="only the standalone codec points (sorted sets, geometric gaps); prints them as JSON")
@@ -309,6 +310,10 @@ def run_fqbfs(args, world, rank, local):
     warm_roots, timed_roots = warm_and_timed(roots, world, rank, args.warmup, args.steps)
     stream = torch.cuda.current_stream()
 
+    # launch autotuning (not timed): codec grids on synthetic sets, then the bottom-up and hub grids
+    # on two warm-up roots; every timed section below runs with the tuned table
+    from paper_1704_00513_gb300 import autotune
+    tuned = [] if args.no_tune else autotune.tune_codec(dev, log_sizes=(20, 24, 26)) + autotune.tune_bfs(g, warm_roots[:2])
     for r in warm_roots:
         g.bfs(r, depth=depth, parent=parent, flags=flags, max_levels=64)
     torch.cuda.synchronize()
@@ -390,6 +395,8 @@ def run_fqbfs(args, world, rank, local):
         codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])
     batched = None
     if not args.no_batched and rank == 0:
+        if not args.no_tune:
+            tuned += autotune.tune_batch(dev)
         batched = {"codec_4096_segments": batched_codec(dev, peaks["hbm_gbs"]),
                    "msbfs_scale22_64_roots": batched_msbfs(dev)}
     served = None
@@ -421,6 +428,7 @@ def run_fqbfs(args, world, rank, local):
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "codec": codec, "batched": batched, "serving": served,
                 "cpu_baseline": cpu, "e2e": e2e,
+                "autotune": [{k: e[k] for k in ("site", "class", "ctas_per_sm", "ms", "default_ms")} for e in tuned],
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -349,6 +349,27 @@ fq_status fq_server_info(fq_server *s, uint64_t *resident, uint64_t *in_use, uin
 /* The server's clock (seconds, monotonic) used for the request timestamps. */
 double fq_server_clock(void);
 
+/* ------------------------------------------------------------------ launch autotuning
+ * Grid sizes of the launches whose best size depends on the GPU and the input size, settable per
+ * size class (floor(log2(items)), 0..40) as CTAs per SM; 0 restores the built-in choice.  A tuner
+ * (paper_1704_00513_gb300/autotune.py) times the candidates on synthetic inputs and caches the
+ * winners in a JSON file.  The table is process-wide and read at each launch; a device-loop BFS graph
+ * (FQ_BFS_DEVICE_LOOP) that baked the old grids is rebuilt on its next call. */
+#define FQ_TUNE_ENC_WIDTHS 0u   /* encode, widths kernel (items: ids)                   */
+#define FQ_TUNE_ENC_PACK 1u     /* encode, pack kernel (items: ids)                     */
+#define FQ_TUNE_DEC_UNPACK 2u   /* decode, unpack kernel (items: ids)                   */
+#define FQ_TUNE_BAT_ENCODE 3u   /* batched encode, persistent kernel (items: all ids)   */
+#define FQ_TUNE_BAT_DUNPACK 4u  /* batched decode, unpack kernel (items: all ids)       */
+#define FQ_TUNE_BU_SWEEP 5u     /* BFS bottom-up sweep (items: vertices)                */
+#define FQ_TUNE_TD_HUB 6u       /* BFS top-down hub items (items: vertices)             */
+#define FQ_TUNE_NUM_SITES 7u
+#define FQ_TUNE_MAX_CLASS 40u
+
+/* FQ_EINVAL for an unknown site, a class above FQ_TUNE_MAX_CLASS or more than 32 CTAs per SM. */
+fq_status fq_tune_set(uint32_t site, uint32_t size_class, uint32_t ctas_per_sm);
+/* The value set for (site, class), 0 if none (or the arguments are out of range). */
+uint32_t fq_tune_get(uint32_t site, uint32_t size_class);
+
 #ifdef __cplusplus
 }
 #endif

@@ -620,7 +620,7 @@ fq_status fq_frontier_encode_batch(const uint32_t *d_ids, const uint64_t *d_seg_
     static bool done[64] = {false};
     if (allow_smem_b(bat_encode_kernel, kBatchSmem, done) != cudaSuccess) return FQ_ECUDA;
     bat_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)3 * num_sms());
+    const uint32_t grid = tuned_grid(FQ_TUNE_BAT_ENCODE, total_ids, (uint64_t)3 * num_sms(), a.b.tiles_cap);
     bat_encode_kernel<<<grid, kEncThreads, kBatchSmem, st>>>(a);
     bat_fixup_kernel<<<(uint32_t)std::min<uint64_t>(S, (uint64_t)8 * num_sms()), 256, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? FQ_OK : FQ_ECUDA;
@@ -643,7 +643,7 @@ fq_status fq_frontier_decode_batch(const uint8_t *d_in, const uint64_t *d_in_off
     const uint32_t grid = (uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)8 * num_sms());
     bat_dtiles_kernel<<<grid, kEncThreads, 0, st>>>(a);
     bat_dscan_kernel<<<(uint32_t)std::min<uint64_t>(S, (uint64_t)8 * num_sms()), kEncThreads, 0, st>>>(a);
-    bat_dunpack_kernel<<<(uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)3 * num_sms()), kEncThreads,
+    bat_dunpack_kernel<<<tuned_grid(FQ_TUNE_BAT_DUNPACK, total_ids, (uint64_t)3 * num_sms(), a.b.tiles_cap), kEncThreads,
                          kBatchDecSmem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? FQ_OK : FQ_ECUDA;
 }

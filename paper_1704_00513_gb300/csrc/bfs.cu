@@ -685,6 +685,7 @@ struct fq_graph {
     const uint32_t *dl_parent;
     const uint8_t *dl_log;
     uint32_t dl_mode;
+    uint32_t dl_tune;  // tuning-table generation the graph's grids were taken from
 };
 
 namespace {
@@ -796,7 +797,7 @@ cudaError_t step_top_down(fq_graph *g, bool codec, uint64_t n_f, int32_t newdept
     td_expand_kernel<<<grid, kThreads, 0, st>>>(qin, n_f, g->off, g->cols, vis32, next32, d_depth, d_parent, newdepth,
                                                 g->items, &g->ctr->hub_items, g->items_cap, g->n, g->sq.ctl,
                                                 &g->ctr->m_f_next, ls);
-    td_hub_kernel<<<sms * 6, kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32, next32,
+    td_hub_kernel<<<tuned_grid(FQ_TUNE_TD_HUB, g->n, (uint64_t)sms * 6, (uint64_t)sms * 32), kThreads, 0, st>>>(g->items, &g->ctr->hub_items, g->items_cap, g->cols, vis32, next32,
                                                 d_depth, d_parent, newdepth, g->off, &g->ctr->m_f_next, ls);
     return cudaGetLastError();
 }
@@ -814,7 +815,8 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
     const int sms = num_sms();
     const uint64_t *fin = codec ? g->fbits2 : g->fbits;
     const uint64_t words32 = cdiv(g->n, 32);
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16);
+    const uint32_t grid = tuned_grid(FQ_TUNE_BU_SWEEP, g->n, std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16),
+                                     cdiv(words32, kThreads / 32));
     bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
         reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
         reinterpret_cast<uint32_t *>(g->next), g->off, g->cols, d_depth, d_parent, newdepth, g->n, &g->ctr->examined,
@@ -1156,7 +1158,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         // the whole search is one graph launch; the host reads the records once at the end
         const uint32_t mode = (codec ? 0u : FQ_BFS_NO_CODEC) | (want_visited ? FQ_BFS_VISITED_STREAM : 0u);
         if (!g->dl_exec || g->dl_depth != d_depth || g->dl_parent != d_parent || g->dl_log != d_stream_log ||
-            g->dl_mode != mode) {
+            g->dl_mode != mode || g->dl_tune != tune_generation()) {
             if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
             if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
             g->dl_exec = nullptr;
@@ -1169,6 +1171,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             g->dl_parent = d_parent;
             g->dl_log = d_stream_log;
             g->dl_mode = mode;
+            g->dl_tune = tune_generation();
         }
         LoopState *hls = reinterpret_cast<LoopState *>(g->host + kHostLs);
         fq_level_record *hrec = reinterpret_cast<fq_level_record *>(g->host + kHostLs + al256(sizeof(LoopState)));

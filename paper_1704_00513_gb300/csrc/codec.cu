@@ -96,6 +96,22 @@ void note_cuda_error(cudaError_t e, int line)
     g_last_cuda_line = line;
 }
 
+// Autotuned CTAs per SM by launch site and size class (0: the built-in grid).
+static uint8_t g_tune[FQ_TUNE_NUM_SITES][FQ_TUNE_MAX_CLASS + 1];
+static uint32_t g_tune_generation = 0;  // bumped by every change: cached graphs that baked a grid rebuild
+
+uint32_t tune_generation() { return g_tune_generation; }
+
+uint32_t tuned_grid(uint32_t site, uint64_t items, uint64_t default_grid, uint64_t max_grid)
+{
+    uint32_t cls = 0;
+    for (uint64_t x = items; x > 1; x >>= 1) cls++;
+    const uint32_t per_sm = (site < FQ_TUNE_NUM_SITES && cls <= FQ_TUNE_MAX_CLASS) ? g_tune[site][cls] : 0u;
+    uint64_t g = per_sm ? (uint64_t)per_sm * (uint64_t)num_sms() : default_grid;
+    g = std::min<uint64_t>(g, std::max<uint64_t>(max_grid, 1));
+    return (uint32_t)std::max<uint64_t>(g, 1);
+}
+
 int num_sms()
 {
     static int cached[64] = {0};
@@ -1117,17 +1133,16 @@ cudaError_t launch_encode(EncArgs a, uint64_t n_max, cudaStream_t st)
     if (a.fb) raw_items = std::max<uint64_t>(raw_items, cdiv(a.nbits, 64));
     if (a.m_out) raw_items = std::max<uint64_t>(raw_items, cdiv(a.m_nbits, 64));
     static int occ_wx[64], occ_px[64];
+    const uint64_t pack_items = std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads));
     if (a.px) {
-        const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_widths_kernel<true>, kEncThreads, occ_wx));
-        const uint32_t gp = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads)),
-                                                         resident_grid(enc_pack_kernel<true>, kEncThreads, occ_px));
+        const uint32_t gw = tuned_grid(FQ_TUNE_ENC_WIDTHS, n_max, resident_grid(enc_widths_kernel<true>, kEncThreads, occ_wx), tiles);
+        const uint32_t gp = tuned_grid(FQ_TUNE_ENC_PACK, n_max, resident_grid(enc_pack_kernel<true>, kEncThreads, occ_px), pack_items);
         enc_widths_kernel<true><<<gw, kEncThreads, 0, st>>>(a);
         enc_pack_kernel<true><<<gp, kEncThreads, 0, st>>>(a);
         return cudaGetLastError();
     }
-    const uint32_t gw = (uint32_t)std::min<uint64_t>(tiles, resident_grid(enc_widths_kernel<false>, kEncThreads, occ_w));
-    const uint32_t gp = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads)),
-                                                     resident_grid(enc_pack_kernel<false>, kEncThreads, occ_p));
+    const uint32_t gw = tuned_grid(FQ_TUNE_ENC_WIDTHS, n_max, resident_grid(enc_widths_kernel<false>, kEncThreads, occ_w), tiles);
+    const uint32_t gp = tuned_grid(FQ_TUNE_ENC_PACK, n_max, resident_grid(enc_pack_kernel<false>, kEncThreads, occ_p), pack_items);
     enc_widths_kernel<false><<<gw, kEncThreads, 0, st>>>(a);
     enc_pack_kernel<false><<<gp, kEncThreads, 0, st>>>(a);
     return cudaGetLastError();
@@ -1186,7 +1201,8 @@ cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
     dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
     dec_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
     FQ_CUDA_TRY(prepare_unpack());
-    dec_unpack_kernel<<<grid_for(std::max(tiles * kEncThreads, cap), kEncThreads, 3 * num_sms()), kEncThreads, kDecSmem,
+    dec_unpack_kernel<<<tuned_grid(FQ_TUNE_DEC_UNPACK, cap, grid_for(std::max(tiles * kEncThreads, cap), kEncThreads, 3 * num_sms()),
+                                   cdiv(std::max(tiles * kEncThreads, cap), kEncThreads)), kEncThreads, kDecSmem,
                         st>>>(a);
     return cudaGetLastError();
 }
@@ -1274,6 +1290,22 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
     cudaError_t e = reset_status(s, n, st);
     if (e == cudaSuccess) e = encode_fq(d_ids, n, nullptr, n, d_out, cap, d_out_bytes, s, st);
     return cuda_status(e);
+}
+
+fq_status fq_tune_set(uint32_t site, uint32_t size_class, uint32_t ctas_per_sm)
+{
+    if (site >= FQ_TUNE_NUM_SITES || size_class > FQ_TUNE_MAX_CLASS || ctas_per_sm > 32u) return FQ_EINVAL;
+    if (g_tune[site][size_class] != (uint8_t)ctas_per_sm) {
+        g_tune[site][size_class] = (uint8_t)ctas_per_sm;
+        g_tune_generation++;
+    }
+    return FQ_OK;
+}
+
+uint32_t fq_tune_get(uint32_t site, uint32_t size_class)
+{
+    if (site >= FQ_TUNE_NUM_SITES || size_class > FQ_TUNE_MAX_CLASS) return 0u;
+    return g_tune[site][size_class];
 }
 
 fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,

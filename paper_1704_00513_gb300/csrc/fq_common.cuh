@@ -256,6 +256,12 @@ __device__ unsigned long long cta_chunk_scan_u32(const uint32_t *in, uint32_t *o
 namespace fq {
 // The last CUDA error the library saw in this thread (reported by fq_last_cuda_error()).
 void note_cuda_error(cudaError_t e, int line);
+// Grid of a tunable launch site for `items` work items: the autotuned CTAs per SM (fq_tune_set)
+// times the SM count when one is set for the items' size class, else default_grid; at most
+// max_grid, at least 1.
+uint32_t tuned_grid(uint32_t site, uint64_t items, uint64_t default_grid, uint64_t max_grid);
+// Changes whenever the tuning table does (a graph that captured grids must then be rebuilt).
+uint32_t tune_generation();
 }
 
 #define FQ_CUDA_TRY(expr)                                \

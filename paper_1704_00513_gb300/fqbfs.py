@@ -23,6 +23,8 @@ FQ_OK, FQ_EINVAL, FQ_ENOMEM, FQ_ENOSPC, FQ_ECORRUPT, FQ_EUNSORTED, FQ_ETIMEOUT, 
 FQ_TOP_DOWN, FQ_BOTTOM_UP = 0, 1
 FQ_BFS_VISITED_STREAM, FQ_BFS_FORCE_TOP_DOWN, FQ_BFS_FORCE_BOTTOM_UP, FQ_BFS_TIMING, FQ_BFS_NO_CODEC = 1, 2, 4, 8, 16
 FQ_BFS_DEVICE_LOOP = 32
+TUNE_SITES = ("enc_widths", "enc_pack", "dec_unpack", "bat_encode", "bat_dunpack", "bu_sweep", "td_hub")
+TUNE_MAX_CLASS = 40
 KCLASS = ("top_down", "bottom_up", "compact", "encode", "decode", "other")
 
 _u64, _u32, _i32, _vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
@@ -64,6 +66,8 @@ _SIGS = {
     "fq_work_status": ([_vp, _vp, ctypes.POINTER(_u64)], _i32),
     "fq_frontier_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_encode_px": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_tune_set": ([_u32, _u32, _u32], _i32),
+    "fq_tune_get": ([_u32, _u32], _u32),
     "fq_frontier_decode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_encode_static": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "fq_bitmap_encode": ([_vp, _u64, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
@@ -152,6 +156,18 @@ def workspace(max_ids: int, max_nbits: int, device="cuda") -> torch.Tensor:
 
 
 # ----------------------------------------------------------------------------- codec calls
+
+def tune_set(site: str | int, size_class: int, ctas_per_sm: int) -> None:
+    """Grid of launch site `site` for inputs of size class floor(log2(items)): ctas_per_sm CTAs per SM
+    (0 restores the built-in grid)."""
+    idx = TUNE_SITES.index(site) if isinstance(site, str) else int(site)
+    _check(lib().fq_tune_set(idx, int(size_class), int(ctas_per_sm)), "fq_tune_set")
+
+
+def tune_get(site: str | int, size_class: int) -> int:
+    idx = TUNE_SITES.index(site) if isinstance(site, str) else int(site)
+    return int(lib().fq_tune_get(idx, int(size_class)))
+
 
 def fq_frontier_encode(ids: torch.Tensor, out: torch.Tensor | None = None, work: torch.Tensor | None = None,
                        stream=None, sync: bool = True, nbytes: torch.Tensor | None = None, px: bool = False):
