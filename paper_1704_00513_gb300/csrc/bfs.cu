@@ -948,8 +948,9 @@ cudaError_t seg_compact(void *p)
 }
 
 // Build the device-driven loop for these buffers and mode:
-//   init -> while(h_while) { begin -> [if h_dense: Q+B from bitmap | Q+B mirrored] -> [V] ->
+//   init -> while(h_while) { begin -> [if h_dense: Q+B from bitmap | Q+B mirrored] ->
 //                            [if h_dir: top-down | bottom-up] -> compact [-> log] -> end }
+// with V's encode on a parallel branch from begin to compact (overlapped with the rest).
 cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
 {
     fq_graph *g = b.g;
@@ -991,10 +992,11 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             if ((e = cudaGraphAddChildGraphNode(&c0, enc[0], nullptr, 0, sg_dense)) != cudaSuccess) goto done;
             if ((e = cudaGraphAddChildGraphNode(&c1, enc[1], nullptr, 0, sg_sparse)) != cudaSuccess) goto done;
         }
-        if (b.want_v) {
-            if ((e = cudaGraphAddChildGraphNode(&tmp, body, &n_last, 1, sg_v)) != cudaSuccess) goto done;
-            n_last = tmp;
-        }
+        // V_d is coded on a branch of its own, beside the Q/B encode, decode and expansion (it reads
+        // only the previous compaction's positions and the visited bitmap, which this level's
+        // expansion does not touch); the compaction waits for both branches.
+        cudaGraphNode_t n_v = nullptr;
+        if (b.want_v && (e = cudaGraphAddChildGraphNode(&n_v, body, &n_begin, 1, sg_v)) != cudaSuccess) goto done;
         if ((e = add_conditional(&tmp, body, &n_last, h_dir, cudaGraphCondTypeIf, 2, dir)) != cudaSuccess) goto done;
         n_last = tmp;
         {
@@ -1002,7 +1004,10 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, sg_td)) != cudaSuccess) goto done;
             if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, sg_bu)) != cudaSuccess) goto done;
         }
-        if ((e = cudaGraphAddChildGraphNode(&tmp, body, &n_last, 1, sg_cmp)) != cudaSuccess) goto done;
+        {
+            const cudaGraphNode_t deps[2] = {n_last, n_v};
+            if ((e = cudaGraphAddChildGraphNode(&tmp, body, deps, n_v ? 2 : 1, sg_cmp)) != cudaSuccess) goto done;
+        }
         n_last = tmp;
         {
             LoopState *ls = g->ls;
