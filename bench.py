@@ -393,6 +393,7 @@ def run_fqbfs(args, world, rank, local):
 
     if not args.no_codec:
         codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])
+        codec["threshold"] = codec_threshold(dev)
     batched = None
     if not args.no_batched and rank == 0:
         if not args.no_tune:
@@ -515,6 +516,62 @@ def codec_points(dev, peak_gbs, points=CODEC_POINTS, reps=5):
         del ids, out, work, dec
         torch.cuda.empty_cache()
     return res
+
+
+LINKS_GBPS = {"nvlink5_per_direction": 900.0, "pcie5_x16": 64.0, "infiniband_ndr": 50.0}
+
+
+def codec_threshold(dev, logs=range(4, 25, 2), mean_gap=16.0, reps=20):
+    """The compression threshold's break-even size (sec. 5.4.2): for each n, the per-call encode and
+    decode time on this GPU (calls replayed from a captured CUDA graph, so launch gaps but not the
+    host's launch rate count) and the stream size; for each link bandwidth B, the smallest measured
+    n for which encode + |stream|/B + decode beats 4n/B."""
+    from paper_1704_00513_gb300 import fqbfs, inputs
+    stream = torch.cuda.current_stream()
+    pts = []
+    for L in logs:
+        n = 1 << L
+        v = inputs.geometric_set(n, mean_gap, seed=SEED + L, device=dev)
+        ids = torch.where(v >= 2**31, v - 2**32, v).to(torch.int32)
+        out = torch.empty(fqbfs.fq_queue_bound(n), dtype=torch.uint8, device=dev)
+        work = fqbfs.workspace(n, 0, dev)
+        nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+        dec = torch.empty(n, dtype=torch.int32, device=dev)
+        ndec = torch.zeros(1, dtype=torch.int64, device=dev)
+        s0, s1 = _events()
+        for _ in range(3):
+            fqbfs.fq_frontier_encode(ids, out=out, work=work, sync=False, nbytes=nbytes)
+        torch.cuda.synchronize()
+        size = int(nbytes.item())
+        for _ in range(3):
+            fqbfs.fq_frontier_decode(out, cap=n, out=dec, work=work, in_bytes=size, sync=False, n_out=ndec)
+        torch.cuda.synchronize()
+
+        # reps calls captured back to back in a CUDA graph, so the time is the GPU's, not the
+        # Python loop's launch rate
+        def timed(call):
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr):
+                for _ in range(reps):
+                    call()
+            gr.replay()
+            torch.cuda.synchronize()
+            s0.record(stream)
+            gr.replay()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            return s0.elapsed_time(s1) / reps / 1e3
+
+        t_enc = timed(lambda: fqbfs.fq_frontier_encode(ids, out=out, work=work, sync=False, nbytes=nbytes))
+        t_dec = timed(lambda: fqbfs.fq_frontier_decode(out, cap=n, out=dec, work=work, in_bytes=size, sync=False,
+                                                       n_out=ndec))
+        pts.append({"n": n, "bytes": size, "encode_us": t_enc * 1e6, "decode_us": t_dec * 1e6})
+    even = {}
+    for link, gbps in LINKS_GBPS.items():
+        b = gbps * 1e9
+        wins = [p["n"] for p in pts if (p["encode_us"] + p["decode_us"]) * 1e-6 + p["bytes"] / b < 4 * p["n"] / b]
+        even[link] = min(wins) if wins else None
+    return {"mean_gap": mean_gap, "points": pts, "break_even_ids": even}
 
 
 def _events():

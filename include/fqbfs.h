@@ -226,7 +226,10 @@ typedef struct fq_bfs_opts {
     uint32_t alpha; /* top-down -> bottom-up when m_f * alpha > m_u   (0 selects 14) */
     uint32_t beta;  /* bottom-up -> top-down when n_f * beta < n      (0 selects 24) */
     uint32_t flags;
-    uint32_t reserved;
+    uint32_t min_codec_ids; /* compression threshold: a level whose frontier has fewer ids skips the
+                               codec stage (its frontier is consumed raw; Q_d, B_d record 0 bytes and
+                               are not logged); 0 codes every level.  sec. 5.4.2 "Usage of
+                               compression thresholds" */
 } fq_bfs_opts;
 
 /* kernel classes reported by FQ_BFS_TIMING */

@@ -59,7 +59,7 @@ static_assert(sizeof(Counters) == 256, "counter block is 256 bytes");
 // before each run; loop_init_kernel sets the rest; loop_end_kernel advances it once per level.
 struct LoopParams {
     uint32_t root, alpha, beta, flags;
-    uint32_t max_levels, pad;
+    uint32_t max_levels, min_codec_ids;
     unsigned long long log_cap;
 };
 struct LoopState {
@@ -68,6 +68,7 @@ struct LoopState {
     unsigned long long log_used;
     uint32_t d, dir;
     int32_t status, soft_status;  // a hard error stops the loop; ENOSPC of the log does not
+    uint32_t coded, pad;          // this level runs the codec stage (the frontier reaches the threshold)
     fq_bfs_stats stats;
 };
 constexpr uint32_t kMaxDeviceRecords = 4096;
@@ -514,7 +515,9 @@ __global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m)
 
 // Direction rule of the host loop: m_f*alpha > m_u  <=>  m_f > floor(m_u/alpha), and
 // n_f*beta < n  <=>  n_f < ceil(n/beta), so no product can overflow.
-__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int has_dense, cudaGraphConditionalHandle h_dense,
+// Handles set here: h_enc (0 queue + mirrored bitmap, 1 queue + bitmap from the bitmap, 2 no codec
+// stage) and h_dir (0 top-down, 1 bottom-up, +2 when the level skips the codec stage).
+__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGraphConditionalHandle h_enc,
                                   cudaGraphConditionalHandle h_dir)
 {
     const uint32_t flags = ls->p.flags;
@@ -525,8 +528,10 @@ __global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int has_dense, cuda
     else if (dir == FQ_TOP_DOWN && ls->m_f > ls->m_u / alpha) dir = FQ_BOTTOM_UP;
     else if (dir == FQ_BOTTOM_UP && ls->n_f < (n + beta - 1) / beta) dir = FQ_TOP_DOWN;
     ls->dir = dir;
-    if (has_dense) cudaGraphSetConditional(h_dense, 2ull * ls->n_f > n ? 1u : 0u);
-    cudaGraphSetConditional(h_dir, dir == FQ_TOP_DOWN ? 1u : 0u);
+    const bool coded = codec && ls->n_f >= ls->p.min_codec_ids;
+    ls->coded = coded ? 1u : 0u;
+    if (codec) cudaGraphSetConditional(h_enc, !coded ? 2u : (2ull * ls->n_f > n ? 1u : 0u));
+    cudaGraphSetConditional(h_dir, (dir == FQ_TOP_DOWN ? 0u : 1u) + (coded ? 0u : 2u));
 }
 
 // Appends the level's Q_d, B_d [, V_d] to the stream log when they fit (the test loop_end_kernel
@@ -534,7 +539,9 @@ __global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int has_dense, cuda
 __global__ void log_append_kernel(const LoopState *ls, const Counters *ctr, const uint8_t *qs, const uint8_t *bs,
                                   const uint8_t *vs, uint8_t *log, int want_v)
 {
-    const unsigned long long qb = ctr->q_bytes, bb = ctr->b_bytes, vb = want_v ? ctr->v_bytes : 0ull;
+    const bool coded = ls->coded != 0u;
+    const unsigned long long qb = coded ? ctr->q_bytes : 0ull, bb = coded ? ctr->b_bytes : 0ull;
+    const unsigned long long vb = want_v ? ctr->v_bytes : 0ull;
     const unsigned long long used = ls->log_used;
     if (used + qb + bb + vb > ls->p.log_cap) return;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
@@ -569,7 +576,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     fq_bfs_stats &st = ls->stats;
     if (ctr->r_err_q != FQ_OK) ls->status = ctr->r_err_q;
     else if (ctr->r_err_v != FQ_OK) ls->status = ctr->r_err_v;
-    else if (codec && dir == FQ_TOP_DOWN && ctr->dec_n != n_f) ls->status = FQ_ECORRUPT;
+    else if (ls->coded && dir == FQ_TOP_DOWN && ctr->dec_n != n_f) ls->status = FQ_ECORRUPT;
     if (ls->status != FQ_OK) {
         ls_out->status = ls->status;
         cudaGraphSetConditional(h_while, 0u);
@@ -577,24 +584,29 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     }
     const unsigned long long examined = dir == FQ_TOP_DOWN ? m_f : ctr->r_examined;
     const unsigned long long nf_next = ctr->n_f_next, mf_next = ctr->r_m_f;
-    const unsigned long long qb = codec ? ctr->q_bytes : 0, bb = codec ? ctr->b_bytes : 0;
+    const bool coded = ls->coded != 0u;
+    const unsigned long long qb = coded ? ctr->q_bytes : 0, bb = coded ? ctr->b_bytes : 0;
     const unsigned long long vb = want_v ? ctr->v_bytes : 0;
     const unsigned long long nbytes = (n + 7) / 8;
     const bool dense = 2ull * n_f > n;
 
-    if (codec) {
-        st.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + nbytes + bb + (want_v ? nbytes + vb : 0);
-        st.kernel_launches[FQ_K_ENCODE] += (dense ? 8 : 2) + (want_v ? 2 : 0);
+    if (coded) {
+        st.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + nbytes + bb;
+        st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
+    }
+    if (want_v) {
+        st.kernel_bytes[FQ_K_ENCODE] += nbytes + vb;
+        st.kernel_launches[FQ_K_ENCODE] += 2;
     }
     if (dir == FQ_TOP_DOWN) {
-        if (codec) {
+        if (coded) {
             st.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
             st.kernel_launches[FQ_K_DECODE] += 3;
         }
         st.kernel_bytes[FQ_K_TOP_DOWN] += 4 * examined + 20 * n_f + 8 * nf_next;
         st.kernel_launches[FQ_K_TOP_DOWN] += 2;
     } else {
-        if (codec) {
+        if (coded) {
             st.kernel_bytes[FQ_K_DECODE] += bb + nbytes;
             st.kernel_launches[FQ_K_DECODE] += 4;
         }
@@ -606,7 +618,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     st.kernel_launches[FQ_K_OTHER] += 2 + (has_log ? 1 : 0);  // loop_begin, loop_end [, log_append]
 
     unsigned long long log_off = ~0ull;
-    if (has_log && codec) {
+    if (has_log && codec && (coded || want_v)) {
         const unsigned long long need = qb + bb + vb;
         if (ls->log_used + need > ls->p.log_cap) {
             ls->soft_status = FQ_ENOSPC;
@@ -937,6 +949,16 @@ cudaError_t seg_bottom_up(void *p)
     }
     return step_bottom_up(c.g, c.codec, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
 }
+cudaError_t seg_top_down_plain(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    return step_top_down(c.g, false, 0, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
+}
+cudaError_t seg_bottom_up_plain(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    return step_bottom_up(c.g, false, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
+}
 cudaError_t seg_compact(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
@@ -956,53 +978,61 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
     fq_graph *g = b.g;
     cudaStream_t cs = g->dl_stream;
     cudaGraph_t sg_init = nullptr, sg_dense = nullptr, sg_sparse = nullptr, sg_v = nullptr, sg_td = nullptr,
-                sg_bu = nullptr, sg_cmp = nullptr, top = nullptr;
+                sg_bu = nullptr, sg_tdp = nullptr, sg_bup = nullptr, sg_cmp = nullptr, top = nullptr;
     LoopBuild ctx = b;
     cudaError_t e = capture_segment(cs, &sg_init, seg_init, &ctx);
     if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_dense, seg_dense, &ctx);
     if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_sparse, seg_sparse, &ctx);
     if (e == cudaSuccess && b.want_v) e = capture_segment(cs, &sg_v, seg_visited, &ctx);
-    if (e == cudaSuccess) e = capture_segment(cs, &sg_td, seg_top_down, &ctx);
-    if (e == cudaSuccess) e = capture_segment(cs, &sg_bu, seg_bottom_up, &ctx);
+    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_td, seg_top_down, &ctx);
+    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_bu, seg_bottom_up, &ctx);
+    if (e == cudaSuccess) e = capture_segment(cs, &sg_tdp, seg_top_down_plain, &ctx);
+    if (e == cudaSuccess) e = capture_segment(cs, &sg_bup, seg_bottom_up_plain, &ctx);
     if (e == cudaSuccess) e = capture_segment(cs, &sg_cmp, seg_compact, &ctx);
     if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
     if (e != cudaSuccess) goto done;
     {
         cudaGraphNode_t n_init, n_while, n_begin, n_last, tmp;
-        cudaGraph_t body, enc[2], dir[2];
-        cudaGraphConditionalHandle h_while, h_dense = 0, h_dir;
+        cudaGraph_t body, enc[3], dir[4];
+        cudaGraphConditionalHandle h_while, h_enc, h_dir;
         if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, sg_init)) != cudaSuccess) goto done;
         if ((e = cudaGraphConditionalHandleCreate(&h_while, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) goto done;
         if ((e = add_conditional(&n_while, top, &n_init, h_while, cudaGraphCondTypeWhile, 1, &body)) != cudaSuccess)
             goto done;
-        if (b.codec && (e = cudaGraphConditionalHandleCreate(&h_dense, body, 0, 0)) != cudaSuccess) goto done;
+        h_enc = 0;  // only a graph with the codec stage has the encode switch
+        if (b.codec && (e = cudaGraphConditionalHandleCreate(&h_enc, body, 0, 0)) != cudaSuccess) goto done;
         if ((e = cudaGraphConditionalHandleCreate(&h_dir, body, 0, 0)) != cudaSuccess) goto done;
         {
             LoopState *ls = g->ls;
             uint64_t n = g->n;
-            int has_dense = b.codec ? 1 : 0;
-            void *args[] = {&ls, &n, &has_dense, &h_dense, &h_dir};
+            int codec = b.codec ? 1 : 0;
+            void *args[] = {&ls, &n, &codec, &h_enc, &h_dir};
             if ((e = add_kernel_node(&n_begin, body, nullptr, (void *)loop_begin_kernel, args)) != cudaSuccess) goto done;
         }
         n_last = n_begin;
-        if (b.codec) {
-            if ((e = add_conditional(&tmp, body, &n_last, h_dense, cudaGraphCondTypeIf, 2, enc)) != cudaSuccess) goto done;
+        if (b.codec) {  // switch: mirrored, from the bitmap, or (below the threshold) no encode
+            if ((e = add_conditional(&tmp, body, &n_last, h_enc, cudaGraphCondTypeSwitch, 3, enc)) != cudaSuccess) goto done;
             n_last = tmp;
             cudaGraphNode_t c0, c1;
-            if ((e = cudaGraphAddChildGraphNode(&c0, enc[0], nullptr, 0, sg_dense)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c1, enc[1], nullptr, 0, sg_sparse)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c0, enc[0], nullptr, 0, sg_sparse)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c1, enc[1], nullptr, 0, sg_dense)) != cudaSuccess) goto done;
         }
         // V_d is coded on a branch of its own, beside the Q/B encode, decode and expansion (it reads
         // only the previous compaction's positions and the visited bitmap, which this level's
         // expansion does not touch); the compaction waits for both branches.
         cudaGraphNode_t n_v = nullptr;
         if (b.want_v && (e = cudaGraphAddChildGraphNode(&n_v, body, &n_begin, 1, sg_v)) != cudaSuccess) goto done;
-        if ((e = add_conditional(&tmp, body, &n_last, h_dir, cudaGraphCondTypeIf, 2, dir)) != cudaSuccess) goto done;
+        // switch: top-down / bottom-up, each with the decode of the coded form, or (+2) on the raw form
+        if ((e = add_conditional(&tmp, body, &n_last, h_dir, cudaGraphCondTypeSwitch, 4, dir)) != cudaSuccess) goto done;
         n_last = tmp;
         {
-            cudaGraphNode_t c0, c1;
-            if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, sg_td)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, sg_bu)) != cudaSuccess) goto done;
+            cudaGraphNode_t c0, c1, c2, c3;
+            // without the codec stage the switch never takes cases 0 and 1; they hold the raw bodies
+            // too, so that no case is an empty graph
+            if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, b.codec ? sg_td : sg_tdp)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, b.codec ? sg_bu : sg_bup)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c2, dir[2], nullptr, 0, sg_tdp)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c3, dir[3], nullptr, 0, sg_bup)) != cudaSuccess) goto done;
         }
         {
             const cudaGraphNode_t deps[2] = {n_last, n_v};
@@ -1020,7 +1050,7 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
         }
     }
 done:
-    for (cudaGraph_t *gp : {&sg_init, &sg_dense, &sg_sparse, &sg_v, &sg_td, &sg_bu, &sg_cmp})
+    for (cudaGraph_t *gp : {&sg_init, &sg_dense, &sg_sparse, &sg_v, &sg_td, &sg_bu, &sg_tdp, &sg_bup, &sg_cmp})
         if (*gp) cudaGraphDestroy(*gp);  // child-graph nodes hold their own copies
     if (e != cudaSuccess) {
         note_cuda_error(e, __LINE__);
@@ -1146,6 +1176,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     const uint32_t alpha = (opts && opts->alpha) ? opts->alpha : 14u;
     const uint32_t beta = (opts && opts->beta) ? opts->beta : 24u;
     const uint32_t flags = opts ? opts->flags : 0u;
+    const uint32_t min_codec_ids = opts ? opts->min_codec_ids : 0u;
     const bool codec = !(flags & FQ_BFS_NO_CODEC);
     const bool want_visited = codec && (flags & FQ_BFS_VISITED_STREAM);
     const uint64_t n = g->n;
@@ -1186,6 +1217,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         prm.beta = beta;
         prm.flags = flags;
         prm.max_levels = h_levels ? std::min<uint32_t>(max_levels, kMaxDeviceRecords) : 0u;
+        prm.min_codec_ids = min_codec_ids;
         prm.log_cap = d_stream_log ? stream_log_cap : 0ull;
         hls->p = prm;
         FQ_TRY(cudaMemcpyAsync(&g->ls->p, &hls->p, sizeof(LoopParams), cudaMemcpyHostToDevice, st));
@@ -1233,7 +1265,8 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         // 1. encode F_d (Q_d and B_d), and V_d
         tm.begin(FQ_K_ENCODE);
         int enc_launches = 0;
-        if (codec) {
+        const bool coded = codec && n_f >= min_codec_ids;  // below the threshold the frontier crosses raw
+        if (coded) {
             const bool dense = 2 * n_f > n;
             FQ_TRY(step_encode_q(g, dense, n_f, nullptr, st));
             enc_launches = dense ? 8 : 2;
@@ -1253,16 +1286,16 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
 
         // 3 + 4. decode the consumed form, expand
         tm.begin(FQ_K_DECODE);
-        if (codec && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, st));
-        if (codec && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, st));
-        tm.end(FQ_K_DECODE, codec ? (dir == FQ_TOP_DOWN ? 3 : 4) : 0);
+        if (coded && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, st));
+        if (coded && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, st));
+        tm.end(FQ_K_DECODE, coded ? (dir == FQ_TOP_DOWN ? 3 : 4) : 0);
         if (dir == FQ_TOP_DOWN) {
             tm.begin(FQ_K_TOP_DOWN);
-            FQ_TRY(step_top_down(g, codec, n_f, newdepth, d_depth, d_parent, nullptr, st));
+            FQ_TRY(step_top_down(g, coded, n_f, newdepth, d_depth, d_parent, nullptr, st));
             tm.end(FQ_K_TOP_DOWN, 2);
         } else {
             tm.begin(FQ_K_BOTTOM_UP);
-            FQ_TRY(step_bottom_up(g, codec, newdepth, d_depth, d_parent, nullptr, st));
+            FQ_TRY(step_bottom_up(g, coded, newdepth, d_depth, d_parent, nullptr, st));
             tm.end(FQ_K_BOTTOM_UP, 1);
         }
 
@@ -1279,25 +1312,26 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         tm.collect(FQ_K_COMPACT);
         if (hc->r_err_q != FQ_OK) return hc->r_err_q;
         if (hc->r_err_v != FQ_OK) return hc->r_err_v;
-        if (codec && dir == FQ_TOP_DOWN && hc->dec_n != n_f) return FQ_ECORRUPT;
+        if (coded && dir == FQ_TOP_DOWN && hc->dec_n != n_f) return FQ_ECORRUPT;
 
         const uint64_t examined = dir == FQ_TOP_DOWN ? m_f : hc->r_examined;
         const uint64_t nf_next = hc->n_f_next, mf_next = hc->r_m_f;
-        const uint64_t qb = codec ? hc->q_bytes : 0, bb = codec ? hc->b_bytes : 0, vb = want_visited ? hc->v_bytes : 0;
+        const uint64_t qb = coded ? hc->q_bytes : 0, bb = coded ? hc->b_bytes : 0, vb = want_visited ? hc->v_bytes : 0;
 
         // algorithmic bytes of this level (design model)
-        if (codec) stats.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + (n + 7) / 8 + bb + (want_visited ? (n + 7) / 8 + vb : 0);
+        if (coded) stats.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + (n + 7) / 8 + bb;
+        if (want_visited) stats.kernel_bytes[FQ_K_ENCODE] += (n + 7) / 8 + vb;
         if (dir == FQ_TOP_DOWN) {
-            if (codec) stats.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
+            if (coded) stats.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
             stats.kernel_bytes[FQ_K_TOP_DOWN] += 4 * examined + 20 * n_f + 8 * nf_next;
         } else {
-            if (codec) stats.kernel_bytes[FQ_K_DECODE] += bb + (n + 7) / 8;
+            if (coded) stats.kernel_bytes[FQ_K_DECODE] += bb + (n + 7) / 8;
             stats.kernel_bytes[FQ_K_BOTTOM_UP] += 3 * ((n + 7) / 8) + 16 * (n - visited_count) + 4 * examined + 8 * nf_next;
         }
         stats.kernel_bytes[FQ_K_COMPACT] += 3 * ((n + 7) / 8) + 20 * nf_next;
 
         uint64_t log_off = ~0ull;
-        if (d_stream_log && codec) {
+        if (d_stream_log && codec && (coded || want_visited)) {
             const uint64_t need = qb + bb + vb;
             if (log_used + need > stream_log_cap) {
                 result = FQ_ENOSPC;

@@ -39,7 +39,7 @@ class FqError(RuntimeError):
 
 
 class fq_bfs_opts(ctypes.Structure):
-    _fields_ = [("alpha", _u32), ("beta", _u32), ("flags", _u32), ("reserved", _u32)]
+    _fields_ = [("alpha", _u32), ("beta", _u32), ("flags", _u32), ("min_codec_ids", _u32)]
 
 
 class fq_bfs_stats(ctypes.Structure):
@@ -352,7 +352,7 @@ class Graph:
 
     def bfs(self, root: int, depth: torch.Tensor | None = None, parent: torch.Tensor | None | bool = True,
             alpha: int = 14, beta: int = 24, flags: int = 0, record_streams: bool = False, max_levels: int = 4096,
-            stream=None) -> BfsResult:
+            stream=None, min_codec_ids: int = 0) -> BfsResult:
         dev = self.offsets.device
         if depth is None:
             depth = torch.empty(self.n, dtype=torch.int32, device=dev)
@@ -360,7 +360,7 @@ class Graph:
             parent = torch.empty(self.n, dtype=torch.int32, device=dev)
         elif parent is False:
             parent = None
-        opts = fq_bfs_opts(alpha, beta, flags, 0)
+        opts = fq_bfs_opts(alpha, beta, flags, min_codec_ids)
         stats = fq_bfs_stats()
         levels = self._levels.get(max_levels)
         if levels is None:  # reused across calls: only the first stats.levels entries are read

@@ -248,3 +248,51 @@ def test_device_loop_log_overflow_reports_enospc(rmat16):
     assert torch.equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
     g.close()
+
+
+@LOOPS
+def test_compression_threshold_skips_small_frontiers(rmat16, loop):
+    """Levels whose frontier has fewer ids than the threshold skip the codec stage: Q_d and B_d are
+    empty, V_d is still coded; every coded level's streams, the depths and the schedule stay exact."""
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    for r in roots[:3]:
+        thr = 200
+        res = g.bfs(r, flags=fqbfs.FQ_BFS_VISITED_STREAM | loop, record_streams=True, min_codec_ids=thr)
+        ref_depth, _ = oracle.bfs(off, cols, r)
+        assert np.array_equal(res.depth.cpu().numpy(), ref_depth)
+        assert oracle.validate(off, cols, r, ref_depth, res.parent.cpu().numpy().view(np.uint32)) == 0
+        ref = oracle.level_streams(ref_depth, record_visited=True)
+        sched = oracle.level_schedule(off, cols, ref_depth)
+        skipped = 0
+        for rec, st, want, sc in zip(res.levels, res.streams, ref, sched):
+            assert rec["direction"] == sc["direction"] and rec["examined"] == sc["examined"]
+            if rec["n_f"] < thr:
+                skipped += 1
+                assert rec["q_bytes"] == 0 and rec["b_bytes"] == 0
+            else:
+                assert np.array_equal(st["Q"].cpu().numpy(), want["Q"])
+                assert np.array_equal(st["B"].cpu().numpy(), want["B"])
+            assert np.array_equal(st["V"].cpu().numpy(), want["V"])
+        assert skipped > 0
+        # a threshold above every frontier: nothing coded but V; same depths
+        res2 = g.bfs(r, flags=fqbfs.FQ_BFS_VISITED_STREAM | loop, min_codec_ids=1 << 30)
+        assert np.array_equal(res2.depth.cpu().numpy(), ref_depth)
+        assert res2.stats["enc_queue_bytes"] == 0 and res2.stats["enc_bitmap_bytes"] == 0
+        assert res2.stats["enc_visited_bytes"] == res.stats["enc_visited_bytes"]
+    g.close()
+
+
+def test_threshold_records_equal_between_loop_drivers(rmat16):
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    for thr in (0, 100, 5000):
+        a = g.bfs(roots[2], flags=fqbfs.FQ_BFS_VISITED_STREAM, record_streams=True, min_codec_ids=thr)
+        b = g.bfs(roots[2], flags=fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP, record_streams=True,
+                  min_codec_ids=thr)
+        assert a.levels == b.levels
+        for k in ("enc_queue_bytes", "enc_bitmap_bytes", "enc_visited_bytes", "kernel_bytes"):
+            assert a.stats[k] == b.stats[k], (thr, k)
+        for k in ("top_down", "bottom_up", "compact", "encode", "decode"):
+            assert a.stats["kernel_launches"][k] == b.stats["kernel_launches"][k], (thr, k)
+    g.close()
