@@ -14,6 +14,9 @@ the BFS depths:
 * ``fb_encode`` / ``fb_decode`` -- bitmap frontiers through the same codec (sec. 3.3, 5.2).
 * ``level_schedule``          -- per-level n_f, m_f, m_u, direction and edges examined of a
   direction-optimising BFS (sec. 3.1; switching rule as read in the design notes).
+* ``fr_encode`` / ``fr_decode`` -- frame of reference on unsorted values (Eq. 5-6).
+* ``pl_encode`` / ``pl_decode`` -- the predecessor list as level sets plus level-relative
+  parent ranks (the predecessor reduction of sec. 6.5, compressed).
 * ``level_streams``           -- the per-level encoded frontier queue, frontier bitmap and
   visited bitmap (the data the method compresses around its exchanges, Alg. "Our BFS algorithm
   with SpVM and compression").
@@ -65,6 +68,9 @@ def _load():
             lib.orc_fq_encode.argtypes, lib.orc_fq_encode.restype = [u32p, u64, u8p, u64, u64p], ctypes.c_int
             lib.orc_fq_decode.argtypes, lib.orc_fq_decode.restype = [u8p, u64, u32p, u64, u64p], ctypes.c_int
             lib.orc_px_size.argtypes, lib.orc_px_size.restype = [u64, u64, u64], u64
+            lib.orc_fr_size.argtypes, lib.orc_fr_size.restype = [u64, u64], u64
+            lib.orc_fr_encode.argtypes, lib.orc_fr_encode.restype = [u32p, u64, u8p, u64, u64p], ctypes.c_int
+            lib.orc_fr_decode.argtypes, lib.orc_fr_decode.restype = [u8p, u64, u32p, u64, u64p], ctypes.c_int
             lib.orc_px_encode.argtypes, lib.orc_px_encode.restype = [u32p, u64, u8p, u64, u64p], ctypes.c_int
             lib.orc_px_decode.argtypes, lib.orc_px_decode.restype = [u8p, u64, u32p, u64, u64p], ctypes.c_int
             lib.orc_fb_encode.argtypes, lib.orc_fb_encode.restype = [u64p, u64, u8p, u64, u64p], ctypes.c_int
@@ -163,6 +169,130 @@ def px_decode(stream, cap: int | None = None):
     if st != OK:
         return st, np.zeros(0, np.uint32)
     return st, out[: n.value].copy()
+
+
+def fr_encode(values, cap: int | None = None):
+    """Frame-of-reference encode of unsorted uint32 values; returns (status, stream bytes)."""
+    v = _as(values, np.uint32)
+    n = v.size
+    cap = fq_raw_size(n) if cap is None else int(cap)
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    nbytes = ctypes.c_uint64(0)
+    st = _load().orc_fr_encode(_ptr(v, ctypes.c_uint32), n, _ptr(out, ctypes.c_uint8), cap, ctypes.byref(nbytes))
+    if st != OK:
+        return st, np.zeros(0, np.uint8)
+    return st, out[: nbytes.value].copy()
+
+
+def fr_decode(stream, cap: int | None = None):
+    """Decode an FR stream; returns (status, uint32 values)."""
+    s = _as(stream, np.uint8)
+    if cap is None:
+        cap = int(s[4:8].view(np.uint32)[0]) if s.size >= 16 else 0
+    out = np.zeros(max(int(cap), 1), dtype=np.uint32)
+    n = ctypes.c_uint64(0)
+    st = _load().orc_fr_decode(_ptr(s, ctypes.c_uint8), s.size, _ptr(out, ctypes.c_uint32), int(cap), ctypes.byref(n))
+    if st != OK:
+        return st, np.zeros(0, np.uint32)
+    return st, out[: n.value].copy()
+
+
+def parent_ranks(depth, parent):
+    """Per level d >= 1 of a BFS tree: for each vertex of F_d in increasing id order, the index of
+    its parent within F_{d-1} (sorted).  The predecessor list as level-relative ranks: with the
+    levels' sets (the Q_d streams) they give back every parent."""
+    depth = _as(depth, np.int32)
+    parent = _as(parent, np.uint32)
+    levels = int(depth.max()) + 1 if depth.size and depth.max() >= 0 else 0
+    sets = [np.nonzero(depth == d)[0].astype(np.uint32) for d in range(levels)]
+    out = []
+    for d in range(1, levels):
+        par = parent[sets[d]]
+        r = np.searchsorted(sets[d - 1], par)
+        if np.any(r >= sets[d - 1].size) or np.any(sets[d - 1][np.minimum(r, sets[d - 1].size - 1)] != par):
+            raise ValueError(f"a parent of level {d} is not in level {d - 1}")
+        out.append(r.astype(np.uint32))
+    return out
+
+
+PL_MAGIC = 0x314C5046  # "FPL1"
+
+
+def pl_encode(depth, parent):
+    """Predecessor-list container "FPL1" of a BFS tree (depth int32[n], -1 unreached; parent
+    uint32[n], parent[root] = root).  The thesis reduces its predecessor list uncompressed at the
+    end of a BFS (sec. 6.5, predecessor reduction; its cost in the results chapter); here it is
+    written as the level sets plus level-relative parent ranks:
+
+      header u32 {"FPL1", n, L, reached}; u64 off[2L]: stream k is [off[k], off[k+1]) from the
+      container's start (off[0] = 16 + 16 L; every stream a multiple of 16 bytes);
+      streams 0 .. L-1: FQ(F_d), the vertices of level d in increasing order (F_0 = {root});
+      streams L .. 2L-2: FR(R_d) for d = 1 .. L-1, R_d[i] = the index of parent[F_d[i]] in F_{d-1}.
+
+    L = max depth + 1.  Raises ValueError if (depth, parent) is not a BFS tree (one vertex at
+    depth 0 that is its own parent, every other reached vertex's parent one level up)."""
+    d = _as(depth, np.int32)
+    p = _as(parent, np.uint32)
+    n = d.size
+    if n == 0 or n > 0xFFFFFFFF or d.max() < 0:
+        raise ValueError("empty tree")
+    L = int(d.max()) + 1
+    sets = [np.nonzero(d == k)[0].astype(np.uint32) for k in range(L)]
+    if sets[0].size != 1 or p[sets[0][0]] != sets[0][0]:
+        raise ValueError("level 0 must hold exactly the root, its own parent")
+    if np.any(d < -1):
+        raise ValueError("depth below -1")
+    ranks = parent_ranks(d, p)
+    streams = []
+    for f in sets:
+        st, q = fq_encode(f)
+        assert st == OK
+        streams.append(q)
+    for r in ranks:
+        st, q = fr_encode(r)
+        assert st == OK
+        streams.append(q)
+    reached = int(sum(f.size for f in sets))
+    head = np.array([PL_MAGIC, n, L, reached], np.uint32).view(np.uint8)
+    off = [16 + 16 * L]
+    for q in streams:
+        off.append(off[-1] + q.size)
+    table = np.array(off, np.uint64).view(np.uint8)
+    return np.concatenate([head, table] + streams)
+
+
+def pl_decode(stream, n: int):
+    """Inverse of pl_encode: (depth int32[n], parent uint32[n]); unreached vertices get depth -1
+    and parent 2^32 - 1.  Raises ValueError on any inconsistency."""
+    s = _as(stream, np.uint8)
+    if s.size < 16:
+        raise ValueError("short container")
+    magic, nn, L, reached = (int(x) for x in s[:16].view(np.uint32))
+    if magic != PL_MAGIC or nn != n or L < 1 or s.size < 16 + 16 * L:
+        raise ValueError("bad container header")
+    off = s[16: 16 + 16 * L].view(np.uint64).astype(np.int64)
+    if off[0] != 16 + 16 * L or off[-1] != s.size or np.any(np.diff(off) < 16) or np.any(off % 16):
+        raise ValueError("bad stream table")
+    depth = np.full(n, -1, np.int32)
+    parent = np.full(n, 0xFFFFFFFF, np.uint32)
+    sets = []
+    for k in range(L):
+        st, f = fq_decode(s[off[k]: off[k + 1]])
+        if st != OK or f.size == 0 or (f.size and int(f.max()) >= n):
+            raise ValueError(f"bad level stream {k}")
+        if np.any(depth[f] != -1):
+            raise ValueError(f"vertex repeated at level {k}")
+        depth[f] = k
+        sets.append(f)
+    if sets[0].size != 1 or sum(f.size for f in sets) != reached:
+        raise ValueError("bad level sizes")
+    parent[sets[0]] = sets[0]
+    for k in range(1, L):
+        st, r = fr_decode(s[off[L + k - 1]: off[L + k]])
+        if st != OK or r.size != sets[k].size or np.any(r >= sets[k - 1].size):
+            raise ValueError(f"bad rank stream of level {k}")
+        parent[sets[k]] = sets[k - 1][r]
+    return depth, parent
 
 
 def fb_encode(words, nbits: int, cap: int | None = None):

@@ -18,6 +18,8 @@
  *   orc_px_encode/decode  binary packing with patched exceptions ("Patched coding and
  *                      Exceptions", sec. 5.2, Eq. 8-9; the PFOR family in sec. 5.3): per block
  *                      the width b that minimises the block's bytes, gaps >= 2^b stored apart
+ *   orc_fr_encode/decode  frame of reference without differencing (Eq. 5-6 as printed: per block
+ *                      the minimum as base, width = bit length of max - min) for unsorted values
  *   orc_fb_encode/decode  frontier/visited bitmap codec: positions of the minority bit value,
  *                      coded with the queue codec, or the raw words (bitmap frontiers, sec. 3.3
  *                      "Sparse vector with pop counting"; lossless requirement, sec. 5.2)
@@ -46,6 +48,8 @@ enum {
 #define ORC_MAGIC_RAW    ((uint32_t)'F' | ((uint32_t)'Q' << 8) | ((uint32_t)'R' << 16) | ((uint32_t)'1' << 24))
 #define ORC_MAGIC_BITMAP ((uint32_t)'F' | ((uint32_t)'B' << 8) | ((uint32_t)'M' << 16) | ((uint32_t)'1' << 24))
 #define ORC_MAGIC_PATCHED ((uint32_t)'F' | ((uint32_t)'Q' << 8) | ((uint32_t)'X' << 16) | ((uint32_t)'1' << 24))
+#define ORC_MAGIC_FOR ((uint32_t)'F' | ((uint32_t)'R' << 8) | ((uint32_t)'P' << 16) | ((uint32_t)'1' << 24))
+#define ORC_MAGIC_FOR_RAW ((uint32_t)'F' | ((uint32_t)'R' << 8) | ((uint32_t)'R' << 16) | ((uint32_t)'1' << 24))
 
 #define ORC_BLOCK 128u /* B, the block length of binary packing (sec. 5.2, S4-BP128 in sec. 5.3) */
 
@@ -500,6 +504,167 @@ int orc_px_decode(const uint8_t *in, uint64_t in_bytes, uint32_t *out, uint64_t 
             if (value > 0xFFFFFFFFu)
                 return ORC_ECORRUPT;
             out[i] = (uint32_t)value;
+        }
+        bit0 += 128u * bk;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ frame of reference "FR"
+ *
+ * Unsorted u32 values in blocks of 128 (Eq. 5: every value of a block is stored as its offset from
+ * the block's minimum; Eq. 6: the block's width is the bit length of max - min).  Layout:
+ *   packed {u32 "FRP1", n, nb, payload_words = 4*sum(b)}, u32 min[nb], u8 b[nb], zero pad to 16,
+ *          per block 4*b_k words, slot j = v[128k+j] - min_k at bits [j*b_k, (j+1)*b_k), slots
+ *          past n are 0;
+ *   raw    {u32 "FRR1", n, 0, n}, u32 v[n], zero pad to 16.
+ * The packed form is written only when strictly smaller than the raw one.
+ */
+
+uint64_t orc_fr_size(uint64_t nb, uint64_t sum_b) { return 16u + pad16(5u * nb) + 16u * sum_b; }
+
+int orc_fr_encode(const uint32_t *v, uint64_t n, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
+{
+    uint64_t nb, k, j, t, i, sum_b = 0, size, packed_size, raw_size, bit0;
+    uint8_t *b;
+    uint32_t *mn;
+    int packed;
+
+    *out_bytes = 0;
+    if (n > 0xFFFFFFFFu)
+        return ORC_EINVAL;
+    nb = (n + ORC_BLOCK - 1u) / ORC_BLOCK;
+    b = (uint8_t *)calloc(nb ? nb : 1u, 1);
+    mn = (uint32_t *)calloc(nb ? nb : 1u, sizeof(uint32_t));
+    if (!b || !mn) {
+        free(b);
+        free(mn);
+        return ORC_ENOMEM;
+    }
+    for (k = 0; k < nb; k++) {
+        uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        for (j = 0; j < ORC_BLOCK; j++) {
+            i = k * ORC_BLOCK + j;
+            if (i < n) {
+                if (v[i] < lo)
+                    lo = v[i];
+                if (v[i] > hi)
+                    hi = v[i];
+            }
+        }
+        mn[k] = lo;
+        b[k] = (uint8_t)orc_bitlen((uint64_t)hi - lo);
+        sum_b += b[k];
+    }
+    packed_size = orc_fr_size(nb, sum_b);
+    raw_size = orc_fq_raw_size(n);
+    packed = (n > 0) && (packed_size < raw_size);
+    size = packed ? packed_size : raw_size;
+    *out_bytes = size;
+    if (size > cap) {
+        free(b);
+        free(mn);
+        return ORC_ENOSPC;
+    }
+    memset(out, 0, size);
+    if (!packed) {
+        put_u32(out + 0, ORC_MAGIC_FOR_RAW);
+        put_u32(out + 4, (uint32_t)n);
+        put_u32(out + 8, 0u);
+        put_u32(out + 12, (uint32_t)n);
+        for (i = 0; i < n; i++)
+            put_u32(out + 16u + 4u * i, v[i]);
+        free(b);
+        free(mn);
+        return ORC_OK;
+    }
+    put_u32(out + 0, ORC_MAGIC_FOR);
+    put_u32(out + 4, (uint32_t)n);
+    put_u32(out + 8, (uint32_t)nb);
+    put_u32(out + 12, (uint32_t)(4u * sum_b));
+    for (k = 0; k < nb; k++) {
+        put_u32(out + 16u + 4u * k, mn[k]);
+        out[16u + 4u * nb + k] = b[k];
+    }
+    bit0 = 8u * (16u + pad16(5u * nb));
+    for (k = 0; k < nb; k++) {
+        for (j = 0; j < ORC_BLOCK; j++) {
+            uint64_t off = 0;
+            i = k * ORC_BLOCK + j;
+            if (i < n)
+                off = (uint64_t)v[i] - mn[k];
+            for (t = 0; t < b[k]; t++)
+                if ((off >> t) & 1u)
+                    set_bit(out, bit0 + j * b[k] + t);
+        }
+        bit0 += 128u * b[k];
+    }
+    free(b);
+    free(mn);
+    return ORC_OK;
+}
+
+/* Inverse of orc_fr_encode.  Rejects (ORC_ECORRUPT): unknown magic, nb != ceil(n/128), a width
+ * > 32, payload_words != 4*sum(b), in_bytes != the layout's size, nonzero pads or padding slots,
+ * and values above 2^32 - 1.  n > cap gives ORC_ENOSPC with *n_out = n. */
+int orc_fr_decode(const uint8_t *in, uint64_t in_bytes, uint32_t *out, uint64_t cap, uint64_t *n_out)
+{
+    uint32_t magic;
+    uint64_t n, nb, words, k, j, t, i, sum_b = 0, payload, bit0;
+
+    *n_out = 0;
+    if (in_bytes < 16u)
+        return ORC_ECORRUPT;
+    magic = get_u32(in);
+    n = get_u32(in + 4);
+    nb = get_u32(in + 8);
+    words = get_u32(in + 12);
+    if (magic == ORC_MAGIC_FOR_RAW) {
+        if (nb != 0u || words != n || in_bytes != orc_fq_raw_size(n))
+            return ORC_ECORRUPT;
+        for (i = 16u + 4u * n; i < in_bytes; i++)
+            if (in[i] != 0u)
+                return ORC_ECORRUPT;
+        *n_out = n;
+        if (n > cap)
+            return ORC_ENOSPC;
+        for (i = 0; i < n; i++)
+            out[i] = get_u32(in + 16u + 4u * i);
+        return ORC_OK;
+    }
+    if (magic != ORC_MAGIC_FOR || nb != (n + ORC_BLOCK - 1u) / ORC_BLOCK || in_bytes < 16u + pad16(5u * nb))
+        return ORC_ECORRUPT;
+    for (k = 0; k < nb; k++) {
+        if (in[16u + 4u * nb + k] > 32u)
+            return ORC_ECORRUPT;
+        sum_b += in[16u + 4u * nb + k];
+    }
+    payload = 16u + pad16(5u * nb);
+    if (words != 4u * sum_b || in_bytes != orc_fr_size(nb, sum_b))
+        return ORC_ECORRUPT;
+    for (i = 16u + 5u * nb; i < payload; i++)
+        if (in[i] != 0u)
+            return ORC_ECORRUPT;
+    *n_out = n;
+    if (n > cap)
+        return ORC_ENOSPC;
+    bit0 = 8u * payload;
+    for (k = 0; k < nb; k++) {
+        uint32_t bk = in[16u + 4u * nb + k];
+        uint64_t base = get_u32(in + 16u + 4u * k);
+        for (j = 0; j < ORC_BLOCK; j++) {
+            uint64_t off = 0;
+            for (t = 0; t < bk; t++)
+                off |= (uint64_t)get_bit(in, bit0 + j * bk + t) << t;
+            i = k * ORC_BLOCK + j;
+            if (i >= n) {
+                if (off != 0u)
+                    return ORC_ECORRUPT;
+                continue;
+            }
+            if (base + off > 0xFFFFFFFFu)
+                return ORC_ECORRUPT;
+            out[i] = (uint32_t)(base + off);
         }
         bit0 += 128u * bk;
     }
