@@ -188,6 +188,46 @@ fq_status fq_bitmap_encode(const uint64_t *d_words, uint64_t nbits, uint8_t *d_o
 fq_status fq_bitmap_decode(const uint8_t *d_in, uint64_t in_bytes, uint64_t *d_words, uint64_t nbits,
                            void *d_work, uint64_t work_bytes, void *stream);
 
+/* ------------------------------------------------------------------ predecessor list
+ * The BFS tree (depth, parent) as one container "FPL1", for the one exchange the thesis leaves
+ * uncompressed: the predecessor reduction at the end of a BFS (sec. 6.5; its volume in the
+ * results chapter exceeds that of all compressed frontier exchanges).  Layout (little-endian):
+ *   u32 {"FPL1" = 0x314C5046, n, L, reached}; u64 off[2L]: stream k occupies [off[k], off[k+1])
+ *   from the container's start, off[0] = 16 + 16 L, every stream a multiple of 16 bytes;
+ *   streams 0 .. L-1: the level sets F_d = {v : depth[v] = d} in increasing order, each an FQ
+ *   stream exactly as fq_frontier_encode writes it (F_0 = {root});
+ *   streams L .. 2L-2: for d = 1 .. L-1, R_d[i] = the index of parent[F_d[i]] within F_{d-1},
+ *   as an FR stream -- frame of reference without differencing (Eq. 5-6): packed
+ *   {u32 "FRP1" = 0x31505246, n, nb = ceil(n/128), payload_words = 4 * sum(b)}, u32 min[nb],
+ *   u8 b[nb] (b = bit length of the block's max - min), zero pad to 16, then per block 4*b words
+ *   with slot j = value - min at bits [j*b, (j+1)*b) (slots past n zero); or raw
+ *   {"FRR1" = 0x31525246, n, 0, n}, u32 values, zero pad to 16; packed only when smaller.
+ * Sizes: fq_pred_bound(n, L) bytes always suffice; the workspace is fq_pred_workspace_bytes(n, L)
+ * (about 21 bytes per vertex), 16-byte aligned, shared by encode and decode. */
+uint64_t fq_pred_bound(uint64_t n, uint32_t levels);
+uint64_t fq_pred_workspace_bytes(uint64_t n, uint32_t levels);
+
+/* Encode the tree d_depth[n] (int32, -1 = unreached), d_parent[n] (uint32; parent[root] = root;
+ * entries of unreached vertices are ignored) with `levels` = max depth + 1 into d_out (capacity
+ * cap, 16-byte aligned); the container's size lands in the device u64 *d_out_bytes (0 on a device
+ * error other than FQ_ENOSPC, the needed size on FQ_ENOSPC).  1 <= levels <= n < 2^32.  Device
+ * errors (workspace status record): FQ_EINVAL with detail = vertex when a depth lies outside
+ * [-1, levels), the depth-0 vertex is not its own parent, or a parent is not one level above its
+ * child; FQ_EINVAL with detail = level when a level is empty or level 0 holds more than one vertex. */
+fq_status fq_pred_encode(const int32_t *d_depth, const uint32_t *d_parent, uint64_t n, uint32_t levels, uint8_t *d_out,
+                         uint64_t cap, uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
+
+/* Decode the container d_in[0..in_bytes) (16-byte aligned) into d_depth[n] and d_parent[n]:
+ * unreached vertices get depth -1 and parent 2^32 - 1.  The header's n must equal n; a container
+ * of more than max_levels levels (the workspace's sizing) gives FQ_ENOSPC with detail = its L.
+ * Validation (FQ_ECORRUPT): header, offset table, every stream's header and size, zero padding,
+ * widths <= 32, matching level and rank counts, exactly one vertex at level 0, ids < n strictly
+ * increasing within a level, no vertex at two levels, every rank below the size of the level above.
+ * Faults in the header, the table or the streams leave d_depth and d_parent untouched; an id that
+ * is out of order, out of range or repeated may leave them partly written. */
+fq_status fq_pred_decode(const uint8_t *d_in, uint64_t in_bytes, int32_t *d_depth, uint32_t *d_parent, uint64_t n,
+                         uint32_t max_levels, void *d_work, uint64_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------ BFS */
 
 typedef struct fq_graph fq_graph;

@@ -197,14 +197,25 @@ def fr_decode(stream, cap: int | None = None):
     return st, out[: n.value].copy()
 
 
+def level_sets(depth):
+    """F_d = {v : depth[v] = d} in increasing order, d = 0 .. max depth (a stable sort of the
+    reached vertices by depth, split by the level counts)."""
+    depth = _as(depth, np.int32)
+    levels = int(depth.max()) + 1 if depth.size and depth.max() >= 0 else 0
+    reached = np.nonzero(depth >= 0)[0]
+    order = reached[np.argsort(depth[reached], kind="stable")].astype(np.uint32)
+    bounds = np.cumsum(np.bincount(depth[reached], minlength=levels))[:-1]
+    return np.split(order, bounds) if levels else []
+
+
 def parent_ranks(depth, parent):
     """Per level d >= 1 of a BFS tree: for each vertex of F_d in increasing id order, the index of
     its parent within F_{d-1} (sorted).  The predecessor list as level-relative ranks: with the
     levels' sets (the Q_d streams) they give back every parent."""
     depth = _as(depth, np.int32)
     parent = _as(parent, np.uint32)
-    levels = int(depth.max()) + 1 if depth.size and depth.max() >= 0 else 0
-    sets = [np.nonzero(depth == d)[0].astype(np.uint32) for d in range(levels)]
+    sets = level_sets(depth)
+    levels = len(sets)
     out = []
     for d in range(1, levels):
         par = parent[sets[d]]
@@ -237,7 +248,9 @@ def pl_encode(depth, parent):
     if n == 0 or n > 0xFFFFFFFF or d.max() < 0:
         raise ValueError("empty tree")
     L = int(d.max()) + 1
-    sets = [np.nonzero(d == k)[0].astype(np.uint32) for k in range(L)]
+    sets = level_sets(d)
+    if any(f.size == 0 for f in sets):
+        raise ValueError("empty level")
     if sets[0].size != 1 or p[sets[0][0]] != sets[0][0]:
         raise ValueError("level 0 must hold exactly the root, its own parent")
     if np.any(d < -1):

@@ -75,6 +75,10 @@ _SIGS = {
     "fq_frontier_encode_batch": ([_vp, _vp, _u32, _u64, _vp, _vp, _vp, _vp, _u64, _vp], _i32),
     "fq_frontier_decode_batch": ([_vp, _vp, _vp, _u32, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "fq_bitmap_decode": ([_vp, _u64, _vp, _u64, _vp, _u64, _vp], _i32),
+    "fq_pred_bound": ([_u64, _u32], _u64),
+    "fq_pred_workspace_bytes": ([_u64, _u32], _u64),
+    "fq_pred_encode": ([_vp, _vp, _u64, _u32, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "fq_pred_decode": ([_vp, _u64, _vp, _vp, _u64, _u32, _vp, _u64, _vp], _i32),
     "fq_msbfs_scratch_bytes": ([_u64], _u64),
     "fq_bfs_run_multi": ([_vp, _vp, _u64, ctypes.POINTER(_u32), _u32, _vp, _vp, _u64, ctypes.POINTER(fq_bfs_stats), _vp],
                          _i32),
@@ -241,6 +245,66 @@ def fq_bitmap_decode(stream_bytes: torch.Tensor, nbits: int, out: torch.Tensor |
            "fq_bitmap_decode")
     _device_status(work, stream, "fq_bitmap_decode")
     return out[: 2 * nwords64]
+
+
+# ----------------------------------------------------------------------------- predecessor list
+
+def fq_pred_bound(n: int, levels: int) -> int:
+    return int(lib().fq_pred_bound(n, levels))
+
+
+def fq_pred_workspace_bytes(n: int, levels: int) -> int:
+    return int(lib().fq_pred_workspace_bytes(n, levels))
+
+
+def pred_workspace(n: int, levels: int, device="cuda") -> torch.Tensor:
+    return torch.empty(fq_pred_workspace_bytes(n, levels), dtype=torch.uint8, device=device)
+
+
+def fq_pred_encode(depth: torch.Tensor, parent: torch.Tensor, levels: int, out: torch.Tensor | None = None,
+                   work: torch.Tensor | None = None, stream=None, sync: bool = True,
+                   nbytes: torch.Tensor | None = None):
+    """The BFS tree (int32 depth, int32/uint32 parent CUDA tensors of n entries; levels = max
+    depth + 1) as an FPL1 container.  Returns (container bytes, size) when sync, else (out buffer,
+    device size tensor)."""
+    n = depth.numel()
+    dev = depth.device
+    if out is None:
+        out = torch.empty(fq_pred_bound(n, levels), dtype=torch.uint8, device=dev)
+    if work is None:
+        work = pred_workspace(n, levels, dev)
+    if nbytes is None:
+        nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check(lib().fq_pred_encode(_ptr(depth), _ptr(parent), n, levels, _ptr(out), out.numel(), _ptr(nbytes), _ptr(work),
+                                work.numel(), _stream(stream)), "fq_pred_encode")
+    if not sync:
+        return out, nbytes
+    _device_status(work, stream, "fq_pred_encode")
+    size = int(nbytes.item())
+    return out[:size], size
+
+
+def fq_pred_decode(container: torch.Tensor, n: int, max_levels: int | None = None, depth: torch.Tensor | None = None,
+                   parent: torch.Tensor | None = None, work: torch.Tensor | None = None, stream=None,
+                   in_bytes: int | None = None, sync: bool = True):
+    """Decode an FPL1 container (uint8 CUDA tensor) into (depth int32[n], parent int32[n]; the
+    uint32 bit patterns, unreached = -1 in both).  max_levels defaults to the container's own
+    level count (read from its header)."""
+    dev = container.device
+    if max_levels is None:
+        max_levels = max(1, int(container[:16].view(torch.int32)[2].item()))
+    if depth is None:
+        depth = torch.empty(n, dtype=torch.int32, device=dev)
+    if parent is None:
+        parent = torch.empty(n, dtype=torch.int32, device=dev)
+    if work is None:
+        work = pred_workspace(n, max_levels, dev)
+    nb = container.numel() if in_bytes is None else in_bytes
+    _check(lib().fq_pred_decode(_ptr(container), nb, _ptr(depth), _ptr(parent), n, max_levels, _ptr(work), work.numel(),
+                                _stream(stream)), "fq_pred_decode")
+    if sync:
+        _device_status(work, stream, "fq_pred_decode")
+    return depth, parent
 
 
 # ----------------------------------------------------------------------------- batched codec

@@ -155,6 +155,32 @@ def pick_roots(offsets: torch.Tensor, k: int, seed: int = 20170402):
     return chosen
 
 
+def random_tree(n: int, level_sizes, seed: int, device="cpu"):
+    """A rooted tree shaped like a BFS tree, without a graph: level d holds level_sizes[d]
+    vertices (level_sizes[0] = 1), taken in the order of a seeded relabelling of 0 .. n-1; each
+    vertex of level d >= 1 gets the parent at position floor(r * |level d-1| / 2^32) of level d-1
+    (r a 32-bit draw); the other vertices are unreached (depth -1, parent 2^32 - 1).
+    Returns (depth int32[n], parent int64[n] holding uint32 values)."""
+    sizes = [int(x) for x in level_sizes]
+    if not sizes or sizes[0] != 1 or min(sizes) < 1 or sum(sizes) > n:
+        raise ValueError("level sizes must start with 1, be positive and fit in n")
+    order = torch.sort(uniform32(seed, 8, 0, n, device=device), stable=True).indices
+    depth = torch.full((n,), -1, dtype=torch.int32, device=device)
+    parent = torch.full((n,), M32, dtype=torch.int64, device=device)
+    start = 0
+    for d, size in enumerate(sizes):
+        here = order[start: start + size]
+        depth[here] = d
+        if d == 0:
+            parent[here] = here
+        else:
+            prev = sizes[d - 1]
+            r = uniform32(seed, 9, start, size, device=device)
+            parent[here] = order[start - prev + ((r * prev) >> 32)]
+        start += size
+    return depth, parent
+
+
 # ----------------------------------------------------------------------------- codec inputs
 
 def geometric_set(n: int, mean_gap: float, seed: int, device="cpu") -> torch.Tensor:
