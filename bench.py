@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-codec", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-pred", action="store_true", help="skip the predecessor-list container measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in launch grids (no autotuning)")
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--codec-only", action="store_true",
@@ -394,6 +395,9 @@ def run_fqbfs(args, world, rank, local):
     if not args.no_codec:
         codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])
         codec["threshold"] = codec_threshold(dev)
+    pred = None
+    if not args.no_pred and rank == 0:
+        pred = predecessor_list(g, timed_roots[0], depth, parent, peaks["hbm_gbs"])
     batched = None
     if not args.no_batched and rank == 0:
         if not args.no_tune:
@@ -427,7 +431,8 @@ def run_fqbfs(args, world, rank, local):
                            "gteps_hmean": hmean, "edges_examined": examined,
                            "host_loop_ms_per_step": host_loop_ms / args.steps,
                            "parallelism": f"replicas{world}"},
-                "roofline": roofline, "codec": codec, "batched": batched, "serving": served,
+                "roofline": roofline, "codec": codec, "predecessor_list": pred, "batched": batched,
+                "serving": served,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "autotune": [{k: e[k] for k in ("site", "class", "ctas_per_sm", "ms", "default_ms")} for e in tuned],
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
@@ -516,6 +521,58 @@ def codec_points(dev, peak_gbs, points=CODEC_POINTS, reps=5):
         del ids, out, work, dec
         torch.cuda.empty_cache()
     return res
+
+
+def predecessor_list(g, root, depth, parent, peak_gbs, reps=5):
+    """The BFS tree of one root (the predecessor list the thesis reduces uncompressed once per
+    search) through fq_pred_encode / fq_pred_decode: container bytes against the raw parent array
+    (4 bytes per vertex) and event-timed throughput, with L2 flushed before every timed call.
+    Algorithmic bytes: encode reads depth and parent (8 per vertex) and writes the container;
+    decode reads the container and writes depth and parent."""
+    from paper_1704_00513_gb300 import fqbfs
+    dev = depth.device
+    res = g.bfs(root, depth=depth, parent=parent, flags=0, max_levels=64)
+    n = depth.numel()
+    L = res.stats["levels"]
+    out = torch.empty(fqbfs.fq_pred_bound(n, L), dtype=torch.uint8, device=dev)
+    work = fqbfs.pred_workspace(n, L, dev)
+    nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    d2 = torch.empty_like(depth)
+    p2 = torch.empty_like(parent)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(call):
+        ts = []
+        for i in range(reps + 2):
+            flush.fill_(i & 0xFF)
+            e0, e1 = _events()
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts)
+
+    t_enc = timed(lambda: fqbfs.fq_pred_encode(depth, parent, L, out=out, work=work, nbytes=nbytes, sync=False))
+    fqbfs.fq_pred_encode(depth, parent, L, out=out, work=work, nbytes=nbytes)
+    size = int(nbytes.item())
+    c = out[:size]
+    t_dec = timed(lambda: fqbfs.fq_pred_decode(c, n, max_levels=L, depth=d2, parent=p2, work=work, sync=False))
+    fqbfs.fq_pred_decode(c, n, max_levels=L, depth=d2, parent=p2, work=work)
+    reached = int(res.stats["reached"])
+    ok = bool(torch.equal(d2, depth)) and bool(torch.equal(torch.where(depth >= 0, p2, parent), parent)) and \
+        bool((p2[depth < 0] == -1).all())
+    enc_alg = 8 * n + size
+    dec_alg = size + 8 * n
+    return {"root": int(root), "levels": L, "vertices": n, "reached": reached, "bytes": size,
+            "raw_parent_bytes": 4 * n, "ratio_vs_parent_array": 4 * n / size,
+            "bits_per_reached_vertex": 8 * size / max(1, reached),
+            "encode_ms": t_enc * 1e3, "decode_ms": t_dec * 1e3,
+            "encode_GBps": enc_alg / t_enc / 1e9, "decode_GBps": dec_alg / t_dec / 1e9,
+            "encode_frac": enc_alg / t_enc / 1e9 / peak_gbs, "decode_frac": dec_alg / t_dec / 1e9 / peak_gbs,
+            "l2": "flushed (256 MB write) before every timed call", "roundtrip_ok": ok}
 
 
 LINKS_GBPS = {"nvlink5_per_direction": 900.0, "pcie5_x16": 64.0, "infiniband_ndr": 50.0}

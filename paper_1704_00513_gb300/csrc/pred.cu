@@ -9,18 +9,24 @@
 // reference without differencing, Eq. 5-6).  An index needs at most bitlen(|F_{d-1}| - 1) bits,
 // and a level set of dense ids packs to a few bits per id.
 //
-// Encode (7 launches for up to 256 levels, 3 more per further 8-bit digit of the level count):
+// Encode (8 launches for up to 256 levels, 4 more per further 8-bit digit of the level count):
 //   pe_init     status record, level counters
 //   pe_hist     per tile of 4096 vertices: digit counts of the level (the first pass also
 //               validates depth and the root)
-//   pe_plan     one CTA: scan of the tile counts, level offsets, stream sizes in blocks
+//   pe_rowscan  one CTA per digit: that digit's tile counts scanned
+//   pe_plan     one CTA: digit bases, level offsets, checks, stream sizes in blocks
 //   pe_scatter  stable scatter by digit; the last pass records (level, index in level) per vertex
-//   pe_widths   one warp per 128-value block: width and base; rank blocks first look up each
-//               parent's index (and check that the parent is one level up)
-//   pe_layout   one CTA: width scan, stream sizes, container header and offset table
-//   pe_pack     one warp per block: stream headers, base and width tables, packed payloads
-// Decode: pd_plan (header, table, stream headers), pd_widths, pd_scan, pd_unpack, pd_fill,
-// pd_scatter (depth and parent of every reached vertex, duplicate and order checks).
+//   pe_widths   tiles of 64 blocks, 8 per warp: width and base of each block and in-tile
+//               prefixes; rank blocks first look up each parent's index (and check that the
+//               parent is one level up)
+//   pe_layout   one CTA: tile prefixes, stream sizes, container header and offset table
+//   pe_pack     8 blocks per warp: stream headers, base and width tables, packed payloads
+// Decode: pd_plan (header, table, stream headers), pd_widths, pd_scan (tile prefixes, payload
+// sizes), pd_unpack; then, for a workspace of at most 128 levels, pd_chunks (where each level
+// enters each chunk of 4096 ids) and pd_build (each chunk's depth and parent assembled in shared
+// memory and written once, with the order and duplicate checks); for more levels pd_fill,
+// pd_scatter (depth and parent of every reached vertex) and pd_verify (ids increasing within a
+// level, no vertex at two levels).
 #include <algorithm>
 
 #include "codec_dev.cuh"
@@ -34,11 +40,17 @@ constexpr uint32_t kPWarps = kPT / 32;
 constexpr uint32_t kSortItems = 4096;         // vertices (or positions) per sort tile
 constexpr uint32_t kWarpItems = kSortItems / kPWarps;  // 512: 16 chunks of 32 per warp
 constexpr uint32_t kRadix = 256;
+constexpr uint32_t kBW = 8;                   // 128-value blocks per warp per tile
+constexpr uint32_t kBT = kPWarps * kBW;       // 64 blocks per tile
+constexpr uint32_t kPosPerThread = 8;         // positions per thread in the decode scatter and check
+constexpr uint32_t kPosTile = kPT * kPosPerThread;
+constexpr uint32_t kVmIds = 4096;             // vertex ids per chunk of the vertex-ordered decode
+constexpr uint32_t kVmLevels = 128;           // most levels the vertex-ordered decode takes
 constexpr uint32_t kMagicPl = 0x314C5046u;    // "FPL1"
 constexpr uint32_t kMagicForP = 0x31505246u;  // "FRP1"
 constexpr uint32_t kMagicForR = 0x31525246u;  // "FRR1"
 constexpr uint32_t kWherePredEnc = 7, kWherePredDec = 8;
-constexpr unsigned long long kNoPos = ~0ull;
+constexpr uint32_t kNoPos = 0xffffffffu;  // position of an unreached vertex
 
 struct PStream {
     unsigned long long off;   // byte offset of the stream in the container
@@ -48,7 +60,7 @@ struct PStream {
     uint32_t blk0;            // first global block index
     uint32_t mode;            // kModePacked / kModeRaw
     uint32_t words;           // decode: payload words announced by the header
-    uint32_t pad_;
+    uint32_t pstart;          // payload units (16 bytes) of all blocks before the stream's first one
 };
 
 struct PWork {
@@ -57,12 +69,18 @@ struct PWork {
     PStream *st;               // [2L]
     uint32_t *S;               // [n] reached vertices ordered by (level, id)
     uint32_t *S2;              // [n] radix ping-pong; decode: bitmap of vertices seen
-    unsigned long long *lvpos; // [n] encode: level << 32 | index in level (kNoPos if unreached)
+    uint32_t *gpos;            // [n] encode: the vertex's position in S (kNoPos if unreached); its level
+                               // is the d with lo[d] <= position < lo[d+1], its index position - lo[d]
     uint32_t *R;               // [n] at a child's position in S: its parent's index in the level above
-    uint32_t *hist;            // [256 * tiles] digit counts per tile, scanned in place
-    uint32_t *bw;              // [nb_max + 1] block widths, scanned in place into payload prefixes
+    uint32_t *hist;            // [256 * tiles] digit counts per tile; each digit's row scanned in place
+    uint32_t *rsum;            // [256] digit totals
+    uint32_t *dbase;           // [256] first position of each digit
+    uint32_t *bw;              // [nb_max] block widths (payload units of 16 bytes)
+    uint32_t *lpre;            // [nb_max] payload units before the block within its tile of 64 blocks
+    uint32_t *tsum;            // [nt_max + 1] tile totals, scanned in place into tile prefixes
     uint32_t *bbase;           // [nb_max] block bases
-    uint64_t n, L, tiles, nb_max;
+    uint32_t *cstart;          // decode, L <= kVmLevels: [L][nch + 1] first position of each id chunk per level
+    uint64_t n, L, tiles, nb_max, nch;
 };
 
 uint64_t al256(uint64_t x) { return (x + 255u) / 256u * 256u; }
@@ -77,11 +95,17 @@ uint64_t pred_layout(uint64_t n, uint64_t L, PWork *w, void *base)
     const uint64_t o_st = o; o = al256(o + sizeof(PStream) * 2 * L);
     const uint64_t o_s = o; o = al256(o + 4 * n);
     const uint64_t o_s2 = o; o = al256(o + 4 * n);
-    const uint64_t o_lv = o; o = al256(o + 8 * n);
+    const uint64_t o_lv = o; o = al256(o + 4 * n);
     const uint64_t o_r = o; o = al256(o + 4 * n);
     const uint64_t o_h = o; o = al256(o + 4 * kRadix * tiles);
-    const uint64_t o_bw = o; o = al256(o + 4 * (nbm + 1));
+    const uint64_t o_rs = o; o = al256(o + 4 * kRadix);
+    const uint64_t o_db = o; o = al256(o + 4 * kRadix);
+    const uint64_t o_bw = o; o = al256(o + 4 * nbm);
+    const uint64_t o_lp = o; o = al256(o + 4 * nbm);
+    const uint64_t o_ts = o; o = al256(o + 4 * (cdiv(nbm, kBT) + 1));
     const uint64_t o_bb = o; o = al256(o + 4 * nbm);
+    const uint64_t nch = cdiv(n, kVmIds);
+    const uint64_t o_cs = o; o = al256(o + (L <= kVmLevels ? 4 * L * (nch + 1) : 0));
     if (w && base) {
         uint8_t *p = static_cast<uint8_t *>(base);
         w->ctl = reinterpret_cast<Ctl *>(p);
@@ -89,11 +113,17 @@ uint64_t pred_layout(uint64_t n, uint64_t L, PWork *w, void *base)
         w->st = reinterpret_cast<PStream *>(p + o_st);
         w->S = reinterpret_cast<uint32_t *>(p + o_s);
         w->S2 = reinterpret_cast<uint32_t *>(p + o_s2);
-        w->lvpos = reinterpret_cast<unsigned long long *>(p + o_lv);
+        w->gpos = reinterpret_cast<uint32_t *>(p + o_lv);
         w->R = reinterpret_cast<uint32_t *>(p + o_r);
         w->hist = reinterpret_cast<uint32_t *>(p + o_h);
+        w->rsum = reinterpret_cast<uint32_t *>(p + o_rs);
+        w->dbase = reinterpret_cast<uint32_t *>(p + o_db);
         w->bw = reinterpret_cast<uint32_t *>(p + o_bw);
+        w->lpre = reinterpret_cast<uint32_t *>(p + o_lp);
+        w->tsum = reinterpret_cast<uint32_t *>(p + o_ts);
         w->bbase = reinterpret_cast<uint32_t *>(p + o_bb);
+        w->cstart = reinterpret_cast<uint32_t *>(p + o_cs);
+        w->nch = nch;
         w->n = n;
         w->L = L;
         w->tiles = tiles;
@@ -166,19 +196,25 @@ __global__ void pe_init(PWork w, uint32_t zero_counts)
             w.lo[i] = 0;
 }
 
-// Key of item i of a sort pass: the first pass walks vertex ids 0 .. n-1 (unreached ones drop
-// out), later passes walk the previous pass's output.  Returns the level, or -1 for no item.
+// Keys of a warp's kWarpItems sort items, all loads issued first: the first pass walks vertex
+// ids 0 .. n-1 (unreached ones drop out), later passes the previous pass's output.  key = level,
+// or -1 for no item; v = the vertex.
+constexpr uint32_t kChunks = kWarpItems / 32u;
+
 template <bool kFirst>
-__device__ __forceinline__ int64_t sort_item(const PWork &w, const int32_t *depth, const uint32_t *in, uint64_t i,
-                                             uint64_t items, uint32_t *v)
+__device__ __forceinline__ void load_keys(const int32_t *depth, const uint32_t *in, uint64_t base, uint64_t items,
+                                          uint32_t lane, int32_t key[kChunks], uint32_t v[kChunks])
 {
-    if (i >= items) return -1;
-    if (kFirst) {
-        *v = (uint32_t)i;
-        return depth[i];
+#pragma unroll
+    for (uint32_t c = 0; c < kChunks; c++) {
+        const uint64_t i = base + 32u * c + lane;
+        v[c] = kFirst ? (uint32_t)i : (i < items ? in[i] : 0u);
     }
-    *v = in[i];
-    return depth[*v];
+#pragma unroll
+    for (uint32_t c = 0; c < kChunks; c++) {
+        const uint64_t i = base + 32u * c + lane;
+        key[c] = i < items ? depth[kFirst ? i : (uint64_t)v[c]] : -1;
+    }
 }
 
 template <bool kFirst>
@@ -194,12 +230,15 @@ __global__ void __launch_bounds__(kPT) pe_hist(PWork w, const int32_t *depth, co
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t items = kFirst ? w.n : w.lo[w.L];
     const uint64_t base = (uint64_t)blockIdx.x * kSortItems + (uint64_t)warp * kWarpItems;
-    for (uint32_t c = 0; c < kWarpItems / 32u; c++) {
+    int32_t key[kChunks];
+    uint32_t vv[kChunks];
+    load_keys<kFirst>(depth, in, base, items, lane, key, vv);
+#pragma unroll
+    for (uint32_t c = 0; c < kChunks; c++) {
         const uint64_t i = base + 32u * c + lane;
-        uint32_t v = 0;
-        int64_t d = sort_item<kFirst>(w, depth, in, i, items, &v);
+        int32_t d = key[c];
         if (kFirst && i < items) {
-            if (d < -1 || d >= (int64_t)w.L) {
+            if (d < -1 || (int64_t)d >= (int64_t)w.L) {
                 set_error(w.ctl, FQ_EINVAL, kWherePredEnc, i);
                 d = -1;
             } else if (d == 0 && parent[i] != (uint32_t)i) {
@@ -222,12 +261,23 @@ __global__ void __launch_bounds__(kPT) pe_hist(PWork w, const int32_t *depth, co
     for (uint32_t r = threadIdx.x; r < digits; r += kPT) w.hist[(uint64_t)r * w.tiles + blockIdx.x] = cnt[r];
 }
 
-// Exclusive scan of the digit counts of a later pass.
-__global__ void __launch_bounds__(kScanThreads) pe_scan(PWork w, uint32_t digits)
+// One CTA per digit: that digit's counts over all tiles, scanned in place; the digit's total.
+__global__ void __launch_bounds__(kScanThreads) pe_rowscan(PWork w)
 {
     __shared__ unsigned long long sm[33];
-    if (w.ctl->code != FQ_OK) return;  // uniform: nothing else writes the record during this kernel
-    cta_chunk_scan_u32<kScanThreads>(w.hist, w.hist, (uint64_t)digits * w.tiles, sm);
+    if (w.ctl->code != FQ_OK) return;  // uniform: nothing writes the record during this kernel
+    const unsigned long long total =
+        cta_chunk_scan_u32<kScanThreads>(w.hist + (uint64_t)blockIdx.x * w.tiles, w.hist + (uint64_t)blockIdx.x * w.tiles,
+                                         w.tiles, sm);
+    if (threadIdx.x == 0) w.rsum[blockIdx.x] = (uint32_t)total;
+}
+
+// Digit bases of a later pass.
+__global__ void __launch_bounds__(kScanThreads) pe_dscan(PWork w, uint32_t digits)
+{
+    __shared__ unsigned long long sm[33];
+    if (w.ctl->code != FQ_OK) return;
+    cta_chunk_scan_u32<kScanThreads>(w.rsum, w.dbase, digits, sm);
 }
 
 // First-pass scan, level offsets, checks, and the stream table's counts and block offsets.
@@ -239,12 +289,12 @@ __global__ void __launch_bounds__(kScanThreads) pe_plan(PWork w, uint32_t digits
     __syncthreads();
     if (s_abort) return;
     const uint64_t L = w.L;
-    const unsigned long long reached = cta_chunk_scan_u32<kScanThreads>(w.hist, w.hist, (uint64_t)digits * w.tiles, sm);
+    const unsigned long long reached = cta_chunk_scan_u32<kScanThreads>(w.rsum, w.dbase, digits, sm);
     __syncthreads();
     if (from_counts) {
         cta_chunk_scan_u32<kScanThreads>(w.lo, w.lo, L, sm);
     } else {
-        for (uint64_t d = threadIdx.x; d < L; d += kScanThreads) w.lo[d] = w.hist[d * w.tiles];
+        for (uint64_t d = threadIdx.x; d < L; d += kScanThreads) w.lo[d] = w.dbase[d];
     }
     if (threadIdx.x == 0) w.lo[L] = (uint32_t)reached;
     __syncthreads();
@@ -289,12 +339,15 @@ __global__ void __launch_bounds__(kPT) pe_scatter(PWork w, const int32_t *depth,
     const uint64_t items = kFirst ? w.n : w.lo[w.L];
     const uint64_t tbase = (uint64_t)blockIdx.x * kSortItems;
     const uint32_t wofs = warp * kWarpItems;
-    for (uint32_t c = 0; c < kWarpItems / 32u; c++) {  // the warp's digit counts, keys kept in shared memory
+    int32_t key[kChunks];
+    uint32_t vv[kChunks];
+    load_keys<kFirst>(depth, in, tbase + wofs, items, lane, key, vv);
+#pragma unroll
+    for (uint32_t c = 0; c < kChunks; c++) {  // the warp's digit counts, keys kept in shared memory
         const uint32_t li = wofs + 32u * c + lane;
-        uint32_t v = 0;
-        const int64_t d = sort_item<kFirst>(w, depth, in, tbase + li, items, &v);
-        s_key[li] = (int32_t)(d >= 0 ? d : -1);
-        if (!kFirst) s_v[li] = v;
+        const int32_t d = key[c] >= 0 ? key[c] : -1;
+        s_key[li] = d;
+        if (!kFirst) s_v[li] = vv[c];
         const bool valid = d >= 0;
         const uint32_t act = __ballot_sync(0xffffffffu, valid);
         if (valid) {
@@ -305,7 +358,7 @@ __global__ void __launch_bounds__(kPT) pe_scatter(PWork w, const int32_t *depth,
     }
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < digits; r += kPT) {  // warp bases: tile base + earlier warps of the tile
-        uint32_t run = w.hist[(uint64_t)r * w.tiles + blockIdx.x];
+        uint32_t run = w.dbase[r] + w.hist[(uint64_t)r * w.tiles + blockIdx.x];
         for (uint32_t q = 0; q < kPWarps; q++) {
             const uint32_t x = wc[q][r];
             wc[q][r] = run;
@@ -330,49 +383,54 @@ __global__ void __launch_bounds__(kPT) pe_scatter(PWork w, const int32_t *depth,
         __syncwarp();
         if (valid) {
             out[pos] = v;
-            if (last) w.lvpos[v] = ((unsigned long long)(uint32_t)d << 32) | (pos - w.lo[d]);
+            if (last) w.gpos[v] = pos;
         } else if (kFirst && tbase + li < items) {
-            w.lvpos[tbase + li] = kNoPos;
+            w.gpos[tbase + li] = kNoPos;
         }
     }
 }
 
-// Block gb's values, 4 per lane (slots 4*lane .. 4*lane+3): level-set ids, or parent indices
-// (looked up and written to R when `lookup`).  Returns the stream index; *cnt = valid slots.
-__device__ __forceinline__ uint32_t block_values(const PWork &w, const uint32_t *parent, uint32_t gb, uint32_t lane,
-                                                 bool lookup, uint32_t v[4], uint32_t *cnt, bool *is_rank)
+// One 128-value block of a tile, as seen by a warp: lane i < kBW computes the record of block
+// gb0 + i; bcast() hands record i to every lane.
+struct BInfo {
+    unsigned long long g0;  // position of the block's first value in S (level sets) or R (ranks)
+    uint32_t cnt;           // values in the block; 0 = no block
+    uint32_t k;             // stream
+    uint32_t d;             // level
+    uint32_t isR;           // rank (FR) stream
+};
+
+__device__ __forceinline__ BInfo lane_block_info(const PWork &w, uint32_t L, uint64_t gb0, uint64_t NB, uint32_t lane)
 {
-    const uint32_t K = (uint32_t)(2 * w.L - 1);
-    const uint32_t k = stream_of_block(w.st, K, gb);
-    const PStream s = w.st[k];
-    const uint32_t j = gb - s.blk0;
-    const bool isR = k >= w.L;
-    const uint32_t d = isR ? k - (uint32_t)w.L + 1u : k;
-    const uint64_t g0 = (uint64_t)w.lo[d] + (uint64_t)kBlock * j;
-    const uint32_t c = min(kBlock, s.n - kBlock * j);
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const uint32_t i = 4u * lane + q;
-        v[q] = 0;
-        if (i >= c) continue;
-        if (!isR) {
-            v[q] = w.S[g0 + i];
-        } else if (lookup) {
-            const uint32_t child = w.S[g0 + i];
-            const uint32_t p = parent[child];
-            const unsigned long long x = p < w.n ? w.lvpos[p] : kNoPos;
-            uint32_t r = 0;
-            if (x == kNoPos || (uint32_t)(x >> 32) != d - 1u) set_error(w.ctl, FQ_EINVAL, kWherePredEnc, child);
-            else r = (uint32_t)x;
-            w.R[g0 + i] = r;
-            v[q] = r;
-        } else {
-            v[q] = w.R[g0 + i];
-        }
+    BInfo b{};
+    const uint64_t gb = gb0 + lane;
+    if (lane < kBW && gb < NB) {
+        const uint32_t k = stream_of_block(w.st, 2u * L - 1u, (uint32_t)gb);
+        const uint32_t n = w.st[k].n, j = (uint32_t)gb - w.st[k].blk0;
+        b.isR = k >= L;
+        b.d = b.isR ? k - L + 1u : k;
+        b.g0 = (unsigned long long)w.lo[b.d] + (unsigned long long)kBlock * j;
+        b.cnt = min(kBlock, n - kBlock * j);
+        b.k = k;
     }
-    *cnt = c;
-    *is_rank = isR;
-    return k;
+    return b;
+}
+
+__device__ __forceinline__ BInfo bcast(const BInfo &b, uint32_t i)
+{
+    BInfo r;
+    r.g0 = __shfl_sync(0xffffffffu, b.g0, i);
+    r.cnt = __shfl_sync(0xffffffffu, b.cnt, i);
+    r.k = __shfl_sync(0xffffffffu, b.k, i);
+    r.d = __shfl_sync(0xffffffffu, b.d, i);
+    r.isR = __shfl_sync(0xffffffffu, b.isR, i);
+    return r;
+}
+
+// Payload units (16 bytes) of all blocks before global block x: tile prefix + in-tile prefix.
+__device__ __forceinline__ uint32_t prefix_at(const PWork &w, uint64_t x, uint64_t NB, uint64_t NT)
+{
+    return x < NB ? w.tsum[x / kBT] + w.lpre[x] : w.tsum[NT];
 }
 
 // Gaps of a level-set block (slot 0 and padding slots 0); ids are strictly increasing by construction.
@@ -387,44 +445,123 @@ __device__ __forceinline__ void block_gaps(const uint32_t v[4], uint32_t cnt, ui
     }
 }
 
-__global__ void __launch_bounds__(kPT) pe_widths(PWork w, const uint32_t *parent)
+// In-tile exclusive prefix of the tile's 64 widths (s_w) by warp 0, and the tile's total.
+__device__ __forceinline__ void tile_prefix(const PWork &w, const uint32_t *s_w, uint64_t t, uint64_t NB, uint32_t lane)
 {
-    if (w.ctl->code != FQ_OK) return;  // warp-level work only: no CTA barrier below
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t NB = w.ctl->nb;
-    for (uint64_t gb = ((uint64_t)blockIdx.x * kPT + threadIdx.x) / 32u; gb < NB; gb += (uint64_t)gridDim.x * kPWarps) {
-        uint32_t v[4], cnt;
-        bool isR;
-        block_values(w, parent, (uint32_t)gb, lane, true, v, &cnt, &isR);
-        uint32_t width, base;
-        if (!isR) {
-            uint32_t g[4];
-            block_gaps(v, cnt, lane, g);
-            width = bitlen32(__reduce_max_sync(0xffffffffu, max(max(g[0], g[1]), max(g[2], g[3]))));
-            base = __shfl_sync(0xffffffffu, v[0], 0);
-        } else {
-            uint32_t mn = 0xffffffffu, mx = 0u;
+    const uint32_t a = s_w[2u * lane], b = s_w[2u * lane + 1u];
+    const uint32_t incl = warp_incl_scan(a + b), ex = incl - a - b;
+    const uint64_t gb = t * kBT + 2u * lane;
+    if (gb < NB) w.lpre[gb] = ex;
+    if (gb + 1 < NB) w.lpre[gb + 1] = ex + a;
+    if (lane == 31) w.tsum[t] = incl;
+}
+
+// Widths and bases of all blocks, tile by tile (64 blocks, 8 per warp with all their loads in
+// flight together).  Rank blocks first look up each child's parent and its (level, index) record,
+// check that the parent is one level up, and store the index in R.
+__global__ void __launch_bounds__(kPT, 3) pe_widths(PWork w, const uint32_t *parent)
+{
+    __shared__ uint32_t s_w[kBT];
+    __shared__ int s_abort;
+    __shared__ unsigned long long s_nb;
+    if (threadIdx.x == 0) {
+        s_abort = w.ctl->code != FQ_OK;
+        s_nb = w.ctl->nb;
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t NB = s_nb, NT = dcdiv(NB, kBT);
+    const uint32_t L = (uint32_t)w.L;
+    for (uint64_t t = blockIdx.x; t < NT; t += gridDim.x) {
+        const uint64_t gb0 = t * kBT + (uint64_t)warp * kBW;
+        const BInfo mine = lane_block_info(w, L, gb0, NB, lane);
+        uint32_t myw = 0, myb = 0;
+        constexpr uint32_t H = kBW / 2;  // blocks per round: all their loads in flight together
+#pragma unroll 1
+        for (uint32_t h = 0; h < kBW; h += H) {
+            BInfo bi[H];
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (4u * lane + q < cnt) {
-                    mn = min(mn, v[q]);
-                    mx = max(mx, v[q]);
+            for (uint32_t i = 0; i < H; i++) bi[i] = bcast(mine, h + i);
+            uint32_t v[H][4], p[H][4];
+#pragma unroll
+            for (uint32_t i = 0; i < H; i++)
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t slot = 4u * lane + q;
+                    v[i][q] = slot < bi[i].cnt ? w.S[bi[i].g0 + slot] : 0u;
                 }
-            mn = __reduce_min_sync(0xffffffffu, mn);
-            mx = __reduce_max_sync(0xffffffffu, mx);
-            width = bitlen32(mx - mn);
-            base = mn;
+            // rank blocks: each child's parent, then the parent's (level, index) record
+#pragma unroll
+            for (uint32_t i = 0; i < H; i++)
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++)
+                    p[i][q] = (bi[i].isR && 4u * lane + q < bi[i].cnt) ? parent[v[i][q]] : 0u;
+            uint32_t x[H][4];
+#pragma unroll
+            for (uint32_t i = 0; i < H; i++)
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++)
+                    x[i][q] = (bi[i].isR && 4u * lane + q < bi[i].cnt && p[i][q] < w.n) ? w.gpos[p[i][q]] : kNoPos;
+#pragma unroll
+            for (uint32_t i = 0; i < H; i++) {
+                if (!bi[i].isR) continue;  // uniform over the warp
+                const uint32_t up0 = w.lo[bi[i].d - 1], up1 = w.lo[bi[i].d];  // level d - 1 in S
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t slot = 4u * lane + q;
+                    if (slot >= bi[i].cnt) continue;
+                    uint32_t r = 0;
+                    if (x[i][q] == kNoPos || x[i][q] < up0 || x[i][q] >= up1)
+                        set_error(w.ctl, FQ_EINVAL, kWherePredEnc, v[i][q]);
+                    else
+                        r = x[i][q] - up0;
+                    w.R[bi[i].g0 + slot] = r;
+                    v[i][q] = r;
+                }
+            }
+#pragma unroll
+            for (uint32_t i = 0; i < H; i++) {
+                uint32_t width = 0, base = 0;
+                if (!bi[i].isR) {
+                    uint32_t g[4];
+                    block_gaps(v[i], bi[i].cnt, lane, g);
+                    width = bitlen32(__reduce_max_sync(0xffffffffu, max(max(g[0], g[1]), max(g[2], g[3]))));
+                    base = __shfl_sync(0xffffffffu, v[i][0], 0);
+                } else {
+                    uint32_t mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+                    for (uint32_t q = 0; q < 4; q++)
+                        if (4u * lane + q < bi[i].cnt) {
+                            mn = min(mn, v[i][q]);
+                            mx = max(mx, v[i][q]);
+                        }
+                    mn = __reduce_min_sync(0xffffffffu, mn);
+                    mx = __reduce_max_sync(0xffffffffu, mx);
+                    width = bitlen32(mx - mn);
+                    base = mn;
+                }
+                if (lane == h + i) {
+                    myw = bi[i].cnt ? width : 0u;
+                    myb = base;
+                }
+            }
         }
-        if (lane == 0) {
-            w.bw[gb] = width;
-            w.bbase[gb] = base;
+        if (lane < kBW) {
+            if (gb0 + lane < NB) {
+                w.bw[gb0 + lane] = myw;
+                w.bbase[gb0 + lane] = myb;
+            }
+            s_w[warp * kBW + lane] = myw;
         }
+        __syncthreads();
+        if (warp == 0) tile_prefix(w, s_w, t, NB, lane);
+        __syncthreads();
     }
 }
 
-__device__ __forceinline__ unsigned long long stream_bytes(const PStream &s, const uint32_t *P, uint32_t *mode)
+__device__ __forceinline__ unsigned long long stream_bytes(const PStream &s, unsigned long long sumb, uint32_t *mode)
 {
-    const unsigned long long sumb = P[s.blk0 + s.nb] - P[s.blk0];
     const unsigned long long packed = 16u + dpad16(5ull * s.nb) + 16u * sumb;
     const unsigned long long raw = 16u + dpad16(4ull * s.n);
     const bool is_packed = s.n > 0 && packed < raw;
@@ -432,6 +569,7 @@ __device__ __forceinline__ unsigned long long stream_bytes(const PStream &s, con
     return is_packed ? packed : raw;
 }
 
+// Tile prefixes, each stream's payload start, sizes and offsets, the container header and table.
 __global__ void __launch_bounds__(kScanThreads) pe_layout(PWork w, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
 {
     __shared__ unsigned long long sm[33];
@@ -442,18 +580,23 @@ __global__ void __launch_bounds__(kScanThreads) pe_layout(PWork w, uint8_t *out,
         if (threadIdx.x == 0) *out_bytes = 0;
         return;
     }
-    const uint64_t NB = w.ctl->nb, L = w.L, K = 2 * L - 1;
-    const unsigned long long sumb = cta_chunk_scan_u32<kScanThreads>(w.bw, w.bw, NB, sm);
-    if (threadIdx.x == 0) w.bw[NB] = (uint32_t)sumb;
+    const uint64_t NB = w.ctl->nb, NT = dcdiv(NB, kBT), L = w.L, K = 2 * L - 1;
+    const unsigned long long sumb = cta_chunk_scan_u32<kScanThreads>(w.tsum, w.tsum, NT, sm);
+    if (threadIdx.x == 0) w.tsum[NT] = (uint32_t)sumb;
     __syncthreads();
+    for (uint64_t k = threadIdx.x; k < K; k += kScanThreads) w.st[k].pstart = prefix_at(w, w.st[k].blk0, NB, NT);
+    __syncthreads();
+    auto sumb_of = [&](uint64_t k) -> unsigned long long {
+        return (k + 1 < K ? w.st[k + 1].pstart : w.tsum[NT]) - w.st[k].pstart;
+    };
     const unsigned long long head = 16u + 16u * L;
     const unsigned long long body = cta_scan_fn(
-        K, [&](uint64_t k) { uint32_t m; return stream_bytes(w.st[k], w.bw, &m); },
+        K, [&](uint64_t k) { uint32_t m; return stream_bytes(w.st[k], sumb_of(k), &m); },
         [&](uint64_t k, unsigned long long pre) {
-            PStream s = w.st[k];
-            s.size = stream_bytes(s, w.bw, &s.mode);
-            s.off = head + pre;
-            w.st[k] = s;
+            uint32_t m;
+            w.st[k].size = stream_bytes(w.st[k], sumb_of(k), &m);
+            w.st[k].mode = m;
+            w.st[k].off = head + pre;
         },
         sm);
     const unsigned long long total = head + body;
@@ -474,64 +617,100 @@ __global__ void __launch_bounds__(kScanThreads) pe_layout(PWork w, uint8_t *out,
     for (uint64_t k = threadIdx.x; k <= K; k += kScanThreads) tab[k] = k < K ? w.st[k].off : total;
 }
 
-__global__ void __launch_bounds__(kPT) pe_pack(PWork w, const uint32_t *parent, uint8_t *out)
+// Stream headers, base and width tables, payloads (packed) or values (raw); 8 blocks per warp.
+__global__ void __launch_bounds__(kPT) pe_pack(PWork w, uint8_t *out)
 {
+    __shared__ uint32_t s_val[kPWarps][kBW][kBlock];
     __shared__ uint32_t rows[kPWarps][4 * 32 + 4];
     if (w.ctl->code != FQ_OK) return;  // warp-level work only
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint64_t NB = w.ctl->nb;
-    for (uint64_t gb = ((uint64_t)blockIdx.x * kPT + threadIdx.x) / 32u; gb < NB; gb += (uint64_t)gridDim.x * kPWarps) {
-        uint32_t v[4], cnt;
-        bool isR;
-        const uint32_t k = block_values(w, parent, (uint32_t)gb, lane, false, v, &cnt, &isR);
-        const PStream s = w.st[k];
-        const uint32_t j = (uint32_t)gb - s.blk0;
-        uint8_t *dst = out + s.off;
-        uint32_t *dw = reinterpret_cast<uint32_t *>(dst);
-        if (s.mode == kModeRaw) {
-            if (j == 0 && lane == 0) {
-                dw[0] = isR ? kMagicForR : kMagicRaw;
-                dw[1] = s.n;
-                dw[2] = 0u;
-                dw[3] = s.n;
+    const uint64_t NB = w.ctl->nb, NT = dcdiv(NB, kBT);
+    const uint32_t L = (uint32_t)w.L;
+    for (uint64_t t = blockIdx.x; t < NT; t += gridDim.x) {
+        const uint64_t gb0 = t * kBT + (uint64_t)warp * kBW;
+        const BInfo mine = lane_block_info(w, L, gb0, NB, lane);
+        uint32_t mw = 0, mb = 0, mp = 0;  // lane i: block i's width, base, payload units before it in its stream
+        if (mine.cnt) {
+            const uint64_t gb = gb0 + lane;
+            mw = w.bw[gb];
+            mb = w.bbase[gb];
+            mp = prefix_at(w, gb, NB, NT) - w.st[mine.k].pstart;
+        }
+        {  // the 8 blocks' values, all loads in flight, staged in shared memory
+            uint32_t v[kBW][4];
+#pragma unroll
+            for (uint32_t i = 0; i < kBW; i++) {
+                const BInfo bi = bcast(mine, i);
+                const uint32_t *src = bi.isR ? w.R : w.S;
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t slot = 4u * lane + q;
+                    v[i][q] = slot < bi.cnt ? src[bi.g0 + slot] : 0u;
+                }
             }
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (4u * lane + q < cnt) dw[4u + kBlock * j + 4u * lane + q] = v[q];
-            if (j + 1 == s.nb) {  // zero words up to the 16-byte boundary
-                const uint32_t padw = (uint32_t)((dpad16(4ull * s.n) - 4ull * s.n) / 4u);
-                if (lane < padw) dw[4u + s.n + lane] = 0u;
-            }
-            continue;
+            for (uint32_t i = 0; i < kBW; i++)
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) s_val[warp][i][4u * lane + q] = v[i][q];
         }
-        const uint32_t nb = s.nb;
-        if (j == 0) {
+        __syncwarp();
+#pragma unroll 1
+        for (uint32_t i = 0; i < kBW; i++) {
+            const BInfo bi = bcast(mine, i);
+            const uint32_t b = __shfl_sync(0xffffffffu, mw, i), base = __shfl_sync(0xffffffffu, mb, i);
+            const uint32_t poff = __shfl_sync(0xffffffffu, mp, i);
+            if (!bi.cnt) continue;  // uniform over the warp
+            uint32_t v[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) v[q] = s_val[warp][i][4u * lane + q];
+            const PStream s = w.st[bi.k];
+            const uint32_t j = (uint32_t)(gb0 + i) - s.blk0;
+            const bool isR = bi.isR;
+            uint8_t *dst = out + s.off;
+            uint32_t *dw = reinterpret_cast<uint32_t *>(dst);
+            if (s.mode == kModeRaw) {
+                if (j == 0 && lane == 0) {
+                    dw[0] = isR ? kMagicForR : kMagicRaw;
+                    dw[1] = s.n;
+                    dw[2] = 0u;
+                    dw[3] = s.n;
+                }
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++)
+                    if (4u * lane + q < bi.cnt) dw[4u + kBlock * j + 4u * lane + q] = v[q];
+                if (j + 1 == s.nb) {  // zero words up to the 16-byte boundary
+                    const uint32_t padw = (uint32_t)((dpad16(4ull * s.n) - 4ull * s.n) / 4u);
+                    if (lane < padw) dw[4u + s.n + lane] = 0u;
+                }
+                continue;
+            }
+            const uint32_t nb = s.nb;
+            if (j == 0) {
+                if (lane == 0) {
+                    dw[0] = isR ? kMagicForP : kMagicPacked;
+                    dw[1] = s.n;
+                    dw[2] = nb;
+                    dw[3] = (uint32_t)((s.size - 16u - dpad16(5ull * nb)) / 4u);
+                }
+                const uint32_t t0 = 16u + 5u * nb, t1 = (uint32_t)(16u + dpad16(5ull * nb));
+                if (t0 + lane < t1) dst[t0 + lane] = 0u;
+            }
             if (lane == 0) {
-                dw[0] = isR ? kMagicForP : kMagicPacked;
-                dw[1] = s.n;
-                dw[2] = nb;
-                dw[3] = 4u * (w.bw[s.blk0 + nb] - w.bw[s.blk0]);
+                dw[4u + j] = base;
+                dst[16u + 4u * nb + j] = (uint8_t)b;
             }
-            const uint32_t t0 = 16u + 5u * nb, t1 = (uint32_t)(16u + dpad16(5ull * nb));
-            if (t0 + lane < t1) dst[t0 + lane] = 0u;
-        }
-        const uint32_t b = w.bw[gb + 1] - w.bw[gb];
-        const uint32_t base = w.bbase[gb];
-        if (lane == 0) {
-            dw[4u + j] = base;
-            dst[16u + 4u * nb + j] = (uint8_t)b;
-        }
-        uint32_t g[4];
-        if (!isR) {
-            block_gaps(v, cnt, lane, g);
-        } else {
+            uint32_t g[4];
+            if (!isR) {
+                block_gaps(v, bi.cnt, lane, g);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; q++) g[q] = (4u * lane + q < cnt) ? v[q] - base : 0u;
+                for (uint32_t q = 0; q < 4; q++) g[q] = (4u * lane + q < bi.cnt) ? v[q] - base : 0u;
+            }
+            uint32_t words[4];
+            pack_block_words(g, b, rows[warp], lane, words);
+            store_block_words(dst + 16u + dpad16(5ull * nb) + 16ull * poff, words, b, lane, 0ull, ~0ull);
         }
-        uint32_t words[4];
-        pack_block_words(g, b, rows[warp], lane, words);
-        uint8_t *pk = dst + 16u + dpad16(5ull * nb) + 16ull * (w.bw[gb] - w.bw[s.blk0]);
-        store_block_words(pk, words, b, lane, 0ull, ~0ull);
+        __syncwarp();
     }
 }
 
@@ -636,113 +815,165 @@ __global__ void __launch_bounds__(kScanThreads) pd_plan(PWork w, const uint8_t *
     }
 }
 
+// Widths of every block from the streams' width tables (0 for raw streams), tile prefixes.
 __global__ void __launch_bounds__(kPT) pd_widths(PWork w, const uint8_t *in)
 {
-    if (w.ctl->code != FQ_OK) return;
+    __shared__ uint32_t s_w[kBT];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = w.ctl->code != FQ_OK;
+    __syncthreads();
+    if (s_abort) return;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t K = 2u * w.ctl->mode - 1u;
-    const uint64_t NB = w.ctl->nb;
-    for (uint64_t gb = (uint64_t)blockIdx.x * kPT + threadIdx.x; gb < NB; gb += (uint64_t)gridDim.x * kPT) {
-        const uint32_t k = stream_of_block(w.st, K, (uint32_t)gb);
-        const PStream s = w.st[k];
-        uint32_t b = 0;
-        if (s.mode == kModePacked) {
-            b = in[s.off + 16u + 4ull * s.nb + (gb - s.blk0)];
-            if (b > 32u) {
-                set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, k);
-                b = 0;
+    const uint64_t NB = w.ctl->nb, NT = dcdiv(NB, kBT);
+    for (uint64_t t = blockIdx.x; t < NT; t += gridDim.x) {
+        if (threadIdx.x < kBT) {
+            const uint64_t gb = t * kBT + threadIdx.x;
+            uint32_t b = 0;
+            if (gb < NB) {
+                const uint32_t k = stream_of_block(w.st, K, (uint32_t)gb);
+                const PStream s = w.st[k];
+                if (s.mode == kModePacked) {
+                    b = in[s.off + 16u + 4ull * s.nb + (gb - s.blk0)];
+                    if (b > 32u) {
+                        set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, k);
+                        b = 0;
+                    }
+                }
+                w.bw[gb] = b;
             }
+            s_w[threadIdx.x] = b;
         }
-        w.bw[gb] = b;
+        __syncthreads();
+        if (warp == 0) tile_prefix(w, s_w, t, NB, lane);
+        __syncthreads();
     }
 }
 
+// Tile prefixes, each stream's payload start; every packed stream's widths must add up to its
+// announced payload.
 __global__ void __launch_bounds__(kScanThreads) pd_scan(PWork w)
 {
     __shared__ unsigned long long sm[33];
     if (w.ctl->code != FQ_OK) return;  // uniform: pd_widths has finished
-    const uint64_t NB = w.ctl->nb, K = 2u * w.ctl->mode - 1u;
-    const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(w.bw, w.bw, NB, sm);
-    if (threadIdx.x == 0) w.bw[NB] = (uint32_t)total;
+    const uint64_t NB = w.ctl->nb, NT = dcdiv(NB, kBT), K = 2u * w.ctl->mode - 1u;
+    const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(w.tsum, w.tsum, NT, sm);
+    if (threadIdx.x == 0) w.tsum[NT] = (uint32_t)total;
+    __syncthreads();
+    for (uint64_t k = threadIdx.x; k < K; k += kScanThreads) w.st[k].pstart = prefix_at(w, w.st[k].blk0, NB, NT);
     __syncthreads();
     for (uint64_t k = threadIdx.x; k < K; k += kScanThreads) {
         const PStream s = w.st[k];
-        if (s.mode == kModePacked && 4ull * (w.bw[s.blk0 + s.nb] - w.bw[s.blk0]) != s.words)
-            set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, k);
+        const uint32_t next = k + 1 < K ? w.st[k + 1].pstart : w.tsum[NT];
+        if (s.mode == kModePacked && 4ull * (next - s.pstart) != s.words) set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, k);
     }
 }
 
+// Level-set ids into S and parent indices into R, 8 blocks per warp: the payload words of all 8
+// are staged in shared memory before any is decoded.
 __global__ void __launch_bounds__(kPT) pd_unpack(PWork w, const uint8_t *in)
 {
-    __shared__ uint32_t rows[kPWarps][4 * 32 + 4];
+    __shared__ uint32_t rows[kPWarps][kBW][4 * 32 + 4];
     if (w.ctl->code != FQ_OK) return;  // warp-level work only
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t L = w.ctl->mode, K = 2u * L - 1u;
-    const uint64_t NB = w.ctl->nb;
-    uint32_t *row = rows[warp];
-    for (uint64_t gb = ((uint64_t)blockIdx.x * kPT + threadIdx.x) / 32u; gb < NB; gb += (uint64_t)gridDim.x * kPWarps) {
-        const uint32_t k = stream_of_block(w.st, K, (uint32_t)gb);
-        const PStream s = w.st[k];
-        const uint32_t j = (uint32_t)gb - s.blk0;
-        const bool isR = k >= L;
-        const uint32_t d = isR ? k - L + 1u : k;
-        const uint64_t g0 = (uint64_t)w.lo[d] + (uint64_t)kBlock * j;
-        const uint32_t cnt = min(kBlock, s.n - kBlock * j);
-        const uint32_t above = isR ? w.lo[d] - w.lo[d - 1] : 0u;  // size of level d - 1
-        uint32_t *dstv = isR ? w.R : w.S;
-        const uint8_t *src = in + s.off;
-        bool ok = true;
-        uint32_t out[4];
-        if (s.mode == kModeRaw) {
-            const uint32_t *vw = reinterpret_cast<const uint32_t *>(src + 16) + (uint64_t)kBlock * j;
+    const uint32_t L = w.ctl->mode;
+    const uint64_t NB = w.ctl->nb, NT = dcdiv(NB, kBT);
+    for (uint64_t t = blockIdx.x; t < NT; t += gridDim.x) {
+        const uint64_t gb0 = t * kBT + (uint64_t)warp * kBW;
+        const BInfo mine = lane_block_info(w, L, gb0, NB, lane);
+        uint32_t mw = 0, mp = 0, mmode = 0, mj = 0;
+        unsigned long long moff = 0;
+        if (mine.cnt) {
+            const uint64_t gb = gb0 + lane;
+            const PStream s = w.st[mine.k];
+            mw = w.bw[gb];
+            mp = prefix_at(w, gb, NB, NT) - s.pstart;
+            mmode = s.mode;
+            mj = (uint32_t)gb - s.blk0;
+            moff = s.off + 16u + (s.mode == kModeRaw ? 4ull * kBlock * mj : dpad16(5ull * s.nb) + 16ull * mp);
+        }
+        {  // stage the 8 blocks: payload words (packed) or values (raw), all loads in flight
+            uint32_t x[kBW][4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) out[q] = (4u * lane + q < cnt) ? vw[4u * lane + q] : 0u;
-            if (j + 1 == s.nb) {
-                const uint32_t padw = (uint32_t)((dpad16(4ull * s.n) - 4ull * s.n) / 4u);
-                if (lane < padw && reinterpret_cast<const uint32_t *>(src + 16)[s.n + lane] != 0u) ok = false;
-            }
-        } else {
-            const uint32_t nb = s.nb;
-            if (j == 0) {
-                const uint32_t t0 = 16u + 5u * nb, t1 = (uint32_t)(16u + dpad16(5ull * nb));
-                if (t0 + lane < t1 && src[t0 + lane] != 0u) ok = false;
-            }
-            const uint32_t b = w.bw[gb + 1] - w.bw[gb];
-            const uint32_t base = ld_u32(src + 16u + 4u * j);
-            const uint32_t *pk = reinterpret_cast<const uint32_t *>(src + 16u + dpad16(5ull * nb) +
-                                                                   16ull * (w.bw[gb] - w.bw[s.blk0]));
-            // stage the block's 4b words, then three zero words past them for the slot reader
+            for (uint32_t i = 0; i < kBW; i++) {
+                const uint32_t cnt = __shfl_sync(0xffffffffu, mine.cnt, i), b = __shfl_sync(0xffffffffu, mw, i);
+                const uint32_t mode = __shfl_sync(0xffffffffu, mmode, i);
+                const unsigned long long o = __shfl_sync(0xffffffffu, moff, i);
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(in + o);
 #pragma unroll
-            for (uint32_t q = 0; q < 4; q++) {
-                const uint32_t i = lane + 32u * q;
-                row[i] = i < 4u * b ? pk[i] : 0u;
-            }
-            if (lane < 4u) row[128u + lane] = 0u;
-            __syncwarp();
-            uint32_t g[4];
-            extract_slots(row, b, lane, g);
-            __syncwarp();
-            if (!isR) {
-                unsigned long long last;
-                ok = scan_slots(g, base, j, s.n, lane, out, &last) && ok;
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const bool valid = 4u * lane + q < cnt;
-                    const unsigned long long x = (unsigned long long)base + g[q];
-                    if ((!valid && g[q] != 0u) || (valid && x > 0xffffffffull)) ok = false;
-                    out[q] = (uint32_t)x;
+                for (uint32_t q = 0; q < 4; q++) {
+                    const uint32_t idx = mode == kModeRaw ? 4u * lane + q : lane + 32u * q;
+                    const bool live = cnt && (mode == kModeRaw ? idx < cnt : idx < 4u * b);
+                    x[i][q] = live ? src[idx] : 0u;
                 }
             }
-        }
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const uint32_t i = 4u * lane + q;
-            if (i < cnt) {
-                if (isR && out[q] >= above) ok = false;
-                dstv[g0 + i] = out[q];
+            for (uint32_t i = 0; i < kBW; i++) {
+                const uint32_t mode = __shfl_sync(0xffffffffu, mmode, i);
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) rows[warp][i][mode == kModeRaw ? 4u * lane + q : lane + 32u * q] = x[i][q];
+                if (lane < 4u) rows[warp][i][128u + lane] = 0u;
             }
         }
-        if (!ok) set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, k);
+        __syncwarp();
+#pragma unroll 1
+        for (uint32_t i = 0; i < kBW; i++) {
+            const BInfo bi = bcast(mine, i);
+            const uint32_t b = __shfl_sync(0xffffffffu, mw, i);
+            if (!bi.cnt) continue;  // uniform
+            const PStream s = w.st[bi.k];
+            const uint32_t j = (uint32_t)(gb0 + i) - s.blk0;
+            const uint8_t *src = in + s.off;
+            const bool isR = bi.isR;
+            const uint32_t cnt = bi.cnt, d = bi.d;
+            const uint32_t above = isR ? w.lo[d] - w.lo[d - 1] : 0u;  // size of level d - 1
+            bool ok = true;
+            uint32_t out[4];
+            if (s.mode == kModeRaw) {
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) out[q] = rows[warp][i][4u * lane + q];
+                if (j + 1 == s.nb) {
+                    const uint32_t padw = (uint32_t)((dpad16(4ull * s.n) - 4ull * s.n) / 4u);
+                    if (lane < padw && reinterpret_cast<const uint32_t *>(src + 16)[s.n + lane] != 0u) ok = false;
+                }
+            } else {
+                if (j == 0) {
+                    const uint32_t t0 = 16u + 5u * s.nb, t1 = (uint32_t)(16u + dpad16(5ull * s.nb));
+                    if (t0 + lane < t1 && src[t0 + lane] != 0u) ok = false;
+                }
+                const uint32_t base = ld_u32(src + 16u + 4u * j);
+                if (!isR && cnt == kBlock && b <= 16u) {  // full narrow block: 32-bit extraction and scan
+                    uint32_t last;
+                    ok = unpack_full_narrow(rows[warp][i], b, base, lane, out, &last) && ok;
+                } else {
+                    uint32_t g[4];
+                    extract_slots(rows[warp][i], b, lane, g);
+                    if (!isR) {
+                        unsigned long long last;
+                        ok = scan_slots(g, base, j, s.n, lane, out, &last) && ok;
+                    } else {
+#pragma unroll
+                        for (uint32_t q = 0; q < 4; q++) {
+                            const bool valid = 4u * lane + q < cnt;
+                            const unsigned long long x = (unsigned long long)base + g[q];
+                            if ((!valid && g[q] != 0u) || (valid && x > 0xffffffffull)) ok = false;
+                            out[q] = (uint32_t)x;
+                        }
+                    }
+                }
+            }
+            uint32_t *dstv = isR ? w.R : w.S;
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                const uint32_t slot = 4u * lane + q;
+                if (slot < cnt) {
+                    if (isR && out[q] >= above) ok = false;
+                    dstv[bi.g0 + slot] = out[q];
+                }
+            }
+            if (!ok) set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, bi.k);
+        }
+        __syncwarp();
     }
 }
 
@@ -754,34 +985,225 @@ __global__ void __launch_bounds__(kPT) pd_fill(PWork w, int32_t *depth, uint32_t
         depth[v] = -1;
         parent[v] = 0xffffffffu;
     }
-    for (uint64_t i = (uint64_t)blockIdx.x * kPT + threadIdx.x; i < (w.n + 31) / 32; i += stride) w.S2[i] = 0u;
 }
 
+// Level of position g: the largest d < L with lo[d] <= g.
+__device__ __forceinline__ uint32_t level_of(const uint32_t *lo, uint32_t L, uint64_t g)
+{
+    uint32_t a = 0, b = L;
+    while (b - a > 1) {
+        const uint32_t mid = (a + b) / 2;
+        if (lo[mid] <= g) a = mid;
+        else b = mid;
+    }
+    return a;
+}
+
+// depth and parent of every reached vertex; kPosPerThread positions per thread, loads batched.
 __global__ void __launch_bounds__(kPT) pd_scatter(PWork w, int32_t *depth, uint32_t *parent)
 {
     if (w.ctl->code != FQ_OK) return;
     const uint32_t L = w.ctl->mode;
     const uint64_t reached = w.ctl->n;
-    for (uint64_t g = (uint64_t)blockIdx.x * kPT + threadIdx.x; g < reached; g += (uint64_t)gridDim.x * kPT) {
-        uint32_t lo = 0, hi = L;  // level: largest d with lo[d] <= g
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) / 2;
-            if (w.lo[mid] <= g) lo = mid;
-            else hi = mid;
+    for (uint64_t base = (uint64_t)blockIdx.x * kPosTile; base < reached; base += (uint64_t)gridDim.x * kPosTile) {
+        uint32_t v[kPosPerThread], d[kPosPerThread], r[kPosPerThread], pv[kPosPerThread];
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            v[i] = g < reached ? w.S[g] : 0u;
+            d[i] = g < reached ? level_of(w.lo, L, g) : 0u;
         }
-        const uint32_t d = lo;
-        const uint32_t v = w.S[g];
-        if (v >= w.n || (g > w.lo[d] && w.S[g - 1] >= v)) {
-            set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, g);
-            continue;
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            r[i] = (g < reached && d[i] > 0) ? w.R[g] : 0u;
         }
-        const uint32_t bit = 1u << (v & 31u);
-        if (atomicOr(&w.S2[v >> 5], bit) & bit) {  // the vertex already appeared at some level
-            set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, g);
-            continue;
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            pv[i] = (g < reached && d[i] > 0) ? w.S[w.lo[d[i] - 1] + r[i]] : v[i];
         }
-        depth[v] = (int32_t)d;
-        parent[v] = d == 0 ? v : w.S[w.lo[d - 1] + w.R[g]];
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            if (g >= reached) continue;
+            if (v[i] >= w.n) {
+                set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, g);
+                continue;
+            }
+            depth[v[i]] = (int32_t)d[i];
+            parent[v[i]] = pv[i];
+        }
+    }
+}
+
+// After the scatter: ids strictly increasing within each level, and every vertex holding the
+// level it was listed at (a vertex listed at two levels fails at one of them).
+__global__ void __launch_bounds__(kPT) pd_verify(PWork w, const int32_t *depth)
+{
+    if (w.ctl->code != FQ_OK) return;
+    const uint32_t L = w.ctl->mode;
+    const uint64_t reached = w.ctl->n;
+    for (uint64_t base = (uint64_t)blockIdx.x * kPosTile; base < reached; base += (uint64_t)gridDim.x * kPosTile) {
+        uint32_t v[kPosPerThread], pv[kPosPerThread], d[kPosPerThread];
+        int32_t got[kPosPerThread];
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            v[i] = g < reached ? w.S[g] : 0u;
+            pv[i] = (g < reached && g > 0) ? w.S[g - 1] : 0u;
+            d[i] = g < reached ? level_of(w.lo, L, g) : 0u;
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            got[i] = (g < reached && v[i] < w.n) ? depth[v[i]] : (int32_t)d[i];
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            if (g >= reached) continue;
+            const bool first = g == w.lo[d[i]];
+            if (v[i] >= w.n || (!first && pv[i] >= v[i]) || got[i] != (int32_t)d[i])
+                set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, g);
+        }
+    }
+}
+
+// ---- vertex-ordered decode (at most kVmLevels levels): chunks of kVmIds ids built in shared memory
+
+// For every level d and id chunk c: the first position of level d whose id lies in chunk c or later
+// (cstart[d][nch] = end of the level).  Written only at chunk changes; an unsorted level leaves
+// entries that pd_build's checks reject.
+__global__ void __launch_bounds__(kPT) pd_chunks(PWork w)
+{
+    if (w.ctl->code != FQ_OK) return;
+    const uint32_t L = w.ctl->mode;
+    const uint64_t reached = w.ctl->n, nch = w.nch;
+    for (uint64_t base = (uint64_t)blockIdx.x * kPosTile; base < reached; base += (uint64_t)gridDim.x * kPosTile) {
+        uint32_t v[kPosPerThread], pv[kPosPerThread], d[kPosPerThread];
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            v[i] = g < reached ? w.S[g] : 0u;
+            pv[i] = (g < reached && g > 0) ? w.S[g - 1] : 0u;
+            d[i] = g < reached ? level_of(w.lo, L, g) : 0u;
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kPosPerThread; i++) {
+            const uint64_t g = base + threadIdx.x + (uint64_t)kPT * i;
+            if (g >= reached) continue;
+            uint32_t *row = w.cstart + (uint64_t)d[i] * (nch + 1);
+            const uint64_t c = min((uint64_t)(v[i] / kVmIds), nch);
+            const int64_t cp = g > w.lo[d[i]] ? (int64_t)min((uint64_t)(pv[i] / kVmIds), nch) : -1;
+            for (int64_t x = cp + 1; x <= (int64_t)c; x++) row[x] = (uint32_t)g;
+            if (g + 1 == w.lo[d[i] + 1])
+                for (uint64_t x = c + 1; x <= nch; x++) row[x] = w.lo[d[i] + 1];
+        }
+    }
+}
+
+// One CTA per chunk: every level's positions with ids in the chunk (checked: ids inside the chunk,
+// increasing within the level, no vertex at two levels), depth and parent built in shared memory,
+// then the chunk written out whole.
+__global__ void __launch_bounds__(kPT) pd_build(PWork w, int32_t *depth, uint32_t *parent)
+{
+    __shared__ int32_t s_d[kVmIds];
+    __shared__ uint32_t s_p[kVmIds];
+    __shared__ uint32_t s_x0[kVmLevels], s_pre[kVmLevels + 1];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = w.ctl->code != FQ_OK;
+    __syncthreads();
+    if (s_abort) return;
+    const uint32_t L = w.ctl->mode, lane = threadIdx.x & 31u;
+    const uint64_t nch = w.nch;
+    for (uint64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint64_t a = c * kVmIds;
+        const uint32_t m = (uint32_t)min((uint64_t)kVmIds, w.n - a);
+        for (uint32_t i = threadIdx.x; i < kVmIds; i += kPT) {
+            s_d[i] = -1;
+            s_p[i] = 0xffffffffu;
+        }
+        if (threadIdx.x < 32) {  // each level's positions in this chunk, and their prefix
+            uint32_t cnt[kVmLevels / 32];
+#pragma unroll
+            for (uint32_t q = 0; q < kVmLevels / 32; q++) {
+                const uint32_t d = lane * (kVmLevels / 32) + q;
+                cnt[q] = 0;
+                if (d >= L) continue;
+                const uint32_t lo = w.lo[d], hi = w.lo[d + 1];
+                const uint32_t *row = w.cstart + (uint64_t)d * (nch + 1);
+                uint32_t x0 = row[c], x1 = row[c + 1];
+                const bool ok = lo <= x0 && x0 <= x1 && x1 <= hi && (c > 0 || x0 == lo) && (c + 1 < nch || x1 == hi);
+                if (!ok) {
+                    set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, (unsigned long long)lo);
+                    x0 = x1 = lo;
+                }
+                s_x0[d] = x0;
+                cnt[q] = x1 - x0;
+            }
+            uint32_t sum = 0;
+#pragma unroll
+            for (uint32_t q = 0; q < kVmLevels / 32; q++) sum += cnt[q];
+            uint32_t run = warp_incl_scan(sum) - sum;
+#pragma unroll
+            for (uint32_t q = 0; q < kVmLevels / 32; q++) {
+                s_pre[lane * (kVmLevels / 32) + q] = run;
+                run += cnt[q];
+            }
+            if (lane == 31) s_pre[kVmLevels] = run;
+        }
+        __syncthreads();
+        const uint32_t total = s_pre[kVmLevels];
+        for (uint32_t it0 = 0; it0 < total; it0 += 4u * kPT) {
+            uint32_t d[4], v[4], r[4], pv[4];
+            uint64_t g[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) {
+                const uint32_t it = it0 + threadIdx.x + u * kPT;
+                d[u] = 0;
+                g[u] = 0;
+                if (it < total) {
+                    uint32_t lo = 0, hi = L;  // the level: largest d with s_pre[d] <= it
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) / 2;
+                        if (s_pre[mid] <= it) lo = mid;
+                        else hi = mid;
+                    }
+                    d[u] = lo;
+                    g[u] = (uint64_t)s_x0[lo] + (it - s_pre[lo]);
+                }
+                v[u] = it < total ? w.S[g[u]] : 0u;
+                pv[u] = (it < total && g[u] > s_x0[d[u]]) ? w.S[g[u] - 1] : 0u;
+                r[u] = (it < total && d[u] > 0) ? __ldcs(w.R + g[u]) : 0u;
+            }
+            uint32_t par[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) {
+                const uint32_t it = it0 + threadIdx.x + u * kPT;
+                par[u] = (it < total && d[u] > 0) ? w.S[w.lo[d[u] - 1] + r[u]] : v[u];
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) {
+                const uint32_t it = it0 + threadIdx.x + u * kPT;
+                if (it >= total) continue;
+                if (v[u] < a || v[u] - a >= m || (g[u] > s_x0[d[u]] && pv[u] >= v[u])) {
+                    set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, g[u]);
+                    continue;
+                }
+                if (atomicCAS(&s_d[v[u] - a], -1, (int32_t)d[u]) != -1) {  // the vertex is at another level too
+                    set_error(w.ctl, FQ_ECORRUPT, kWherePredDec, g[u]);
+                    continue;
+                }
+                s_p[v[u] - a] = par[u];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += kPT) {  // streaming stores: keep S resident in L2 for the lookups
+            __stcs(depth + a + i, s_d[i]);
+            __stcs(parent + a + i, s_p[i]);
+        }
+        __syncthreads();
     }
 }
 
@@ -820,6 +1242,7 @@ fq_status fq_pred_encode(const int32_t *d_depth, const uint32_t *d_parent, uint6
     pe_init<<<grid_for((uint64_t)levels + 1, kPT), kPT, 0, st>>>(w, multi);
     const uint32_t D0 = digits_of_pass(levels, 0);
     pe_hist<true><<<tiles, kPT, 0, st>>>(w, d_depth, d_parent, nullptr, 0u, D0, multi);
+    pe_rowscan<<<D0, kScanThreads, 0, st>>>(w);
     pe_plan<<<1, kScanThreads, 0, st>>>(w, D0, multi);
     // pass p writes S when P - 1 - p is even, so that the last pass lands in S
     uint32_t *bufs[2] = {w.S, w.S2};
@@ -831,15 +1254,16 @@ fq_status fq_pred_encode(const int32_t *d_depth, const uint32_t *d_parent, uint6
             pe_scatter<true><<<tiles, kPT, 0, st>>>(w, d_depth, nullptr, dst, 0u, D, last);
         } else {
             pe_hist<false><<<tiles, kPT, 0, st>>>(w, d_depth, nullptr, prev, 8u * p, D, 0u);
-            pe_scan<<<1, kScanThreads, 0, st>>>(w, D);
+            pe_rowscan<<<D, kScanThreads, 0, st>>>(w);
+            pe_dscan<<<1, kScanThreads, 0, st>>>(w, D);
             pe_scatter<false><<<tiles, kPT, 0, st>>>(w, d_depth, prev, dst, 8u * p, D, last);
         }
         prev = dst;
     }
-    const uint32_t gridb = grid_for(w.nb_max, kPWarps);
-    pe_widths<<<gridb, kPT, 0, st>>>(w, d_parent);
+    const uint32_t gridt = grid_for(cdiv(w.nb_max, kBT), 1);
+    pe_widths<<<gridt, kPT, 0, st>>>(w, d_parent);
     pe_layout<<<1, kScanThreads, 0, st>>>(w, d_out, cap, d_out_bytes);
-    pe_pack<<<gridb, kPT, 0, st>>>(w, d_parent, d_out);
+    pe_pack<<<gridt, kPT, 0, st>>>(w, d_out);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         note_cuda_error(e, __LINE__);
@@ -858,13 +1282,20 @@ fq_status fq_pred_decode(const uint8_t *d_in, uint64_t in_bytes, int32_t *d_dept
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PWork w{};
     pred_layout(n, max_levels, &w, d_work);
-    const uint32_t gridb = grid_for(w.nb_max, kPWarps);
+    const uint32_t gridt = grid_for(cdiv(w.nb_max, kBT), 1);
+    const uint32_t gridp = grid_for(n, kPosTile);
     pd_plan<<<1, kScanThreads, 0, st>>>(w, d_in, in_bytes);
-    pd_widths<<<grid_for(w.nb_max, kPT), kPT, 0, st>>>(w, d_in);
+    pd_widths<<<gridt, kPT, 0, st>>>(w, d_in);
     pd_scan<<<1, kScanThreads, 0, st>>>(w);
-    pd_unpack<<<gridb, kPT, 0, st>>>(w, d_in);
-    pd_fill<<<grid_for(n, kPT), kPT, 0, st>>>(w, d_depth, d_parent);
-    pd_scatter<<<grid_for(n, kPT), kPT, 0, st>>>(w, d_depth, d_parent);
+    pd_unpack<<<gridt, kPT, 0, st>>>(w, d_in);
+    if (max_levels <= kVmLevels) {
+        pd_chunks<<<gridp, kPT, 0, st>>>(w);
+        pd_build<<<grid_for(w.nch, 1), kPT, 0, st>>>(w, d_depth, d_parent);
+    } else {
+        pd_fill<<<grid_for(n, kPT), kPT, 0, st>>>(w, d_depth, d_parent);
+        pd_scatter<<<gridp, kPT, 0, st>>>(w, d_depth, d_parent);
+        pd_verify<<<gridp, kPT, 0, st>>>(w, d_depth);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         note_cuda_error(e, __LINE__);

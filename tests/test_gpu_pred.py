@@ -42,9 +42,16 @@ def encode(depth, parent, levels=None):
     return c
 
 
-def check_round_trip(c, depth, parent):
+# decode workspaces: sized for the container's own level count (the vertex-ordered path when that is
+# at most 128 levels) and for more than 128 levels (the position-ordered path)
+PATHS = pytest.mark.parametrize("max_levels", [None, 200], ids=["own_levels", "over_128_levels"])
+
+
+def check_round_trip(c, depth, parent, max_levels=None):
     n = depth.size
-    gd, gp = fqbfs.fq_pred_decode(c, n)
+    if max_levels is not None:
+        max_levels = max(max_levels, levels_of(depth))
+    gd, gp = fqbfs.fq_pred_decode(c, n, max_levels=max_levels)
     gd = gd.cpu().numpy()
     gp = gp.cpu().numpy().view(np.uint32)
     assert np.array_equal(gd, depth)
@@ -87,8 +94,9 @@ SHAPES = {
 }
 
 
+@PATHS
 @pytest.mark.parametrize("name", list(SHAPES))
-def test_random_trees_match_oracle(name):
+def test_random_trees_match_oracle(name, max_levels):
     n, sizes = SHAPES[name]
     depth_t, parent_t = inputs.random_tree(n, sizes, seed=hash(name) % 1000 + 7)
     depth = depth_t.numpy()
@@ -96,7 +104,7 @@ def test_random_trees_match_oracle(name):
     c = encode(depth, parent)
     want = oracle.pl_encode(depth, parent.astype(np.uint32))
     assert np.array_equal(c.cpu().numpy(), want)
-    check_round_trip(c, depth, parent)
+    check_round_trip(c, depth, parent, max_levels)
 
 
 @pytest.mark.parametrize("n", [65536, 65537])
@@ -241,8 +249,9 @@ MUTATIONS = [("magic", _mut_magic, True), ("table", _mut_table, True), ("stream_
              ("rank_range", _mut_rank_range, True), ("id_range", _mut_id_range, False)]
 
 
+@PATHS
 @pytest.mark.parametrize("name,mut,untouched", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_decode_rejects(name, mut, untouched):
+def test_decode_rejects(name, mut, untouched, max_levels):
     depth, parent = small_tree()
     c = encode(depth, parent)
     b = c.cpu().numpy().copy()
@@ -252,7 +261,7 @@ def test_decode_rejects(name, mut, untouched):
     gd = torch.full((n,), 7, dtype=torch.int32, device="cuda")
     gp = torch.full((n,), 7, dtype=torch.int32, device="cuda")
     with pytest.raises(fqbfs.FqError) as e:
-        fqbfs.fq_pred_decode(torch.from_numpy(b).cuda(), n, max_levels=L, depth=gd, parent=gp)
+        fqbfs.fq_pred_decode(torch.from_numpy(b).cuda(), n, max_levels=max_levels or L, depth=gd, parent=gp)
     assert e.value.status == fqbfs.FQ_ECORRUPT
     if untouched:
         assert bool((gd == 7).all()) and bool((gp == 7).all())
@@ -260,7 +269,8 @@ def test_decode_rejects(name, mut, untouched):
         oracle.pl_decode(b, n)
 
 
-def test_decode_repeated_and_unsorted_ids():
+@PATHS
+def test_decode_repeated_and_unsorted_ids(max_levels):
     n = 40
     depth = np.full(n, -1, np.int32)
     parent = np.full(n, 0xFFFFFFFF, np.int64)
@@ -268,11 +278,12 @@ def test_decode_repeated_and_unsorted_ids():
     parent[[5, 9, 12, 20]] = [5, 5, 5, 12]
     b = encode(depth, parent).cpu().numpy()
     L, off = table(b)
-    for pos, val in ((off[2] + 16, 9), (off[1] + 20, 3)):  # level 2 = {9}: repeated; level 1 = [9, 3]: unsorted
+    # level 2 = {9}: repeated; level 1 = [9, 3]: unsorted; level 2 = {40}: beyond n
+    for pos, val in ((off[2] + 16, 9), (off[1] + 20, 3), (off[2] + 16, 40)):
         bb = b.copy()
         bb[pos: pos + 4] = np.array([val], np.uint32).view(np.uint8)
         with pytest.raises(fqbfs.FqError) as e:
-            fqbfs.fq_pred_decode(torch.from_numpy(bb).cuda(), n)
+            fqbfs.fq_pred_decode(torch.from_numpy(bb).cuda(), n, max_levels=max_levels)
         assert e.value.status == fqbfs.FQ_ECORRUPT
         with pytest.raises(ValueError):
             oracle.pl_decode(bb, n)
