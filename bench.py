@@ -579,7 +579,7 @@ LINKS_GBPS = {"nvlink5_per_direction": 900.0, "pcie5_x16": 64.0, "infiniband_ndr
 
 
 def codec_threshold(dev, logs=range(4, 25, 2), mean_gap=16.0, reps=20):
-    """The compression threshold's break-even size (sec. 5.4.2): for each n, the per-call encode and
+    """The compression threshold's break-even size (sec. 5.4.3): for each n, the per-call encode and
     decode time on this GPU (calls replayed from a captured CUDA graph, so launch gaps but not the
     host's launch rate count) and the stream size; for each link bandwidth B, the smallest measured
     n for which encode + |stream|/B + decode beats 4n/B."""

@@ -23,17 +23,17 @@
  *  - One workspace (or graph handle) must not be used by two calls that may overlap in time.
  *
  * Stream formats (all little-endian; sizes are multiples of 16 bytes)
- *  FQ, a strictly increasing uint32 sequence v[0..n) (a frontier queue, sec. 4.1.3):
+ *  FQ, a strictly increasing uint32 sequence v[0..n) (a frontier queue, sec. 4.1.4):
  *    packed  {u32 'FQP1', n, nb = ceil(n/128), payload_words}, u32 base[nb], u8 b[nb],
  *            zeros to 16 B, then per block k the 128 slots at b_k bits each (4*b_k u32 words;
  *            slot j at bits [j*b_k, (j+1)*b_k), LSB first).  Slot 0 is 0 and base_k = v[128k]
  *            (frame of reference, Eq. 5); slot j >= 1 is v[128k+j] - v[128k+j-1] - 1 (delta
- *            coding, sec. 5.2); slots past n are 0; b_k = bit length of the block's largest
+ *            coding, sec. 5.1); slots past n are 0; b_k = bit length of the block's largest
  *            slot (Eq. 6 read as a ceiling, Eq. 7).
  *    raw     {u32 'FQR1', n, 0, n}, u32 v[n], zeros to 16 B.
- *    The packed form is written only when strictly smaller than the raw one (sec. 5.2
- *    "Lossless": the encoding must be smaller than the input; sec. 5.4.2 thresholds).
- *  FQX, the same sequence with patched exceptions (sec. 5.2 "Patched coding and Exceptions",
+ *    The packed form is written only when strictly smaller than the raw one (sec. 5.1
+ *    "Lossless": the encoding must be smaller than the input; sec. 5.4.3 thresholds).
+ *  FQX, the same sequence with patched exceptions (sec. 5.1 "Patched coding and Exceptions",
  *    Eq. 8-9; the PFOR family of sec. 5.3), written by fq_frontier_encode_px:
  *    {u32 'FQX1', n, nb, payload_words, E, 0, 0, 0}, u32 base[nb], u8 b[nb], u8 e[nb], zeros to
  *    16 B, the blocks' low b_k bits of every slot as in FQ, u8 slot[E] (each block's exception
@@ -104,13 +104,13 @@ fq_status fq_work_status(const void *d_work, void *stream, uint64_t *h_detail);
  * (capacity cap bytes).  The stream's size is written to the device u64 *d_out_bytes (0 on a
  * device-detected error; the needed size on FQ_ENOSPC).  Device errors: FQ_EUNSORTED,
  * FQ_ENOSPC.  The frontier queue compress step of Alg. "Our BFS algorithm with SpVM and
- * compression" (delta + binary packing, sec. 5.2-5.3). */
+ * compression" (delta + binary packing, sec. 5.1, 5.3). */
 fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
                              uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
 
 /* The same as fq_frontier_encode with the FQX (patched exceptions) format: a block whose largest
  * gaps are rare outliers keeps a small width and stores the outliers apart.  Same arguments,
- * workspace, bound (fq_queue_bound) and errors.  "Patched coding and Exceptions", sec. 5.2. */
+ * workspace, bound (fq_queue_bound) and errors.  "Patched coding and Exceptions", sec. 5.1. */
 fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
                                 uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
 
@@ -177,7 +177,7 @@ fq_status fq_frontier_encode_static(const uint32_t *d_ids, uint64_t n, uint8_t *
 /* ------------------------------------------------------------------ bitmap codec */
 
 /* Encode the bitmap d_words (ceil(nbits/64) words; bits >= nbits ignored) as an FB stream at
- * d_out (capacity cap); size to *d_out_bytes.  nbits <= 2^32.  Bitmap frontiers, sec. 3.3
+ * d_out (capacity cap); size to *d_out_bytes.  nbits <= 2^32.  Bitmap frontiers, sec. 3.1
  * ("Sparse vector with pop counting"), coded with the queue codec. */
 fq_status fq_bitmap_encode(const uint64_t *d_words, uint64_t nbits, uint8_t *d_out, uint64_t cap,
                            uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
@@ -190,7 +190,7 @@ fq_status fq_bitmap_decode(const uint8_t *d_in, uint64_t in_bytes, uint64_t *d_w
 
 /* ------------------------------------------------------------------ predecessor list
  * The BFS tree (depth, parent) as one container "FPL1", for the one exchange the thesis leaves
- * uncompressed: the predecessor reduction at the end of a BFS (sec. 6.5; its volume in the
+ * uncompressed: the predecessor reduction at the end of a BFS (sec. 4.1.4; its volume in the
  * results chapter exceeds that of all compressed frontier exchanges).  Layout (little-endian):
  *   u32 {"FPL1" = 0x314C5046, n, L, reached}; u64 off[2L]: stream k occupies [off[k], off[k+1])
  *   from the container's start, off[0] = 16 + 16 L, every stream a multiple of 16 bytes;
@@ -268,7 +268,7 @@ typedef struct fq_bfs_opts {
     uint32_t flags;
     uint32_t min_codec_ids; /* compression threshold: a level whose frontier has fewer ids skips the
                                codec stage (its frontier is consumed raw; Q_d, B_d record 0 bytes and
-                               are not logged); 0 codes every level.  sec. 5.4.2 "Usage of
+                               are not logged); 0 codes every level.  sec. 5.4.3 "Usage of
                                compression thresholds" */
 } fq_bfs_opts;
 

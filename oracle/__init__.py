@@ -10,13 +10,13 @@ the BFS depths:
 
 * ``bfs`` / ``validate``      -- FIFO BFS and the BFS-tree checks (Alg. "BFS based on
   replicated-CSR and SpMV"; Graph500 validation, Alg. "A Graph 500 application").
-* ``fq_encode`` / ``fq_decode`` -- delta + binary packing, blocks of 128 (sec. 5.2-5.3, Eq. 5-7).
-* ``fb_encode`` / ``fb_decode`` -- bitmap frontiers through the same codec (sec. 3.3, 5.2).
+* ``fq_encode`` / ``fq_decode`` -- delta + binary packing, blocks of 128 (sec. 5.1, 5.3, Eq. 5-7).
+* ``fb_encode`` / ``fb_decode`` -- bitmap frontiers through the same codec (sec. 3.1, 5.1).
 * ``level_schedule``          -- per-level n_f, m_f, m_u, direction and edges examined of a
   direction-optimising BFS (sec. 3.1; switching rule as read in the design notes).
 * ``fr_encode`` / ``fr_decode`` -- frame of reference on unsorted values (Eq. 5-6).
 * ``pl_encode`` / ``pl_decode`` -- the predecessor list as level sets plus level-relative
-  parent ranks (the predecessor reduction of sec. 6.5, compressed).
+  parent ranks (the predecessor reduction of sec. 4.1.4, compressed).
 * ``level_streams``           -- the per-level encoded frontier queue, frontier bitmap and
   visited bitmap (the data the method compresses around its exchanges, Alg. "Our BFS algorithm
   with SpVM and compression").
@@ -232,7 +232,7 @@ PL_MAGIC = 0x314C5046  # "FPL1"
 def pl_encode(depth, parent):
     """Predecessor-list container "FPL1" of a BFS tree (depth int32[n], -1 unreached; parent
     uint32[n], parent[root] = root).  The thesis reduces its predecessor list uncompressed at the
-    end of a BFS (sec. 6.5, predecessor reduction; its cost in the results chapter); here it is
+    end of a BFS (sec. 4.1.4, the predecessor list bitmap; its cost in sec. 7.2); here it is
     written as the level sets plus level-relative parent ranks:
 
       header u32 {"FPL1", n, L, reached}; u64 off[2L]: stream k is [off[k], off[k+1]) from the

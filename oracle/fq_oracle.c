@@ -13,16 +13,16 @@
  *   orc_validate       BFS-tree checks (the "5 rules" of Graph500 validation, Alg. "A Graph 500
  *                      application"; the rules are not listed in the thesis, our reading)
  *   orc_fq_encode/decode  delta + frame-of-reference binary packing in blocks of 128
- *                      ("Binary packing", "Delta compression" in sec. 5.2; S4-BP128 in sec. 5.3;
+ *                      ("Binary packing", "Delta compression" in sec. 5.1; S4-BP128 in sec. 5.3;
  *                      width formula Eq. 6/7), written bit by bit
  *   orc_px_encode/decode  binary packing with patched exceptions ("Patched coding and
- *                      Exceptions", sec. 5.2, Eq. 8-9; the PFOR family in sec. 5.3): per block
+ *                      Exceptions", sec. 5.1, Eq. 8-9; the PFOR family in sec. 5.3): per block
  *                      the width b that minimises the block's bytes, gaps >= 2^b stored apart
  *   orc_fr_encode/decode  frame of reference without differencing (Eq. 5-6 as printed: per block
  *                      the minimum as base, width = bit length of max - min) for unsorted values
  *   orc_fb_encode/decode  frontier/visited bitmap codec: positions of the minority bit value,
- *                      coded with the queue codec, or the raw words (bitmap frontiers, sec. 3.3
- *                      "Sparse vector with pop counting"; lossless requirement, sec. 5.2)
+ *                      coded with the queue codec, or the raw words (bitmap frontiers, sec. 3.1
+ *                      "Sparse vector with pop counting"; lossless requirement, sec. 5.1)
  *   orc_bu_examined    edges a bottom-up sweep examines at one level (direction optimisation,
  *                      sec. 3.1)
  *
@@ -51,7 +51,7 @@ enum {
 #define ORC_MAGIC_FOR ((uint32_t)'F' | ((uint32_t)'R' << 8) | ((uint32_t)'P' << 16) | ((uint32_t)'1' << 24))
 #define ORC_MAGIC_FOR_RAW ((uint32_t)'F' | ((uint32_t)'R' << 8) | ((uint32_t)'R' << 16) | ((uint32_t)'1' << 24))
 
-#define ORC_BLOCK 128u /* B, the block length of binary packing (sec. 5.2, S4-BP128 in sec. 5.3) */
+#define ORC_BLOCK 128u /* B, the block length of binary packing (sec. 5.1, S4-BP128 in sec. 5.3) */
 
 enum { ORC_FB_RAW = 0, ORC_FB_SET = 1, ORC_FB_CLEAR = 2 };
 
@@ -100,9 +100,9 @@ static uint32_t get_bit(const uint8_t *buf, uint64_t t) { return (uint32_t)((buf
 /* ------------------------------------------------------------------ queue codec "FQ"
  *
  * Input: a strictly increasing sequence v[0..n) of uint32 (a frontier queue is a sorted set,
- * sec. 4.1.3).  Blocks of B = 128 slots.  In block k, slot 0 holds 0 (the block's first value is
+ * sec. 4.1.4).  Blocks of B = 128 slots.  In block k, slot 0 holds 0 (the block's first value is
  * stored whole as base_k, the frame of reference, Eq. 5), slot j >= 1 holds the d-gap
- * v[128k+j] - v[128k+j-1] - 1 (delta coding, sec. 5.2; the "- 1" uses uniqueness), and slots
+ * v[128k+j] - v[128k+j-1] - 1 (delta coding, sec. 5.1; the "- 1" uses uniqueness), and slots
  * past n hold 0.  The block width b_k is the bit length of its largest slot (Eq. 6), so every
  * slot fits in b_k bits.  Slot j occupies bits [j*b_k, (j+1)*b_k) of the block's bit string.
  *
@@ -110,7 +110,7 @@ static uint32_t get_bit(const uint8_t *buf, uint64_t t) { return (uint32_t)((buf
  * u8 b[nb], zeros up to a 16-byte boundary, then the nb bit strings (block k is 4*b_k u32
  * words).  Raw stream: {magic "FQR1", n, 0, n}, u32 v[n], zeros up to 16 bytes.  The packed
  * form is used only when strictly smaller (the encoded data must be smaller than the input,
- * sec. 5.2 "Lossless"; compression threshold, sec. 5.4.2), so ties and n = 0 are raw.
+ * sec. 5.1 "Lossless"; compression threshold, sec. 5.4.3), so ties and n = 0 are raw.
  */
 
 uint64_t orc_fq_raw_size(uint64_t n) { return 16u + pad16(4u * n); }
@@ -281,7 +281,7 @@ int orc_fq_decode(const uint8_t *in, uint64_t in_bytes, uint32_t *out, uint64_t 
 
 /* ------------------------------------------------------------------ patched codec "PX"
  *
- * Binary packing with exceptions (sec. 5.2 "Patched coding and Exceptions": a value that does
+ * Binary packing with exceptions (sec. 5.1 "Patched coding and Exceptions": a value that does
  * not fit in the block's b bits -- a gap >= 2^b, Eq. 8-9 -- is stored apart; PFOR family,
  * sec. 5.3).  Same gaps, blocks and raw fallback as FQ.  Per block k the width b_k is the b in
  * 0..32 that minimises the block's bytes 16*b + 5*e_b, e_b = number of gaps >= 2^b (each

@@ -9,7 +9,7 @@
 
 namespace fq {
 
-constexpr uint32_t kBlock = 128;          // B: ids per packed block (sec. 5.2, S4-BP128 in sec. 5.3)
+constexpr uint32_t kBlock = 128;          // B: ids per packed block (sec. 5.1, S4-BP128 in sec. 5.3)
 constexpr uint32_t kEncThreads = 256;     // CTA size of the block-parallel codec kernels
 constexpr uint32_t kEncWarps = kEncThreads / 32;
 constexpr uint32_t kBlocksPerWarp = 8;    // 128-id blocks one warp handles per tile

@@ -1,10 +1,11 @@
 // pred.cu -- the predecessor list of a finished BFS as one compressed container and back
 // (fq_pred_encode / fq_pred_decode).
 //
-// The thesis reduces its predecessor list once per BFS, uncompressed (sec. 6.5, predecessor
-// reduction), and its results chapter finds that this one exchange moves more bytes than all the
-// compressed frontier exchanges of the run together.  Here the list is written as the level sets
-// F_0 .. F_{L-1} (FQ streams: delta + binary packing in blocks of 128, sec. 5.2-5.3), followed by,
+// The thesis reduces its predecessor list once per BFS, uncompressed (sec. 4.1.4, the
+// predecessor list bitmap), and its results chapter finds that this one exchange moves more
+// bytes than all the compressed frontier exchanges of the run together.  Here the list is
+// written as the level sets
+// F_0 .. F_{L-1} (FQ streams: delta + binary packing in blocks of 128, sec. 5.1, 5.3), followed by,
 // for every level d >= 1, the index of each vertex's parent inside F_{d-1} (FR streams: frame of
 // reference without differencing, Eq. 5-6).  An index needs at most bitlen(|F_{d-1}| - 1) bits,
 // and a level set of dense ids packs to a few bits per id.

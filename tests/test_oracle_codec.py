@@ -1,7 +1,7 @@
 """Pins of the oracle's queue codec (FQ) and bitmap codec (FB) to facts outside the oracle:
 the worked examples in tests/golden (hand-computed from the format, Eq. 6-7 of the thesis),
 the closed-form stream size recomputed with Python integers, round-trip identity (the codec is
-lossless, sec. 5.2), and corrupted-stream rejection."""
+lossless, sec. 5.1), and corrupted-stream rejection."""
 import json
 import os
 import random

@@ -1,6 +1,6 @@
 """Pins of the oracle's frame-of-reference stream FR (Eq. 5-6 on unsorted values) and of the
 predecessor-list container FPL1 (level sets plus level-relative parent ranks -- the predecessor
-reduction of sec. 6.5, compressed): hand-worked streams, brute-force ranks, round trips on BFS
+reduction of sec. 4.1.4, compressed): hand-worked streams, brute-force ranks, round trips on BFS
 trees of small R-MAT graphs, and rejection of malformed containers."""
 import json
 import os
