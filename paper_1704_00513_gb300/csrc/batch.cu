@@ -36,6 +36,7 @@ struct BatchScratch {
     unsigned long long *status;     // [T] look-back words (encode)
     uint32_t *tile_sum;             // [T] decode
     uint32_t *tile_off;             // [T] decode: segment-local payload offset (16-byte units)
+    uint32_t *tile_seg;             // [T] decode: the segment of each global tile (written by the plan)
     uint64_t tiles_cap;
 };
 
@@ -52,6 +53,7 @@ uint64_t batch_layout(uint64_t total_ids, uint64_t S, BatchScratch *b, void *bas
     const uint64_t o_st = o; o = al256(o + 8 * T);
     const uint64_t o_ts = o; o = al256(o + 4 * T);
     const uint64_t o_to = o; o = al256(o + 4 * T);
+    const uint64_t o_sg = o; o = al256(o + 4 * T);
     if (b && base) {
         uint8_t *p = static_cast<uint8_t *>(base);
         b->ctl = reinterpret_cast<Ctl *>(p);
@@ -60,10 +62,12 @@ uint64_t batch_layout(uint64_t total_ids, uint64_t S, BatchScratch *b, void *bas
         b->status = reinterpret_cast<unsigned long long *>(p + o_st);
         b->tile_sum = reinterpret_cast<uint32_t *>(p + o_ts);
         b->tile_off = reinterpret_cast<uint32_t *>(p + o_to);
+        b->tile_seg = reinterpret_cast<uint32_t *>(p + o_sg);
         b->tiles_cap = T;
     }
     return o;
 }
+
 
 __device__ __forceinline__ uint32_t find_segment(const unsigned long long *tile_base, uint32_t S, uint64_t g)
 {
@@ -202,6 +206,8 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_encode_kernel(BEnc a)
     if (T == 0) return;
 
     // tile g -> (segment, its ids, its length, local tile); bulk staging needs a full, aligned tile
+    // (a binary search over the tile bases: measured faster here than the plan's tile map, which
+    // the decode kernels use)
     auto locate = [&](uint64_t g, uint32_t &s, const uint32_t *&ids, uint64_t &n, uint64_t &t) {
         s = find_segment(a.b.tile_base, a.S, g);
         ids = a.ids + a.seg_off[s];
@@ -400,7 +406,9 @@ __global__ void __launch_bounds__(kScanThreads) bat_dplan_kernel(BDec a)
     for (uint64_t s = s0; s < s1; s++) {
         a.b.tile_base[s] = run;
         const SegInfo si = a.b.seg[s];
-        run += si.mode == kModePacked ? dcdiv(si.nb, kTileBlocks) : si.mode == kModeRaw ? dcdiv(si.n, kBTileIds) : 0;
+        const uint64_t nt = si.mode == kModePacked ? dcdiv(si.nb, kTileBlocks) : si.mode == kModeRaw ? dcdiv(si.n, kBTileIds) : 0;
+        for (uint64_t g = run; g < run + nt && g < a.b.tiles_cap; g++) a.b.tile_seg[g] = (uint32_t)s;
+        run += nt;
         a.n_out[s] = si.mode == kModeNone ? 0 : si.n;
     }
     if (threadIdx.x == 0) {
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(kEncThreads) bat_dtiles_kernel(BDec a)
     __shared__ uint32_t ws[kEncWarps];
     const uint64_t T = min((uint64_t)a.b.tile_base[a.S], a.b.tiles_cap);
     for (uint64_t g = blockIdx.x; g < T; g += gridDim.x) {
-        const uint32_t s = find_segment(a.b.tile_base, a.S, g);
+        const uint32_t s = a.b.tile_seg[g];
         const SegInfo si = a.b.seg[s];
         if (si.mode != kModePacked) continue;  // uniform per CTA
         const uint64_t t = g - a.b.tile_base[s];
@@ -501,7 +509,7 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
         mbar_init_fence();
         const uint64_t g0 = blockIdx.x;
         if (g0 < T) {
-            const uint32_t s = find_segment(a.b.tile_base, a.S, g0);
+            const uint32_t s = a.b.tile_seg[g0];
             const SegInfo si = a.b.seg[s];
             const uint32_t by = tile_bytes(g0, s, si);
             if (by) bulk_load(dbuf, payload_at(g0, s, si), by, &bars[0]);
@@ -513,11 +521,11 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
         const uint64_t g = blockIdx.x + i * gridDim.x;
         if (g >= T) break;
         const uint32_t stage = (uint32_t)(i & 1u);
-        const uint32_t s = find_segment(a.b.tile_base, a.S, g);
+        const uint32_t s = a.b.tile_seg[g];
         const SegInfo si = a.b.seg[s];
         const uint64_t gn = g + gridDim.x;
         if (threadIdx.x == 0 && gn < T) {
-            const uint32_t s2 = find_segment(a.b.tile_base, a.S, gn);
+            const uint32_t s2 = a.b.tile_seg[gn];
             const SegInfo si2 = a.b.seg[s2];
             const uint32_t by = tile_bytes(gn, s2, si2);
             if (by) bulk_load(dbuf + (stage ^ 1u) * kDecStageB, payload_at(gn, s2, si2), by, &bars[stage ^ 1u]);
