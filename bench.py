@@ -736,7 +736,7 @@ def batched_codec(dev, peak_gbs, S=4096, lo=16, hi=1 << 20, mean_gap=16.0, seed=
            "batched_graph_GBps": 2 * alg / t_bg / 1e9, "batched_graph_frac": 2 * alg / t_bg / 1e9 / peak_gbs,
            "plain_calls_GBps": 2 * alg / t_p / 1e9, "plain_graph_GBps": 2 * alg / t_pg / 1e9,
            "batched_over_plain_graph": t_pg / t_bg, "batched_over_plain_calls": t_p / t_bg,
-           "launches_batched": 7, "launches_plain": 7 * S, "roundtrip_ok": ok and ok_plain}
+           "launches_batched": 8, "launches_plain": 7 * S, "roundtrip_ok": ok and ok_plain}
     del b, ids, out_ids, work
     torch.cuda.empty_cache()
     return res

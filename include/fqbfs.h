@@ -126,7 +126,7 @@ fq_status fq_frontier_decode(const uint8_t *d_in, uint64_t in_bytes, uint32_t *d
                              uint64_t *d_n, void *d_work, uint64_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ batched codec
- * S independent frontier segments in a fixed number of launches (3 to encode, 4 to decode,
+ * S independent frontier segments in a fixed number of launches (4 to encode, 4 to decode,
  * whatever S is): the grouping of many small transfers into one that the thesis applies to its
  * exchanges (sec. 6.5, data-transfer grouping), applied to the codec.  Stream s is byte-for-byte
  * what fq_frontier_encode writes for segment s alone.

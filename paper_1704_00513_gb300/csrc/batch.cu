@@ -3,11 +3,13 @@
 //
 // The thesis groups many small transfers into one (custom MPI datatypes, sec. 6.5) and exchanges
 // one compressed frontier per processor pair; here S sorted id segments of any lengths become S
-// independent FQ streams (each exactly what fq_frontier_encode writes for that segment) through
-// one persistent kernel: tiles of 8192 ids of all segments are handed out in ticket order, each
-// tile's payload offset comes from a decoupled look-back over the earlier tiles of its own
-// segment, and the CTA holding a segment's last tile writes that stream's header.  Decoding runs
-// the inverse over all tiles of all streams.  Launch count: encode 3, decode 4, for any S.
+// independent FQ streams (each exactly what fq_frontier_encode writes for that segment).  The ids
+// of all segments are cut into tiles of 8192 (a segment's last tile may be short).  Encode: a plan
+// (segment tiles, empty-segment headers, the tile -> segment map), a widths pass (each tile's sum
+// of block widths), one scan of the tile sums, and a pack pass in which every tile finds its
+// payload offset and its segment's packed/raw decision from the scan and writes its blocks, its
+// table entries, and (first tile) the header -- 4 launches for any S, with no inter-CTA waiting.
+// Decoding runs the inverse over all tiles of all streams (4 launches).
 #include <algorithm>
 
 #include "codec_dev.cuh"
@@ -17,7 +19,6 @@ namespace fq {
 namespace {
 
 constexpr uint32_t kBTileIds = kTileBlocks * kBlock;  // 8192 ids per tile
-constexpr size_t kBatchSmem = 2 * (size_t)kBTileIds * sizeof(uint32_t);
 constexpr uint32_t kDecStageB = kTileBlocks * 32u * 16u + 16u;
 constexpr size_t kBatchDecSmem = 2 * (size_t)kDecStageB;
 
@@ -33,10 +34,10 @@ struct BatchScratch {
     Ctl *ctl;
     unsigned long long *tile_base;  // [S + 1] first global tile of each segment
     SegInfo *seg;                   // [S]
-    unsigned long long *status;     // [T] look-back words (encode)
+    unsigned long long *status;     // [T + 1] encode: exclusive prefix of the tile width sums
     uint32_t *tile_sum;             // [T] decode
     uint32_t *tile_off;             // [T] decode: segment-local payload offset (16-byte units)
-    uint32_t *tile_seg;             // [T] decode: the segment of each global tile (written by the plan)
+    uint32_t *tile_seg;             // [T] the segment of each global tile (written by the plan kernels)
     uint64_t tiles_cap;
 };
 
@@ -50,7 +51,7 @@ uint64_t batch_layout(uint64_t total_ids, uint64_t S, BatchScratch *b, void *bas
     uint64_t o = 256;
     const uint64_t o_tb = o; o = al256(o + 8 * (S + 1));
     const uint64_t o_seg = o; o = al256(o + sizeof(SegInfo) * (S ? S : 1));
-    const uint64_t o_st = o; o = al256(o + 8 * T);
+    const uint64_t o_st = o; o = al256(o + 8 * (T + 1));
     const uint64_t o_ts = o; o = al256(o + 4 * T);
     const uint64_t o_to = o; o = al256(o + 4 * T);
     const uint64_t o_sg = o; o = al256(o + 4 * T);
@@ -69,17 +70,6 @@ uint64_t batch_layout(uint64_t total_ids, uint64_t S, BatchScratch *b, void *bas
 }
 
 
-__device__ __forceinline__ uint32_t find_segment(const unsigned long long *tile_base, uint32_t S, uint64_t g)
-{
-    // largest s with tile_base[s] <= g (segments with no tile have equal bases; the last such wins)
-    uint32_t lo = 0, hi = S;  // answer in [lo, hi)
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) / 2;
-        if (tile_base[mid] <= g) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ void reset_ctl(Ctl *c)
 {
@@ -129,6 +119,8 @@ __global__ void __launch_bounds__(kScanThreads) bat_plan_kernel(BEnc a)
         const uint64_t lo = a.seg_off[s], hi = a.seg_off[s + 1];
         const uint64_t n = hi >= lo ? hi - lo : 0;
         const uint64_t nt = dcdiv(dcdiv(n, kBlock), kTileBlocks);
+        if (hi >= lo && n <= 0xffffffffull)
+            for (uint64_t g = run; g < run + nt && g < a.b.tiles_cap; g++) a.b.tile_seg[g] = (uint32_t)s;
         run += hi >= lo && n <= 0xffffffffull ? nt : 0;
         SegInfo si{};
         si.n = n;
@@ -147,202 +139,206 @@ __global__ void __launch_bounds__(kScanThreads) bat_plan_kernel(BEnc a)
             }
         }
     }
-    if (threadIdx.x == 0) a.b.tile_base[S] = total;
-    __syncthreads();
-    const uint64_t T = min((uint64_t)total, a.b.tiles_cap);
-    for (uint64_t t = threadIdx.x; t < T; t += kScanThreads) a.b.status[t] = 0ull;
-    if (threadIdx.x == 0 && total > a.b.tiles_cap) set_error(a.b.ctl, FQ_EINVAL, kWhereEncPlan, total);
+    if (threadIdx.x == 0) {
+        a.b.tile_base[S] = total;
+        if (total > a.b.tiles_cap) set_error(a.b.ctl, FQ_EINVAL, kWhereEncPlan, total);
+    }
 }
 
-// The stream decision for segment s once all its tiles are published.
-__device__ void bat_finalize(const BEnc &a, uint32_t s, uint64_t n, uint64_t nb, unsigned long long total)
+// Ids i .. i+3 of a segment (zeros past n); a segment may start anywhere, so the 128-bit load is
+// taken only where the address allows it (the same for every lane of a warp).
+__device__ __forceinline__ void load4_any(const uint32_t *ids, uint64_t i, uint64_t n, uint32_t v[4])
 {
-    Ctl *c = a.b.ctl;
-    __threadfence();
-    uint8_t *out = a.out + a.out_off[s];
-    const uint64_t cap = a.out_off[s + 1] - a.out_off[s];
-    SegInfo si = a.b.seg[s];
-    si.total_b = total;
-    const uint64_t packed = 16u + dpad16(5u * nb) + 16u * total;
-    const uint64_t raw = 16u + dpad16(4u * n);
-    const bool is_packed = n > 0 && packed < raw;
-    const uint64_t size = is_packed ? packed : raw;
-    si.mode = is_packed ? kModePacked : kModeRaw;
-    if (size > cap) {
-        set_error(c, FQ_ENOSPC, kWhereEncPlan, s);
-        si.mode = kModeNone;
-        a.out_bytes[s] = size;
-        a.b.seg[s] = si;
-        return;
-    }
-    uint32_t *h = reinterpret_cast<uint32_t *>(out);
-    if (is_packed) {
-        h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
-        for (uint64_t p = 16u + 5u * nb; p < 16u + dpad16(5u * nb); p++) out[p] = 0;
+    if (i + 3 < n && (reinterpret_cast<uintptr_t>(ids + i) & 15u) == 0) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(ids + i);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     } else {
-        h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = (i + j < n) ? ids[i + j] : 0u;
     }
-    a.out_bytes[s] = size;
-    a.b.seg[s] = si;
 }
 
-__global__ void __launch_bounds__(kEncThreads, 3) bat_encode_kernel(BEnc a)
+// The tile's 64 blocks, 8 per warp with all loads in flight: lane's ids and gaps of each; the
+// widths (warp-uniform); the first unsorted position (segment-local) in *bad.
+__device__ __forceinline__ void tile_gaps(const uint32_t *ids, uint64_t n, uint64_t t, uint32_t warp, uint32_t lane,
+                                          bool check, uint32_t v[kBlocksPerWarp][4], uint32_t gp[kBlocksPerWarp][4],
+                                          uint32_t b[kBlocksPerWarp], unsigned long long *bad)
 {
-    extern __shared__ __align__(128) uint32_t sbuf[];  // [2][kBTileIds]
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t s_tile, s_next;
+    const uint64_t nb = dcdiv(n, kBlock);
+    uint32_t prev[kBlocksPerWarp];
+#pragma unroll
+    for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+        const uint64_t k = t * kTileBlocks + warp * kBlocksPerWarp + i;
+        prev[i] = 0u;
+        if (k < nb) {
+            load4_any(ids, k * kBlock + 4u * lane, n, v[i]);
+            if (check && lane == 0 && k > 0) prev[i] = ids[k * kBlock - 1];
+        } else {
+            v[i][0] = v[i][1] = v[i][2] = v[i][3] = 0u;
+        }
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+        const uint64_t k = t * kTileBlocks + warp * kBlocksPerWarp + i;
+        b[i] = 0u;
+        gp[i][0] = gp[i][1] = gp[i][2] = gp[i][3] = 0u;
+        if (k < nb) {  // uniform over the warp
+            unsigned long long dummy = ~0ull;
+            gaps_of(v[i], prev[i], check && k > 0, k, n, lane, gp[i], check ? bad : &dummy);
+            b[i] = bitlen32(__reduce_or_sync(0xffffffffu, gp[i][0] | gp[i][1] | gp[i][2] | gp[i][3]));
+        }
+    }
+}
+
+// Pass 1: each tile's sum of block widths (and the sortedness check).
+__global__ void __launch_bounds__(kEncThreads) bat_widths_kernel(BEnc a)
+{
+    __shared__ uint32_t s_sum[kEncWarps];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = a.b.ctl->code != FQ_OK;  // the plan rejected the segment table
+    __syncthreads();
+    if (s_abort) return;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint64_t T = a.b.tile_base[a.S];
+    for (uint64_t g = blockIdx.x; g < T; g += gridDim.x) {
+        const uint32_t s = a.b.tile_seg[g];
+        const uint32_t *ids = a.ids + a.seg_off[s];
+        const uint64_t n = a.seg_off[s + 1] - a.seg_off[s];
+        const uint64_t t = g - a.b.tile_base[s];
+        uint32_t v[kBlocksPerWarp][4], gp[kBlocksPerWarp][4], b[kBlocksPerWarp];
+        unsigned long long bad = ~0ull;
+        tile_gaps(ids, n, t, warp, lane, true, v, gp, b, &bad);
+        if (bad != ~0ull) set_error(a.b.ctl, FQ_EUNSORTED, kWhereEncWidths, a.seg_off[s] + bad);
+        uint32_t sum = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kBlocksPerWarp; i++) sum += b[i];
+        if (lane == 0) s_sum[warp] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (uint32_t q = 0; q < kEncWarps; q++) tot += s_sum[q];
+            a.b.tile_sum[g] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 2 (one CTA): exclusive prefix of all tile sums, in coalesced rounds of 4,096 tiles.
+__global__ void __launch_bounds__(kScanThreads) bat_escan_kernel(BEnc a)
+{
+    __shared__ unsigned long long sm[33];
+    if (a.b.ctl->code != FQ_OK) return;  // uniform: the widths pass has finished
+    const uint64_t T = a.b.tile_base[a.S];
+    unsigned long long carry = 0;
+    for (uint64_t base = 0; base < T; base += 4u * kScanThreads) {
+        const uint64_t i0 = base + 4u * threadIdx.x;
+        uint32_t x[4];
+#pragma unroll
+        for (uint32_t j = 0; j < 4; j++) x[j] = i0 + j < T ? a.b.tile_sum[i0 + j] : 0u;
+        unsigned long long tot = 0;
+        unsigned long long run = carry + cta_excl_scan64<kScanThreads>((unsigned long long)x[0] + x[1] + x[2] + x[3], sm, &tot);
+#pragma unroll
+        for (uint32_t j = 0; j < 4; j++) {
+            if (i0 + j < T) a.b.status[i0 + j] = run;
+            run += x[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) a.b.status[T] = carry;
+}
+
+// Pass 3: per tile, its segment's decision (packed only when smaller than raw) and payload
+// offset from the scan; the tile's blocks packed (or its ids copied raw), its base and width
+// table entries; the first tile of a segment writes the header and the stream size.
+__global__ void __launch_bounds__(kEncThreads) bat_pack_kernel(BEnc a)
+{
     __shared__ uint32_t sw[kTileBlocks], spre[kTileBlocks];
-    __shared__ unsigned long long s_excl, s_total;
-    __shared__ unsigned long long s_red[kEncWarps];
-    __shared__ uint32_t s_first;
     __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
     __shared__ int s_abort;
     Ctl *c = a.b.ctl;
-    if (threadIdx.x == 0) s_abort = c->code != FQ_OK;  // the plan rejected the segment table
+    if (threadIdx.x == 0) s_abort = c->code != FQ_OK;
     __syncthreads();
     if (s_abort) return;
-    const uint64_t T = a.b.tile_base[a.S];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    if (T == 0) return;
-
-    // tile g -> (segment, its ids, its length, local tile); bulk staging needs a full, aligned tile
-    // (a binary search over the tile bases: measured faster here than the plan's tile map, which
-    // the decode kernels use)
-    auto locate = [&](uint64_t g, uint32_t &s, const uint32_t *&ids, uint64_t &n, uint64_t &t) {
-        s = find_segment(a.b.tile_base, a.S, g);
-        ids = a.ids + a.seg_off[s];
-        n = a.seg_off[s + 1] - a.seg_off[s];
-        t = g - a.b.tile_base[s];
-    };
-    auto bulk_ok = [&](const uint32_t *ids, uint64_t n, uint64_t t) {
-        return ((reinterpret_cast<uintptr_t>(ids + t * kBTileIds) & 15u) == 0) && (t + 1) * kBTileIds <= n;
-    };
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init_fence();
-        s_next = atomicAdd(&c->tile_ticket, 1u);
-        if (s_next < T) {
-            uint32_t s; const uint32_t *ids; uint64_t n, t;
-            locate(s_next, s, ids, n, t);
-            if (bulk_ok(ids, n, t)) bulk_load(sbuf, ids + t * kBTileIds, kBTileIds * 4u, &bars[0]);
-        }
-    }
-    __syncthreads();
-    uint32_t phase0 = 0u, phase1 = 0u;
-    for (uint32_t it = 0;; it++) {
-        if (threadIdx.x == 0) {
-            s_tile = s_next;
-            s_next = (s_next < T) ? atomicAdd(&c->tile_ticket, 1u) : (uint32_t)T;
-        }
-        __syncthreads();
-        const uint64_t g = s_tile, gn = s_next;
-        if (g >= T) break;
-        const uint32_t stage = it & 1u;
-        uint32_t *sb = sbuf + stage * kBTileIds;
-        uint32_t s; const uint32_t *ids; uint64_t n, t;
-        locate(g, s, ids, n, t);
-        if (threadIdx.x == 0 && gn < T) {  // the next ticket's ids into the other stage
-            uint32_t s2; const uint32_t *ids2; uint64_t n2, t2;
-            locate(gn, s2, ids2, n2, t2);
-            if (bulk_ok(ids2, n2, t2))
-                bulk_load(sbuf + (stage ^ 1u) * kBTileIds, ids2 + t2 * kBTileIds, kBTileIds * 4u, &bars[stage ^ 1u]);
-        }
-        if (bulk_ok(ids, n, t)) {
-            if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(c, FQ_ETIMEOUT, kWhereEncWidths, g);
-            if (stage) phase1 ^= 1u;
-            else phase0 ^= 1u;
-        } else {
-            for (uint32_t i = threadIdx.x; i < kBTileIds; i += kEncThreads) {
-                const uint64_t gi = t * kBTileIds + i;
-                sb[i] = gi < n ? ids[gi] : 0u;
-            }
-            __syncthreads();
-        }
-        const uint64_t nb = dcdiv(n, kBlock);
-        const uint64_t ntiles_s = dcdiv(nb, kTileBlocks);
+    const uint64_t T = a.b.tile_base[a.S];
+    const unsigned long long *pre = a.b.status;
+    for (uint64_t g = blockIdx.x; g < T; g += gridDim.x) {
+        const uint32_t s = a.b.tile_seg[g];
+        const uint32_t *ids = a.ids + a.seg_off[s];
+        const uint64_t n = a.seg_off[s + 1] - a.seg_off[s];
+        const uint64_t g0 = a.b.tile_base[s], t = g - g0;
+        const uint64_t nb = dcdiv(n, kBlock), ntiles_s = a.b.tile_base[s + 1] - g0;
+        const unsigned long long excl = pre[g] - pre[g0], total = pre[g0 + ntiles_s] - pre[g0];
         uint8_t *out = a.out + a.out_off[s];
         const uint64_t cap = a.out_off[s + 1] - a.out_off[s];
-        const uint64_t bound = min(cap, 16u + dpad16(4u * n));
-        const uint64_t payload = 16u + dpad16(5u * nb);
-        unsigned long long *status = a.b.status + a.b.tile_base[s];
-
-        // widths and bases
-        unsigned long long bad = ~0ull;
+        const uint64_t packed = 16u + dpad16(5u * nb) + 16u * total;
+        const uint64_t raw = 16u + dpad16(4u * n);
+        const bool is_packed = packed < raw;  // n > 0: the segment has a tile
+        const uint64_t size = is_packed ? packed : raw;
+        if (size > cap) {  // uniform over the CTA
+            if (t == 0 && threadIdx.x == 0) {
+                set_error(c, FQ_ENOSPC, kWhereEncPlan, s);
+                a.out_bytes[s] = size;
+            }
+            continue;
+        }
+        uint32_t *h = reinterpret_cast<uint32_t *>(out);
+        if (t == 0 && threadIdx.x == 0) {
+            if (is_packed) {
+                h[0] = kMagicPacked; h[1] = (uint32_t)n; h[2] = (uint32_t)nb; h[3] = (uint32_t)(4u * total);
+            } else {
+                h[0] = kMagicRaw; h[1] = (uint32_t)n; h[2] = 0u; h[3] = (uint32_t)n;
+            }
+            a.out_bytes[s] = size;
+        }
+        if (!is_packed) {  // raw body: this tile's ids, and the zero words to 16 bytes after the last
+            for (uint32_t i = threadIdx.x; i < kBTileIds; i += kEncThreads) {
+                const uint64_t gi = t * kBTileIds + i;
+                if (gi < n) h[4u + gi] = ids[gi];
+            }
+            if (t + 1 == ntiles_s) {
+                const uint32_t padw = (uint32_t)((dpad16(4u * n) - 4u * n) / 4u);
+                if (threadIdx.x < padw) h[4u + n + threadIdx.x] = 0u;
+            }
+            continue;
+        }
+        if (t == 0) {  // zero bytes after the width table, to 16 bytes
+            const uint64_t p = 16u + 5u * nb + threadIdx.x;
+            if (p < 16u + dpad16(5u * nb)) out[p] = 0u;
+        }
+        uint32_t v[kBlocksPerWarp][4], gp[kBlocksPerWarp][4], b[kBlocksPerWarp];
+        tile_gaps(ids, n, t, warp, lane, false, v, gp, b, nullptr);
+#pragma unroll
         for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
             const uint32_t lb = warp * kBlocksPerWarp + i;
             const uint64_t k = t * kTileBlocks + lb;
-            uint32_t b = 0;
-            if (k < nb) {
-                const uint4 q = *reinterpret_cast<const uint4 *>(sb + lb * kBlock + 4u * lane);
-                const uint32_t v[4] = {q.x, q.y, q.z, q.w};
-                uint32_t prevb = 0;
-                if (lane == 0 && k > 0) prevb = lb > 0 ? sb[lb * kBlock - 1] : ids[k * kBlock - 1];
-                uint32_t gg[4];
-                gaps_of(v, prevb, k > 0, k, n, lane, gg, &bad);
-                b = bitlen32(__reduce_or_sync(0xffffffffu, gg[0] | gg[1] | gg[2] | gg[3]));
-                if (lane == 0 && 16u + 4u * k + 4 <= bound) *reinterpret_cast<uint32_t *>(out + 16u + 4u * k) = v[0];
+            if (lane == 0) {
+                sw[lb] = b[i];
+                if (k < nb) {
+                    h[4u + k] = v[i][0];
+                    out[16u + 4u * nb + k] = (uint8_t)b[i];
+                }
             }
-            if (lane == 0) sw[lb] = b;
         }
-        if (bad != ~0ull) set_error(c, FQ_EUNSORTED, kWhereEncWidths, a.seg_off[s] + bad);
         __syncthreads();
         if (warp == 0) {
             const uint32_t x0 = sw[2 * lane], x1 = sw[2 * lane + 1];
             const uint32_t incl = warp_incl_scan(x0 + x1);
             spre[2 * lane] = incl - x0 - x1;
             spre[2 * lane + 1] = incl - x1;
-            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane == 0) {
-                publish(status, t, t == 0 ? kFlagPrefix : kFlagAgg, total);
-                s_total = total;
-            }
         }
         __syncthreads();
-        unsigned long long excl = 0;
-        if (t > 0) excl = lookback(status, t, c, s_red, &s_first);
-        if (threadIdx.x == 0) {
-            if (t > 0) publish(status, t, kFlagPrefix, excl + s_total);
-            s_excl = excl;
-        }
-        __syncthreads();
-        excl = s_excl;
-        if (threadIdx.x < kTileBlocks) {
-            const uint64_t k = t * kTileBlocks + threadIdx.x;
-            const uint64_t pw = 16u + 4u * nb + k;
-            if (k < nb && pw + 1 <= bound) out[pw] = (uint8_t)sw[threadIdx.x];
-        }
-        // pack from the staged ids
+        const uint64_t payload = 16u + dpad16(5u * nb);
+#pragma unroll
         for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
             const uint32_t lb = warp * kBlocksPerWarp + i;
             const uint64_t k = t * kTileBlocks + lb;
-            const uint32_t b = sw[lb];
-            if (k >= nb || b == 0) continue;
-            const uint4 q = *reinterpret_cast<const uint4 *>(sb + lb * kBlock + 4u * lane);
-            const uint32_t v[4] = {q.x, q.y, q.z, q.w};
-            uint32_t gg[4];
-            unsigned long long dummy = ~0ull;
-            gaps_of(v, 0u, false, k, n, lane, gg, &dummy);
+            if (k >= nb || b[i] == 0) continue;  // uniform over the warp
             uint32_t w4[4];
-            pack_block_words(gg, b, pk[warp], lane, w4);
-            const uint64_t rel = payload + 16u * (excl + spre[lb]);
-            store_block_words(out + rel, w4, b, lane, rel, bound);
+            pack_block_words(gp[i], b[i], pk[warp], lane, w4);
+            store_block_words(out + payload + 16u * (excl + spre[lb]), w4, b[i], lane, 0ull, ~0ull);
         }
-        if (t == ntiles_s - 1 && threadIdx.x == 0) bat_finalize(a, s, n, nb, excl + s_total);
         __syncthreads();
-    }
-}
-
-// Raw bodies of the segments whose stream is raw.
-__global__ void bat_fixup_kernel(BEnc a)
-{
-    for (uint64_t s = blockIdx.x; s < a.S; s += gridDim.x) {
-        const SegInfo si = a.b.seg[s];
-        if (si.mode != kModeRaw) continue;
-        const uint32_t *ids = a.ids + a.seg_off[s];
-        uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + a.out_off[s] + 16);
-        const uint64_t padded = dcdiv(si.n, 4) * 4;
-        for (uint64_t i = threadIdx.x; i < padded; i += blockDim.x) dst[i] = i < si.n ? ids[i] : 0u;
     }
 }
 
@@ -625,12 +621,11 @@ fq_status fq_frontier_encode_batch(const uint32_t *d_ids, const uint64_t *d_seg_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     BEnc a{d_ids, d_seg_off, S, d_out, d_out_off, d_out_bytes, {}};
     batch_layout(total_ids, S, &a.b, d_work);
-    static bool done[64] = {false};
-    if (allow_smem_b(bat_encode_kernel, kBatchSmem, done) != cudaSuccess) return FQ_ECUDA;
     bat_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
-    const uint32_t grid = tuned_grid(FQ_TUNE_BAT_ENCODE, total_ids, (uint64_t)3 * num_sms(), a.b.tiles_cap);
-    bat_encode_kernel<<<grid, kEncThreads, kBatchSmem, st>>>(a);
-    bat_fixup_kernel<<<(uint32_t)std::min<uint64_t>(S, (uint64_t)8 * num_sms()), 256, 0, st>>>(a);
+    const uint32_t grid = tuned_grid(FQ_TUNE_BAT_ENCODE, total_ids, (uint64_t)4 * num_sms(), a.b.tiles_cap);
+    bat_widths_kernel<<<grid, kEncThreads, 0, st>>>(a);
+    bat_escan_kernel<<<1, kScanThreads, 0, st>>>(a);
+    bat_pack_kernel<<<grid, kEncThreads, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? FQ_OK : FQ_ECUDA;
 }
 
