@@ -94,7 +94,7 @@ struct BEnc {
 
 // ---- encode ----
 
-// One CTA: segment sizes, tiles per segment and their prefix, cleared look-back words, headers
+// One CTA: segment sizes, tiles per segment and their prefix, the tile -> segment map, headers
 // of empty segments.
 __global__ void __launch_bounds__(kScanThreads) bat_plan_kernel(BEnc a)
 {

@@ -1,6 +1,6 @@
 // codec_dev.cuh -- device building blocks shared by the single-stream codec (codec.cu) and the
-// batched codec (batch.cu): byte helpers, the decoupled look-back, TMA bulk staging, gap
-// extraction and block packing/unpacking.
+// batched codec (batch.cu): byte helpers, TMA bulk staging, gap extraction and block
+// packing/unpacking.
 #pragma once
 
 #include "fq_common.cuh"
@@ -13,68 +13,7 @@ __device__ __forceinline__ uint64_t dcdiv(uint64_t a, uint64_t b) { return (a + 
 __device__ __forceinline__ uint32_t ld_u32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
 
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
-{
-    return *reinterpret_cast<const volatile unsigned long long *>(p);
-}
-
-__device__ __forceinline__ void publish(unsigned long long *status, uint64_t t, unsigned long long flag,
-                                        unsigned long long value)
-{
-    __threadfence();
-    atomicExch(status + t, flag | (value & kValueMask));
-}
-
-// CTA-wide: sum of the width sums of tiles 0 .. t-1 (t >= 1), by decoupled look-back.  Every
-// thread polls one predecessor, so one round covers kEncThreads tiles: the running prefix moves
-// that many tiles per L2 round trip.  All threads of the CTA must call it.
-static __device__ unsigned long long lookback(unsigned long long *status, uint64_t t, Ctl *c, unsigned long long *red,
-                                       uint32_t *s_first)
-{
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    unsigned long long excl = 0;
-    long long base = (long long)t - 1;
-    for (;;) {
-        const long long idx = base - (long long)tid;
-        unsigned long long w = kFlagPrefix;  // before tile 0: an empty prefix
-        if (idx >= 0) {
-            uint32_t spins = 0;
-            w = ld_volatile_u64(status + idx);
-            while ((w >> 62) == 0ull) {
-                if (++spins > kSpinLimit) {
-                    set_error(c, FQ_ETIMEOUT, kWhereEncWidths, (unsigned long long)idx);
-                    w = kFlagPrefix;
-                    break;
-                }
-                __nanosleep(32);
-                w = ld_volatile_u64(status + idx);
-            }
-        }
-        __threadfence();
-        if (tid == 0) *s_first = kEncThreads;
-        __syncthreads();
-        if ((w >> 62) == 2ull) atomicMin(s_first, tid);  // nearest predecessor holding a full prefix
-        __syncthreads();
-        const uint32_t first = *s_first;
-        unsigned long long val = (tid <= first) ? (w & kValueMask) : 0ull;
-        val = warp_sum64(val);
-        if (lane == 0) red[warp] = val;
-        __syncthreads();
-        unsigned long long sum = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < kEncWarps; i++) sum += red[i];
-        __syncthreads();
-        excl += sum;
-        if (first < kEncThreads) return excl;
-        base -= kEncThreads;
-    }
-}
-
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls before a bounded wait gives up
 
 // ---- TMA staging helpers (1-D bulk copies into shared memory, completion on an mbarrier) ----
 

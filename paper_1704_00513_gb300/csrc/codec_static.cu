@@ -56,7 +56,7 @@ extern "C" fq_status fq_frontier_encode_static(const uint32_t *d_ids, uint64_t n
     if (static_scratch_address(&scratch) != cudaSuccess) return FQ_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     fq::Scratch s = fq::carve(scratch, n, 0);
-    // the status record and the look-back words must start cleared; the rest is rewritten by each call
+    // the status record must start cleared; the rest is rewritten by each call
     cudaError_t e = fq::reset_status(s, n, st);
     if (e == cudaSuccess) e = fq::encode_fq(d_ids, n, nullptr, n, d_out, cap, d_out_bytes, s, st);
     return e == cudaSuccess ? FQ_OK : FQ_ECUDA;

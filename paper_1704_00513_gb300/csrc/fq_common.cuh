@@ -106,7 +106,7 @@ cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
                       uint64_t cap, uint64_t *n_out, const Scratch &s, cudaStream_t st);
 cudaError_t decode_fb(const uint8_t *in, uint64_t in_bytes_host, const uint64_t *in_bytes_dev, uint64_t *words,
                       uint64_t nbits, const Scratch &s, cudaStream_t st);
-// Reset the status record to FQ_OK and clear the look-back words of up to max_ids ids.
+// Reset the status record to FQ_OK (max_ids: the largest call the scratch serves).
 cudaError_t reset_status(const Scratch &s, uint64_t max_ids, cudaStream_t st);
 
 // Optional mirror of an FQ encode: the same ids written a second time as an FB stream in SET
@@ -144,8 +144,7 @@ __device__ __forceinline__ void set_error(Ctl *c, int32_t code, uint32_t where, 
     }
 }
 
-// Clear a Scratch's control block (status OK, no mode) and its first ntiles look-back words;
-// called by threads tid = 0 .. nthreads-1 of one kernel.
+// Clear a Scratch's control block (status OK, no mode); called by one thread.
 __device__ __forceinline__ void reset_scratch_device(const Scratch &s)
 {
     Ctl *c = s.ctl;
