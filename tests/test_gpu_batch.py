@@ -100,3 +100,34 @@ def test_batch_unsorted_segment_reports_global_index():
     with pytest.raises(fqbfs.FqError) as e:
         b.encode(ids_d)
     assert e.value.status == fqbfs.FQ_EUNSORTED and e.value.detail == 1400
+
+
+def test_batch_encode_reports_enospc_per_segment():
+    """A segment whose output room is one 16-byte unit short gets FQ_ENOSPC (detail = segment) and
+    its needed size in out_bytes; the other segments are still written exactly."""
+    lengths = [3000, 20000, 77, 0, 9000]
+    segs, off, ids = make_batch(lengths, seed=5)
+    seg_off, ids_d = to_dev(off, ids)
+    ref = [oracle.fq_encode(s)[1] for s in segs]
+    caps = np.array([r.size for r in ref], np.int64)
+    caps[1] -= 16
+    out_off = np.zeros(len(segs) + 1, np.int64)
+    out_off[1:] = np.cumsum(caps)
+    out = torch.zeros(int(out_off[-1]), dtype=torch.uint8, device="cuda")
+    out_off_d = torch.from_numpy(out_off).cuda()
+    out_bytes = torch.zeros(len(segs), dtype=torch.int64, device="cuda")
+    work = torch.empty(fqbfs.fq_batch_workspace_bytes(ids.size, len(segs)), dtype=torch.uint8, device="cuda")
+    L = fqbfs.lib()
+    st = L.fq_frontier_encode_batch(ids_d.data_ptr(), seg_off.data_ptr(), len(segs), ids.size, out.data_ptr(),
+                                    out_off_d.data_ptr(), out_bytes.data_ptr(), work.data_ptr(), work.numel(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == fqbfs.FQ_OK
+    with pytest.raises(fqbfs.FqError) as e:
+        fqbfs._device_status(work, None, "fq_frontier_encode_batch")
+    assert e.value.status == fqbfs.FQ_ENOSPC and e.value.detail == 1
+    sizes = out_bytes.cpu().numpy()
+    assert sizes[1] == ref[1].size
+    ob = out.cpu().numpy()
+    for s in (0, 2, 3, 4):
+        assert sizes[s] == ref[s].size
+        assert np.array_equal(ob[out_off[s]: out_off[s] + sizes[s]], ref[s]), s
