@@ -79,7 +79,6 @@ __device__ __forceinline__ void reset_ctl(Ctl *c)
     c->mode = c->mode2 = kModeNone;
     c->fb_mode = kFbRaw;
     c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = 0;
-    c->tile_ticket = 0;
 }
 
 struct BEnc {

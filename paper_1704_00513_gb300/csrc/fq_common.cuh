@@ -57,7 +57,7 @@ struct Ctl {
     unsigned long long total_b;
     unsigned long long out_bytes;
     unsigned long long fq_offset;  // byte offset of the FQ stream inside the container
-    uint32_t tile_ticket;          // single-pass encode: next tile to hand out
+    uint32_t reserved0;
     uint32_t mode2;                // mode of the mirrored FB stream (kMode*), kModeNone if absent
     unsigned long long out2_bytes;
     unsigned long long total_e;    // patched codec: exceptions over all blocks
@@ -155,7 +155,6 @@ __device__ __forceinline__ void reset_scratch_device(const Scratch &s)
     c->mode2 = kModeNone;
     c->fb_mode = kFbRaw;
     c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = c->total_e = 0;
-    c->tile_ticket = 0;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
