@@ -4,8 +4,10 @@ One step = one BFS from one root over the resident scale-24 R-MAT graph (16,777,
 edgefactor 16, initiator 0.57/0.19/0.19/0.05), with every level's frontier encoded as a sorted
 queue stream (Q_d) and a bitmap stream (B_d), the visited bitmap as V_d, the consumed form
 decoded and expanded on the device.  value = GTEPS = undirected edges inside the reached
-components / timed seconds (whole job).  The CSR (2.2 GB) is larger than L2, so no flush is
-needed between steps.
+components / timed seconds (whole job).  The roots are independent searches: the timed pass keeps
+--concurrency of them in flight (default 4, each on its own handle, stream and host thread over
+the one resident CSR); the rate of one search at a time is measured on the same roots and
+reported beside it.  The CSR (2.2 GB) is larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fqbfs|reference] [--scale S]
 
@@ -25,6 +27,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -57,6 +60,9 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-pred", action="store_true", help="skip the predecessor-list container measurement")
+    p.add_argument("--concurrency", type=int, default=4,
+                   help="searches in flight in the timed pass: each on its own handle, stream and host thread "
+                        "(independent roots; 1 = one search at a time)")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in launch grids (no autotuning)")
     p.add_argument("--serve-seconds", type=float, default=4.0)
     p.add_argument("--codec-only", action="store_true",
@@ -322,42 +328,80 @@ def run_fqbfs(args, world, rank, local):
     kms = {k: 0.0 for k in fqbfs.KCLASS}
     kbytes = {k: 0 for k in fqbfs.KCLASS}
     klaunch = {k: 0 for k in fqbfs.KCLASS}
-    edges = 0
-    examined = 0
-    qraw = qenc = braw = benc = venc = 0
     levels = []
-    barrier(world)
+    conc = max(1, args.concurrency)
+    # the timed pass runs `conc` searches at once: independent roots on their own handles (sharing the
+    # resident CSR), streams and host threads; the other handles are built and warmed here, untimed
+    handles = [g] + [fqbfs.Graph(off, cols) for _ in range(conc - 1)]
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(conc - 1)]
+    outs = [(depth, parent)] + [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev))
+                                for _ in range(conc - 1)]
+    for k in range(1, conc):
+        with torch.cuda.stream(streams[k]):
+            for r in warm_roots:
+                handles[k].bfs(r, depth=outs[k][0], parent=outs[k][1], flags=flags, max_levels=64, stream=streams[k])
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        start = torch.cuda.Event(enable_timing=True)
-        stop = torch.cuda.Event(enable_timing=True)
-        per_root = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in timed_roots]
-        root_edges = []
-        start.record(stream)
-        for (e0, e1), r in zip(per_root, timed_roots):
-            e0.record(stream)
-            res = g.bfs(r, depth=depth, parent=parent, flags=flags, max_levels=64)
-            e1.record(stream)
-            s = res.stats
-            root_edges.append(s["reached_edges"])
-            examined += s["edges_examined"]
-            edges += s["reached_edges"]
-            qraw += s["raw_queue_bytes"]; qenc += s["enc_queue_bytes"]
-            braw += s["raw_bitmap_bytes"]; benc += s["enc_bitmap_bytes"]; venc += s["enc_visited_bytes"]
-            levels.append(s["levels"])
-            for k in fqbfs.KCLASS:
-                klaunch[k] += s["kernel_launches"][k]
-        stop.record(stream)
+
+    def one_pass(nconc):
+        """Time the rank's roots with nconc searches in flight; returns (ms, per-root records)."""
+        recs = [[] for _ in range(nconc)]
+
+        def work(k):
+            st = streams[k]
+            with torch.cuda.stream(st):
+                for r in timed_roots[k::nconc]:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    res = handles[k].bfs(r, depth=outs[k][0], parent=outs[k][1], flags=flags, max_levels=64, stream=st)
+                    e1.record(st)
+                    recs[k].append((e0, e1, res.stats))
+
+        barrier(world)
         torch.cuda.synchronize()
-    barrier(world)
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        stream.synchronize()
+        threads = [threading.Thread(target=work, args=(k,)) for k in range(1, nconc)]
+        for t in threads:
+            t.start()
+        work(0)
+        for t in threads:
+            t.join()
+        stops = []
+        for k in range(nconc):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(streams[k])
+            stops.append(e)
+        torch.cuda.synchronize()
+        barrier(world)
+        return max(start.elapsed_time(e) for e in stops), [x for rk in recs for x in rk]
+
+    with ClockSampler(local) as clk:
+        ms, recs = one_pass(conc)
     clocks = clk.summary()
-    ms = start.elapsed_time(stop)
+    edges = examined = 0
+    qraw = qenc = braw = benc = venc = 0
+    for e0, e1, st_ in recs:
+        examined += st_["edges_examined"]
+        edges += st_["reached_edges"]
+        qraw += st_["raw_queue_bytes"]; qenc += st_["enc_queue_bytes"]
+        braw += st_["raw_bitmap_bytes"]; benc += st_["enc_bitmap_bytes"]; venc += st_["enc_visited_bytes"]
+        levels.append(st_["levels"])
+        for k in fqbfs.KCLASS:
+            klaunch[k] += st_["kernel_launches"][k]
     t_max = max_over_ranks(ms, world)
     edges_all = sum_over_ranks(float(edges), world)
     value = edges_all / (t_max / 1e3) / 1e9
-    # Graph500-style harmonic mean of the per-root rates (this rank's roots)
-    root_ms = [a.elapsed_time(b) for a, b in per_root]
-    hmean = len(root_ms) / sum((t / 1e3) / max(1, e) * 1e9 for t, e in zip(root_ms, root_edges))
+    # the same roots one search at a time (the rate a single search sees), and the Graph500-style
+    # harmonic mean of the per-root rates, each root timed alone
+    if conc > 1:
+        ms1, recs1 = one_pass(1)
+        seq_value = edges_all / (max_over_ranks(ms1, world) / 1e3) / 1e9
+    else:
+        ms1, recs1, seq_value = ms, recs, value
+    hmean = len(recs1) / sum((e0.elapsed_time(e1) / 1e3) / max(1, st_["reached_edges"]) * 1e9 for e0, e1, st_ in recs1)
+    for k in range(1, conc):
+        handles[k].close()
 
     # per-class kernel time of the same searches (host-driven loop, events around each class)
     prof_klaunch = {k: 0 for k in fqbfs.KCLASS}
@@ -428,7 +472,9 @@ def run_fqbfs(args, world, rank, local):
                            "l2": "no flush: the 2.2 GB CSR exceeds L2", "levels_mean": statistics.mean(levels),
                            "level_loop": ("device (one CUDA graph per search)" if args.level_loop == "device"
                                           else "host (one counter read per level)"),
-                           "gteps_hmean": hmean, "edges_examined": examined,
+                           "concurrent_searches": conc, "gteps_one_search_at_a_time": seq_value,
+                           "ms_per_root_one_at_a_time": ms1 / args.steps,
+                           "gteps_hmean_one_at_a_time": hmean, "edges_examined": examined,
                            "host_loop_ms_per_step": host_loop_ms / args.steps,
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "codec": codec, "predecessor_list": pred, "batched": batched,
