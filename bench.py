@@ -346,15 +346,21 @@ def run_fqbfs(args, world, rank, local):
         """Time the rank's roots with nconc searches in flight; returns (ms, per-root records)."""
         recs = [[] for _ in range(nconc)]
 
+        errors = []
+
         def work(k):
-            st = streams[k]
-            with torch.cuda.stream(st):
-                for r in timed_roots[k::nconc]:
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(st)
-                    res = handles[k].bfs(r, depth=outs[k][0], parent=outs[k][1], flags=flags, max_levels=64, stream=st)
-                    e1.record(st)
-                    recs[k].append((e0, e1, res.stats))
+            try:
+                st = streams[k]
+                with torch.cuda.stream(st):
+                    for r in timed_roots[k::nconc]:
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(st)
+                        res = handles[k].bfs(r, depth=outs[k][0], parent=outs[k][1], flags=flags, max_levels=64,
+                                             stream=st)
+                        e1.record(st)
+                        recs[k].append((e0, e1, res.stats))
+            except Exception as e:  # re-raised in the main thread: no root may go uncounted
+                errors.append(e)
 
         barrier(world)
         torch.cuda.synchronize()
@@ -367,6 +373,8 @@ def run_fqbfs(args, world, rank, local):
         work(0)
         for t in threads:
             t.join()
+        if errors:
+            raise errors[0]
         stops = []
         for k in range(nconc):
             e = torch.cuda.Event(enable_timing=True)
@@ -451,9 +459,11 @@ def run_fqbfs(args, world, rank, local):
     served = None
     if not args.no_serving and rank == 0:
         served = serving(dev, (off, cols, roots), seconds=args.serve_seconds)
-    e2e = None
+    e2e = e2e_pred = None
     if not args.no_e2e:
         e2e = run_e2e(args, off, cols, timed_roots, world)
+        if not args.no_pred:
+            e2e_pred = run_e2e(args, off, cols, timed_roots, world, container=True)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         off_h = off.cpu().numpy()
@@ -479,7 +489,7 @@ def run_fqbfs(args, world, rank, local):
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "codec": codec, "predecessor_list": pred, "batched": batched,
                 "serving": served,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "cpu_baseline": cpu, "e2e": e2e, "e2e_tree_container": e2e_pred,
                 "autotune": [{k: e[k] for k in ("site", "class", "ctas_per_sm", "ms", "default_ms")} for e in tuned],
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
                 "clocks": clocks}
@@ -888,60 +898,102 @@ def serving(dev, graph24, seconds=4.0, rate=2000.0, budget=100 << 30, seed=SEED)
     return res
 
 
-def run_e2e(args, off, cols, roots, world):
+def run_e2e(args, off, cols, roots, world, container: bool = False):
     """Same metric through the C ABI with host buffers: upload the CSR from pinned memory, build
-    the handle, run the roots and copy each root's depth and parent arrays to pinned host memory,
-    all inside the timed region.  The copy-out of root i overlaps the search of root i+1: after
-    each search its outputs are staged on the device (double-buffered) and a second stream copies
-    the stage to the host while the next search runs; the clock stops when the last copy lands."""
+    the handles, run the roots and copy each root's result to pinned host memory, all inside the
+    timed region.  As in the timed pass, --concurrency searches are in flight, each on its own
+    handle, stream and host thread; a thread copies each of its roots' results out on its stream
+    right after the search, so one thread's copy-out overlaps the others' searches.  The result is
+    the depth and parent arrays (8 B per vertex), or with `container` the BFS tree encoded on the
+    device as the predecessor-list container (fq_pred_encode), whose size is read first and whose
+    bytes alone cross to the host."""
     from paper_1704_00513_gb300 import fqbfs
     n = off.numel() - 1
+    conc = max(1, args.concurrency)
     off_h = off.cpu().pin_memory()
     cols_h = cols.cpu().pin_memory()
-    host = [(torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory())
-            for _ in range(2)]
+    L = 64
+    room = fqbfs.fq_pred_bound(n, L) if container else 0
+    host = [(torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory(),
+             torch.empty(max(room, 1), dtype=torch.uint8).pin_memory()) for _ in range(conc)]
     dev = off.device
-    stream = torch.cuda.current_stream()
-    copier = torch.cuda.Stream(device=dev)
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream(device=dev) for _ in range(conc - 1)]
+    edges = [0] * conc
+    d2h = [0] * conc
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     off_d = off_h.to(dev, non_blocking=True)
     cols_d = cols_h.to(dev, non_blocking=True)
-    g = fqbfs.Graph(off_d, cols_d)
-    depth_d = torch.empty(n, dtype=torch.int32, device=dev)
-    parent_d = torch.empty(n, dtype=torch.int32, device=dev)
-    stage = [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev))
-             for _ in range(2)]
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    edges = 0
-    for i, r in enumerate(roots):
-        res = g.bfs(r, depth=depth_d, parent=parent_d, flags=fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP,
-                    max_levels=64)
-        edges += res.stats["reached_edges"]
-        b = i & 1
-        if i >= 2:
-            stream.wait_event(copied[b])  # the stage's previous copy-out has landed
-        stage[b][0].copy_(depth_d, non_blocking=True)
-        stage[b][1].copy_(parent_d, non_blocking=True)
-        copier.wait_stream(stream)
-        with torch.cuda.stream(copier):
-            host[b][0].copy_(stage[b][0], non_blocking=True)
-            host[b][1].copy_(stage[b][1], non_blocking=True)
-            copied[b].record(copier)
-    copier.synchronize()
-    stream.synchronize()
+    torch.cuda.current_stream().synchronize()
+
+    def work(k):
+        st = streams[k]
+        with torch.cuda.stream(st):
+            g = fqbfs.Graph(off_d, cols_d)
+            depth_d = torch.empty(n, dtype=torch.int32, device=dev)
+            parent_d = torch.empty(n, dtype=torch.int32, device=dev)
+            if container:
+                buf = torch.empty(room, dtype=torch.uint8, device=dev)
+                pw = fqbfs.pred_workspace(n, L, dev)
+                nb = torch.zeros(1, dtype=torch.int64, device=dev)
+            size = 0
+            for r in roots[k::conc]:
+                res = g.bfs(r, depth=depth_d, parent=parent_d,
+                            flags=fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP, max_levels=64, stream=st)
+                edges[k] += res.stats["reached_edges"]
+                if container:
+                    fqbfs.fq_pred_encode(depth_d, parent_d, res.stats["levels"], out=buf, work=pw, stream=st,
+                                         sync=False, nbytes=nb)
+                    size = int(nb.item())
+                    host[k][2][:size].copy_(buf[:size], non_blocking=True)
+                    d2h[k] += size + 8
+                else:
+                    host[k][0].copy_(depth_d, non_blocking=True)
+                    host[k][1].copy_(parent_d, non_blocking=True)
+                    d2h[k] += 8 * n
+            st.synchronize()
+            if not roots[k::conc]:
+                ok = True
+            elif container:
+                dd, _ = fqbfs.fq_pred_decode(host[k][2][:size].to(dev), n, max_levels=L, stream=st)
+                ok = bool(torch.equal(dd, depth_d))
+            else:
+                ok = bool(torch.equal(host[k][0].to(dev), depth_d))
+            g.close()
+            return ok
+
+    oks = [True] * conc
+    errors = []
+
+    def run(k):
+        try:
+            oks[k] = work(k)
+        except Exception as e:  # re-raised in the main thread: no root may go uncounted
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(k,)) for k in range(1, conc)]
+    for t in threads:
+        t.start()
+    run(0)
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    g.close()
     dt = max_over_ranks(dt, world)
-    edges = sum_over_ranks(float(edges), world)
+    total_edges = sum_over_ranks(float(sum(edges)), world)
     k = len(roots)
-    ok = bool(torch.equal(host[(k - 1) & 1][0].to(dev), depth_d)) if k else True
-    return {"value": edges / dt / 1e9, "unit": "GTEPS",
+    return {"value": total_edges / dt / 1e9, "unit": "GTEPS",
             "h2d_bytes_per_step": int((off.numel() * 8 + cols.numel() * 4) / k + 4),
-            "d2h_bytes_per_step": int(8 * n + 512),
-            "copy_out": "each root's depth and parent (8 B per vertex) to pinned host memory, overlapped with the next root's search",
-            "last_root_copy_ok": ok}
+            "d2h_bytes_per_step": int(sum(d2h) / k + 512),
+            "concurrent_searches": conc,
+            "copy_out": ("each root's BFS tree as the predecessor-list container (encoded on the device), its size "
+                         "then its bytes to pinned host memory" if container else
+                         "each root's depth and parent (8 B per vertex) to pinned host memory, on the searching "
+                         "thread's stream right after its search"),
+            "last_copy_ok": all(oks)}
 
 
 def main():

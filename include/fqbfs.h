@@ -260,7 +260,11 @@ fq_status fq_graph_destroy(fq_graph *g);
                                       so no level waits on the host.  Same results, records and
                                       streams as the host-driven loop; FQ_BFS_TIMING is ignored
                                       (kernel_ms stay 0).  Needs a driver with conditional graph
-                                      nodes (CUDA 12.4 or later).                                */
+                                      nodes (CUDA 12.4 or later).  The build captures streams:
+                                      the library keeps handle creation and destruction in other
+                                      threads from overlapping it; other code must not synchronise
+                                      the whole device or free device memory meanwhile (build a
+                                      handle's graph before starting concurrent work).           */
 
 typedef struct fq_bfs_opts {
     uint32_t alpha; /* top-down -> bottom-up when m_f * alpha > m_u   (0 selects 14) */

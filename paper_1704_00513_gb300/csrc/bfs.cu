@@ -19,6 +19,7 @@
 // The host reads one 256-byte counter record per level (termination test and direction).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "fq_common.cuh"
@@ -855,6 +856,11 @@ cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Handle creation and destruction synchronise the whole device and free memory, which would
+// invalidate a stream capture running in another thread; the device-loop build (its captures and
+// instantiation) and those calls therefore never overlap.
+std::mutex g_capture_mu;
+
 cudaError_t capture_segment(cudaStream_t cs, cudaGraph_t *out, cudaError_t (*fn)(void *), void *ctx)
 {
     *out = nullptr;
@@ -1069,6 +1075,7 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
 {
     if (!out || !d_offsets || (m && !d_cols) || n == 0 || n > 0xffffffffull) return FQ_EINVAL;
     *out = nullptr;
+    std::lock_guard<std::mutex> lock(g_capture_mu);
     fq_graph *g = new (std::nothrow) fq_graph();
     if (!g) return FQ_ENOMEM;
     g->off = d_offsets;
@@ -1155,6 +1162,7 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
 fq_status fq_graph_destroy(fq_graph *g)
 {
     if (!g) return FQ_EINVAL;
+    std::lock_guard<std::mutex> lock(g_capture_mu);
     cudaDeviceSynchronize();
     if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
     if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
@@ -1195,6 +1203,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         const uint32_t mode = (codec ? 0u : FQ_BFS_NO_CODEC) | (want_visited ? FQ_BFS_VISITED_STREAM : 0u);
         if (!g->dl_exec || g->dl_depth != d_depth || g->dl_parent != d_parent || g->dl_log != d_stream_log ||
             g->dl_mode != mode || g->dl_tune != tune_generation()) {
+            std::lock_guard<std::mutex> lock(g_capture_mu);
             if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
             if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
             g->dl_exec = nullptr;

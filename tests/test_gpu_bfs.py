@@ -296,3 +296,40 @@ def test_threshold_records_equal_between_loop_drivers(rmat16):
         for k in ("top_down", "bottom_up", "compact", "encode", "decode"):
             assert a.stats["kernel_launches"][k] == b.stats["kernel_launches"][k], (thr, k)
     g.close()
+
+
+def test_concurrent_handles_in_threads(rmat16):
+    """Four host threads, each creating its own handle, running device-loop searches on its own
+    stream (the first one builds the handle's graph by stream capture) and destroying the handle,
+    all at once: every depth array equals the one-thread result (the library keeps handle creation
+    and destruction from overlapping another thread's capture)."""
+    import threading
+    off, cols, roots = rmat16
+    off_d, cols_d = to_dev(off, cols)
+    flags = fqbfs.FQ_BFS_DEVICE_LOOP | fqbfs.FQ_BFS_VISITED_STREAM
+    g0 = fqbfs.Graph(off_d, cols_d)
+    want = {r: g0.bfs(r, flags=flags).depth.cpu().numpy() for r in roots}
+    g0.close()
+    got, errors = {}, []
+
+    def work(k):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                for rep in range(2):
+                    g = fqbfs.Graph(off_d, cols_d)
+                    for r in roots[k::4]:
+                        got[(k, rep, r)] = g.bfs(r, flags=flags, stream=st).depth.cpu().numpy()
+                    g.close()
+        except Exception as e:  # reported below, in the main thread
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert len(got) == 2 * len(roots)
+    for (k, rep, r), d in got.items():
+        assert np.array_equal(d, want[r]), (k, rep, r)
