@@ -5,7 +5,7 @@ edgefactor 16, initiator 0.57/0.19/0.19/0.05), with every level's frontier encod
 queue stream (Q_d) and a bitmap stream (B_d), the visited bitmap as V_d, the consumed form
 decoded and expanded on the device.  value = GTEPS = undirected edges inside the reached
 components / timed seconds (whole job).  The roots are independent searches: the timed pass keeps
---concurrency of them in flight (default 4, each on its own handle, stream and host thread over
+--concurrency of them in flight (default 6, each on its own handle, stream and host thread over
 the one resident CSR); the rate of one search at a time is measured on the same roots and
 reported beside it.  The CSR (2.2 GB) is larger than L2, so no flush is needed between steps.
 
@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-pred", action="store_true", help="skip the predecessor-list container measurement")
-    p.add_argument("--concurrency", type=int, default=4,
+    p.add_argument("--concurrency", type=int, default=6,
                    help="searches in flight in the timed pass: each on its own handle, stream and host thread "
                         "(independent roots; 1 = one search at a time)")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in launch grids (no autotuning)")
