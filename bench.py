@@ -233,7 +233,7 @@ def make_graph(scale, edgefactor, device):
 def oracle_step(off_h, cols_h, root):
     """One root on the CPU oracle: FIFO BFS + encoding of every level's Q_d, B_d, V_d."""
     import oracle
-    depth, parent = oracle.bfs(off_h, cols_h, root)
+    depth, _ = oracle.bfs(off_h, cols_h, root)
     streams = oracle.level_streams(depth, record_visited=True)
     reached = depth >= 0
     edges = int(np.diff(off_h)[reached].sum()) // 2
@@ -861,7 +861,7 @@ def serving(dev, graph24, seconds=4.0, rate=2000.0, budget=100 << 30, seed=SEED)
         n = int(np.exp(rng.uniform(np.log(1 << 10), np.log(1 << 24))))
         v = inputs.geometric_set(n, 16.0, seed=seed + i, device=dev)
         ids = v.to(torch.int32)
-        enc, size = fqbfs.fq_frontier_encode(ids)
+        enc, _ = fqbfs.fq_frontier_encode(ids)
         pool.append((ids.cpu().pin_memory(), enc.cpu().pin_memory(), n))
     n_max = max(p[2] for p in pool)
     outs_codec = [torch.empty(fqbfs.fq_queue_bound(n_max), dtype=torch.uint8).pin_memory() for _ in range(16)]
