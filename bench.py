@@ -65,6 +65,9 @@ def parse():
                         "(independent roots; 1 = one search at a time)")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in launch grids (no autotuning)")
     p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--codec-grid", action="store_true",
+                   help="with --codec-only: the full sweep grid (n = 2^10 .. 2^28 by 4x, mean gap 1 .. 4096 by 2x, "
+                        "ids below 2^32) and the bitmap densities, instead of the default points")
     p.add_argument("--codec-only", action="store_true",
                    help="only the standalone codec points (sorted sets, geometric gaps); prints them as JSON")
     return p.parse_args()
@@ -446,6 +449,7 @@ def run_fqbfs(args, world, rank, local):
 
     if not args.no_codec:
         codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])
+        codec["bitmaps"] = bitmap_points(dev, peaks["hbm_gbs"])
         codec["threshold"] = codec_threshold(dev)
     pred = None
     if not args.no_pred and rank == 0:
@@ -500,6 +504,65 @@ CODEC_POINTS = ((26, 1.0, None), (26, 16.0, None), (24, 128.0, None), (28, 4.0, 
                 (25, 16.0, (0.01, 256, 16384)), (24, 4.0, (0.002, 4096, 65536)))
 
 
+def gap_entropy(ids: torch.Tensor) -> float:
+    """Empirical entropy (bits) of the gap histogram of sorted ids, -sum p log2 p over the distinct
+    gaps v[i] - v[i-1] - 1 (Eq. 2 applied to the gaps; for reporting only)."""
+    v = ids.to(torch.int64) & 0xFFFFFFFF
+    if v.numel() < 2:
+        return 0.0
+    _, counts = torch.unique(v[1:] - v[:-1] - 1, return_counts=True)
+    p = counts.to(torch.float64) / counts.sum()
+    return float(-(p * torch.log2(p)).sum())
+
+
+BITMAP_DENSITIES = (0.0001, 0.001, 0.01, 0.05, 0.1, 0.25, 0.5)
+
+
+def bitmap_points(dev, peak_gbs, log_bits=(24, 30), densities=BITMAP_DENSITIES, reps=5):
+    """The bitmap codec (FB) on i.i.d. Bernoulli bitmaps: 2^24 bits (a scale-24 frontier bitmap,
+    2 MiB, L2-resident) and 2^30 bits (128 MiB, larger than L2), at the densities of the codec
+    sweep.  Algorithmic bytes N/8 + |stream|; ratio N/8 over the stream; the mode chosen."""
+    from paper_1704_00513_gb300 import fqbfs, inputs
+    res = []
+    stream = torch.cuda.current_stream()
+    for lb in log_bits:
+        nbits = 1 << lb
+        work = fqbfs.workspace(0, nbits, dev)
+        out = torch.empty(fqbfs.fq_bitmap_bound(nbits), dtype=torch.uint8, device=dev)
+        dec = torch.empty(2 * ((nbits + 63) // 64), dtype=torch.int32, device=dev)
+        for dens in densities:
+            words = inputs.bernoulli_bitmap(nbits, dens, seed=SEED + lb, device=dev)
+            enc, size = fqbfs.fq_bitmap_encode(words, nbits, out=out, work=work)
+            mode = int(enc[4:8].view(torch.int32)[0].item()) if size >= 8 else -1
+            e0, e1 = _events()
+            for _ in range(2):
+                fqbfs.fq_bitmap_encode(words, nbits, out=out, work=work)
+            e0.record(stream)
+            for _ in range(reps):
+                fqbfs.fq_bitmap_encode(words, nbits, out=out, work=work)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_enc = e0.elapsed_time(e1) / reps / 1e3
+            e0.record(stream)
+            for _ in range(reps):
+                fqbfs.fq_bitmap_decode(out[:size], nbits, out=dec, work=work)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_dec = e0.elapsed_time(e1) / reps / 1e3
+            ok = bool(torch.equal(dec, words))
+            alg = nbits // 8 + size
+            res.append({"nbits": nbits, "density": dens, "bytes": size, "ratio": (nbits / 8) / size,
+                        "mode": {0: "raw", 1: "set", 2: "clear"}.get(mode, mode),
+                        "encode_GBps": alg / t_enc / 1e9, "decode_GBps": alg / t_dec / 1e9,
+                        "encode_frac": alg / t_enc / 1e9 / peak_gbs, "decode_frac": alg / t_dec / 1e9 / peak_gbs,
+                        "l2": "resident (2 MiB)" if nbits <= (1 << 24) else "larger than L2",
+                        "roundtrip_ok": ok})
+            del words
+        del work, out, dec
+        torch.cuda.empty_cache()
+    return res
+
+
 def codec_points(dev, peak_gbs, points=CODEC_POINTS, reps=5):
     """Standalone frontier codec throughput on sorted sets with geometric gaps (the codec sweep's
     shape), plus two sets with rare large gaps (outliers: fraction, range): algorithmic bytes
@@ -545,7 +608,9 @@ def codec_points(dev, peak_gbs, points=CODEC_POINTS, reps=5):
         ok = bool(torch.equal(dec, ids))
         alg = 4 * n + size
         pt = {"n": n, "mean_gap": mu, "outliers": list(outl) if outl else None, "bytes": size, "ratio": 4 * n / size,
-              "bits_per_id": 8 * size / n,
+              "ratio_pct": 100.0 * size / (4 * n), "bits_per_id": 8 * size / n,
+              "gap_entropy_bits": gap_entropy(ids), "input_Mids_per_s_encode": n / t_enc / 1e6,
+              "input_Mids_per_s_decode": n / t_dec / 1e6,
               "encode_GBps": alg / t_enc / 1e9, "decode_GBps": alg / t_dec / 1e9,
               "encode_frac": alg / t_enc / 1e9 / peak_gbs, "decode_frac": alg / t_dec / 1e9 / peak_gbs,
               "roundtrip_ok": ok}
@@ -1003,8 +1068,14 @@ def main():
         from paper_1704_00513_gb300 import build as fqbuild
         fqbuild.build()
         peaks, _ = measured_peaks()
-        print(json.dumps({"codec_sweep": codec_points(torch.device("cuda", torch.cuda.current_device()),
-                                                      peaks["hbm_gbs"])}), flush=True)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if args.codec_grid:
+            grid = tuple((ln, float(mu), None) for ln in range(10, 29, 2) for mu in (2 ** e for e in range(13))
+                         if (1 << ln) * (mu + 1) < (1 << 32))
+            print(json.dumps({"codec_grid": codec_points(dev, peaks["hbm_gbs"], points=grid, reps=3),
+                              "bitmaps": bitmap_points(dev, peaks["hbm_gbs"])}), flush=True)
+        else:
+            print(json.dumps({"codec_sweep": codec_points(dev, peaks["hbm_gbs"])}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
