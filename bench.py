@@ -259,6 +259,31 @@ def cpu_baseline(off_h, cols_h, roots, budget_s=12.0, max_roots=3):
                       f"every level's Q_d, B_d, V_d ({dt:.1f} s, single-threaded C)"}
 
 
+def cpu_openmp(off_h, cols_h, roots, budget_s=10.0, max_roots=16):
+    """The OpenMP CPU baseline (cpu_baseline/, bit-exact with the oracle) on all host cores: the
+    same roots with the same per-level Q_d, B_d, V_d encoding, within a time budget.  None if the
+    host compiler cannot build it."""
+    try:
+        import cpu_baseline
+        cpu_baseline.build()
+        cores = cpu_baseline.threads()
+    except Exception as e:  # e.g. no OpenMP runtime on the host
+        return {"value": None, "unavailable": f"{type(e).__name__}: {e}"[:200]}
+    cpu_baseline.bfs(off_h, cols_h, roots[-1])  # warm: page in the CSR, start the thread pool
+    t0 = time.perf_counter()
+    edges = done = 0
+    for r in roots[:max_roots]:
+        edges += cpu_baseline.bfs(off_h, cols_h, r)["reached_edges"]
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": edges / dt / 1e9, "unit": "GTEPS", "cores": cores, "kind": "openmp",
+            "sample": f"{done} of {len(roots)} roots of the same graph: direction-optimising BFS + FQ/FB encoding of "
+                      f"every level's Q_d, B_d, V_d, byte-identical to the oracle ({dt:.1f} s, {cores} threads, "
+                      "gcc -O3 -fopenmp)"}
+
+
 # ----------------------------------------------------------------------------- main arms
 
 def run_reference(args, world, rank):
@@ -468,7 +493,7 @@ def run_fqbfs(args, world, rank, local):
         e2e = run_e2e(args, off, cols, timed_roots, world)
         if not args.no_pred:
             e2e_pred = run_e2e(args, off, cols, timed_roots, world, container=True)
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         off_h = off.cpu().numpy()
         cols_h = cols.cpu().numpy().view(np.uint32)
@@ -476,6 +501,7 @@ def run_fqbfs(args, world, rank, local):
         del g
         torch.cuda.empty_cache()
         cpu = cpu_baseline(off_h, cols_h, timed_roots)
+        cpu_omp = cpu_openmp(off_h, cols_h, timed_roots)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -493,7 +519,7 @@ def run_fqbfs(args, world, rank, local):
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "codec": codec, "predecessor_list": pred, "batched": batched,
                 "serving": served,
-                "cpu_baseline": cpu, "e2e": e2e, "e2e_tree_container": e2e_pred,
+                "cpu_baseline": cpu, "cpu_openmp": cpu_omp, "e2e": e2e, "e2e_tree_container": e2e_pred,
                 "autotune": [{k: e[k] for k in ("site", "class", "ctas_per_sm", "ms", "default_ms")} for e in tuned],
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
                 "clocks": clocks}
