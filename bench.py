@@ -502,6 +502,7 @@ def run_fqbfs(args, world, rank, local):
         torch.cuda.empty_cache()
         cpu = cpu_baseline(off_h, cols_h, timed_roots)
         cpu_omp = cpu_openmp(off_h, cols_h, timed_roots)
+    csr_bytes = off.numel() * 8 + cols.numel() * 4
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -509,7 +510,10 @@ def run_fqbfs(args, world, rank, local):
                 "config": {"workload": f"rmat{args.scale}_dobfs_codec", "scale": args.scale,
                            "edgefactor": args.edgefactor, "vertices": n, "directed_edges": int(cols.numel()),
                            "roots_per_rank": args.steps, "streams": "Q_d, B_d, V_d encoded every level",
-                           "l2": "no flush: the 2.2 GB CSR exceeds L2", "levels_mean": statistics.mean(levels),
+                           "l2": (f"no flush: the {csr_bytes / 1e9:.1f} GB CSR exceeds L2" if csr_bytes > L2_BYTES else
+                                  f"L2-resident: the {csr_bytes / 1e6:.0f} MB CSR fits in L2, so the roofline "
+                                  "figures are not HBM-bound"),
+                           "levels_mean": statistics.mean(levels),
                            "level_loop": ("device (one CUDA graph per search)" if args.level_loop == "device"
                                           else "host (one counter read per level)"),
                            "concurrent_searches": conc, "gteps_one_search_at_a_time": seq_value,
@@ -721,6 +725,8 @@ def predecessor_list(g, root, depth, parent, peak_gbs, reps=5):
             "encode_frac": enc_alg / t_enc / 1e9 / peak_gbs, "decode_frac": dec_alg / t_dec / 1e9 / peak_gbs,
             "l2": "flushed (256 MB write) before every timed call", "roundtrip_ok": ok}
 
+
+L2_BYTES = 129 << 20  # GB300's L2 (129 MB)
 
 LINKS_GBPS = {"nvlink5_per_direction": 900.0, "pcie5_x16": 64.0, "infiniband_ndr": 50.0}
 
