@@ -523,7 +523,8 @@ def run_fqbfs(args, world, rank, local):
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "codec": codec, "predecessor_list": pred, "batched": batched,
                 "serving": served,
-                "cpu_baseline": cpu, "cpu_openmp": cpu_omp, "e2e": e2e, "e2e_tree_container": e2e_pred,
+                "cpu_baseline": cpu, "cpu_openmp": cpu_omp, "paper_figures": PAPER_FIGURES,
+                "e2e": e2e, "e2e_tree_container": e2e_pred,
                 "autotune": [{k: e[k] for k in ("site", "class", "ctas_per_sm", "ms", "default_ms")} for e in tuned],
                 "gpu_launches": int(sum_over_ranks(float(sum(klaunch.values())), world)),
                 "clocks": clocks}
@@ -727,6 +728,22 @@ def predecessor_list(g, root, depth, parent, peak_gbs, reps=5):
 
 
 L2_BYTES = 129 << 20  # GB300's L2 (129 MB)
+
+# The thesis' own figures for this path, with the hardware it names (context, not targets; it
+# prints no absolute BFS TEPS).
+PAPER_FIGURES = {
+    "codec_S4-BP128_on_one_frontier_buffer": {
+        "encode_MI_per_s": 3207.85, "decode_MI_per_s": 4701.06, "bits_per_int": 15.11,
+        "buffer": "29,899 sorted ids in [1, 65532]",
+        "hardware": "Intel Xeon E5-1620 @ 3.6 GHz (SSE4.1 code path)", "where": "sec. 5.4.1"},
+    "codec_ParaPFOR_GOV2_quoted": {"decode_MI_per_s": 1300, "hardware": "Fermi-class GPU (external paper)",
+                                   "where": "sec. 5.4.1"},
+    "exchange_volume_scale22_16_gpus": {
+        "column": "7,160,177,440 B -> 610,980,576 B (-91.46 %)", "row": "4,904,056,832 B -> 403,202,512 B (-91.77 %)",
+        "hardware": "8 nodes x 2 GTX 480 (Fermi), GigE", "where": "sec. 7.2.4"},
+    "bfs_teps": {"relative": "compressed BFS about 200 % of the uncompressed baseline's TEPS",
+                 "hardware": "Keeneland, 64 nodes x 1 Tesla M2090 (Fermi), InfiniBand QDR", "where": "ch. 8"},
+}
 
 LINKS_GBPS = {"nvlink5_per_direction": 900.0, "pcie5_x16": 64.0, "infiniband_ndr": 50.0}
 
