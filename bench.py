@@ -735,9 +735,9 @@ PAPER_FIGURES = {
     "codec_S4-BP128_on_one_frontier_buffer": {
         "encode_MI_per_s": 3207.85, "decode_MI_per_s": 4701.06, "bits_per_int": 15.11,
         "buffer": "29,899 sorted ids in [1, 65532]",
-        "hardware": "Intel Xeon E5-1620 @ 3.6 GHz (SSE4.1 code path)", "where": "sec. 5.4.1"},
+        "hardware": "Intel Xeon E5-1620 @ 3.6 GHz (SSE4.1 code path)", "where": "sec. 5.4.2"},
     "codec_ParaPFOR_GOV2_quoted": {"decode_MI_per_s": 1300, "hardware": "Fermi-class GPU (external paper)",
-                                   "where": "sec. 5.4.1"},
+                                   "where": "sec. 5.4.1-5.4.2"},
     "exchange_volume_scale22_16_gpus": {
         "column": "7,160,177,440 B -> 610,980,576 B (-91.46 %)", "row": "4,904,056,832 B -> 403,202,512 B (-91.77 %)",
         "hardware": "8 nodes x 2 GTX 480 (Fermi), GigE", "where": "sec. 7.2.4"},
