@@ -438,6 +438,22 @@ def run_fqbfs(args, world, rank, local):
     hmean = len(recs1) / sum((e0.elapsed_time(e1) / 1e3) / max(1, st_["reached_edges"]) * 1e9 for e0, e1, st_ in recs1)
     for k in range(1, conc):
         handles[k].close()
+    # the same roots with the queue streams in the patched-exceptions format (FQ_BFS_PATCHED), one
+    # search at a time: its queue ratio and rate beside the plain FQ streams'
+    pq_raw = pq_enc = pe = 0
+    with torch.cuda.stream(stream):
+        for r in warm_roots[:1]:
+            g.bfs(r, depth=depth, parent=parent, flags=flags | fqbfs.FQ_BFS_PATCHED, max_levels=64)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for r in timed_roots:
+            st_ = g.bfs(r, depth=depth, parent=parent, flags=flags | fqbfs.FQ_BFS_PATCHED, max_levels=64).stats
+            pq_raw += st_["raw_queue_bytes"]; pq_enc += st_["enc_queue_bytes"]; pe += st_["reached_edges"]
+        p1.record(stream)
+        torch.cuda.synchronize()
+    patched = {"flag": "FQ_BFS_PATCHED", "gteps_one_at_a_time": pe / (p0.elapsed_time(p1) / 1e3) / 1e9,
+               "queue_ratio": pq_raw / max(1, pq_enc), "queue_bits_per_id": 8.0 * pq_enc / max(1, pq_raw / 4)}
 
     # per-class kernel time of the same searches (host-driven loop, events around each class)
     prof_klaunch = {k: 0 for k in fqbfs.KCLASS}
@@ -470,7 +486,7 @@ def run_fqbfs(args, world, rank, local):
              "queue_bits_per_id": 8.0 * qenc / max(1, qraw / 4),
              "encode_GBps": kbytes["encode"] / max(1e-9, kms["encode"] / 1e3) / 1e9,
              "decode_GBps": kbytes["decode"] / max(1e-9, kms["decode"] / 1e3) / 1e9,
-             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}}
+             "kernel_ms": {k: round(v, 3) for k, v in kms.items()}, "patched_queues": patched}
 
     if not args.no_codec:
         codec["sweep"] = codec_points(dev, peaks["hbm_gbs"])

@@ -253,6 +253,10 @@ fq_status fq_graph_destroy(fq_graph *g);
 #define FQ_BFS_TIMING 0x8u         /* time every kernel class with CUDA events (fills stats)    */
 #define FQ_BFS_NO_CODEC 0x10u      /* skip the codec stage: expand the raw queue/bitmap (the plain
                                       BFS the codec stage is measured against; no streams)      */
+#define FQ_BFS_PATCHED 0x40u       /* the per-level queue streams Q_d in the FQX format (patched
+                                      exceptions, as fq_frontier_encode_px writes them) instead of FQ;
+                                      B_d is then encoded from the bitmap rather than mirrored.  The
+                                      top-down level decodes FQX like FQ.                          */
 #define FQ_BFS_DEVICE_LOOP 0x20u   /* run the level loop on the device: one CUDA graph (built on
                                       the first call per handle, output buffers and stream-log
                                       buffer, then reused) whose while node repeats the level and

@@ -409,9 +409,10 @@ def level_schedule(offsets, cols, depth, alpha: int = 14, beta: int = 24):
     return levels
 
 
-def level_streams(depth, record_visited: bool = False):
-    """Per level d: Q_d = FQ(F_d), B_d = FB(F_d as an n-bit bitmap), and (optionally)
-    V_d = FB(visited after level d) -- all functions of the depths only."""
+def level_streams(depth, record_visited: bool = False, patched: bool = False):
+    """Per level d: Q_d = FQ(F_d) (with `patched`, the PX stream of F_d), B_d = FB(F_d as an
+    n-bit bitmap), and (optionally) V_d = FB(visited after level d) -- all functions of the
+    depths only."""
     dp = _as(depth, np.int32)
     n = dp.size
     out = []
@@ -419,7 +420,7 @@ def level_streams(depth, record_visited: bool = False):
     visited = np.zeros((n + 63) // 64, np.uint64)
     for d in range(max_d + 1):
         f = np.nonzero(dp == d)[0].astype(np.uint32)
-        st, q = fq_encode(f)
+        st, q = px_encode(f) if patched else fq_encode(f)
         assert st == OK
         fbits = ids_to_bitmap(f, n)
         st, b = fb_encode(fbits, n)

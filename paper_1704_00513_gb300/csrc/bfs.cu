@@ -759,15 +759,21 @@ cudaError_t step_init(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_
     return cudaGetLastError();
 }
 
-// Step 1: Q_d, and B_d (mirrored from the queue when 2 n_f <= n, else from the bitmap).
-cudaError_t step_encode_q(fq_graph *g, bool dense, uint64_t n_f, const LoopState *ls, cudaStream_t st)
+// Step 1: Q_d, and B_d (mirrored from the queue when 2 n_f <= n, else from the bitmap).  With px,
+// Q_d is an FQX stream (patched exceptions) and B_d always comes from the bitmap (its inner stream
+// is FQ, so it cannot be mirrored from Q_d).
+cudaError_t step_encode_q(fq_graph *g, bool dense, uint64_t n_f, const LoopState *ls, cudaStream_t st, bool px)
 {
     const uint64_t n = g->n;
     const uint64_t *n_dev = ls ? reinterpret_cast<const uint64_t *>(&ls->n_f) : nullptr;
     const uint64_t n_max = ls ? n : n_f;
     uint64_t *q_bytes = reinterpret_cast<uint64_t *>(&g->ctr->q_bytes);
     uint64_t *b_bytes = reinterpret_cast<uint64_t *>(&g->ctr->b_bytes);
-    if (!dense) {
+    if (px) {
+        FQ_CU(encode_fq(g->q, n_f, n_dev, n_max, g->qs, g->qs_cap, q_bytes, g->sq, st, true));
+        FQ_CU(reset_status(g->sq, n / 2 + 1, st));
+        FQ_CU(encode_fb(g->fbits, n, g->bs, g->bs_cap, b_bytes, g->sq, st));
+    } else if (!dense) {
         Mirror mb;
         mb.out = g->bs;
         mb.cap = g->bs_cap;
@@ -882,7 +888,7 @@ struct LoopBuild {
     int32_t *depth;
     uint32_t *parent;
     uint8_t *log;
-    bool codec, want_v;
+    bool codec, want_v, px;
 };
 
 cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGraphNode_t *dep, void *func,
@@ -925,12 +931,12 @@ cudaError_t seg_init(void *p)
 cudaError_t seg_dense(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_encode_q(c.g, true, 0, c.g->ls, c.g->dl_stream);
+    return step_encode_q(c.g, true, 0, c.g->ls, c.g->dl_stream, c.px);
 }
 cudaError_t seg_sparse(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_encode_q(c.g, false, 0, c.g->ls, c.g->dl_stream);
+    return step_encode_q(c.g, false, 0, c.g->ls, c.g->dl_stream, c.px);
 }
 cudaError_t seg_visited(void *p)
 {
@@ -1187,6 +1193,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     const uint32_t min_codec_ids = opts ? opts->min_codec_ids : 0u;
     const bool codec = !(flags & FQ_BFS_NO_CODEC);
     const bool want_visited = codec && (flags & FQ_BFS_VISITED_STREAM);
+    const bool px = codec && (flags & FQ_BFS_PATCHED);
     const uint64_t n = g->n;
 
 #define FQ_TRY(expr)                                  \
@@ -1200,7 +1207,8 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
 
     if (flags & FQ_BFS_DEVICE_LOOP) {
         // the whole search is one graph launch; the host reads the records once at the end
-        const uint32_t mode = (codec ? 0u : FQ_BFS_NO_CODEC) | (want_visited ? FQ_BFS_VISITED_STREAM : 0u);
+        const uint32_t mode = (codec ? 0u : FQ_BFS_NO_CODEC) | (want_visited ? FQ_BFS_VISITED_STREAM : 0u) |
+                              (px ? FQ_BFS_PATCHED : 0u);
         if (!g->dl_exec || g->dl_depth != d_depth || g->dl_parent != d_parent || g->dl_log != d_stream_log ||
             g->dl_mode != mode || g->dl_tune != tune_generation()) {
             std::lock_guard<std::mutex> lock(g_capture_mu);
@@ -1209,7 +1217,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             g->dl_exec = nullptr;
             g->dl_graph = nullptr;
             if (!g->dl_stream) FQ_TRY(cudaStreamCreateWithFlags(&g->dl_stream, cudaStreamNonBlocking));
-            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited};
+            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited, px};
             FQ_TRY(build_device_loop(b, &g->dl_graph));
             FQ_TRY(cudaGraphInstantiate(&g->dl_exec, g->dl_graph, 0));
             g->dl_depth = d_depth;
@@ -1277,7 +1285,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         const bool coded = codec && n_f >= min_codec_ids;  // below the threshold the frontier crosses raw
         if (coded) {
             const bool dense = 2 * n_f > n;
-            FQ_TRY(step_encode_q(g, dense, n_f, nullptr, st));
+            FQ_TRY(step_encode_q(g, dense, n_f, nullptr, st, px));
             enc_launches = dense ? 8 : 2;
         }
         if (want_visited) {

@@ -1160,9 +1160,9 @@ cudaError_t reset_status(const Scratch &s, uint64_t max_ids, cudaStream_t st)
 }
 
 cudaError_t encode_fq(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max, uint8_t *out,
-                      uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
+                      uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st, bool px)
 {
-    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0};
+    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, nullptr, 0, nullptr, nullptr, 0, px ? 1 : 0};
     return launch_encode(a, n_dev ? n_max : n_host, st);
 }
 

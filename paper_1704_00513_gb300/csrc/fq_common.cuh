@@ -94,11 +94,11 @@ inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 // ------------------------------------------------------------------ internal launches
 // Every launch helper enqueues on `st` and returns cudaGetLastError().
 
-// FQ-encode ids[0..n).  n is *n_dev when n_dev != nullptr (device-resident count, then
-// n_max bounds it for the grid), else n_host.  Container: FQ stream at out (fb == false) or an
+// FQ-encode ids[0..n) (FQX, patched exceptions, with px).  n is *n_dev when n_dev != nullptr
+// (device-resident count, then n_max bounds it for the grid), else n_host.  Container: FQ stream at out (fb == false) or an
 // FB stream whose inner FQ starts at out + 16 (fb == true; positions come from the bitmap plan).
 cudaError_t encode_fq(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max, uint8_t *out,
-                      uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st);
+                      uint64_t cap, uint64_t *out_bytes, const Scratch &s, cudaStream_t st, bool px = false);
 cudaError_t encode_fb(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap, uint64_t *out_bytes,
                       const Scratch &s, cudaStream_t st);
 // Decode: in_bytes is in_bytes_host unless in_bytes_dev != nullptr.

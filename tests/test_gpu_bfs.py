@@ -333,3 +333,28 @@ def test_concurrent_handles_in_threads(rmat16):
     assert len(got) == 2 * len(roots)
     for (k, rep, r), d in got.items():
         assert np.array_equal(d, want[r]), (k, rep, r)
+
+
+@LOOPS
+def test_patched_queue_streams(rmat16, loop):
+    """FQ_BFS_PATCHED: every level's Q_d is the oracle's FQX (patched exceptions) stream of F_d,
+    B_d and V_d the oracle's FB streams; the top-down levels consume the decoded FQX queues, so
+    depths, trees and the schedule are unchanged."""
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    fqx = 0
+    for r in roots[:4]:
+        res = g.bfs(r, flags=loop | fqbfs.FQ_BFS_PATCHED | fqbfs.FQ_BFS_VISITED_STREAM, record_streams=True)
+        depth = res.depth.cpu().numpy()
+        ref_depth, _ = oracle.bfs(off, cols, r)
+        assert np.array_equal(depth, ref_depth)
+        assert oracle.validate(off, cols, r, depth, res.parent.cpu().numpy().view(np.uint32)) == 0
+        sched = oracle.level_schedule(off, cols, ref_depth)
+        assert [(x["n_f"], x["direction"], x["examined"]) for x in res.levels] == \
+            [(x["n_f"], x["direction"], x["examined"]) for x in sched]
+        for got, want in zip(res.streams, oracle.level_streams(ref_depth, record_visited=True, patched=True)):
+            for k in ("Q", "B", "V"):
+                assert np.array_equal(got[k].cpu().numpy(), want[k]), (r, got["level"], k)
+            fqx += int(got["Q"][:4].cpu().numpy().view(np.uint32)[0] == 0x31585146)
+    assert fqx > 0  # the patched form was chosen for some levels
+    g.close()
