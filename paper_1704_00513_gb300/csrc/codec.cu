@@ -986,13 +986,13 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
         const uint32_t *sp = reinterpret_cast<const uint32_t *>(buf + stage * kDecStage);
         const uint32_t git = (uint32_t)(grp % (kTileBlocks / kBlocksPerWarp));
         const uint64_t k0 = grp * kBlocksPerWarp;
-#pragma unroll 2
-        for (uint32_t i = 0; i < kBlocksPerWarp; i++) {
+        // One block of the group (any width, patched or not).
+        auto one_block = [&](uint32_t i) {
             const uint64_t k = k0 + i;
             const uint32_t in = __shfl_sync(0xffffffffu, cur.info, git * (kBlocksPerWarp / 2) + (i >> 1));
             const uint32_t base = __shfl_sync(0xffffffffu, cur.base, i);
             const uint32_t next = __shfl_sync(0xffffffffu, cur.base, i + 1);
-            if (k >= nb) break;
+            if (k >= nb) return;
             const uint32_t b = (i & 1u) ? (in >> 24) : ((in >> 16) & 0xffu);
             const uint32_t pre = (in & 0xffffu) + ((i & 1u) ? ((in >> 16) & 0xffu) : 0u) - cur.pre;
             const uint32_t *pk = sp + 4u * pre;
@@ -1070,6 +1070,62 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
 #pragma unroll
                 for (int j = 0; j < 4; j++)
                     if (i0 + j < n) emit_id(a, clear_mode, i0 + j, out[j]);
+            }
+        };
+        // Blocks in pairs: two full unpatched blocks of width <= 8 (and a block after them, whose
+        // base bounds the second) share one warp scan -- each block's increments sum below 2^15,
+        // so the two prefix sums ride in the halves of one 32-bit scan without a carry between them.
+        for (uint32_t i = 0; i < kBlocksPerWarp; i += 2) {
+            const uint64_t kA = k0 + i;
+            const uint32_t in = __shfl_sync(0xffffffffu, cur.info, git * (kBlocksPerWarp / 2) + (i >> 1));
+            const uint32_t ine = px ? __shfl_sync(0xffffffffu, cur.infoe, git * (kBlocksPerWarp / 2) + (i >> 1)) : 0u;
+            const uint32_t baseA = __shfl_sync(0xffffffffu, cur.base, i), baseB = __shfl_sync(0xffffffffu, cur.base, i + 1);
+            const uint32_t nextB = __shfl_sync(0xffffffffu, cur.base, i + 2);
+            if (kA >= nb) break;
+            const uint32_t bA = (in >> 16) & 0xffu, bB = in >> 24;
+            if (!(kA + 2 < nb && bA <= 8u && bB <= 8u && (ine >> 16) == 0u)) {  // uniform over the warp
+                one_block(i);
+                one_block(i + 1);
+                continue;
+            }
+            const uint32_t preA = (in & 0xffffu) - cur.pre, preB = preA + bA;
+            uint32_t gA[4], gB[4];
+            extract_narrow(sp + 4u * preA, bA, lane, gA);
+            extract_narrow(sp + 4u * preB, bB, lane, gB);
+            const uint32_t fA = lane ? gA[0] + 1u : 0u, fB = lane ? gB[0] + 1u : 0u;  // slot 0 is the base itself
+            const uint32_t sA = fA + gA[1] + gA[2] + gA[3] + 3u, sB = fB + gB[1] + gB[2] + gB[3] + 3u;
+            const uint32_t both = sA | (sB << 16);
+            const uint32_t incl = warp_incl_scan(both), ex = incl - both;
+            uint32_t oA[4], oB[4];
+            uint32_t vA = baseA + (ex & 0xffffu) + fA, vB = baseB + (ex >> 16) + fB;
+            oA[0] = vA;
+            oB[0] = vB;
+#pragma unroll
+            for (int j = 1; j < 4; j++) {
+                vA += gA[j] + 1u;
+                vB += gB[j] + 1u;
+                oA[j] = vA;
+                oB[j] = vB;
+            }
+            bool goodA = !(lane == 0 && gA[0] != 0u), goodB = !(lane == 0 && gB[0] != 0u);
+            if (lane == 31) {  // each block's last id: no wrap, and below the next block's base
+                const unsigned long long lastA = (unsigned long long)baseA + (incl & 0xffffu);
+                const unsigned long long lastB = (unsigned long long)baseB + (incl >> 16);
+                goodA = goodA && lastA < baseB;
+                goodB = goodB && lastB < nextB;
+            }
+            if (!goodA) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, kA * kBlock);
+            if (!goodB) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, (kA + 1) * kBlock);
+            const uint64_t iA = kA * kBlock + 4u * lane, iB = iA + kBlock;
+            if (!a.fb) {  // full blocks: every slot holds an id
+                *reinterpret_cast<uint4 *>(a.ids + iA) = make_uint4(oA[0], oA[1], oA[2], oA[3]);
+                *reinterpret_cast<uint4 *>(a.ids + iB) = make_uint4(oB[0], oB[1], oB[2], oB[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    emit_id(a, clear_mode, iA + j, oA[j]);
+                    emit_id(a, clear_mode, iB + j, oB[j]);
+                }
             }
         }
         if (gn >= ngroups) break;
