@@ -556,10 +556,20 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
             }
             __syncthreads();
             const uint32_t *sp = reinterpret_cast<const uint32_t *>(dbuf + stage * kDecStageB);
-            for (uint32_t bi = 0; bi < kBlocksPerWarp; bi++) {
+            auto store4 = [&](uint64_t k, const uint32_t out[4]) {
+                const uint64_t i0 = k * kBlock + 4u * lane;
+                if (vec_ok && i0 + 3 < n) {
+                    *reinterpret_cast<uint4 *>(ids + i0) = make_uint4(out[0], out[1], out[2], out[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (i0 + j < n) ids[i0 + j] = out[j];
+                }
+            };
+            auto one_block = [&](uint32_t bi) {
                 const uint32_t local = warp * kBlocksPerWarp + bi;
                 const uint64_t k = t * kTileBlocks + local;
-                if (k >= nb) break;
+                if (k >= nb) return;
                 uint32_t out[4];
                 const uint32_t b = wd[k];
                 bool good;
@@ -573,14 +583,25 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
                     if (k + 1 < nb && lane == 31 && last >= (unsigned long long)bases[k + 1]) good = false;
                 }
                 if (!good) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecUnpack, s);
-                const uint64_t i0 = k * kBlock + 4u * lane;
-                if (vec_ok && i0 + 3 < n) {
-                    *reinterpret_cast<uint4 *>(ids + i0) = make_uint4(out[0], out[1], out[2], out[3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        if (i0 + j < n) ids[i0 + j] = out[j];
+                store4(k, out);
+            };
+            for (uint32_t bi = 0; bi < kBlocksPerWarp; bi += 2) {  // full narrow blocks in pairs, one scan each
+                const uint32_t local = warp * kBlocksPerWarp + bi;
+                const uint64_t k = t * kTileBlocks + local;
+                if (k >= nb) break;
+                const uint32_t bA = wd[k], bB = k + 1 < nb ? wd[k + 1] : 0u;
+                if (!(k + 2 < nb && bA <= 8u && bB <= 8u)) {  // uniform over the warp
+                    one_block(bi);
+                    one_block(bi + 1);
+                    continue;
                 }
+                uint32_t oA[4], oB[4];
+                bool goodA, goodB;
+                unpack_pair_narrow(sp + 4u * spre[local], bA, bases[k], sp + 4u * spre[local + 1], bB, bases[k + 1],
+                                   bases[k + 2], lane, oA, oB, &goodA, &goodB);
+                if (!goodA || !goodB) set_error(a.b.ctl, FQ_ECORRUPT, kWhereDecUnpack, s);
+                store4(k, oA);
+                store4(k + 1, oB);
             }
         }
         __syncthreads();

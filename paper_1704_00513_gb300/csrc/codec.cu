@@ -1089,31 +1089,10 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
                 continue;
             }
             const uint32_t preA = (in & 0xffffu) - cur.pre, preB = preA + bA;
-            uint32_t gA[4], gB[4];
-            extract_narrow(sp + 4u * preA, bA, lane, gA);
-            extract_narrow(sp + 4u * preB, bB, lane, gB);
-            const uint32_t fA = lane ? gA[0] + 1u : 0u, fB = lane ? gB[0] + 1u : 0u;  // slot 0 is the base itself
-            const uint32_t sA = fA + gA[1] + gA[2] + gA[3] + 3u, sB = fB + gB[1] + gB[2] + gB[3] + 3u;
-            const uint32_t both = sA | (sB << 16);
-            const uint32_t incl = warp_incl_scan(both), ex = incl - both;
             uint32_t oA[4], oB[4];
-            uint32_t vA = baseA + (ex & 0xffffu) + fA, vB = baseB + (ex >> 16) + fB;
-            oA[0] = vA;
-            oB[0] = vB;
-#pragma unroll
-            for (int j = 1; j < 4; j++) {
-                vA += gA[j] + 1u;
-                vB += gB[j] + 1u;
-                oA[j] = vA;
-                oB[j] = vB;
-            }
-            bool goodA = !(lane == 0 && gA[0] != 0u), goodB = !(lane == 0 && gB[0] != 0u);
-            if (lane == 31) {  // each block's last id: no wrap, and below the next block's base
-                const unsigned long long lastA = (unsigned long long)baseA + (incl & 0xffffu);
-                const unsigned long long lastB = (unsigned long long)baseB + (incl >> 16);
-                goodA = goodA && lastA < baseB;
-                goodB = goodB && lastB < nextB;
-            }
+            bool goodA, goodB;
+            unpack_pair_narrow(sp + 4u * preA, bA, baseA, sp + 4u * preB, bB, baseB, nextB, lane, oA, oB, &goodA,
+                               &goodB);
             if (!goodA) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, kA * kBlock);
             if (!goodB) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecUnpack, (kA + 1) * kBlock);
             const uint64_t iA = kA * kBlock + 4u * lane, iB = iA + kBlock;

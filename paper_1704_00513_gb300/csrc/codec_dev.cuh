@@ -256,6 +256,41 @@ __device__ __forceinline__ bool unpack_full_narrow(const uint32_t *pk, uint32_t 
     return scan_full32(g, base, lane, out, last);
 }
 
+// Two FULL consecutive blocks A, B of width <= 8 with one warp scan: each block's increments
+// g + 1 sum below 2^15 (127 slots of at most 256), so the two prefix sums ride in the halves of one
+// 32-bit word without a carry between them.  nextB is the base of the block after B.  good*
+// report, per block, slot 0 holding 0 and the last id staying below the next block's base (no
+// wrap: the bases are u32).  All 32 lanes must call it.
+__device__ __forceinline__ void unpack_pair_narrow(const uint32_t *pkA, uint32_t bA, uint32_t baseA,
+                                                   const uint32_t *pkB, uint32_t bB, uint32_t baseB, uint32_t nextB,
+                                                   uint32_t lane, uint32_t oA[4], uint32_t oB[4], bool *goodA,
+                                                   bool *goodB)
+{
+    uint32_t gA[4], gB[4];
+    extract_narrow(pkA, bA, lane, gA);
+    extract_narrow(pkB, bB, lane, gB);
+    const uint32_t fA = lane ? gA[0] + 1u : 0u, fB = lane ? gB[0] + 1u : 0u;  // slot 0 is the base itself
+    const uint32_t sA = fA + gA[1] + gA[2] + gA[3] + 3u, sB = fB + gB[1] + gB[2] + gB[3] + 3u;
+    const uint32_t both = sA | (sB << 16);
+    const uint32_t incl = warp_incl_scan(both), ex = incl - both;
+    uint32_t vA = baseA + (ex & 0xffffu) + fA, vB = baseB + (ex >> 16) + fB;
+    oA[0] = vA;
+    oB[0] = vB;
+#pragma unroll
+    for (int j = 1; j < 4; j++) {
+        vA += gA[j] + 1u;
+        vB += gB[j] + 1u;
+        oA[j] = vA;
+        oB[j] = vB;
+    }
+    *goodA = !(lane == 0 && gA[0] != 0u);
+    *goodB = !(lane == 0 && gB[0] != 0u);
+    if (lane == 31) {
+        *goodA = *goodA && (unsigned long long)baseA + (incl & 0xffffu) < baseB;
+        *goodB = *goodB && (unsigned long long)baseB + (incl >> 16) < nextB;
+    }
+}
+
 // The b-bit slot values of one block whose payload words start at pk (readable two words past
 // the block): lane's slots 4*lane .. 4*lane+3 in g[].
 __device__ __forceinline__ void extract_slots(const uint32_t *pk, uint32_t b, uint32_t lane, uint32_t g[4])
