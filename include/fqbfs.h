@@ -409,7 +409,7 @@ double fq_server_clock(void);
 #define FQ_TUNE_ENC_WIDTHS 0u   /* encode, widths kernel (items: ids)                   */
 #define FQ_TUNE_ENC_PACK 1u     /* encode, pack kernel (items: ids)                     */
 #define FQ_TUNE_DEC_UNPACK 2u   /* decode, unpack kernel (items: ids)                   */
-#define FQ_TUNE_BAT_ENCODE 3u   /* batched encode, persistent kernel (items: all ids)   */
+#define FQ_TUNE_BAT_ENCODE 3u   /* batched encode, widths and pack kernels (items: all ids) */
 #define FQ_TUNE_BAT_DUNPACK 4u  /* batched decode, unpack kernel (items: all ids)       */
 #define FQ_TUNE_BU_SWEEP 5u     /* BFS bottom-up sweep (items: vertices)                */
 #define FQ_TUNE_TD_HUB 6u       /* BFS top-down hub items (items: vertices)             */

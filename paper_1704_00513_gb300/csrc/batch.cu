@@ -608,18 +608,6 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
     }
 }
 
-template <typename K>
-cudaError_t allow_smem_b(K kernel, size_t bytes, bool *done)
-{
-    int dev = 0;
-    FQ_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!done[dev]) {
-        FQ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        done[dev] = true;
-    }
-    return cudaSuccess;
-}
 
 }  // namespace
 }  // namespace fq
@@ -660,8 +648,8 @@ fq_status fq_frontier_decode_batch(const uint8_t *d_in, const uint64_t *d_in_off
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     BDec a{d_in, d_in_off, d_in_bytes, S, d_ids, d_seg_off, d_n, {}};
     batch_layout(total_ids, S, &a.b, d_work);
-    static bool done[64] = {false};
-    if (allow_smem_b(bat_dunpack_kernel, kBatchDecSmem, done) != cudaSuccess) return FQ_ECUDA;
+    static std::atomic<bool> done[64];
+    if (allow_smem(bat_dunpack_kernel, kBatchDecSmem, done) != cudaSuccess) return FQ_ECUDA;
     bat_dplan_kernel<<<1, kScanThreads, 0, st>>>(a);
     const uint32_t grid = (uint32_t)std::min<uint64_t>(a.b.tiles_cap, (uint64_t)8 * num_sms());
     bat_dtiles_kernel<<<grid, kEncThreads, 0, st>>>(a);

@@ -850,13 +850,8 @@ cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
     cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt);
     cmp_scan_kernel<<<1, kScanThreads, 0, st>>>(g->tile_cnt, g->tile_off, g->vis_cnt, g->vtile_off, g->cmp_tiles, g->n,
                                                 g->ctr, g->sq, g->sv);
-    static bool smem_set[64];
-    int dev = 0;
-    FQ_CU(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
-        FQ_CU(cudaFuncSetAttribute(cmp_extract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCmpSmem));
-        smem_set[dev] = true;
-    }
+    static std::atomic<bool> smem_set[64];
+    FQ_CU(allow_smem(cmp_extract_kernel, kCmpSmem, smem_set));
     cmp_extract_kernel<<<ct, kThreads, kCmpSmem, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
                                                        g->vtile_off, g->q, g->sv, want_v ? 1 : 0);
     return cudaGetLastError();

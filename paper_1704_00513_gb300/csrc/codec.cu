@@ -97,16 +97,18 @@ void note_cuda_error(cudaError_t e, int line)
 }
 
 // Autotuned CTAs per SM by launch site and size class (0: the built-in grid).
-static uint8_t g_tune[FQ_TUNE_NUM_SITES][FQ_TUNE_MAX_CLASS + 1];
-static uint32_t g_tune_generation = 0;  // bumped by every change: cached graphs that baked a grid rebuild
+// The tuning table and its generation are set from any host thread (fq_tune_set) and read at
+// every launch, hence atomics.
+static std::atomic<uint8_t> g_tune[FQ_TUNE_NUM_SITES][FQ_TUNE_MAX_CLASS + 1];
+static std::atomic<uint32_t> g_tune_generation{0};  // bumped by every change: cached graphs that baked a grid rebuild
 
-uint32_t tune_generation() { return g_tune_generation; }
+uint32_t tune_generation() { return g_tune_generation.load(); }
 
 uint32_t tuned_grid(uint32_t site, uint64_t items, uint64_t default_grid, uint64_t max_grid)
 {
     uint32_t cls = 0;
     for (uint64_t x = items; x > 1; x >>= 1) cls++;
-    const uint32_t per_sm = (site < FQ_TUNE_NUM_SITES && cls <= FQ_TUNE_MAX_CLASS) ? g_tune[site][cls] : 0u;
+    const uint32_t per_sm = (site < FQ_TUNE_NUM_SITES && cls <= FQ_TUNE_MAX_CLASS) ? g_tune[site][cls].load(std::memory_order_relaxed) : 0u;
     uint64_t g = per_sm ? (uint64_t)per_sm * (uint64_t)num_sms() : default_grid;
     g = std::min<uint64_t>(g, std::max<uint64_t>(max_grid, 1));
     return (uint32_t)std::max<uint64_t>(g, 1);
@@ -114,16 +116,16 @@ uint32_t tuned_grid(uint32_t site, uint64_t items, uint64_t default_grid, uint64
 
 int num_sms()
 {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return 152;
-    if (!cached[dev]) {
-        int v = 0;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (!v) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-        cached[dev] = v;
+        cached[dev].store(v, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return v;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -1126,48 +1128,34 @@ uint64_t enc_tiles(uint64_t n) { return cdiv(cdiv(n, kBlock), kTileBlocks); }
 // CTAs of `kernel` (static shared memory only) resident on the whole GPU at once, cached per device
 // in `cache`: a grid-stride kernel launched with exactly this many CTAs runs in a single wave.
 template <typename K>
-uint64_t resident_grid(K kernel, int threads, int *cache)
+uint64_t resident_grid(K kernel, int threads, std::atomic<int> *cache)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return (uint64_t)num_sms();
-    if (!cache[dev]) {
-        int per_sm = 0;
+    int per_sm = cache[dev].load(std::memory_order_relaxed);
+    if (!per_sm) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0)
             per_sm = 1;
-        cache[dev] = per_sm;
+        cache[dev].store(per_sm, std::memory_order_relaxed);
     }
-    return (uint64_t)cache[dev] * num_sms();
-}
-
-// Kernels with more than 48 KB of dynamic shared memory must opt in, once per device.
-template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes, bool *done)
-{
-    int dev = 0;
-    FQ_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!done[dev]) {
-        FQ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        done[dev] = true;
-    }
-    return cudaSuccess;
+    return (uint64_t)per_sm * num_sms();
 }
 
 cudaError_t prepare_unpack()
 {
-    static bool done[64] = {false};
+    static std::atomic<bool> done[64];
     return allow_smem(dec_unpack_kernel, kDecSmem, done);
 }
 
 // W then P, with grids of at most one resident wave (both kernels stride over their tiles).
 cudaError_t launch_encode(EncArgs a, uint64_t n_max, cudaStream_t st)
 {
-    static int occ_w[64], occ_p[64];
+    static std::atomic<int> occ_w[64], occ_p[64];
     const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(n_max));
     uint64_t raw_items = cdiv(n_max, 4) * 4;  // the raw bodies P may have to copy instead
     if (a.fb) raw_items = std::max<uint64_t>(raw_items, cdiv(a.nbits, 64));
     if (a.m_out) raw_items = std::max<uint64_t>(raw_items, cdiv(a.m_nbits, 64));
-    static int occ_wx[64], occ_px[64];
+    static std::atomic<int> occ_wx[64], occ_px[64];
     const uint64_t pack_items = std::max<uint64_t>(tiles, cdiv(raw_items, kEncThreads));
     if (a.px) {
         const uint32_t gw = tuned_grid(FQ_TUNE_ENC_WIDTHS, n_max, resident_grid(enc_widths_kernel<true>, kEncThreads, occ_wx), tiles);
@@ -1330,17 +1318,14 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
 fq_status fq_tune_set(uint32_t site, uint32_t size_class, uint32_t ctas_per_sm)
 {
     if (site >= FQ_TUNE_NUM_SITES || size_class > FQ_TUNE_MAX_CLASS || ctas_per_sm > 32u) return FQ_EINVAL;
-    if (g_tune[site][size_class] != (uint8_t)ctas_per_sm) {
-        g_tune[site][size_class] = (uint8_t)ctas_per_sm;
-        g_tune_generation++;
-    }
+    if (g_tune[site][size_class].exchange((uint8_t)ctas_per_sm) != (uint8_t)ctas_per_sm) g_tune_generation++;
     return FQ_OK;
 }
 
 uint32_t fq_tune_get(uint32_t site, uint32_t size_class)
 {
     if (site >= FQ_TUNE_NUM_SITES || size_class > FQ_TUNE_MAX_CLASS) return 0u;
-    return g_tune[site][size_class];
+    return g_tune[site][size_class].load();
 }
 
 fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/fqbfs.h"
 
 namespace fq {
@@ -270,3 +272,20 @@ uint32_t tune_generation();
             return _e;                                   \
         }                                                \
     } while (0)
+
+namespace fq {
+// Kernels with more than 48 KB of dynamic shared memory opt in once per device; done[dev] records
+// it.  Host threads may race here: the attribute call is idempotent, and the flag is atomic.
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<bool> *done)
+{
+    int dev = 0;
+    FQ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!done[dev].load(std::memory_order_acquire)) {
+        FQ_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done[dev].store(true, std::memory_order_release);
+    }
+    return cudaSuccess;
+}
+}  // namespace fq
