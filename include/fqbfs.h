@@ -6,8 +6,8 @@
  * direction-optimising BFS over a CSR graph in which every level's frontier is compressed with
  * delta coding + binary packing in blocks of 128 (the thesis' S4-BP128 choice, sec. 5.3),
  * measured in bytes, decompressed and consumed on the device -- the codec stage that the thesis
- * wraps around its two per-level exchanges (Alg. "Our BFS algorithm with SpVM and
- * compression", compress -> ALLGATHERV -> decompress, compress -> ALLTOALLV -> decompress).
+ * wraps around its two per-level exchanges (Algorithm 4: compress -> ALLGATHERV -> decompress,
+ * compress -> ALLTOALLV -> decompress).
  *
  * Conventions for every call
  *  - Pointers named d_* are device pointers, h_* host pointers.  The caller owns every buffer.
@@ -103,8 +103,7 @@ fq_status fq_work_status(const void *d_work, void *stream, uint64_t *h_detail);
 /* Encode the strictly increasing ids d_ids[0..n) (n < 2^32) as an FQ stream at d_out
  * (capacity cap bytes).  The stream's size is written to the device u64 *d_out_bytes (0 on a
  * device-detected error; the needed size on FQ_ENOSPC).  Device errors: FQ_EUNSORTED,
- * FQ_ENOSPC.  The frontier queue compress step of Alg. "Our BFS algorithm with SpVM and
- * compression" (delta + binary packing, sec. 5.1, 5.3). */
+ * FQ_ENOSPC.  The frontier queue compress step of Algorithm 4 (delta + binary packing, sec. 5.1, 5.3). */
 fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
                              uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
 
@@ -336,7 +335,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
  * k <= 64 roots traversed together in one persistent cooperative kernel launch: each vertex holds
  * a 64-bit mask of the roots that reached it, and a level ORs the frontier masks of the
  * neighbours into the not-yet-seen bits (the thesis' SpMV frontier step, t = A (x) f masked by
- * the visited list, Alg. "BFS based on replicated-CSR and SpVM", bit-sliced over the roots).
+ * the visited list, Algorithm 2, bit-sliced over the roots).
  * d_depth[i * n + v] (k x n, row-major int32) = hop distance of v from h_roots[i], -1 if
  * unreachable -- equal to fq_bfs_run's depth for that root.  The graph is the CSR of
  * fq_graph_create.  Scratch: fq_msbfs_scratch_bytes(n) bytes (about 36 bytes per vertex).

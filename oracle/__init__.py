@@ -8,8 +8,8 @@ The arithmetic lives in ``fq_oracle.c`` (plain single-threaded C, compiled by ``
 this module is argument marshalling plus the per-level bookkeeping that is a direct function of
 the BFS depths:
 
-* ``bfs`` / ``validate``      -- FIFO BFS and the BFS-tree checks (Alg. "BFS based on
-  replicated-CSR and SpMV"; Graph500 validation, Alg. "A Graph 500 application").
+* ``bfs`` / ``validate``      -- FIFO BFS and the BFS-tree checks (Algorithm 2; Graph500
+  validation, Algorithm 1).
 * ``fq_encode`` / ``fq_decode`` -- delta + binary packing, blocks of 128 (sec. 5.1, 5.3, Eq. 5-7).
 * ``fb_encode`` / ``fb_decode`` -- bitmap frontiers through the same codec (sec. 3.1, 5.1).
 * ``level_schedule``          -- per-level n_f, m_f, m_u, direction and edges examined of a
@@ -18,8 +18,7 @@ the BFS depths:
 * ``pl_encode`` / ``pl_decode`` -- the predecessor list as level sets plus level-relative
   parent ranks (the predecessor reduction of sec. 4.1.4, compressed).
 * ``level_streams``           -- the per-level encoded frontier queue, frontier bitmap and
-  visited bitmap (the data the method compresses around its exchanges, Alg. "Our BFS algorithm
-  with SpVM and compression").
+  visited bitmap (the data the method compresses around its exchanges, Algorithm 4).
 """
 from __future__ import annotations
 

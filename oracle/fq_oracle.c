@@ -8,10 +8,10 @@
  * Breadth-First Searches" (arXiv 1704.00513) in the most direct form available.
  *
  * Contents (each function cites the passage it follows):
- *   orc_bfs            textbook FIFO-queue BFS -> hop depth and a BFS tree      (Alg. "BFS
- *                      based on replicated-CSR and SpMV", sec. 4.1.2)
- *   orc_validate       BFS-tree checks (the "5 rules" of Graph500 validation, Alg. "A Graph 500
- *                      application"; the rules are not listed in the thesis, our reading)
+ *   orc_bfs            textbook FIFO-queue BFS -> hop depth and a BFS tree
+ *                      (Algorithm 2, sec. 4.1.2)
+ *   orc_validate       BFS-tree checks (the "5 rules" of Graph500 validation, Algorithm 1;
+ *                      the rules are not listed in the thesis, our reading)
  *   orc_fq_encode/decode  delta + frame-of-reference binary packing in blocks of 128
  *                      ("Binary packing", "Delta compression" in sec. 5.1; S4-BP128 in sec. 5.3;
  *                      width formula Eq. 6/7), written bit by bit

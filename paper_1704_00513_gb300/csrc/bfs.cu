@@ -1,11 +1,11 @@
 // bfs.cu -- level-synchronous, direction-optimising BFS with the per-level frontier codec
 // stage, and its C ABI (fq_graph_create / fq_graph_destroy / fq_bfs_run).
 //
-// One level d (the loop of Alg. "Our BFS algorithm with SpVM and compression", on one GPU):
+// One level d (the loop of Algorithm 4, on one GPU):
 //   1. encode F_d as Q_d (sorted queue, FQ) and B_d (bitmap, FB), and the visited bitmap as
 //      V_d -- the compress steps before the thesis' ALLGATHERV/ALLTOALLV; the byte counts are
 //      the exchange volume.  When 2|F_d| <= n the set positions of the frontier bitmap are the
-//      queue itself, so one single-pass encode writes Q_d and B_d together; V_d's positions were
+//      queue itself, so one encode call writes Q_d and B_d together; V_d's positions were
 //      extracted by the previous level's compaction;
 //   2. choose the direction from (n_f, m_f, m_u): top-down -> bottom-up when m_f*alpha > m_u,
 //      back when n_f*beta < n (direction optimisation, sec. 3.1);

@@ -1,8 +1,8 @@
 // msbfs.cu -- multi-source BFS: up to 64 roots traversed together, one bit per root in a 64-bit
 // mask per vertex, all levels in one persistent (cooperative) kernel launch.
 //
-// A level-synchronous BFS (the thesis' frontier / visited-list recurrence, Alg. "BFS based on
-// replicated-CSR and SpMV") run for k roots at once, the sparse vectors becoming bit-sliced:
+// A level-synchronous BFS (the thesis' frontier / visited-list recurrence, Algorithm 2) run for
+// k roots at once, the sparse vectors becoming bit-sliced:
 //   seen[v]     roots that reached v,      frontier[v]  roots that reached v at this level,
 //   next[v]     roots arriving at the next level (OR of frontier[u] over the neighbours u, masked
 //               by not-seen -- the SpMV t = A (x) f with the element-wise mask of the thesis).
