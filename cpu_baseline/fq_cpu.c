@@ -6,7 +6,7 @@
  * when n_f * beta < n; direction optimisation as in sec. 3.1 of the thesis) with every level's
  * frontier queue Q_d, frontier bitmap B_d and visited bitmap V_d encoded in the FQ / FB formats of
  * include/fqbfs.h (delta + binary packing in blocks of 128, sec. 5.1; packed only when smaller,
- * sec. 5.1 "Lossless").  Every result is byte-identical to the plain oracle's; only the work is
+ * the losslessness requirement of sec. 5.1).  Every result is byte-identical to the plain oracle's; only the work is
  * spread over threads: the codec over 128-id blocks, the BFS over frontier vertices (top-down) or
  * 64-vertex words (bottom-up), the queue extraction over word ranges.
  *

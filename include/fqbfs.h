@@ -31,9 +31,9 @@
  *            coding, sec. 5.1); slots past n are 0; b_k = bit length of the block's largest
  *            slot (Eq. 6 read as a ceiling, Eq. 7).
  *    raw     {u32 'FQR1', n, 0, n}, u32 v[n], zeros to 16 B.
- *    The packed form is written only when strictly smaller than the raw one (sec. 5.1
- *    "Lossless": the encoding must be smaller than the input; sec. 5.4.3 thresholds).
- *  FQX, the same sequence with patched exceptions (sec. 5.1 "Patched coding and Exceptions",
+ *    The packed form is written only when strictly smaller than the raw one (sec. 5.1's
+ *    losslessness requirement: the encoding must be smaller than the input; sec. 5.4.3 thresholds).
+ *  FQX, the same sequence with patched exceptions (patched coding, sec. 5.1,
  *    Eq. 8-9; the PFOR family of sec. 5.3), written by fq_frontier_encode_px:
  *    {u32 'FQX1', n, nb, payload_words, E, 0, 0, 0}, u32 base[nb], u8 b[nb], u8 e[nb], zeros to
  *    16 B, the blocks' low b_k bits of every slot as in FQ, u8 slot[E] (each block's exception
@@ -109,7 +109,7 @@ fq_status fq_frontier_encode(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, 
 
 /* The same as fq_frontier_encode with the FQX (patched exceptions) format: a block whose largest
  * gaps are rare outliers keeps a small width and stores the outliers apart.  Same arguments,
- * workspace, bound (fq_queue_bound) and errors.  "Patched coding and Exceptions", sec. 5.1. */
+ * workspace, bound (fq_queue_bound) and errors.  Patched coding, sec. 5.1. */
 fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_out, uint64_t cap,
                                 uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
 
@@ -177,7 +177,7 @@ fq_status fq_frontier_encode_static(const uint32_t *d_ids, uint64_t n, uint8_t *
 
 /* Encode the bitmap d_words (ceil(nbits/64) words; bits >= nbits ignored) as an FB stream at
  * d_out (capacity cap); size to *d_out_bytes.  nbits <= 2^32.  Bitmap frontiers, sec. 3.1
- * ("Sparse vector with pop counting"), coded with the queue codec. */
+ * (the popcount-indexed sparse vector), coded with the queue codec. */
 fq_status fq_bitmap_encode(const uint64_t *d_words, uint64_t nbits, uint8_t *d_out, uint64_t cap,
                            uint64_t *d_out_bytes, void *d_work, uint64_t work_bytes, void *stream);
 
@@ -275,8 +275,8 @@ typedef struct fq_bfs_opts {
     uint32_t flags;
     uint32_t min_codec_ids; /* compression threshold: a level whose frontier has fewer ids skips the
                                codec stage (its frontier is consumed raw; Q_d, B_d record 0 bytes and
-                               are not logged); 0 codes every level.  sec. 5.4.3 "Usage of
-                               compression thresholds" */
+                               are not logged); 0 codes every level.  Compression
+                               thresholds, sec. 5.4.3 */
 } fq_bfs_opts;
 
 /* kernel classes reported by FQ_BFS_TIMING */

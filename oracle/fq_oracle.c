@@ -13,16 +13,16 @@
  *   orc_validate       BFS-tree checks (the "5 rules" of Graph500 validation, Algorithm 1;
  *                      the rules are not listed in the thesis, our reading)
  *   orc_fq_encode/decode  delta + frame-of-reference binary packing in blocks of 128
- *                      ("Binary packing", "Delta compression" in sec. 5.1; S4-BP128 in sec. 5.3;
+ *                      (binary packing and delta coding, sec. 5.1; S4-BP128 in sec. 5.3;
  *                      width formula Eq. 6/7), written bit by bit
- *   orc_px_encode/decode  binary packing with patched exceptions ("Patched coding and
- *                      Exceptions", sec. 5.1, Eq. 8-9; the PFOR family in sec. 5.3): per block
+ *   orc_px_encode/decode  binary packing with patched exceptions (patched coding, sec. 5.1,
+ *                      Eq. 8-9; the PFOR family in sec. 5.3): per block
  *                      the width b that minimises the block's bytes, gaps >= 2^b stored apart
  *   orc_fr_encode/decode  frame of reference without differencing (Eq. 5-6 as printed: per block
  *                      the minimum as base, width = bit length of max - min) for unsorted values
  *   orc_fb_encode/decode  frontier/visited bitmap codec: positions of the minority bit value,
- *                      coded with the queue codec, or the raw words (bitmap frontiers, sec. 3.1
- *                      "Sparse vector with pop counting"; lossless requirement, sec. 5.1)
+ *                      coded with the queue codec, or the raw words (bitmap frontiers and the
+ *                      popcount-indexed sparse vector, sec. 3.1; lossless requirement, sec. 5.1)
  *   orc_bu_examined    edges a bottom-up sweep examines at one level (direction optimisation,
  *                      sec. 3.1)
  *
@@ -110,7 +110,7 @@ static uint32_t get_bit(const uint8_t *buf, uint64_t t) { return (uint32_t)((buf
  * u8 b[nb], zeros up to a 16-byte boundary, then the nb bit strings (block k is 4*b_k u32
  * words).  Raw stream: {magic "FQR1", n, 0, n}, u32 v[n], zeros up to 16 bytes.  The packed
  * form is used only when strictly smaller (the encoded data must be smaller than the input,
- * sec. 5.1 "Lossless"; compression threshold, sec. 5.4.3), so ties and n = 0 are raw.
+ * the losslessness requirement of sec. 5.1; compression threshold, sec. 5.4.3), so ties and n = 0 are raw.
  */
 
 uint64_t orc_fq_raw_size(uint64_t n) { return 16u + pad16(4u * n); }
@@ -281,7 +281,7 @@ int orc_fq_decode(const uint8_t *in, uint64_t in_bytes, uint32_t *out, uint64_t 
 
 /* ------------------------------------------------------------------ patched codec "PX"
  *
- * Binary packing with exceptions (sec. 5.1 "Patched coding and Exceptions": a value that does
+ * Binary packing with exceptions (patched coding, sec. 5.1: a value that does
  * not fit in the block's b bits -- a gap >= 2^b, Eq. 8-9 -- is stored apart; PFOR family,
  * sec. 5.3).  Same gaps, blocks and raw fallback as FQ.  Per block k the width b_k is the b in
  * 0..32 that minimises the block's bytes 16*b + 5*e_b, e_b = number of gaps >= 2^b (each

@@ -14,7 +14,7 @@
 //   4. expand: top-down over the decoded queue (t = A (x) f masked by the visited list) or
 //      bottom-up against the decoded bitmap; depth/parent written by the discovering thread;
 //   5. compact the next-frontier bitmap into the sorted queue F_{d+1} (popcount + prefix sum,
-//      sec. 3.1 "Sparse vector with pop counting"), visited |= next, count n_f and m_f, and
+//      the popcount-indexed sparse vector of sec. 3.1), visited |= next, count n_f and m_f, and
 //      extract the positions V_{d+1} will code.
 // The host reads one 256-byte counter record per level (termination test and direction).
 #include <algorithm>

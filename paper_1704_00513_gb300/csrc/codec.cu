@@ -1,7 +1,7 @@
 // codec.cu -- GPU kernels of the frontier codec (FQ queue streams, FB bitmap streams) and its
 // C ABI.  Delta coding + frame-of-reference binary packing in blocks of 128 ids, the integer
-// codec the thesis wraps around its per-level exchanges (sec. 5.1 "Binary packing" and "Delta
-// compression"; S4-BP128 chosen in sec. 5.3; width = bit length, Eq. 6-7).  The byte layout is
+// codec the thesis wraps around its per-level exchanges (binary packing and delta coding, sec.
+// 5.1; S4-BP128 chosen in sec. 5.3; width = bit length, Eq. 6-7).  The byte layout is
 // this library's own (documented in include/fqbfs.h), designed for warp-per-block GPU decoding:
 // every block's payload is 16*b_k bytes, so it starts on a 16-byte boundary and a warp moves
 // it with b_k 128-bit accesses.

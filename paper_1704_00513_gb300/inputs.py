@@ -9,7 +9,7 @@ Random numbers come from a counter-based generator: ``mix32`` is the "lowbias32"
 integer finaliser published by C. Wellons (hash-prospector), applied to (seed, counter)
 pairs.  Multiplications are split into 16-bit halves so that no int64 product overflows.
 
-Graph recipe (the thesis' Graph500 Kronecker input, sec. 2.7.1 "Synthetic data": vertices =
+Graph recipe (the thesis' Graph500 Kronecker input, synthetic data of sec. 2.7.1: vertices =
 2^scale, edges = edgefactor * 2^scale; initiator A/B/C/D = 0.57/0.19/0.19/0.05):
   1. edge e, bit level l in 0..scale-1: r = mix32(mix32(s ^ e) ^ c_l); the quadrant is A if
      r < tA, B if r < tB, C if r < tC, else D, with tA/tB/tC the cumulative initiator

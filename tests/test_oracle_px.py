@@ -1,5 +1,5 @@
 """Pins of the oracle's patched-exceptions codec (PX: binary packing in blocks of 128 with gaps
->= 2^b stored apart -- thesis sec. 5.1 "Patched coding and Exceptions", Eq. 8-9; the PFOR family
+>= 2^b stored apart -- patched coding, thesis sec. 5.1, Eq. 8-9; the PFOR family
 of sec. 5.3): hand-worked streams, round trips, the per-block width choice checked by brute force
 on the stream's own header, and rejection of malformed streams."""
 import json
