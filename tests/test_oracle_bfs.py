@@ -168,6 +168,31 @@ def test_level_schedule_by_hand():
     assert oracle.bu_examined(off, cols, depth, 1) == 9
 
 
+def test_level_schedule_switches_back_by_hand():
+    # root 0 -- hub 1 -- leaves 2..60, and a tail 60 - 61 - ... - 99: n = 100, 99 edges, degree
+    # sum 198.  Depths: 0, 1, leaves 2, then 61 + k at 3 + k (99 at 41).
+    edges = [(0, 1)] + [(1, i) for i in range(2, 61)] + [(i, i + 1) for i in range(60, 99)]
+    off, cols = csr_from_edges(100, edges)
+    depth, _ = oracle.bfs(off, cols, 0)
+    assert depth[:61].tolist() == [0, 1] + [2] * 59 and depth[61:].tolist() == list(range(3, 42))
+    lv = oracle.level_schedule(off, cols, depth, alpha=14, beta=24)
+    assert len(lv) == 42
+    got = lambda d: (lv[d]["n_f"], lv[d]["m_f"], lv[d]["m_u"], lv[d]["direction"], lv[d]["examined"])
+    assert got(0) == (1, 1, 197, 0, 1)          # 14 > 197? no: top-down, deg(0) examined
+    # 60 * 14 > 137: bottom-up.  Unvisited 2..99: leaves 2..60 find 1 first (59 edges); the
+    # tail 61..98 scans both neighbours (76), 99 its one (1)
+    assert got(1) == (1, 60, 137, 1, 136)
+    # 59 * 24 < 100? no: stays bottom-up.  61 finds 60 first (1); 62..98 scan two (74); 99 one
+    assert got(2) == (59, 60, 77, 1, 76)
+    assert got(3) == (1, 2, 75, 0, 2)           # 1 * 24 < 100: back to top-down
+    for d in range(4, 27):                      # 2 * 14 > m_u only once m_u < 28
+        assert lv[d]["direction"] == 0 and lv[d]["m_u"] == 77 - 2 * (d - 2) >= 28
+    assert got(27) == (1, 2, 27, 1, 26)         # 86 finds 85 (1); 87..98 two each (24); 99 one
+    assert got(28) == (1, 2, 25, 0, 2)          # 24 < 100: top-down again
+    assert got(29) == (1, 2, 23, 1, 22)         # 28 > 23: bottom-up; 88 (1) + 89..98 (20) + 99 (1)
+    assert oracle.bu_examined(off, cols, depth, 1) == 136
+
+
 def test_level_streams_are_the_level_sets():
     off, cols = csr_from_edges(300, [(i, (7 * i + 3) % 300) for i in range(300)] + [(i, i + 1) for i in range(299)])
     depth, _ = oracle.bfs(off, cols, 17)
