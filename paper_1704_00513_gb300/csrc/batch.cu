@@ -519,11 +519,12 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
         const uint32_t s = a.b.tile_seg[g];
         const SegInfo si = a.b.seg[s];
         const uint64_t gn = g + gridDim.x;
+        uint32_t pf_by = 0;  // thread 0: bytes of the next tile's copy issued into the other stage
         if (threadIdx.x == 0 && gn < T) {
             const uint32_t s2 = a.b.tile_seg[gn];
             const SegInfo si2 = a.b.seg[s2];
-            const uint32_t by = tile_bytes(gn, s2, si2);
-            if (by) bulk_load(dbuf + (stage ^ 1u) * kDecStageB, payload_at(gn, s2, si2), by, &bars[stage ^ 1u]);
+            pf_by = tile_bytes(gn, s2, si2);
+            if (pf_by) bulk_load(dbuf + (stage ^ 1u) * kDecStageB, payload_at(gn, s2, si2), pf_by, &bars[stage ^ 1u]);
         }
         const uint64_t t = g - a.b.tile_base[s];
         const uint8_t *fq = a.in + a.in_off[s];
@@ -549,12 +550,21 @@ __global__ void __launch_bounds__(kEncThreads, 3) bat_dunpack_kernel(BDec a)
                 spre[2 * lane] = incl - x0 - x1;
                 spre[2 * lane + 1] = incl - x1;
             }
+            // Bounded wait for the tile's payload (the barrier also publishes spre).  A copy still
+            // missing after it is reported; thread 0 then lets the CTA's copies in flight land
+            // (bounded again) before the shared memory is released, and the CTA leaves.
+            if (!__syncthreads_and(by == 0u || mbar_wait(&bars[stage], stage ? phase1 : phase0))) {
+                if (threadIdx.x == 0) {
+                    set_error(a.b.ctl, FQ_ETIMEOUT, kWhereDecUnpack, g);
+                    mbar_wait(&bars[stage], stage ? phase1 : phase0);
+                    if (pf_by) mbar_wait(&bars[stage ^ 1u], stage ? phase0 : phase1);
+                }
+                return;
+            }
             if (by) {
-                if (!mbar_wait(&bars[stage], stage ? phase1 : phase0)) set_error(a.b.ctl, FQ_ETIMEOUT, kWhereDecUnpack, g);
                 if (stage) phase1 ^= 1u;
                 else phase0 ^= 1u;
             }
-            __syncthreads();
             const uint32_t *sp = reinterpret_cast<const uint32_t *>(dbuf + stage * kDecStageB);
             auto store4 = [&](uint64_t k, const uint32_t out[4]) {
                 const uint64_t i0 = k * kBlock + 4u * lane;

@@ -981,7 +981,16 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
         if (gn < ngroups && lane == 0 && nxt.bytes)
             bulk_load(buf + (stage ^ 1u) * kDecStage, payload + nxt.off, nxt.bytes, &bar[stage ^ 1u]);
         if (cur.bytes) {
-            if (!mbar_wait(&bar[stage], stage ? phase1 : phase0)) set_error(a.s.ctl, FQ_ETIMEOUT, kWhereDecUnpack, grp);
+            // Bounded wait for the group's payload.  A copy still missing after it is reported;
+            // lane 0 then lets the warp's copies in flight land (bounded again), and the warp leaves.
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[stage], stage ? phase1 : phase0))) {
+                if (lane == 0) {
+                    set_error(a.s.ctl, FQ_ETIMEOUT, kWhereDecUnpack, grp);
+                    mbar_wait(&bar[stage], stage ? phase1 : phase0);
+                    if (gn < ngroups && nxt.bytes) mbar_wait(&bar[stage ^ 1u], stage ? phase0 : phase1);
+                }
+                return;
+            }
             if (stage) phase1 ^= 1u;
             else phase0 ^= 1u;
         }
