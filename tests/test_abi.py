@@ -55,3 +55,28 @@ def test_host_size_functions_match_stream_definitions(lib):
     assert a >= 256 and fqbfs.fq_workspace_bytes(10**6, 0) > a
     assert fqbfs.fq_workspace_bytes(0, 2**24) >= 4 * (2**23)    # room for the minority positions
     assert lib.fq_status_string(4) == b"FQ_ECORRUPT"
+
+
+def test_status_strings_name_every_code(lib):
+    names = ["FQ_OK", "FQ_EINVAL", "FQ_ENOMEM", "FQ_ENOSPC", "FQ_ECORRUPT", "FQ_EUNSORTED", "FQ_ETIMEOUT", "FQ_ECUDA",
+             "FQ_EBUSY"]
+    for code, name in enumerate(names):
+        assert lib.fq_status_string(code) == name.encode()
+    assert lib.fq_status_string(-1) == b"FQ_UNKNOWN" and lib.fq_status_string(99) == b"FQ_UNKNOWN"
+
+
+@pytest.mark.parametrize("n,sizes", [
+    (1, [1]),                          # a lone root
+    (16, [1, 15]),                     # a star: one level of 15 leaves
+    (300, [1] * 300),                  # a path: 300 levels of one vertex (every stream raw)
+    (1000, [1, 5, 40, 300, 600]),      # all reached, widening levels
+    (5000, [1, 3, 200, 1800, 40, 2]),  # some vertices unreached, a narrowing tail
+])
+def test_pred_bound_holds_oracle_containers(lib, n, sizes):
+    from paper_1704_00513_gb300 import inputs
+    import numpy as np
+    depth, parent = inputs.random_tree(n, sizes, seed=7 + n)
+    blob = oracle.pl_encode(depth.numpy(), parent.numpy().astype(np.uint32))
+    assert len(blob) <= fqbfs.fq_pred_bound(n, len(sizes))
+    # the bound grows with the size and the number of levels
+    assert fqbfs.fq_pred_bound(n, len(sizes)) <= fqbfs.fq_pred_bound(n + 128, len(sizes) + 1)
