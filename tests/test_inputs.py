@@ -55,3 +55,34 @@ def test_geometric_set_and_bitmap():
     ids = torch.tensor([0, 5, 63, 64, 9999])
     ww = inputs.ids_to_words32(ids, 10000).numpy().view(np.uint64)
     assert ww[0] == (1 | 1 << 5 | 1 << 63) and ww[1] == 1 and ww[9999 // 64] == 1 << (9999 % 64)
+
+
+def test_rmat_quadrants_follow_the_initiator_at_every_level():
+    # bit l of (u, v) picks the quadrant at level l: (0,0) = A, (0,1) = B, (1,0) = C, (1,1) = D
+    u, v = inputs.rmat_edges(12, 16, seed=5)
+    m = u.numel()
+    assert m == 16 << 12
+    for lvl in range(12):
+        ub, vb = (u >> lvl) & 1, (v >> lvl) & 1
+        freq = [((ub == r) & (vb == c)).sum().item() / m for r, c in ((0, 0), (0, 1), (1, 0), (1, 1))]
+        for f, want in zip(freq, (0.57, 0.19, 0.19, 0.05)):
+            assert abs(f - want) < 0.01, (lvl, freq)
+
+
+def test_geometric_gaps_have_the_stated_law():
+    v = inputs.geometric_set(200000, 16.0, seed=9)
+    g = torch.diff(v) - 1                                       # failures before success, p = 1/16
+    assert abs((g == 0).double().mean().item() - 1 / 16) < 0.003
+    assert abs((g == 1).double().mean().item() - (15 / 16) / 16) < 0.003
+    assert torch.equal(inputs.geometric_set(1000, 1.0, seed=9), torch.arange(1000))  # mean gap 1: a run
+
+
+def test_outlier_set_widens_the_stated_fraction():
+    base = inputs.geometric_set(200000, 16.0, seed=11)
+    v = inputs.outlier_set(200000, 16.0, 0.01, 256, 16384, seed=11)
+    extra = torch.diff(v, prepend=torch.zeros(1, dtype=torch.int64)) - torch.diff(
+        base, prepend=torch.zeros(1, dtype=torch.int64))
+    hit = extra > 0
+    assert abs(hit.double().mean().item() - 0.01) < 0.0015
+    assert extra[hit].min().item() >= 256 and extra[hit].max().item() < 16384
+    assert (torch.diff(v) >= 1).all()                           # still strictly increasing
