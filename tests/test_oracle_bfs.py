@@ -139,6 +139,9 @@ def test_validator_catches_planted_mistakes():
     assert planted(lambda d, p: (d.__setitem__(4, 1), p.__setitem__(4, 0))) == 2
     assert planted(lambda d, p: (d.__setitem__(3, -1), p.__setitem__(3, 0xFFFFFFFF))) == 3
     assert planted(lambda d, p: p.__setitem__(5, 0)) == 4            # unreached with a parent
+    # a consistent parent chain 0-1-2-3 (3 at depth 3 under 2) that the chord 1-3 contradicts:
+    # rules 1, 2 and 4 hold, the edge joins depths 1 and 3
+    assert planted(lambda d, p: (d.__setitem__(3, 3), p.__setitem__(3, 2))) == 3
     # any valid parent choice passes: vertex 3 can hang off 1 or 2? only 1 (depth 1)
     d, p = depth.copy(), parent.copy()
     p[3] = 1
@@ -166,6 +169,10 @@ def test_level_schedule_by_hand():
     # level 3: F={10}, n_f=1 -> 24 < 11? no -> bottom-up; nothing unvisited
     assert (lv[3]["n_f"], lv[3]["direction"], lv[3]["examined"]) == (1, 1, 0)
     assert oracle.bu_examined(off, cols, depth, 1) == 9
+    # the switch needs m_f * alpha strictly above m_u: at level 0, 1 * 19 = 19 = m_u stays
+    # top-down, 1 * 20 > 19 switches
+    assert oracle.level_schedule(off, cols, depth, alpha=19, beta=24)[0]["direction"] == 0
+    assert oracle.level_schedule(off, cols, depth, alpha=20, beta=24)[0]["direction"] == 1
 
 
 def test_level_schedule_switches_back_by_hand():
@@ -191,6 +198,12 @@ def test_level_schedule_switches_back_by_hand():
     assert got(28) == (1, 2, 25, 0, 2)          # 24 < 100: top-down again
     assert got(29) == (1, 2, 23, 1, 22)         # 28 > 23: bottom-up; 88 (1) + 89..98 (20) + 99 (1)
     assert oracle.bu_examined(off, cols, depth, 1) == 136
+    # the switch back needs n_f * beta strictly below n: at level 3, 1 * 100 = 100 = n stays
+    # bottom-up (62 finds 61 (1); 63..98 two each (72); 99 one: 74 edges), 1 * 99 < 100 switches
+    lv100 = oracle.level_schedule(off, cols, depth, alpha=14, beta=100)
+    assert (lv100[3]["direction"], lv100[3]["examined"]) == (1, 74)
+    lv99 = oracle.level_schedule(off, cols, depth, alpha=14, beta=99)
+    assert (lv99[3]["direction"], lv99[3]["examined"]) == (0, 2)
 
 
 def test_level_streams_are_the_level_sets():

@@ -214,6 +214,18 @@ def test_fq_decoder_rejects_overflow_and_order():
     c = s.copy()
     c[4 + 4:8 + 4] = np.frombuffer((2**32 - 10).to_bytes(4, "little"), np.uint8)
     assert oracle.fq_decode(c)[0] == oracle.ECORRUPT
+    # packed blocks out of order: block 1's base at or below block 0's last id (254)
+    ids = np.arange(0, 512, 2, dtype=np.uint32)
+    st, s = oracle.fq_encode(ids)
+    assert st == oracle.OK and _u32(s, 0) == 0x31505146 and _u32(s, 2) == 2 and _u32(s, 5) == 256
+    for base1 in (254, 100):
+        c = s.copy()
+        c[20:24] = np.frombuffer(int(base1).to_bytes(4, "little"), np.uint8)
+        assert oracle.fq_decode(c)[0] == oracle.ECORRUPT, base1
+    c = s.copy()
+    c[20:24] = np.frombuffer((255).to_bytes(4, "little"), np.uint8)   # still above 254: valid
+    st, back = oracle.fq_decode(c)
+    assert st == oracle.OK and back[128] == 255 and back[-1] == 255 + 127 * 2
     # raw stream out of order
     st, r = oracle.fq_encode(np.array([1, 2**31], np.uint32))
     assert _u32(r, 0) == 0x31525146

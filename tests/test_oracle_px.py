@@ -150,3 +150,19 @@ def test_two_exceptions_must_be_in_slot_order():
     c = s.copy()
     c[xpos], c[xpos + 1] = c[xpos + 1], c[xpos]
     assert oracle.px_decode(c)[0] == oracle.ECORRUPT
+
+
+def test_cost_tie_goes_to_the_larger_width():
+    # One full block: 16 gaps of 31 at slots 1..16, the other 111 gaps 0.  Costs 16*b + 5*e_b:
+    # b = 0 -> 5*16 = 80 (16 exceptions); b = 1..4 -> 16*b + 80; b = 5 -> 80 (no exceptions);
+    # b >= 6 -> 96 or more.  b = 0 and b = 5 tie; the rule takes b = 5, so the block carries no
+    # exception it could avoid at the same cost.
+    gaps = np.zeros(128, np.int64)
+    gaps[1:17] = 31
+    ids = (1000 + np.cumsum(gaps + 1) - 1).astype(np.uint32)
+    assert ids[0] == 1000 and np.all(np.diff(ids.astype(np.int64)) - 1 == gaps[1:])
+    st, s = oracle.px_encode(ids)
+    assert st == oracle.OK
+    n, nb, b, e, slots, high = parse(s)
+    assert (n, nb) == (128, 1) and b.tolist() == [5] and e.tolist() == [0] and slots.size == 0
+    assert s.size == 32 + 16 + 16 * 5      # header, base + width + count padded, 5 payload vectors
