@@ -131,7 +131,14 @@ def _check(status: int, what: str):
 
 
 def _ptr(t: torch.Tensor | None):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """The device address of a tensor the library reads or writes as one dense block: it must
+    live on a CUDA device and be contiguous, else the call is refused before anything runs."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA tensor, got {tuple(t.shape)} on {t.device}"
+                         f"{'' if t.is_contiguous() else f' with strides {t.stride()}'}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _device_status(work: torch.Tensor, stream, what: str):

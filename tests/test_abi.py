@@ -6,6 +6,7 @@ import os
 import re
 
 import pytest
+import torch
 
 import oracle
 from paper_1704_00513_gb300 import build as fqbuild
@@ -80,3 +81,17 @@ def test_pred_bound_holds_oracle_containers(lib, n, sizes):
     assert len(blob) <= fqbfs.fq_pred_bound(n, len(sizes))
     # the bound grows with the size and the number of levels
     assert fqbfs.fq_pred_bound(n, len(sizes)) <= fqbfs.fq_pred_bound(n + 128, len(sizes) + 1)
+
+
+def test_binding_refuses_host_tensors_before_any_call(lib):
+    ids = torch.arange(0, 300, 3, dtype=torch.int32)             # host memory: never handed to the library
+    with pytest.raises(ValueError, match="contiguous CUDA tensor"):
+        fqbfs.fq_frontier_encode(ids)
+    with pytest.raises(ValueError, match="contiguous CUDA tensor"):
+        fqbfs.fq_frontier_decode(torch.zeros(32, dtype=torch.uint8), cap=10)
+    with pytest.raises(ValueError, match="contiguous CUDA tensor"):
+        fqbfs.fq_bitmap_encode(torch.zeros(4, dtype=torch.int32), 128)
+    with pytest.raises(ValueError, match="contiguous CUDA tensor"):
+        fqbfs.fq_pred_encode(torch.zeros(4, dtype=torch.int32), torch.zeros(4, dtype=torch.int32), 1)
+    with pytest.raises(ValueError, match="strides"):
+        fqbfs._ptr(torch.zeros(8, 2)[:, 0])                        # a strided view is refused too
