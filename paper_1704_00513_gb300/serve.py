@@ -5,7 +5,6 @@ from __future__ import annotations
 
 import ctypes
 import math
-import time
 from dataclasses import dataclass
 
 import numpy as np

@@ -4,7 +4,6 @@ and on the GPU that a tuning run keeps only measured gains and that outputs do n
 grids chosen."""
 import json
 
-import numpy as np
 import pytest
 import torch
 

@@ -2,7 +2,6 @@
 on sets across block edges and bitmaps of every density regime; BFS depths equal, trees valid,
 every level's Q_d, B_d, V_d byte-identical, on small graphs and R-MAT graphs, with one thread and
 with several."""
-import os
 
 import numpy as np
 import pytest
