@@ -1202,7 +1202,7 @@ cudaError_t encode_fq_mirror(const uint32_t *ids, uint64_t n_host, const uint64_
                              uint8_t *out, uint64_t cap, uint64_t *out_bytes, const Mirror &m, const Scratch &s,
                              cudaStream_t st)
 {
-    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words, m.nbits};
+    EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words, m.nbits, 0};
     return launch_encode(a, n_dev ? n_max : n_host, st);
 }
 
@@ -1210,7 +1210,7 @@ cudaError_t encode_fb_positions(const uint64_t *words, uint64_t nbits, uint8_t *
                                 uint64_t *out_bytes, const Scratch &s, cudaStream_t st)
 {
     EncArgs a{s.positions, 0, reinterpret_cast<const uint64_t *>(&s.ctl->n), out, cap, out_bytes, 1, nbits, words, s,
-              nullptr, 0, nullptr, nullptr, 0};
+              nullptr, 0, nullptr, nullptr, 0, 0};
     return launch_encode(a, nbits / 2 + 1, st);
 }
 
