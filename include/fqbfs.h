@@ -120,7 +120,10 @@ fq_status fq_frontier_encode_px(const uint32_t *d_ids, uint64_t n, uint8_t *d_ou
  * range, nonzero high parts that fit above the width);
  * a failure sets FQ_ECORRUPT.  Header-level faults are caught before any output is written;
  * value-level faults may leave d_ids partly written.  Never writes more than cap ids
- * (FQ_ENOSPC if the stream holds more).  The decompress step of the same algorithm. */
+ * (FQ_ENOSPC if the stream holds more).  Payloads reach shared memory by TMA bulk copies whose
+ * waits are bounded: a copy that has not landed after the bound sets FQ_ETIMEOUT, and the warp
+ * that waited lets its copies in flight land (bounded again) and stops, leaving d_ids partly
+ * written.  The decompress step of the same algorithm. */
 fq_status fq_frontier_decode(const uint8_t *d_in, uint64_t in_bytes, uint32_t *d_ids, uint64_t cap,
                              uint64_t *d_n, void *d_work, uint64_t work_bytes, void *stream);
 
@@ -147,7 +150,8 @@ fq_status fq_frontier_encode_batch(const uint32_t *d_ids, const uint64_t *d_seg_
 /* Stream s is d_in[in_off[s] .. in_off[s] + in_bytes[s]) (in_off multiples of 16).  Its ids are
  * written to d_ids + seg_off[s], at most seg_off[s+1] - seg_off[s] of them; their count lands in
  * d_n[s].  Every stream is validated like fq_frontier_decode; a failure sets FQ_ECORRUPT (detail
- * = segment) and that segment's count to 0, the others are still decoded. */
+ * = segment) and that segment's count to 0, the others are still decoded.  A tile payload copy
+ * that outlasts its bounded wait sets FQ_ETIMEOUT (detail = tile), and that CTA stops decoding. */
 fq_status fq_frontier_decode_batch(const uint8_t *d_in, const uint64_t *d_in_off, const uint64_t *d_in_bytes, uint32_t S,
                                    uint32_t *d_ids, const uint64_t *d_seg_off, uint64_t total_ids, uint64_t *d_n,
                                    void *d_work, uint64_t work_bytes, void *stream);
