@@ -55,6 +55,16 @@ MUTATIONS = [
     ("switch_back_on_equality", PY, "elif direction == BOTTOM_UP and n_f * beta < n:",
      "elif direction == BOTTOM_UP and n_f * beta <= n:", 1, BFS),
     ("never_switch_back", PY, "elif direction == BOTTOM_UP and n_f * beta < n:", "elif False:", 1, BFS),
+    ("bitmap_raw_only_when_strictly_larger", C, "    if (16u + inner_bytes >= raw_size) {",
+     "    if (16u + inner_bytes > raw_size) {", 1, CODEC),
+    ("raw_size_unpadded", C, "uint64_t orc_fq_raw_size(uint64_t n) { return 16u + pad16(4u * n); }",
+     "uint64_t orc_fq_raw_size(uint64_t n) { return 16u + 4u * n; }", 1, CODEC),
+    ("px_high_part_shifted_one_short", C, "            g[slot] |= high << bk;",
+     "            g[slot] |= high << (bk ? bk - 1 : 0);", 1, PX),
+    ("px_high_part_stored_unshifted", C, "put_u32(out + xhigh + 4u * x, (uint32_t)(gap >> b[k]));",
+     "put_u32(out + xhigh + 4u * x, (uint32_t)(gap));", 1, PX),
+    ("px_decode_accepts_zero_high_part", C, "            if (high == 0u || (high >> (32u - bk)) != 0u)",
+     "            if ((high >> (32u - bk)) != 0u)", 1, PX),
     ("m_u_counts_the_frontier", PY, "        visited_deg += m_f\n        m_u = total - visited_deg",
      "        m_u = total - visited_deg\n        visited_deg += m_f", 1, BFS),
 ]

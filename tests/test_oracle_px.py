@@ -166,3 +166,19 @@ def test_cost_tie_goes_to_the_larger_width():
     n, nb, b, e, slots, high = parse(s)
     assert (n, nb) == (128, 1) and b.tolist() == [5] and e.tolist() == [0] and slots.size == 0
     assert s.size == 32 + 16 + 16 * 5      # header, base + width + count padded, 5 payload vectors
+
+
+def test_exception_at_slot_0_is_rejected():
+    # slot 0 holds the block's base itself (gap 0), so no exception may name it: move the one
+    # exception of a hand-sized block (a 70000 gap at slot 64) to slot 0
+    gaps = np.zeros(128, np.int64)
+    gaps[64] = 70000
+    ids = (np.cumsum(gaps + 1) - 1).astype(np.uint32)
+    st, s = oracle.px_encode(ids)
+    assert st == oracle.OK
+    n, nb, b, e, slots, high = parse(s)
+    assert e.tolist() == [1] and slots.tolist() == [64]
+    xpos = 32 + (6 * nb + 15) // 16 * 16 + 16 * int(b.sum())
+    c = s.copy()
+    c[xpos] = 0
+    assert oracle.px_decode(c)[0] == oracle.ECORRUPT
