@@ -65,6 +65,13 @@ MUTATIONS = [
      "put_u32(out + xhigh + 4u * x, (uint32_t)(gap));", 1, PX),
     ("px_decode_accepts_zero_high_part", C, "            if (high == 0u || (high >> (32u - bk)) != 0u)",
      "            if ((high >> (32u - bk)) != 0u)", 1, PX),
+    ("visited_stream_misses_its_own_level", PY,
+     "            visited |= fbits\n            st, v = fb_encode(visited, n)",
+     "            st, v = fb_encode(visited, n)\n            visited |= fbits", 1, BFS),
+    ("container_counts_one_vertex_short", PY, "    reached = int(sum(f.size for f in sets))\n    head",
+     "    reached = int(sum(f.size for f in sets)) - 1\n    head", 1, PRED),
+    ("container_rank_streams_reversed", PY, "    for r in ranks:\n        st, q = fr_encode(r)",
+     "    for r in ranks[::-1]:\n        st, q = fr_encode(r)", 1, PRED),
     ("m_u_counts_the_frontier", PY, "        visited_deg += m_f\n        m_u = total - visited_deg",
      "        m_u = total - visited_deg\n        visited_deg += m_f", 1, BFS),
 ]
