@@ -68,6 +68,10 @@ def parse():
     p.add_argument("--codec-grid", action="store_true",
                    help="with --codec-only: the full sweep grid (n = 2^10 .. 2^28 by 4x, mean gap 1 .. 4096 by 2x, "
                         "ids below 2^32) and the bitmap densities, instead of the default points")
+    p.add_argument("--level-log", default="bench_levels.jsonl",
+                   help="JSONL file receiving one record per BFS level of the profiled pass (root, level, direction, "
+                        "n_f, m_f, m_u, edges examined, stream sizes, kernel time and model bytes per class); '' "
+                        "disables it")
     p.add_argument("--codec-only", action="store_true",
                    help="only the standalone codec points (sorted sets, geometric gaps); prints them as JSON")
     return p.parse_args()
@@ -457,18 +461,46 @@ def run_fqbfs(args, world, rank, local):
 
     # per-class kernel time of the same searches (host-driven loop, events around each class)
     prof_klaunch = {k: 0 for k in fqbfs.KCLASS}
+    prof_levels = []
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     for r in timed_roots:
-        s = g.bfs(r, depth=depth, parent=parent, flags=prof_flags, max_levels=64).stats
+        res_p = g.bfs(r, depth=depth, parent=parent, flags=prof_flags, max_levels=64)
+        s = res_p.stats
         for k in fqbfs.KCLASS:
             kms[k] += s["kernel_ms"][k]
             kbytes[k] += s["kernel_bytes"][k]
             prof_klaunch[k] += s["kernel_launches"][k]
+        prof_levels.append((r, s["isolated"], res_p.levels))
     p1.record(stream)
     torch.cuda.synchronize()
     host_loop_ms = p0.elapsed_time(p1)
+    # the roofline numerator again, from the level records through the library's model: it must
+    # equal what the searches accumulated
+    deg_h = (off[1:] - off[:-1]).cpu().numpy()
+    model_bytes = {k: 0 for k in fqbfs.KCLASS}
+    level_lines = []
+    for r, n_iso, lv in prof_levels:
+        visited = 0
+        for i, rec in enumerate(lv):
+            visited += rec["n_f"]
+            nxt = lv[i + 1]["n_f"] if i + 1 < len(lv) else 0
+            mb = fqbfs.level_bytes(n, n_iso, deg_h[r] == 0, rec, visited, nxt)
+            for k in fqbfs.KCLASS:
+                model_bytes[k] += mb[k]
+            level_lines.append({"root": int(r), "level": rec["level"],
+                                "direction": "bottom_up" if rec["direction"] else "top_down",
+                                "n_f": rec["n_f"], "m_f": rec["m_f"], "m_u": rec["m_u"], "examined": rec["examined"],
+                                "q_bytes": rec["q_bytes"], "b_bytes": rec["b_bytes"], "v_bytes": rec["v_bytes"],
+                                "kernel_ms": {k: round(v, 5) for k, v in rec["kernel_ms"].items() if v},
+                                "model_bytes": {k: v for k, v in mb.items() if v}})
+    if model_bytes != kbytes:
+        raise RuntimeError(f"level-record model {model_bytes} != accumulated kernel bytes {kbytes}")
+    if args.level_log and rank == 0:
+        with open(args.level_log, "w") as f:
+            for line in level_lines:
+                f.write(json.dumps(line) + "\n")
 
     # dominant kernel class and its roofline (algorithmic bytes / event-timed duration)
     peaks, peak_kind = measured_peaks()
@@ -480,7 +512,9 @@ def run_fqbfs(args, world, rank, local):
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": dom, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": kbytes[dom] / max(1, launches),
-                "launches": launches, "avg_launch_ms": kms[dom] / max(1, launches)}
+                "launches": launches, "avg_launch_ms": kms[dom] / max(1, launches),
+                "model": "fq_bfs_level_bytes over the profiled pass's level records (equal to the searches' own sums)",
+                "level_log": args.level_log or None}
     codec = {"queue_ratio": qraw / max(1, qenc), "bitmap_ratio": braw / max(1, benc),
              "visited_ratio": braw / max(1, venc),
              "queue_bits_per_id": 8.0 * qenc / max(1, qraw / 4),

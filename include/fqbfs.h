@@ -95,7 +95,11 @@ typedef struct fq_device_status {
 } fq_device_status;
 
 /* Synchronise `stream`, then read the status record of workspace d_work.  Returns its code
- * (FQ_OK if the device found nothing wrong); *h_detail (may be NULL) receives the detail. */
+ * (FQ_OK if the device found nothing wrong); *h_detail (may be NULL) receives the detail.  The
+ * record carries the outcome of the device-side checks that sec. 5.1's losslessness requirement
+ * implies (a stream that does not decode to strictly increasing ids is rejected, never returned
+ * silently wrong), and of Algorithm 5's compress/decompress steps run on the device, where no
+ * host code sees the data. */
 fq_status fq_work_status(const void *d_work, void *stream, uint64_t *h_detail);
 
 /* ------------------------------------------------------------------ frontier queue codec */
@@ -236,15 +240,34 @@ fq_status fq_pred_decode(const uint8_t *d_in, uint64_t in_bytes, int32_t *d_dept
 typedef struct fq_graph fq_graph;
 
 /* Wrap an undirected graph in CSR form: d_offsets[n+1] (int64, offsets[0] = 0,
- * offsets[n] = m), d_cols[m] (uint32 < n, each row sorted, symmetric, no self-loops).  The
- * handle borrows both arrays (the caller keeps them alive and unchanged) and allocates its
- * workspace (about 30 bytes per vertex) with cudaMalloc on the current device.  n < 2^32.
- * Synchronous. */
+ * offsets[n] = m), d_cols[m] (uint32 < n, each row sorted, symmetric, no self-loops) -- the
+ * adjacency matrix A, held as compressed sparse rows, that Algorithm 2 multiplies with the
+ * frontier (the synthetic graph of sec. 2.7.1, symmetrised as Graph 500 inputs are).  The handle
+ * borrows both arrays (the caller keeps them alive and unchanged) and allocates its workspace
+ * (about 30 bytes per vertex) on the current device: through the allocator installed with
+ * fq_set_allocator when there is one, else cudaMalloc.  It also counts the vertices of degree 0
+ * (reported as fq_bfs_stats.isolated).  n < 2^32.  Synchronous.
+ * Errors: FQ_EINVAL (arguments), FQ_ENOMEM (the workspace or the pinned host record could not be
+ * allocated; nothing is left allocated), FQ_ECUDA. */
 fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, uint64_t m,
                           fq_graph **out);
 
-/* Free a handle's workspace (synchronises the device first). */
+/* Free a handle's workspace (synchronises the device first), through the allocator it was
+ * allocated with. */
 fq_status fq_graph_destroy(fq_graph *g);
+
+/* Device memory for graph handles from the caller's own pool (the thesis has no counterpart:
+ * this serves callers whose device memory must all come from one allocator, such as a framework's
+ * caching pool).  alloc(bytes, ctx) returns a 256-byte aligned device pointer or NULL (the
+ * create call then fails with FQ_ENOMEM and releases everything it took); release(ptr, bytes, ctx)
+ * takes back what alloc gave.  Process-wide; applies to fq_graph_create calls made after it; each
+ * handle remembers the allocator that allocated it.  NULL restores cudaMalloc/cudaFree. */
+typedef struct fq_allocator {
+    void *(*alloc)(uint64_t bytes, void *ctx);
+    void (*release)(void *ptr, uint64_t bytes, void *ctx);
+    void *ctx;
+} fq_allocator;
+fq_status fq_set_allocator(const fq_allocator *a);
 
 #define FQ_TOP_DOWN 0
 #define FQ_BOTTOM_UP 1
@@ -305,7 +328,8 @@ typedef struct fq_bfs_stats {
     uint64_t enc_visited_bytes;/* sum over levels of |V_d| (FQ_BFS_VISITED_STREAM)              */
     double kernel_ms[FQ_NUM_KCLASS];       /* FQ_BFS_TIMING: summed kernel time per class       */
     uint64_t kernel_launches[FQ_NUM_KCLASS];/* launches per class                               */
-    uint64_t kernel_bytes[FQ_NUM_KCLASS];  /* algorithmic bytes per class (design model)        */
+    uint64_t kernel_bytes[FQ_NUM_KCLASS];  /* algorithmic bytes per class (fq_bfs_level_bytes)  */
+    uint64_t isolated;        /* vertices of degree 0 in the graph (never swept bottom-up)      */
 } fq_bfs_stats;
 
 typedef struct fq_level_record {
@@ -317,14 +341,41 @@ typedef struct fq_level_record {
     uint64_t examined;        /* adjacency entries read while expanding F_d                     */
     uint64_t q_bytes, b_bytes, v_bytes; /* |Q_d|, |B_d|, |V_d| (0 when not encoded)             */
     uint64_t log_offset;      /* offset of Q_d, then B_d, then V_d in the stream log (or ~0)    */
+    float kernel_ms[FQ_NUM_KCLASS]; /* FQ_BFS_TIMING, host-driven loop: this level's kernel time
+                                       per class (0 otherwise)                                    */
 } fq_level_record;
 
-/* Breadth-first search from root.  Writes d_depth[n] (hop distance, -1 unreachable) and, if
- * d_parent is not NULL, d_parent[n] (a BFS tree: parent[root] = root, UINT32_MAX unreachable).
+/* The design model of algorithmic bytes behind fq_bfs_stats.kernel_bytes, for one level: the bytes
+ * each kernel class must move by its design (the numerator of its roofline fraction), from the level's
+ * record, the graph's vertex and isolated-vertex counts, whether the root has degree 0,
+ * `visited` = vertices visited once F_d is included (the sum of n_f over levels 0..d) and the
+ * next frontier's size.  Writes out[FQ_NUM_KCLASS]; host only, needs no GPU.  Per class:
+ *   encode    coded level: 4 n_f + |Q_d| + N/8 + |B_d|; V_d: N/8 + |V_d|;
+ *   decode    top-down: |Q_d| + 4 n_f; bottom-up: |B_d| + N/8 (coded levels only);
+ *   top_down  4 per edge examined + 20 per frontier vertex (offsets pair + queue id) + 8 per
+ *             discovered vertex (depth, parent);
+ *   bottom_up 4 N/8 (frontier, visited, isolated and next bitmaps) + 16 per unvisited vertex of
+ *             nonzero degree (its offsets pair; isolated vertices are skipped unread) + 4 per edge
+ *             examined + 8 per discovered vertex;
+ *   compact   3 N/8 + 20 per discovered vertex.
+ * A coded level is one with q_bytes > 0; V_d is coded when v_bytes > 0. */
+void fq_bfs_level_bytes(uint64_t n, uint64_t n_isolated, uint32_t root_isolated, const fq_level_record *rec,
+                        uint64_t visited, uint64_t n_f_next, uint64_t *out);
+
+/* Breadth-first search from root: the thesis' problem statement (sec. 4.1.2: input a source
+ * vertex s, output the predecessor list) solved level-synchronously as in Algorithm 2 (the
+ * frontier f multiplied by A, masked by the visited list, until f is empty), with the per-level
+ * codec stage of Algorithm 4 / 5 (sec. 5.4.4: compress the frontier, measure, decompress) and the
+ * direction optimisation of sec. 3.1.  Writes d_depth[n] (hop distance, -1 unreachable) and, if
+ * d_parent is not NULL, d_parent[n] (a BFS tree: parent[root] = root, UINT32_MAX unreachable;
+ * the validation rules of Algorithm 1 hold, sec. 2.6.3).
  * Level d: encode F_d as Q_d (queue) and B_d (bitmap) [and V_d], decide the direction from
  * (n_f, m_f, m_u), decode the form that direction consumes, expand it (top-down over the
  * decoded queue, or bottom-up against the decoded bitmap), compact the next frontier into a
- * sorted queue.  Stops when the next frontier is empty.
+ * sorted queue.  Stops when the next frontier is empty (the termination test of sec. 4.2.1).
+ * Errors: FQ_EINVAL (arguments), FQ_ECORRUPT / FQ_ETIMEOUT (a per-level stream failed its
+ * round trip, a bounded wait gave up), FQ_ENOSPC (stream log too small; the search itself is
+ * complete), FQ_ECUDA.
  * h_stats (may be NULL) and h_levels[0..max_levels) (may be NULL) receive the per-run and
  * per-level records.  If d_stream_log is not NULL every level's Q_d, B_d [, V_d] are copied
  * there back to back (fails with FQ_ENOSPC when stream_log_cap is exceeded).
@@ -348,6 +399,14 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
  * The level barriers wait with a bound; FQ_ETIMEOUT if one gives up.  The multi-source frontier
  * has no codec stage. */
 uint64_t fq_msbfs_scratch_bytes(uint64_t n);
+
+/* Test hook for the bounded waits of fq_bfs_run_multi (the thesis has no counterpart): while
+ * extra_arrivals > 0, every level barrier waits for that many more CTAs than the grid holds, so
+ * none releases and each wait gives up after spin_limit polls (0 keeps the built-in bound of
+ * 2^24 polls, about 2 s); the call then returns FQ_ETIMEOUT with the GPU context intact.  It
+ * exists so that tests can drive the timeout exit path without faulting anything.  Process-wide;
+ * (0, 0) restores normal barriers.  FQ_EINVAL if extra_arrivals > 1024. */
+fq_status fq_msbfs_barrier_test(uint32_t extra_arrivals, uint32_t spin_limit);
 fq_status fq_bfs_run_multi(const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, const uint32_t *h_roots,
                            uint32_t k, int32_t *d_depth, void *d_scratch, uint64_t scratch_bytes,
                            fq_bfs_stats *h_stats, void *stream);

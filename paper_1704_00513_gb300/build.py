@@ -64,7 +64,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
                 print(log)
     if _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

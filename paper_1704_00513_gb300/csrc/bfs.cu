@@ -22,6 +22,8 @@
 #include <mutex>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fq_common.cuh"
 
 using namespace fq;
@@ -52,7 +54,8 @@ struct Counters {
     int32_t r_err_q, r_err_v;
     uint32_t r_where_q, r_where_v;
     unsigned long long r_detail_q, r_detail_v;
-    unsigned long long pad[15];
+    unsigned long long n_iso;      // degree-0 vertices (counted by iso_kernel at handle creation)
+    unsigned long long pad[14];
 };
 static_assert(sizeof(Counters) == 256, "counter block is 256 bytes");
 
@@ -69,7 +72,8 @@ struct LoopState {
     unsigned long long log_used;
     uint32_t d, dir;
     int32_t status, soft_status;  // a hard error stops the loop; ENOSPC of the log does not
-    uint32_t coded, pad;          // this level runs the codec stage (the frontier reaches the threshold)
+    uint32_t coded;               // this level runs the codec stage (the frontier reaches the threshold)
+    uint32_t root_iso;            // the root has degree 0 (it is visited, and isolated)
     fq_bfs_stats stats;
 };
 constexpr uint32_t kMaxDeviceRecords = 4096;
@@ -120,10 +124,12 @@ __global__ void bfs_init_kernel(const int64_t *off, uint32_t root, uint64_t n, i
     }
 }
 
-// Bitmap of the zero-degree vertices: they are never reached, so the sweep treats them as done.
-__global__ void iso_kernel(const int64_t *off, uint64_t n, uint32_t *iso32)
+// Bitmap of the zero-degree vertices (they are never reached, so the sweep treats them as done),
+// and their number.
+__global__ void iso_kernel(const int64_t *off, uint64_t n, uint32_t *iso32, unsigned long long *count)
 {
     const uint64_t nw = (n + 31) / 32;
+    unsigned long long c = 0;
     for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t m = 0;
         for (uint32_t b = 0; b < 32; b++) {
@@ -131,7 +137,38 @@ __global__ void iso_kernel(const int64_t *off, uint64_t n, uint32_t *iso32)
             if (v < n && off[v + 1] == off[v]) m |= 1u << b;
         }
         iso32[w] = m;
+        c += __popc(m);
     }
+    c = warp_sum64(c);
+    if ((threadIdx.x & 31u) == 0 && c) atomicAdd(count, c);
+}
+
+// The design model of one level's algorithmic bytes per kernel class (fq_bfs_level_bytes, which
+// documents each term), added into out[].  Shared by both level-loop drivers and the host-side
+// entry point, so the bench's roofline numerator can be recomputed from the level records.
+struct LevelIn {
+    uint64_t n, n_iso, visited, n_f, examined, n_f_next, qb, bb, vb;
+    uint32_t dir, root_iso;
+    bool coded, want_v;
+};
+
+__host__ __device__ inline void level_bytes(const LevelIn &x, uint64_t *out)
+{
+    const uint64_t nbytes = (x.n + 7) / 8;
+    if (x.coded) out[FQ_K_ENCODE] += 4 * x.n_f + x.qb + nbytes + x.bb;
+    if (x.want_v) out[FQ_K_ENCODE] += nbytes + x.vb;
+    if (x.dir == FQ_TOP_DOWN) {
+        if (x.coded) out[FQ_K_DECODE] += x.qb + 4 * x.n_f;
+        out[FQ_K_TOP_DOWN] += 4 * x.examined + 20 * x.n_f + 8 * x.n_f_next;
+    } else {
+        if (x.coded) out[FQ_K_DECODE] += x.bb + nbytes;
+        // the sweep reads the offsets pair of every vertex that is neither visited nor isolated;
+        // isolated vertices other than an isolated root are never visited
+        const uint64_t iso_unvisited = x.n_iso - (x.root_iso && x.n_iso ? 1u : 0u);
+        const uint64_t swept = x.n > x.visited + iso_unvisited ? x.n - x.visited - iso_unvisited : 0u;
+        out[FQ_K_BOTTOM_UP] += 4 * nbytes + 16 * swept + 4 * x.examined + 8 * x.n_f_next;
+    }
+    out[FQ_K_COMPACT] += 3 * nbytes + 20 * x.n_f_next;
 }
 
 // Top-down expansion of the decoded queue q[0..nf): each warp takes 32 frontier vertices,
@@ -499,7 +536,7 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
 // loop_end_kernel after it (records, statistics, termination), which set the graph's
 // conditional handles.
 
-__global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m)
+__global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m, uint64_t n_iso)
 {
     ls->n_f = ctr->n_f_next;
     ls->m_f = ctr->r_m_f;
@@ -510,7 +547,9 @@ __global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m)
     ls->dir = FQ_TOP_DOWN;
     ls->status = FQ_OK;
     ls->soft_status = FQ_OK;
+    ls->root_iso = ls->m_f == 0 ? 1u : 0u;
     memset(&ls->stats, 0, sizeof(ls->stats));
+    ls->stats.isolated = n_iso;
     ls->stats.kernel_launches[FQ_K_OTHER] = 2;  // bfs_init_kernel, loop_init_kernel
 }
 
@@ -564,7 +603,7 @@ __global__ void log_append_kernel(const LoopState *ls, const Counters *ctr, cons
 }
 
 __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_level_record *recs, uint64_t n,
-                                int codec, int want_v, int has_log, cudaGraphConditionalHandle h_while)
+                                uint64_t n_iso, int codec, int want_v, int has_log, cudaGraphConditionalHandle h_while)
 {
     // local copies: every load is issued up front, the state is written back once at the end
     LoopState lsv = *ls_out;
@@ -591,30 +630,17 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     const unsigned long long nbytes = (n + 7) / 8;
     const bool dense = 2ull * n_f > n;
 
-    if (coded) {
-        st.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + nbytes + bb;
-        st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
-    }
-    if (want_v) {
-        st.kernel_bytes[FQ_K_ENCODE] += nbytes + vb;
-        st.kernel_launches[FQ_K_ENCODE] += 2;
-    }
+    const LevelIn lin{n, n_iso, ls->visited, n_f, examined, nf_next, qb, bb, vb, dir, ls->root_iso, coded, want_v != 0};
+    level_bytes(lin, st.kernel_bytes);
+    if (coded) st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
+    if (want_v) st.kernel_launches[FQ_K_ENCODE] += 2;
     if (dir == FQ_TOP_DOWN) {
-        if (coded) {
-            st.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
-            st.kernel_launches[FQ_K_DECODE] += 3;
-        }
-        st.kernel_bytes[FQ_K_TOP_DOWN] += 4 * examined + 20 * n_f + 8 * nf_next;
+        if (coded) st.kernel_launches[FQ_K_DECODE] += 3;
         st.kernel_launches[FQ_K_TOP_DOWN] += 2;
     } else {
-        if (coded) {
-            st.kernel_bytes[FQ_K_DECODE] += bb + nbytes;
-            st.kernel_launches[FQ_K_DECODE] += 4;
-        }
-        st.kernel_bytes[FQ_K_BOTTOM_UP] += 3 * nbytes + 16 * (n - ls->visited) + 4 * examined + 8 * nf_next;
+        if (coded) st.kernel_launches[FQ_K_DECODE] += 4;
         st.kernel_launches[FQ_K_BOTTOM_UP] += 1;
     }
-    st.kernel_bytes[FQ_K_COMPACT] += 3 * nbytes + 20 * nf_next;
     st.kernel_launches[FQ_K_COMPACT] += 3;
     st.kernel_launches[FQ_K_OTHER] += 2 + (has_log ? 1 : 0);  // loop_begin, loop_end [, log_append]
 
@@ -640,6 +666,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
         r.b_bytes = bb;
         r.v_bytes = vb;
         r.log_offset = log_off;
+        for (int k = 0; k < FQ_NUM_KCLASS; k++) r.kernel_ms[k] = 0.f;
     }
     st.levels = d + 1;
     if (dir == FQ_BOTTOM_UP && d < 32) st.directions |= 1u << d;
@@ -673,8 +700,11 @@ struct fq_graph {
     const int64_t *off;
     const uint32_t *cols;
     uint64_t n, m, nwords;
+    uint64_t n_iso;   // vertices of degree 0
     int device;
     uint8_t *mem;
+    uint64_t mem_bytes;
+    fq_allocator alloc;  // the allocator mem came from (alloc == NULL: cudaMalloc)
     Counters *ctr;
     Scratch sq, sv;   // codec scratch: Q/B streams and decodes; V stream
     uint32_t *q, *q2;
@@ -706,6 +736,18 @@ namespace {
 uint64_t al256(uint64_t x) { return (x + 255u) / 256u * 256u; }
 constexpr uint64_t kHostLs = 256;  // offset of the LoopState copy in the pinned host block
 
+// NVTX range names of the kernel classes (FQ_K_*): the host-driven loop encloses each class's
+// launches in one range, so profilers can select a class by name.
+const char *const kClassRange[FQ_NUM_KCLASS] = {"fq:top_down", "fq:bottom_up", "fq:compact",
+                                                "fq:encode", "fq:decode", "fq:other"};
+
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
+
 struct Timer {
     fq_graph *g;
     cudaStream_t st;
@@ -714,18 +756,23 @@ struct Timer {
     uint64_t *launches;
     void begin(int k)
     {
+        nvtxRangePushA(kClassRange[k]);
         if (on) cudaEventRecord(g->ev[2 * k], st);
     }
     void end(int k, int nlaunch)
     {
         if (launches) launches[k] += nlaunch;
         if (on) cudaEventRecord(g->ev[2 * k + 1], st);
+        nvtxRangePop();
     }
-    void collect(int k)
+    // Adds the class's elapsed time since begin() to ms[k] and returns it (0 when not timing).
+    float collect(int k)
     {
-        if (!on) return;
+        if (!on) return 0.f;
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, g->ev[2 * k], g->ev[2 * k + 1]) == cudaSuccess) ms[k] += t;
+        if (cudaEventElapsedTime(&t, g->ev[2 * k], g->ev[2 * k + 1]) != cudaSuccess) return 0.f;
+        ms[k] += t;
+        return t;
     }
 };
 
@@ -862,6 +909,11 @@ cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
 // instantiation) and those calls therefore never overlap.
 std::mutex g_capture_mu;
 
+// The allocator fq_graph_create takes handle workspaces from (fq_set_allocator); alloc == NULL
+// selects cudaMalloc.
+std::mutex g_alloc_mu;
+fq_allocator g_alloc = {nullptr, nullptr, nullptr};
+
 cudaError_t capture_segment(cudaStream_t cs, cudaGraph_t *out, cudaError_t (*fn)(void *), void *ctx)
 {
     *out = nullptr;
@@ -920,7 +972,7 @@ cudaError_t seg_init(void *p)
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
     const cudaError_t r = step_init(c.g, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
     if (r != cudaSuccess) return r;
-    loop_init_kernel<<<1, 1, 0, c.g->dl_stream>>>(c.g->ls, c.g->ctr, c.g->m);
+    loop_init_kernel<<<1, 1, 0, c.g->dl_stream>>>(c.g->ls, c.g->ctr, c.g->m, c.g->n_iso);
     return cudaGetLastError();
 }
 cudaError_t seg_dense(void *p)
@@ -1051,8 +1103,9 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             const Counters *ctr = g->ctr;
             fq_level_record *recs = g->recs;
             uint64_t n = g->n;
+            uint64_t n_iso = g->n_iso;
             int codec = b.codec ? 1 : 0, want_v = b.want_v ? 1 : 0, has_log = b.log ? 1 : 0;
-            void *args[] = {&ls, &ctr, &recs, &n, &codec, &want_v, &has_log, &h_while};
+            void *args[] = {&ls, &ctr, &recs, &n, &n_iso, &codec, &want_v, &has_log, &h_while};
             if ((e = add_kernel_node(&tmp, body, &n_last, (void *)loop_end_kernel, args)) != cudaSuccess) goto done;
         }
     }
@@ -1068,9 +1121,44 @@ done:
     return cudaSuccess;
 }
 
+// Frees a handle; the caller holds g_capture_mu.
+void fq_graph_destroy_locked(fq_graph *g)
+{
+    cudaDeviceSynchronize();
+    if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
+    if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
+    if (g->dl_stream) cudaStreamDestroy(g->dl_stream);
+    for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    if (g->host) cudaFreeHost(g->host);
+    if (g->mem) {
+        if (g->alloc.alloc) g->alloc.release(g->mem, g->mem_bytes, g->alloc.ctx);
+        else cudaFree(g->mem);
+    }
+    delete g;
+}
+
 }  // namespace
 
 extern "C" {
+
+fq_status fq_set_allocator(const fq_allocator *a)
+{
+    if (a && (!a->alloc || !a->release)) return FQ_EINVAL;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc = a ? *a : fq_allocator{nullptr, nullptr, nullptr};
+    return FQ_OK;
+}
+
+void fq_bfs_level_bytes(uint64_t n, uint64_t n_isolated, uint32_t root_isolated, const fq_level_record *rec,
+                        uint64_t visited, uint64_t n_f_next, uint64_t *out)
+{
+    if (!rec || !out) return;
+    for (int k = 0; k < FQ_NUM_KCLASS; k++) out[k] = 0;
+    const LevelIn lin{n, n_isolated, visited, rec->n_f, rec->examined, n_f_next, rec->q_bytes, rec->b_bytes,
+                      rec->v_bytes, rec->direction, root_isolated ? 1u : 0u, rec->q_bytes > 0, rec->v_bytes > 0};
+    level_bytes(lin, out);
+}
 
 fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint64_t n, uint64_t m, fq_graph **out)
 {
@@ -1079,6 +1167,10 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     std::lock_guard<std::mutex> lock(g_capture_mu);
     fq_graph *g = new (std::nothrow) fq_graph();
     if (!g) return FQ_ENOMEM;
+    {
+        std::lock_guard<std::mutex> alock(g_alloc_mu);
+        g->alloc = g_alloc;
+    }
     g->off = d_offsets;
     g->cols = d_cols;
     g->n = n;
@@ -1114,15 +1206,28 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     const uint64_t o_vo = o; o = al256(o + 4 * g->cmp_tiles);
     const uint64_t o_ls = o; o = al256(o + sizeof(LoopState));
     const uint64_t o_recs = o; o = al256(o + sizeof(fq_level_record) * kMaxDeviceRecords);
-    if (cudaMalloc(&g->mem, o) != cudaSuccess) {
+    g->mem_bytes = o;
+    if (g->alloc.alloc) {
+        g->mem = static_cast<uint8_t *>(g->alloc.alloc(o, g->alloc.ctx));
+        if (g->mem && (reinterpret_cast<uintptr_t>(g->mem) & 255u)) {  // the contract asks for 256-byte alignment
+            g->alloc.release(g->mem, o, g->alloc.ctx);
+            delete g;
+            return FQ_EINVAL;
+        }
+    } else if (cudaMalloc(&g->mem, o) != cudaSuccess) {
         cudaGetLastError();
+        g->mem = nullptr;
+    }
+    if (!g->mem) {
         delete g;
         return FQ_ENOMEM;
     }
     if (cudaMallocHost(&g->host, kHostLs + al256(sizeof(LoopState)) + sizeof(fq_level_record) * kMaxDeviceRecords) !=
         cudaSuccess) {
         cudaGetLastError();
-        cudaFree(g->mem);
+        g->host = nullptr;
+        if (g->alloc.alloc) g->alloc.release(g->mem, o, g->alloc.ctx);
+        else cudaFree(g->mem);
         delete g;
         return FQ_ENOMEM;
     }
@@ -1148,14 +1253,18 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     g->recs = reinterpret_cast<fq_level_record *>(g->mem + o_recs);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++) cudaEventCreate(&g->ev[i]);
     if (cudaMemset(g->mem, 0, o) != cudaSuccess) {
-        fq_graph_destroy(g);
+        fq_graph_destroy_locked(g);
         return FQ_ECUDA;
     }
-    iso_kernel<<<(uint32_t)std::min<uint64_t>(cdiv(cdiv(n, 32), 256), 4096), 256>>>(d_offsets, n, g->iso32);
-    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
-        fq_graph_destroy(g);
+    iso_kernel<<<(uint32_t)std::min<uint64_t>(cdiv(cdiv(n, 32), 256), 4096), 256>>>(d_offsets, n, g->iso32,
+                                                                                     &g->ctr->n_iso);
+    unsigned long long n_iso = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&n_iso, &g->ctr->n_iso, sizeof(n_iso), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        fq_graph_destroy_locked(g);
         return FQ_ECUDA;
     }
+    g->n_iso = n_iso;
     *out = g;
     return FQ_OK;
 }
@@ -1164,15 +1273,7 @@ fq_status fq_graph_destroy(fq_graph *g)
 {
     if (!g) return FQ_EINVAL;
     std::lock_guard<std::mutex> lock(g_capture_mu);
-    cudaDeviceSynchronize();
-    if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
-    if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
-    if (g->dl_stream) cudaStreamDestroy(g->dl_stream);
-    for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++)
-        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
-    if (g->host) cudaFreeHost(g->host);
-    if (g->mem) cudaFree(g->mem);
-    delete g;
+    fq_graph_destroy_locked(g);
     return FQ_OK;
 }
 
@@ -1190,6 +1291,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     const bool want_visited = codec && (flags & FQ_BFS_VISITED_STREAM);
     const bool px = codec && (flags & FQ_BFS_PATCHED);
     const uint64_t n = g->n;
+    NvtxScope search_range((flags & FQ_BFS_DEVICE_LOOP) ? "fq_bfs_run:device_loop" : "fq_bfs_run:host_loop");
 
 #define FQ_TRY(expr)                                  \
     do {                                              \
@@ -1249,12 +1351,14 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             for (uint32_t d = 0; d < kept; d++) h_levels[d] = hrec[d];
         fq_bfs_stats stats = hls->stats;
         stats.reached_edges /= 2;
+        stats.isolated = g->n_iso;
         if (h_stats) *h_stats = stats;
         return (fq_status)hls->soft_status;
     }
 
     fq_bfs_stats stats;
     memset(&stats, 0, sizeof(stats));
+    stats.isolated = g->n_iso;
     Timer tm{g, st, (flags & FQ_BFS_TIMING) != 0, stats.kernel_ms, stats.kernel_launches};
 
     // ---- level 0 set-up
@@ -1269,6 +1373,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     uint64_t n_f = hc->n_f_next, m_f = hc->r_m_f;
     uint64_t visited_count = n_f;
     uint64_t m_u = g->m - m_f;
+    const uint32_t root_iso = m_f == 0 ? 1u : 0u;
     int dir = FQ_TOP_DOWN;
     uint64_t log_used = 0;
     fq_status result = FQ_OK;
@@ -1318,10 +1423,12 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
 
         FQ_TRY(cudaMemcpyAsync(g->host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         FQ_TRY(cudaStreamSynchronize(st));
-        tm.collect(FQ_K_ENCODE);
-        tm.collect(FQ_K_DECODE);
-        tm.collect(dir == FQ_TOP_DOWN ? FQ_K_TOP_DOWN : FQ_K_BOTTOM_UP);
-        tm.collect(FQ_K_COMPACT);
+        float lms[FQ_NUM_KCLASS] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        lms[FQ_K_ENCODE] = tm.collect(FQ_K_ENCODE);
+        lms[FQ_K_DECODE] = tm.collect(FQ_K_DECODE);
+        const int xk = dir == FQ_TOP_DOWN ? FQ_K_TOP_DOWN : FQ_K_BOTTOM_UP;
+        lms[xk] = tm.collect(xk);
+        lms[FQ_K_COMPACT] = tm.collect(FQ_K_COMPACT);
         if (hc->r_err_q != FQ_OK) return hc->r_err_q;
         if (hc->r_err_v != FQ_OK) return hc->r_err_v;
         if (coded && dir == FQ_TOP_DOWN && hc->dec_n != n_f) return FQ_ECORRUPT;
@@ -1331,16 +1438,9 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         const uint64_t qb = coded ? hc->q_bytes : 0, bb = coded ? hc->b_bytes : 0, vb = want_visited ? hc->v_bytes : 0;
 
         // algorithmic bytes of this level (design model)
-        if (coded) stats.kernel_bytes[FQ_K_ENCODE] += 4 * n_f + qb + (n + 7) / 8 + bb;
-        if (want_visited) stats.kernel_bytes[FQ_K_ENCODE] += (n + 7) / 8 + vb;
-        if (dir == FQ_TOP_DOWN) {
-            if (coded) stats.kernel_bytes[FQ_K_DECODE] += qb + 4 * n_f;
-            stats.kernel_bytes[FQ_K_TOP_DOWN] += 4 * examined + 20 * n_f + 8 * nf_next;
-        } else {
-            if (coded) stats.kernel_bytes[FQ_K_DECODE] += bb + (n + 7) / 8;
-            stats.kernel_bytes[FQ_K_BOTTOM_UP] += 3 * ((n + 7) / 8) + 16 * (n - visited_count) + 4 * examined + 8 * nf_next;
-        }
-        stats.kernel_bytes[FQ_K_COMPACT] += 3 * ((n + 7) / 8) + 20 * nf_next;
+        const LevelIn lin{n, g->n_iso, visited_count, n_f, examined, nf_next, qb, bb, vb, (uint32_t)dir, root_iso,
+                          coded, want_visited};
+        level_bytes(lin, stats.kernel_bytes);
 
         uint64_t log_off = ~0ull;
         if (d_stream_log && codec && (coded || want_visited)) {
@@ -1367,6 +1467,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             r.b_bytes = bb;
             r.v_bytes = vb;
             r.log_offset = log_off;
+            for (int k = 0; k < FQ_NUM_KCLASS; k++) r.kernel_ms[k] = lms[k];
         }
         stats.levels = d + 1;
         if (dir == FQ_BOTTOM_UP && d < 32) stats.directions |= 1u << d;

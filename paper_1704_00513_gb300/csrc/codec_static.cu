@@ -16,7 +16,11 @@
 
 namespace {
 
-// Scratch for encoding up to FQ_STATIC_MAX_IDS ids (about 1.7 MB is used; 2 MiB reserved).
+// Scratch for encoding up to FQ_STATIC_MAX_IDS ids: the encoder's workspace layout for 2^24 ids
+// takes 1,344,256 bytes (status record 256; per 128-id block a width byte, a u32 base, a u32
+// block offset and an exception byte, 10 B x 131,072 blocks; per 8,192-id tile four u32 sums,
+// 4 x 8 KiB; two bitmap-tile words, padded to 256 B each).  2 MiB are reserved, and every call
+// checks its own layout against them.
 constexpr size_t kStaticScratchBytes = 2u << 20;
 static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
 
@@ -53,11 +57,19 @@ extern "C" fq_status fq_frontier_encode_static(const uint32_t *d_ids, uint64_t n
     if (n > FQ_STATIC_MAX_IDS) return FQ_EINVAL;  // beyond the fixed scratch: nothing is enqueued
     if (fq::workspace_bytes(n, 0) > kStaticScratchBytes) return FQ_EINVAL;
     void *scratch = nullptr;
-    if (static_scratch_address(&scratch) != cudaSuccess) return FQ_ECUDA;
+    cudaError_t e = static_scratch_address(&scratch);
+    if (e != cudaSuccess) {
+        fq::note_cuda_error(e, __LINE__);
+        return FQ_ECUDA;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     fq::Scratch s = fq::carve(scratch, n, 0);
     // the status record must start cleared; the rest is rewritten by each call
-    cudaError_t e = fq::reset_status(s, n, st);
+    e = fq::reset_status(s, n, st);
     if (e == cudaSuccess) e = fq::encode_fq(d_ids, n, nullptr, n, d_out, cap, d_out_bytes, s, st);
-    return e == cudaSuccess ? FQ_OK : FQ_ECUDA;
+    if (e != cudaSuccess) {
+        fq::note_cuda_error(e, __LINE__);
+        return FQ_ECUDA;
+    }
+    return FQ_OK;
 }

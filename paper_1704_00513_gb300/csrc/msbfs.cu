@@ -17,6 +17,7 @@
 // The grid barriers spin with a bound; a barrier that gives up sets FQ_ETIMEOUT and every CTA
 // leaves at its next barrier.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -46,7 +47,12 @@ struct MsState {
     unsigned long long *stats;       // [8]: levels, edges examined, reached pairs, reached edges x2
     Ctl *err;
     uint32_t max_levels;
+    uint32_t bar_extra;   // test hook: arrivals a barrier waits for beyond the grid (0 normally)
+    uint32_t spin_limit;  // polls before a barrier wait gives up
 };
+
+// fq_msbfs_barrier_test settings, read at each launch.
+std::atomic<uint32_t> g_bar_extra{0}, g_bar_spins{0};
 
 __device__ __forceinline__ bool grid_sync(const MsState &s, int *s_abort)
 {
@@ -55,14 +61,14 @@ __device__ __forceinline__ bool grid_sync(const MsState &s, int *s_abort)
         volatile unsigned int *gen = s.bar + 1;
         const unsigned int my_gen = *gen;
         __threadfence();
-        if (atomicAdd(s.bar, 1u) == gridDim.x - 1) {
+        if (atomicAdd(s.bar, 1u) == gridDim.x - 1 + s.bar_extra) {
             s.bar[0] = 0;
             __threadfence();
             atomicAdd(s.bar + 1, 1u);
         } else {
             uint32_t spins = 0;
             while (*gen == my_gen) {
-                if (++spins > kBarrierSpins || *reinterpret_cast<volatile unsigned int *>(s.abort_flag)) {
+                if (++spins > s.spin_limit || *reinterpret_cast<volatile unsigned int *>(s.abort_flag)) {
                     if (atomicExch(s.abort_flag, 1u) == 0u) set_error(s.err, FQ_ETIMEOUT, kWhereBfs, 0);
                     break;
                 }
@@ -274,6 +280,14 @@ uint64_t al256m(uint64_t x) { return (x + 255u) / 256u * 256u; }
 
 extern "C" {
 
+fq_status fq_msbfs_barrier_test(uint32_t extra_arrivals, uint32_t spin_limit)
+{
+    if (extra_arrivals > 1024u) return FQ_EINVAL;
+    g_bar_extra.store(extra_arrivals);
+    g_bar_spins.store(spin_limit);
+    return FQ_OK;
+}
+
 uint64_t fq_msbfs_scratch_bytes(uint64_t n)
 {
     const uint64_t G = 4096;  // upper bound on the cooperative grid
@@ -324,6 +338,9 @@ fq_status fq_bfs_run_multi(const int64_t *d_offsets, const uint32_t *d_cols, uin
     s.k = k;
     s.depth = d_depth;
     s.max_levels = (uint32_t)std::min<uint64_t>(n + 1, 0x7fffffffu);
+    s.bar_extra = g_bar_extra.load();
+    const uint32_t spins = g_bar_spins.load();
+    s.spin_limit = spins ? spins : kBarrierSpins;
 
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FQ_ECUDA;

@@ -47,13 +47,22 @@ class fq_bfs_stats(ctypes.Structure):
     _fields_ = [("levels", _u32), ("directions", _u32), ("reached", _u64), ("reached_edges", _u64),
                 ("edges_examined", _u64), ("raw_queue_bytes", _u64), ("enc_queue_bytes", _u64),
                 ("raw_bitmap_bytes", _u64), ("enc_bitmap_bytes", _u64), ("enc_visited_bytes", _u64),
-                ("kernel_ms", ctypes.c_double * 6), ("kernel_launches", _u64 * 6), ("kernel_bytes", _u64 * 6)]
+                ("kernel_ms", ctypes.c_double * 6), ("kernel_launches", _u64 * 6), ("kernel_bytes", _u64 * 6),
+                ("isolated", _u64)]
 
 
 class fq_level_record(ctypes.Structure):
     _fields_ = [("level", _u32), ("direction", _u32), ("n_f", _u64), ("m_f", _u64), ("m_u", _u64),
                 ("examined", _u64), ("q_bytes", _u64), ("b_bytes", _u64), ("v_bytes", _u64),
-                ("log_offset", _u64)]
+                ("log_offset", _u64), ("kernel_ms", ctypes.c_float * 6)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(_vp, _u64, _vp)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, _vp, _u64, _vp)
+
+
+class fq_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("release", _RELEASE_FN), ("ctx", _vp)]
 
 
 _lib = None
@@ -84,6 +93,9 @@ _SIGS = {
     "fq_bfs_run_multi": ([_vp, _vp, _u64, ctypes.POINTER(_u32), _u32, _vp, _vp, _u64, ctypes.POINTER(fq_bfs_stats), _vp],
                          _i32),
     "fq_graph_create": ([_vp, _vp, _u64, _u64, ctypes.POINTER(_vp)], _i32),
+    "fq_set_allocator": ([ctypes.POINTER(fq_allocator)], _i32),
+    "fq_bfs_level_bytes": ([_u64, _u64, _u32, ctypes.POINTER(fq_level_record), _u64, _u64, ctypes.POINTER(_u64)], None),
+    "fq_msbfs_barrier_test": ([_u32, _u32], _i32),
     "fq_graph_destroy": ([_vp], _i32),
     "fq_bfs_run": ([_vp, _u32, _vp, _vp, ctypes.POINTER(fq_bfs_opts), ctypes.POINTER(fq_bfs_stats),
                     ctypes.POINTER(fq_level_record), _u32, _vp, _u64, _vp], _i32),
@@ -329,8 +341,8 @@ class Batch:
         assert seg_off.is_cuda and seg_off.dtype == torch.int64
         self.seg_off = seg_off.contiguous()
         self.S = seg_off.numel() - 1
-        lens = (seg_off[1:] - seg_off[:-1]).cpu()
-        caps = 16 + (4 * lens + 15) // 16 * 16
+        lens = (seg_off[1:] - seg_off[:-1]).cpu().tolist()
+        caps = torch.tensor([fq_queue_bound(x) for x in lens], dtype=torch.int64)
         self.out_off = torch.zeros(self.S + 1, dtype=torch.int64)
         self.out_off[1:] = torch.cumsum(caps, 0)
         self.out_off = self.out_off.to(seg_off.device)
@@ -371,6 +383,36 @@ class BfsResult:
     levels: list
     stream_log: torch.Tensor | None = None
     streams: list = field(default_factory=list)
+
+
+def level_bytes(n: int, n_isolated: int, root_isolated: bool, record: dict, visited: int, n_f_next: int) -> dict:
+    """The library's design model of one level's algorithmic bytes per kernel class
+    (fq_bfs_level_bytes); `record` is a level record as BfsResult.levels holds it."""
+    r = fq_level_record()
+    for k, _ in fq_level_record._fields_:
+        if k != "kernel_ms":
+            setattr(r, k, int(record[k]))
+    out = (_u64 * 6)()
+    lib().fq_bfs_level_bytes(n, n_isolated, 1 if root_isolated else 0, ctypes.byref(r), visited, n_f_next, out)
+    return dict(zip(KCLASS, list(out)))
+
+
+def set_allocator(alloc=None, release=None):
+    """Route the device memory of graph handles created from now on through alloc(bytes) -> int
+    device address (0 on failure) and release(address, bytes); set_allocator() restores
+    cudaMalloc.  The callbacks stay referenced until the next call."""
+    global _allocator_keep
+    if alloc is None:
+        _allocator_keep = None
+        _check(lib().fq_set_allocator(None), "fq_set_allocator")
+        return
+    a = fq_allocator(_ALLOC_FN(lambda nbytes, ctx: alloc(int(nbytes)) or None),
+                     _RELEASE_FN(lambda ptr, nbytes, ctx: release(int(ptr or 0), int(nbytes))), None)
+    _allocator_keep = a
+    _check(lib().fq_set_allocator(ctypes.byref(a)), "fq_set_allocator")
+
+
+_allocator_keep = None
 
 
 def _stats_dict(s: fq_bfs_stats) -> dict:
@@ -455,7 +497,9 @@ class Graph:
         lv = []
         for i in range(min(stats.levels, max_levels)):
             r = levels[i]
-            lv.append({k: getattr(r, k) for k, _ in fq_level_record._fields_})
+            rec = {k: getattr(r, k) for k, _ in fq_level_record._fields_ if k != "kernel_ms"}
+            rec["kernel_ms"] = dict(zip(KCLASS, [float(x) for x in r.kernel_ms]))
+            lv.append(rec)
         res = BfsResult(depth, parent, _stats_dict(stats), lv, log)
         if record_streams:
             for r in lv:

@@ -58,6 +58,13 @@ def test_host_size_functions_match_stream_definitions(lib):
     assert lib.fq_status_string(4) == b"FQ_ECORRUPT"
 
 
+def test_static_encoder_limit_fits_its_fixed_scratch(lib):
+    # fq_frontier_encode_static keeps its scratch in a fixed 2 MiB device array: the workspace of an
+    # encode at its documented limit (2^24 ids) must fit, one id more need not be accepted
+    limit = 1 << 24
+    assert fqbfs.fq_workspace_bytes(limit, 0) == 1_344_256 <= 2 << 20
+
+
 def test_status_strings_name_every_code(lib):
     names = ["FQ_OK", "FQ_EINVAL", "FQ_ENOMEM", "FQ_ENOSPC", "FQ_ECORRUPT", "FQ_EUNSORTED", "FQ_ETIMEOUT", "FQ_ECUDA",
              "FQ_EBUSY"]

@@ -116,3 +116,60 @@ def test_tuning_calls_reject_out_of_range(lib):
     assert lib.fq_tune_get(7, 10) == 0 and lib.fq_tune_get(0, 41) == 0
     assert lib.fq_tune_set(2, 20, 8) == fqbfs.FQ_OK and lib.fq_tune_get(2, 20) == 8
     assert lib.fq_tune_set(2, 20, 0) == fqbfs.FQ_OK and lib.fq_tune_get(2, 20) == 0
+
+
+class _CountingAllocator:
+    """An fq_allocator whose alloc hands out fake aligned addresses (or fails), counting every
+    allocation and release, so a test sees whether a failed create leaves anything behind."""
+
+    def __init__(self, fail: bool):
+        self.fail = fail
+        self.live = {}
+        self.calls = 0
+
+    def alloc(self, nbytes):
+        self.calls += 1
+        if self.fail:
+            return 0
+        addr = 0x7f0000000000 + 0x100000000 * self.calls   # 256-byte aligned, never dereferenced
+        self.live[addr] = nbytes
+        return addr
+
+    def release(self, addr, nbytes):
+        assert self.live.pop(addr) == nbytes
+
+
+def test_graph_create_reports_enomem_when_the_workspace_allocation_fails(lib):
+    a = _CountingAllocator(fail=True)
+    fqbfs.set_allocator(a.alloc, a.release)
+    try:
+        h = ctypes.c_void_p()
+        assert lib.fq_graph_create(A, B, 1000, 5000, ctypes.byref(h)) == fqbfs.FQ_ENOMEM
+        assert not h.value and a.calls == 1 and not a.live
+    finally:
+        fqbfs.set_allocator()
+
+
+def test_graph_create_releases_the_workspace_when_a_later_allocation_fails(lib):
+    # the workspace comes from the hook; the pinned host record that follows cannot be allocated on a
+    # machine without a GPU, so the create must fail with FQ_ENOMEM and hand the workspace back
+    a = _CountingAllocator(fail=False)
+    fqbfs.set_allocator(a.alloc, a.release)
+    try:
+        h = ctypes.c_void_p()
+        assert lib.fq_graph_create(A, B, 1000, 5000, ctypes.byref(h)) == fqbfs.FQ_ENOMEM
+        assert not h.value and a.calls == 1 and not a.live
+    finally:
+        fqbfs.set_allocator()
+
+
+def test_set_allocator_rejects_a_hook_without_release(lib):
+    half = fqbfs.fq_allocator()
+    half.alloc = fqbfs._ALLOC_FN(lambda nbytes, ctx: None)
+    assert lib.fq_set_allocator(ctypes.byref(half)) == EINVAL
+    assert lib.fq_set_allocator(None) == fqbfs.FQ_OK
+
+
+def test_msbfs_barrier_test_hook_arguments(lib):
+    assert lib.fq_msbfs_barrier_test(1025, 0) == EINVAL
+    assert lib.fq_msbfs_barrier_test(0, 0) == fqbfs.FQ_OK

@@ -49,6 +49,7 @@ def check_run(g, off, cols, root, flags=0, streams=True, visited=True):
             assert r["examined"] == oracle.bu_examined(off, cols, ref_depth, r["level"])
     if streams:
         ref = oracle.level_streams(ref_depth, record_visited=visited)
+        assert len(res.streams) == len(ref) == len(sched)
         for got, want in zip(res.streams, ref):
             assert np.array_equal(got["Q"].cpu().numpy(), want["Q"]), got["level"]
             assert np.array_equal(got["B"].cpu().numpy(), want["B"]), got["level"]
@@ -134,36 +135,51 @@ def test_small_graph_shapes(case, loop):
     g.close()
 
 
-def test_rmat24_full_size_sampled_roots():
-    """Scale 24 (16.7M vertices, ~0.5B directed edges) in the launch configuration the benchmark
-    times: two roots checked end to end against the oracle (depths exact, tree valid, schedule
-    equal); the streams of the largest level compared byte for byte."""
+@pytest.fixture(scope="module")
+def rmat24():
     off_d, cols_d = inputs.rmat_csr(24, 16, seed=20170402, device="cuda")
     roots = inputs.pick_roots(off_d, 64, seed=20170402)
-    g = fqbfs.Graph(off_d, cols_d)
     off = off_d.cpu().numpy()
     cols = cols_d.cpu().numpy().view(np.uint32)
-    for root in (roots[0], roots[37]):
-        res = g.bfs(root, flags=fqbfs.FQ_BFS_VISITED_STREAM, record_streams=True)
-        depth = res.depth.cpu().numpy()
-        parent = res.parent.cpu().numpy().view(np.uint32)
-        ref_depth, _ = oracle.bfs(off, cols, root)
-        assert np.array_equal(depth, ref_depth)
-        assert oracle.validate(off, cols, root, depth, parent) == 0
-        sched = oracle.level_schedule(off, cols, ref_depth)
-        for got, want in zip(res.levels, sched):
-            for k in ("n_f", "m_f", "m_u", "direction", "examined"):
-                assert got[k] == want[k], (got["level"], k)
-        big = max(range(len(res.levels)), key=lambda i: res.levels[i]["n_f"])
-        for d in (0, big, len(res.levels) - 1):
-            f = np.nonzero(ref_depth == d)[0].astype(np.uint32)
-            st, q = oracle.fq_encode(f)
-            st, b = oracle.fb_encode(oracle.ids_to_bitmap(f, off.size - 1), off.size - 1)
-            assert np.array_equal(res.streams[d]["Q"].cpu().numpy(), q)
-            assert np.array_equal(res.streams[d]["B"].cpu().numpy(), b)
-            st, v = oracle.fb_encode(oracle.ids_to_bitmap(np.nonzero((ref_depth >= 0) & (ref_depth <= d))[0], off.size - 1),
-                                     off.size - 1)
-            assert np.array_equal(res.streams[d]["V"].cpu().numpy(), v)
+    yield off_d, cols_d, off, cols, roots
+    del off_d, cols_d
+    torch.cuda.empty_cache()
+
+
+def _oracle_root(off, cols, root):
+    """Everything the oracle says about one root: depths, schedule, every level's streams.  The
+    oracle's C calls release the GIL, so roots run in parallel threads."""
+    ref_depth, _ = oracle.bfs(off, cols, root)
+    return ref_depth, oracle.level_schedule(off, cols, ref_depth), oracle.level_streams(ref_depth, record_visited=True)
+
+
+def test_rmat24_full_size_every_level_eight_roots(rmat24):
+    """Scale 24 (16.7M vertices, ~0.5B directed edges) in the launch configuration the benchmark
+    times (device-driven loop, Q_d, B_d and V_d every level): eight of the benchmark's roots checked
+    end to end against the oracle -- depths exact, tree valid, the per-level schedule equal, and
+    every level's three streams byte for byte, with as many streams as the oracle has levels.  Two
+    of the roots also run through the host-driven loop, which must agree on everything."""
+    import concurrent.futures as cf
+    off_d, cols_d, off, cols, roots = rmat24
+    picked = [roots[i] for i in (0, 5, 11, 19, 26, 37, 48, 63)]
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        refs = list(ex.map(lambda r: _oracle_root(off, cols, r), picked))
+    g = fqbfs.Graph(off_d, cols_d)
+    flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP
+    for i, (root, (ref_depth, sched, ref_streams)) in enumerate(zip(picked, refs)):
+        for loop in ([flags, fqbfs.FQ_BFS_VISITED_STREAM] if i < 2 else [flags]):
+            res = g.bfs(root, flags=loop, record_streams=True, max_levels=64)
+            depth = res.depth.cpu().numpy()
+            assert np.array_equal(depth, ref_depth), (root, loop)
+            assert oracle.validate(off, cols, root, depth, res.parent.cpu().numpy().view(np.uint32)) == 0
+            assert res.stats["levels"] == len(sched) == len(res.levels) == len(res.streams) == len(ref_streams)
+            for got, want in zip(res.levels, sched):
+                for k in ("n_f", "m_f", "m_u", "direction", "examined"):
+                    assert got[k] == want[k], (root, got["level"], k)
+            for got, want in zip(res.streams, ref_streams):
+                for k in ("Q", "B", "V"):
+                    assert got[k].numel() == want[k].size, (root, got["level"], k)
+                    assert np.array_equal(got[k].cpu().numpy(), want[k]), (root, got["level"], k)
     g.close()
 
 
