@@ -283,6 +283,15 @@ fq_status fq_set_allocator(const fq_allocator *a);
                                       exceptions, as fq_frontier_encode_px writes them) instead of FQ;
                                       B_d is then encoded from the bitmap rather than mirrored.  The
                                       top-down level decodes FQX like FQ.                          */
+#define FQ_BFS_OVERLAP 0x80u       /* overlap the codec stage with the expansion (overlapped
+                                      communication and software pipelining, sec. 6.5.2): each level
+                                      expands the raw frontier (queue or bitmap) while, beside it on a
+                                      second stream (host-driven loop) or a parallel graph branch
+                                      (device-driven loop), Q_d and B_d are encoded and the form the
+                                      direction consumes is decoded and compared with the raw one
+                                      (FQ_ECORRUPT on any difference); the compaction waits for both.
+                                      Depths, records, statistics and streams are those of the serial
+                                      codec stage.  Ignored with FQ_BFS_NO_CODEC.                  */
 #define FQ_BFS_DEVICE_LOOP 0x20u   /* run the level loop on the device: one CUDA graph (built on
                                       the first call per handle, output buffers and stream-log
                                       buffer, then reused) whose while node repeats the level and

@@ -530,6 +530,39 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
     if (want_v) extract_words(y, wbase, ov, sv.positions, lane, stage);
 }
 
+// ---- round-trip check of the overlapped codec stage (FQ_BFS_OVERLAP) ----
+// With the overlap the expansion consumes the raw frontier, so the decoded form is not consumed;
+// these kernels verify it instead: the decoded queue must equal the raw queue (and hold n_f ids),
+// the decoded bitmap the raw bitmap.  A difference is reported as FQ_ECORRUPT in the codec status
+// (detail: the first differing index), which the compaction's snapshot hands to the loop.
+
+__global__ void rt_check_queue_kernel(const uint32_t *__restrict__ q, const uint32_t *__restrict__ q2, uint64_t nf,
+                                      const unsigned long long *dec_n, Ctl *err, const LoopState *ls)
+{
+    if (ls) nf = ls->n_f;
+    const unsigned long long got = *dec_n;
+    if (got != nf) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_error(err, FQ_ECORRUPT, kWhereBfs, got < nf ? got : nf);
+        return;
+    }
+    const uint64_t nv = nf / 4;  // both queues start 256-byte aligned: 128-bit compares, then the tail
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+        const uint4 a = reinterpret_cast<const uint4 *>(q)[i], b = reinterpret_cast<const uint4 *>(q2)[i];
+        if (a.x != b.x || a.y != b.y || a.z != b.z || a.w != b.w) set_error(err, FQ_ECORRUPT, kWhereBfs, 4 * i);
+    }
+    const uint64_t t = 4 * nv + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nf && q[t] != q2[t]) set_error(err, FQ_ECORRUPT, kWhereBfs, t);
+}
+
+__global__ void rt_check_bitmap_kernel(const uint64_t *__restrict__ a, const uint64_t *__restrict__ b, uint64_t nwords,
+                                       Ctl *err)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride)
+        if (a[i] != b[i]) set_error(err, FQ_ECORRUPT, kWhereBfs, i);
+}
+
 // ---- the device-driven level loop (FQ_BFS_DEVICE_LOOP) ----
 // The same level as the host-driven loop, with the host's per-level decisions taken by two
 // one-thread kernels: loop_begin_kernel before the level (encode form, direction) and
@@ -558,7 +591,7 @@ __global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m,
 // Handles set here: h_enc (0 queue + mirrored bitmap, 1 queue + bitmap from the bitmap, 2 no codec
 // stage) and h_dir (0 top-down, 1 bottom-up, +2 when the level skips the codec stage).
 __global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGraphConditionalHandle h_enc,
-                                  cudaGraphConditionalHandle h_dir)
+                                  cudaGraphConditionalHandle h_dir, int overlap, cudaGraphConditionalHandle h_chk)
 {
     const uint32_t flags = ls->p.flags;
     const unsigned long long alpha = ls->p.alpha, beta = ls->p.beta;
@@ -572,6 +605,8 @@ __global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGrap
     ls->coded = coded ? 1u : 0u;
     if (codec) cudaGraphSetConditional(h_enc, !coded ? 2u : (2ull * ls->n_f > n ? 1u : 0u));
     cudaGraphSetConditional(h_dir, (dir == FQ_TOP_DOWN ? 0u : 1u) + (coded ? 0u : 2u));
+    // overlap: the round-trip check of the form this direction would consume (2: nothing to check)
+    if (overlap) cudaGraphSetConditional(h_chk, coded ? (dir == FQ_TOP_DOWN ? 0u : 1u) : 2u);
 }
 
 // Appends the level's Q_d, B_d [, V_d] to the stream log when they fit (the test loop_end_kernel
@@ -603,7 +638,8 @@ __global__ void log_append_kernel(const LoopState *ls, const Counters *ctr, cons
 }
 
 __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_level_record *recs, uint64_t n,
-                                uint64_t n_iso, int codec, int want_v, int has_log, cudaGraphConditionalHandle h_while)
+                                uint64_t n_iso, int codec, int want_v, int has_log, int overlap,
+                                cudaGraphConditionalHandle h_while)
 {
     // local copies: every load is issued up front, the state is written back once at the end
     LoopState lsv = *ls_out;
@@ -635,10 +671,10 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     if (coded) st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
     if (want_v) st.kernel_launches[FQ_K_ENCODE] += 2;
     if (dir == FQ_TOP_DOWN) {
-        if (coded) st.kernel_launches[FQ_K_DECODE] += 3;
+        if (coded) st.kernel_launches[FQ_K_DECODE] += 3 + (overlap ? 1 : 0);
         st.kernel_launches[FQ_K_TOP_DOWN] += 2;
     } else {
-        if (coded) st.kernel_launches[FQ_K_DECODE] += 4;
+        if (coded) st.kernel_launches[FQ_K_DECODE] += 4 + (overlap ? 1 : 0);
         st.kernel_launches[FQ_K_BOTTOM_UP] += 1;
     }
     st.kernel_launches[FQ_K_COMPACT] += 3;
@@ -718,6 +754,8 @@ struct fq_graph {
     uint64_t cmp_tiles;
     uint8_t *host;  // pinned: Counters copy, then LoopState and level records (device-driven loop)
     cudaEvent_t ev[2 * FQ_NUM_KCLASS];
+    cudaStream_t ov_stream;  // FQ_BFS_OVERLAP, host-driven loop: the codec stage's stream
+    cudaEvent_t ov_ev[2];    //   fork (after the previous compaction) and join (before this one)
     // device-driven level loop: state, records and the cached executable graph with its key
     LoopState *ls;
     fq_level_record *recs;
@@ -754,15 +792,17 @@ struct Timer {
     bool on;
     double *ms;
     uint64_t *launches;
+    cudaStream_t cls_st[FQ_NUM_KCLASS];  // the stream each class's launches go to (0: st)
+    cudaStream_t of(int k) const { return cls_st[k] ? cls_st[k] : st; }
     void begin(int k)
     {
         nvtxRangePushA(kClassRange[k]);
-        if (on) cudaEventRecord(g->ev[2 * k], st);
+        if (on) cudaEventRecord(g->ev[2 * k], of(k));
     }
     void end(int k, int nlaunch)
     {
         if (launches) launches[k] += nlaunch;
-        if (on) cudaEventRecord(g->ev[2 * k + 1], st);
+        if (on) cudaEventRecord(g->ev[2 * k + 1], of(k));
         nvtxRangePop();
     }
     // Adds the class's elapsed time since begin() to ms[k] and returns it (0 when not timing).
@@ -874,6 +914,21 @@ cudaError_t step_decode_b(fq_graph *g, cudaStream_t st)
     return decode_fb(g->bs, 0, reinterpret_cast<const uint64_t *>(&g->ctr->b_bytes), g->fbits2, g->n, g->sq, st);
 }
 
+// Overlap: the decoded queue / bitmap compared with the raw one the expansion consumes.
+cudaError_t step_check_q(fq_graph *g, uint64_t n_f, const LoopState *ls, cudaStream_t st)
+{
+    const uint64_t nmax = ls ? g->n : n_f;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, cdiv(nmax, 4 * 256)), 4 * (uint64_t)num_sms());
+    rt_check_queue_kernel<<<grid, 256, 0, st>>>(g->q, g->q2, n_f, &g->ctr->dec_n, g->sq.ctl, ls);
+    return cudaGetLastError();
+}
+cudaError_t step_check_b(fq_graph *g, cudaStream_t st)
+{
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, cdiv(g->nwords, 256)), 4 * (uint64_t)num_sms());
+    rt_check_bitmap_kernel<<<grid, 256, 0, st>>>(g->fbits, g->fbits2, g->nwords, g->sq.ctl);
+    return cudaGetLastError();
+}
+
 // Step 4, bottom-up: sweep the unvisited vertices against the (decoded) frontier bitmap.
 cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d_depth, uint32_t *d_parent,
                            const LoopState *ls, cudaStream_t st)
@@ -935,7 +990,7 @@ struct LoopBuild {
     int32_t *depth;
     uint32_t *parent;
     uint8_t *log;
-    bool codec, want_v, px;
+    bool codec, want_v, px, overlap;
 };
 
 cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGraphNode_t *dep, void *func,
@@ -1008,6 +1063,20 @@ cudaError_t seg_bottom_up(void *p)
     }
     return step_bottom_up(c.g, c.codec, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
 }
+cudaError_t seg_check_td(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    const cudaError_t r = step_decode_q(c.g, 0, c.g->ls, c.g->dl_stream);
+    if (r != cudaSuccess) return r;
+    return step_check_q(c.g, 0, c.g->ls, c.g->dl_stream);
+}
+cudaError_t seg_check_bu(void *p)
+{
+    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
+    const cudaError_t r = step_decode_b(c.g, c.g->dl_stream);
+    if (r != cudaSuccess) return r;
+    return step_check_b(c.g, c.g->dl_stream);
+}
 cudaError_t seg_top_down_plain(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
@@ -1031,20 +1100,27 @@ cudaError_t seg_compact(void *p)
 // Build the device-driven loop for these buffers and mode:
 //   init -> while(h_while) { begin -> [if h_dense: Q+B from bitmap | Q+B mirrored] ->
 //                            [if h_dir: top-down | bottom-up] -> compact [-> log] -> end }
-// with V's encode on a parallel branch from begin to compact (overlapped with the rest).
+// with V's encode on a parallel branch from begin to compact (overlapped with the rest).  With the
+// overlap the expansion switch holds only raw bodies and forms a branch of its own; the Q/B encode
+// is followed by the round-trip switch h_chk (decode + compare for top-down | bottom-up) on a
+// second branch; the compaction waits for all three.
 cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
 {
     fq_graph *g = b.g;
     cudaStream_t cs = g->dl_stream;
     cudaGraph_t sg_init = nullptr, sg_dense = nullptr, sg_sparse = nullptr, sg_v = nullptr, sg_td = nullptr,
-                sg_bu = nullptr, sg_tdp = nullptr, sg_bup = nullptr, sg_cmp = nullptr, top = nullptr;
+                sg_bu = nullptr, sg_tdp = nullptr, sg_bup = nullptr, sg_cmp = nullptr, sg_ctd = nullptr,
+                sg_cbu = nullptr, top = nullptr;
     LoopBuild ctx = b;
+    const bool ovl = b.codec && b.overlap;
     cudaError_t e = capture_segment(cs, &sg_init, seg_init, &ctx);
     if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_dense, seg_dense, &ctx);
     if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_sparse, seg_sparse, &ctx);
     if (e == cudaSuccess && b.want_v) e = capture_segment(cs, &sg_v, seg_visited, &ctx);
-    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_td, seg_top_down, &ctx);
-    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_bu, seg_bottom_up, &ctx);
+    if (e == cudaSuccess && b.codec && !ovl) e = capture_segment(cs, &sg_td, seg_top_down, &ctx);
+    if (e == cudaSuccess && b.codec && !ovl) e = capture_segment(cs, &sg_bu, seg_bottom_up, &ctx);
+    if (e == cudaSuccess && ovl) e = capture_segment(cs, &sg_ctd, seg_check_td, &ctx);
+    if (e == cudaSuccess && ovl) e = capture_segment(cs, &sg_cbu, seg_check_bu, &ctx);
     if (e == cudaSuccess) e = capture_segment(cs, &sg_tdp, seg_top_down_plain, &ctx);
     if (e == cudaSuccess) e = capture_segment(cs, &sg_bup, seg_bottom_up_plain, &ctx);
     if (e == cudaSuccess) e = capture_segment(cs, &sg_cmp, seg_compact, &ctx);
@@ -1052,8 +1128,8 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
     if (e != cudaSuccess) goto done;
     {
         cudaGraphNode_t n_init, n_while, n_begin, n_last, tmp;
-        cudaGraph_t body, enc[3], dir[4];
-        cudaGraphConditionalHandle h_while, h_enc, h_dir;
+        cudaGraph_t body, enc[3], dir[4], chk[2];
+        cudaGraphConditionalHandle h_while, h_enc, h_dir, h_chk;
         if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, sg_init)) != cudaSuccess) goto done;
         if ((e = cudaGraphConditionalHandleCreate(&h_while, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) goto done;
         if ((e = add_conditional(&n_while, top, &n_init, h_while, cudaGraphCondTypeWhile, 1, &body)) != cudaSuccess)
@@ -1061,11 +1137,13 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
         h_enc = 0;  // only a graph with the codec stage has the encode switch
         if (b.codec && (e = cudaGraphConditionalHandleCreate(&h_enc, body, 0, 0)) != cudaSuccess) goto done;
         if ((e = cudaGraphConditionalHandleCreate(&h_dir, body, 0, 0)) != cudaSuccess) goto done;
+        h_chk = 0;  // only the overlapped stage has the round-trip switch
+        if (ovl && (e = cudaGraphConditionalHandleCreate(&h_chk, body, 0, 0)) != cudaSuccess) goto done;
         {
             LoopState *ls = g->ls;
             uint64_t n = g->n;
-            int codec = b.codec ? 1 : 0;
-            void *args[] = {&ls, &n, &codec, &h_enc, &h_dir};
+            int codec = b.codec ? 1 : 0, overlap = ovl ? 1 : 0;
+            void *args[] = {&ls, &n, &codec, &h_enc, &h_dir, &overlap, &h_chk};
             if ((e = add_kernel_node(&n_begin, body, nullptr, (void *)loop_begin_kernel, args)) != cudaSuccess) goto done;
         }
         n_last = n_begin;
@@ -1075,6 +1153,17 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             cudaGraphNode_t c0, c1;
             if ((e = cudaGraphAddChildGraphNode(&c0, enc[0], nullptr, 0, sg_sparse)) != cudaSuccess) goto done;
             if ((e = cudaGraphAddChildGraphNode(&c1, enc[1], nullptr, 0, sg_dense)) != cudaSuccess) goto done;
+        }
+        // overlap: after the encode, the round-trip check of the form the direction names (value 2,
+        // no body: an uncoded level); the expansion below hangs off begin instead of the encode
+        cudaGraphNode_t n_chk = nullptr;
+        if (ovl) {
+            if ((e = add_conditional(&n_chk, body, &n_last, h_chk, cudaGraphCondTypeSwitch, 2, chk)) != cudaSuccess)
+                goto done;
+            cudaGraphNode_t c0, c1;
+            if ((e = cudaGraphAddChildGraphNode(&c0, chk[0], nullptr, 0, sg_ctd)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c1, chk[1], nullptr, 0, sg_cbu)) != cudaSuccess) goto done;
+            n_last = n_begin;
         }
         // V_d is coded on a branch of its own, beside the Q/B encode, decode and expansion (it reads
         // only the previous compaction's positions and the visited bitmap, which this level's
@@ -1088,14 +1177,18 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             cudaGraphNode_t c0, c1, c2, c3;
             // without the codec stage the switch never takes cases 0 and 1; they hold the raw bodies
             // too, so that no case is an empty graph
-            if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, b.codec ? sg_td : sg_tdp)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, b.codec ? sg_bu : sg_bup)) != cudaSuccess) goto done;
+            const bool dec = b.codec && !ovl;  // the coded bodies decode and consume; raw otherwise
+            if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, dec ? sg_td : sg_tdp)) != cudaSuccess) goto done;
+            if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, dec ? sg_bu : sg_bup)) != cudaSuccess) goto done;
             if ((e = cudaGraphAddChildGraphNode(&c2, dir[2], nullptr, 0, sg_tdp)) != cudaSuccess) goto done;
             if ((e = cudaGraphAddChildGraphNode(&c3, dir[3], nullptr, 0, sg_bup)) != cudaSuccess) goto done;
         }
         {
-            const cudaGraphNode_t deps[2] = {n_last, n_v};
-            if ((e = cudaGraphAddChildGraphNode(&tmp, body, deps, n_v ? 2 : 1, sg_cmp)) != cudaSuccess) goto done;
+            cudaGraphNode_t deps[3] = {n_last, nullptr, nullptr};
+            size_t nd = 1;
+            if (n_v) deps[nd++] = n_v;
+            if (n_chk) deps[nd++] = n_chk;
+            if ((e = cudaGraphAddChildGraphNode(&tmp, body, deps, nd, sg_cmp)) != cudaSuccess) goto done;
         }
         n_last = tmp;
         {
@@ -1104,13 +1197,14 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             fq_level_record *recs = g->recs;
             uint64_t n = g->n;
             uint64_t n_iso = g->n_iso;
-            int codec = b.codec ? 1 : 0, want_v = b.want_v ? 1 : 0, has_log = b.log ? 1 : 0;
-            void *args[] = {&ls, &ctr, &recs, &n, &n_iso, &codec, &want_v, &has_log, &h_while};
+            int codec = b.codec ? 1 : 0, want_v = b.want_v ? 1 : 0, has_log = b.log ? 1 : 0, overlap = ovl ? 1 : 0;
+            void *args[] = {&ls, &ctr, &recs, &n, &n_iso, &codec, &want_v, &has_log, &overlap, &h_while};
             if ((e = add_kernel_node(&tmp, body, &n_last, (void *)loop_end_kernel, args)) != cudaSuccess) goto done;
         }
     }
 done:
-    for (cudaGraph_t *gp : {&sg_init, &sg_dense, &sg_sparse, &sg_v, &sg_td, &sg_bu, &sg_tdp, &sg_bup, &sg_cmp})
+    for (cudaGraph_t *gp : {&sg_init, &sg_dense, &sg_sparse, &sg_v, &sg_td, &sg_bu, &sg_tdp, &sg_bup, &sg_cmp, &sg_ctd,
+                            &sg_cbu})
         if (*gp) cudaGraphDestroy(*gp);  // child-graph nodes hold their own copies
     if (e != cudaSuccess) {
         note_cuda_error(e, __LINE__);
@@ -1128,6 +1222,9 @@ void fq_graph_destroy_locked(fq_graph *g)
     if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
     if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
     if (g->dl_stream) cudaStreamDestroy(g->dl_stream);
+    if (g->ov_stream) cudaStreamDestroy(g->ov_stream);
+    for (int i = 0; i < 2; i++)
+        if (g->ov_ev[i]) cudaEventDestroy(g->ov_ev[i]);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     if (g->host) cudaFreeHost(g->host);
@@ -1290,6 +1387,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     const bool codec = !(flags & FQ_BFS_NO_CODEC);
     const bool want_visited = codec && (flags & FQ_BFS_VISITED_STREAM);
     const bool px = codec && (flags & FQ_BFS_PATCHED);
+    const bool overlap = codec && (flags & FQ_BFS_OVERLAP);
     const uint64_t n = g->n;
     NvtxScope search_range((flags & FQ_BFS_DEVICE_LOOP) ? "fq_bfs_run:device_loop" : "fq_bfs_run:host_loop");
 
@@ -1305,7 +1403,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     if (flags & FQ_BFS_DEVICE_LOOP) {
         // the whole search is one graph launch; the host reads the records once at the end
         const uint32_t mode = (codec ? 0u : FQ_BFS_NO_CODEC) | (want_visited ? FQ_BFS_VISITED_STREAM : 0u) |
-                              (px ? FQ_BFS_PATCHED : 0u);
+                              (px ? FQ_BFS_PATCHED : 0u) | (overlap ? FQ_BFS_OVERLAP : 0u);
         if (!g->dl_exec || g->dl_depth != d_depth || g->dl_parent != d_parent || g->dl_log != d_stream_log ||
             g->dl_mode != mode || g->dl_tune != tune_generation()) {
             std::lock_guard<std::mutex> lock(g_capture_mu);
@@ -1314,7 +1412,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             g->dl_exec = nullptr;
             g->dl_graph = nullptr;
             if (!g->dl_stream) FQ_TRY(cudaStreamCreateWithFlags(&g->dl_stream, cudaStreamNonBlocking));
-            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited, px};
+            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited, px, overlap};
             FQ_TRY(build_device_loop(b, &g->dl_graph));
             FQ_TRY(cudaGraphInstantiate(&g->dl_exec, g->dl_graph, 0));
             g->dl_depth = d_depth;
@@ -1359,7 +1457,11 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     fq_bfs_stats stats;
     memset(&stats, 0, sizeof(stats));
     stats.isolated = g->n_iso;
-    Timer tm{g, st, (flags & FQ_BFS_TIMING) != 0, stats.kernel_ms, stats.kernel_launches};
+    Timer tm{g, st, (flags & FQ_BFS_TIMING) != 0, stats.kernel_ms, stats.kernel_launches, {}};
+    if (overlap && !g->ov_stream) {  // the codec stage's own stream, made on first use
+        FQ_TRY(cudaStreamCreateWithFlags(&g->ov_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; i++) FQ_TRY(cudaEventCreateWithFlags(&g->ov_ev[i], cudaEventDisableTiming));
+    }
 
     // ---- level 0 set-up
     tm.begin(FQ_K_OTHER);
@@ -1379,42 +1481,56 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
     fq_status result = FQ_OK;
 
     for (uint32_t d = 0;; d++) {
-        // 1. encode F_d (Q_d and B_d), and V_d
-        tm.begin(FQ_K_ENCODE);
-        int enc_launches = 0;
         const bool coded = codec && n_f >= min_codec_ids;  // below the threshold the frontier crosses raw
-        if (coded) {
-            const bool dense = 2 * n_f > n;
-            FQ_TRY(step_encode_q(g, dense, n_f, nullptr, st, px));
-            enc_launches = dense ? 8 : 2;
-        }
-        if (want_visited) {
-            FQ_TRY(step_encode_v(g, st));
-            enc_launches += 2;
-        }
-        tm.end(FQ_K_ENCODE, enc_launches);
-
-        // 2. direction
+        // direction (host arithmetic: nothing waits for it)
         if (flags & FQ_BFS_FORCE_TOP_DOWN) dir = FQ_TOP_DOWN;
         else if (flags & FQ_BFS_FORCE_BOTTOM_UP) dir = FQ_BOTTOM_UP;
         else if (dir == FQ_TOP_DOWN && (unsigned __int128)m_f * alpha > (unsigned __int128)m_u) dir = FQ_BOTTOM_UP;
         else if (dir == FQ_BOTTOM_UP && (unsigned __int128)n_f * beta < (unsigned __int128)n) dir = FQ_TOP_DOWN;
         const int32_t newdepth = (int32_t)d + 1;
+        // with the overlap the codec stage forks onto its own stream after the previous compaction
+        // and joins before this level's compaction, while the expansion consumes the raw frontier
+        const bool ovl = overlap && coded;
+        cudaStream_t cst = st;
+        if (ovl) {
+            FQ_TRY(cudaEventRecord(g->ov_ev[0], st));
+            FQ_TRY(cudaStreamWaitEvent(g->ov_stream, g->ov_ev[0], 0));
+            cst = g->ov_stream;
+        }
+        tm.cls_st[FQ_K_ENCODE] = tm.cls_st[FQ_K_DECODE] = ovl ? cst : nullptr;
 
-        // 3 + 4. decode the consumed form, expand
+        // 1. encode F_d (Q_d and B_d), and V_d
+        tm.begin(FQ_K_ENCODE);
+        int enc_launches = 0;
+        if (coded) {
+            const bool dense = 2 * n_f > n;
+            FQ_TRY(step_encode_q(g, dense, n_f, nullptr, cst, px));
+            enc_launches = dense ? 8 : 2;
+        }
+        if (want_visited) {
+            FQ_TRY(step_encode_v(g, cst));
+            enc_launches += 2;
+        }
+        tm.end(FQ_K_ENCODE, enc_launches);
+
+        // 3 + 4. decode the consumed form (overlap: decode and compare with the raw form), expand
         tm.begin(FQ_K_DECODE);
-        if (coded && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, st));
-        if (coded && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, st));
-        tm.end(FQ_K_DECODE, coded ? (dir == FQ_TOP_DOWN ? 3 : 4) : 0);
+        if (coded && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, cst));
+        if (coded && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, cst));
+        if (ovl) FQ_TRY(dir == FQ_TOP_DOWN ? step_check_q(g, n_f, nullptr, cst) : step_check_b(g, cst));
+        tm.end(FQ_K_DECODE, coded ? (dir == FQ_TOP_DOWN ? 3 : 4) + (ovl ? 1 : 0) : 0);
+        if (ovl) FQ_TRY(cudaEventRecord(g->ov_ev[1], cst));
+        const bool consume_decoded = coded && !ovl;
         if (dir == FQ_TOP_DOWN) {
             tm.begin(FQ_K_TOP_DOWN);
-            FQ_TRY(step_top_down(g, coded, n_f, newdepth, d_depth, d_parent, nullptr, st));
+            FQ_TRY(step_top_down(g, consume_decoded, n_f, newdepth, d_depth, d_parent, nullptr, st));
             tm.end(FQ_K_TOP_DOWN, 2);
         } else {
             tm.begin(FQ_K_BOTTOM_UP);
-            FQ_TRY(step_bottom_up(g, coded, newdepth, d_depth, d_parent, nullptr, st));
+            FQ_TRY(step_bottom_up(g, consume_decoded, newdepth, d_depth, d_parent, nullptr, st));
             tm.end(FQ_K_BOTTOM_UP, 1);
         }
+        if (ovl) FQ_TRY(cudaStreamWaitEvent(st, g->ov_ev[1], 0));
 
         // 5. compaction (+ V_{d+1} positions, cleared scratch for the next level)
         tm.begin(FQ_K_COMPACT);

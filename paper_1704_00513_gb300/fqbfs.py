@@ -24,6 +24,7 @@ FQ_TOP_DOWN, FQ_BOTTOM_UP = 0, 1
 FQ_BFS_VISITED_STREAM, FQ_BFS_FORCE_TOP_DOWN, FQ_BFS_FORCE_BOTTOM_UP, FQ_BFS_TIMING, FQ_BFS_NO_CODEC = 1, 2, 4, 8, 16
 FQ_BFS_DEVICE_LOOP = 32
 FQ_BFS_PATCHED = 64
+FQ_BFS_OVERLAP = 128
 TUNE_SITES = ("enc_widths", "enc_pack", "dec_unpack", "bat_encode", "bat_dunpack", "bu_sweep", "td_hub")
 TUNE_MAX_CLASS = 40
 KCLASS = ("top_down", "bottom_up", "compact", "encode", "decode", "other")

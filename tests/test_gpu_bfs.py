@@ -158,7 +158,8 @@ def test_rmat24_full_size_every_level_eight_roots(rmat24):
     times (device-driven loop, Q_d, B_d and V_d every level): eight of the benchmark's roots checked
     end to end against the oracle -- depths exact, tree valid, the per-level schedule equal, and
     every level's three streams byte for byte, with as many streams as the oracle has levels.  Two
-    of the roots also run through the host-driven loop, which must agree on everything."""
+    of the roots also run through the host-driven loop and with the overlapped codec stage, which
+    must agree on everything."""
     import concurrent.futures as cf
     off_d, cols_d, off, cols, roots = rmat24
     picked = [roots[i] for i in (0, 5, 11, 19, 26, 37, 48, 63)]
@@ -167,7 +168,8 @@ def test_rmat24_full_size_every_level_eight_roots(rmat24):
     g = fqbfs.Graph(off_d, cols_d)
     flags = fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_DEVICE_LOOP
     for i, (root, (ref_depth, sched, ref_streams)) in enumerate(zip(picked, refs)):
-        for loop in ([flags, fqbfs.FQ_BFS_VISITED_STREAM] if i < 2 else [flags]):
+        variants = [flags, fqbfs.FQ_BFS_VISITED_STREAM, flags | fqbfs.FQ_BFS_OVERLAP] if i < 2 else [flags]
+        for loop in variants:
             res = g.bfs(root, flags=loop, record_streams=True, max_levels=64)
             depth = res.depth.cpu().numpy()
             assert np.array_equal(depth, ref_depth), (root, loop)
@@ -373,4 +375,50 @@ def test_patched_queue_streams(rmat16, loop):
                 assert np.array_equal(got[k].cpu().numpy(), want[k]), (r, got["level"], k)
             fqx += int(got["Q"][:4].cpu().numpy().view(np.uint32)[0] == 0x31585146)
     assert fqx > 0  # the patched form was chosen for some levels
+    g.close()
+
+
+@LOOPS
+@pytest.mark.parametrize("extra", [0, fqbfs.FQ_BFS_PATCHED, fqbfs.FQ_BFS_FORCE_BOTTOM_UP, fqbfs.FQ_BFS_FORCE_TOP_DOWN])
+def test_overlapped_codec_stage_gives_the_serial_results(rmat16, loop, extra):
+    """FQ_BFS_OVERLAP: the expansion consumes the raw frontier while the codec stage (encode, decode,
+    round-trip compare) runs beside it; depths, level records, statistics and every stream are those
+    of the serial stage (whose expansion consumes the decoded form), and the oracle's."""
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    base = loop | extra | fqbfs.FQ_BFS_VISITED_STREAM
+    for r in roots[:4]:
+        a = g.bfs(r, flags=base, record_streams=True)
+        da = a.depth.clone()
+        b = g.bfs(r, flags=base | fqbfs.FQ_BFS_OVERLAP, record_streams=True)
+        assert torch.equal(da, b.depth)
+        ref_depth, _ = oracle.bfs(off, cols, r)
+        assert np.array_equal(b.depth.cpu().numpy(), ref_depth)
+        assert oracle.validate(off, cols, r, ref_depth, b.parent.cpu().numpy().view(np.uint32)) == 0
+        assert a.levels == b.levels
+        for k in ("levels", "directions", "reached", "reached_edges", "edges_examined", "raw_queue_bytes",
+                  "enc_queue_bytes", "raw_bitmap_bytes", "enc_bitmap_bytes", "enc_visited_bytes", "kernel_bytes"):
+            assert a.stats[k] == b.stats[k], k
+        coded = sum(1 for x in a.levels if x["q_bytes"])
+        assert b.stats["kernel_launches"]["decode"] == a.stats["kernel_launches"]["decode"] + coded  # + the compares
+        assert len(a.streams) == len(b.streams) == len(a.levels)
+        for sa, sb in zip(a.streams, b.streams):
+            for key in ("Q", "B", "V"):
+                assert torch.equal(sa[key], sb[key]), (sa["level"], key)
+    g.close()
+
+
+@LOOPS
+def test_overlap_with_threshold(rmat16, loop):
+    off, cols, roots = rmat16
+    g = fqbfs.Graph(*to_dev(off, cols))
+    for r in roots[4:6]:
+        a = g.bfs(r, flags=loop | fqbfs.FQ_BFS_VISITED_STREAM, record_streams=True, min_codec_ids=300)
+        da = a.depth.clone()
+        b = g.bfs(r, flags=loop | fqbfs.FQ_BFS_VISITED_STREAM | fqbfs.FQ_BFS_OVERLAP, record_streams=True,
+                  min_codec_ids=300)
+        assert torch.equal(da, b.depth) and a.levels == b.levels
+        for sa, sb in zip(a.streams, b.streams):
+            for key in ("Q", "B", "V"):
+                assert torch.equal(sa[key], sb[key]), (sa["level"], key)
     g.close()
