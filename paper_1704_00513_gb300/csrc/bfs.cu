@@ -55,7 +55,8 @@ struct Counters {
     uint32_t r_where_q, r_where_v;
     unsigned long long r_detail_q, r_detail_v;
     unsigned long long n_iso;      // degree-0 vertices (counted by iso_kernel at handle creation)
-    unsigned long long pad[14];
+    uint32_t cmp_ticket, pad32;    // compaction CTAs done with their counts (the last one resets it)
+    unsigned long long pad[13];
 };
 static_assert(sizeof(Counters) == 256, "counter block is 256 bytes");
 
@@ -355,6 +356,92 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_kernel(const uint32_t *__re
     if (lane == 0 && degsum) atomicAdd(m_f_next, degsum);
 }
 
+// Head records of the bottom-up sweep (graphs with fewer than 2^32 adjacency entries): per vertex
+// its adjacency start, its degree and its first two neighbours (UINT32_MAX where absent), so that a
+// vertex whose parent is among its first two neighbours is settled from one coalesced 16-byte load,
+// without the dependent random read of its adjacency list.
+__global__ void head_kernel(const int64_t *__restrict__ off, const uint32_t *__restrict__ cols, uint64_t n,
+                            uint4 *__restrict__ hc)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const long long s = off[v], d = off[v + 1] - s;
+        hc[v] = make_uint4((uint32_t)s, (uint32_t)d, d > 0 ? cols[s] : 0xffffffffu, d > 1 ? cols[s + 1] : 0xffffffffu);
+    }
+}
+
+// The bottom-up sweep of bu_sweep_kernel over head records: the first two neighbours come with the
+// record (their frontier bits are tested together), the rest of the list is scanned as there.
+__global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t *__restrict__ front32,
+                                                                 const uint32_t *__restrict__ visited32,
+                                                                 const uint32_t *__restrict__ iso32,
+                                                                 uint32_t *__restrict__ next32,
+                                                                 const uint4 *__restrict__ hc,
+                                                                 const uint32_t *__restrict__ cols, int32_t *depth,
+                                                                 uint32_t *parent, int32_t newdepth, uint64_t n,
+                                                                 unsigned long long *examined,
+                                                                 unsigned long long *m_f_next, const LoopState *ls)
+{
+    if (ls) newdepth = (int32_t)ls->d + 1;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long cnt = 0, degsum = 0;
+    for (uint64_t word = gw; word * 32u < n; word += nw) {
+        const uint32_t done = visited32[word] | iso32[word];
+        if (done == 0xffffffffu) continue;
+        const uint64_t w = word * 32u + lane;
+        bool found = false;
+        uint32_t par = 0;
+        if (w < n && !((done >> lane) & 1u)) {
+            const uint4 h = hc[w];
+            const uint32_t deg = h.y;
+            const bool h0 = deg > 0 && ((front32[h.z >> 5] >> (h.z & 31u)) & 1u);
+            const bool h1 = deg > 1 && ((front32[h.w >> 5] >> (h.w & 31u)) & 1u);
+            uint32_t j;  // entries examined
+            if (h0 || h1) {
+                found = true;
+                par = h0 ? h.z : h.w;
+                j = h0 ? 1u : 2u;
+            } else {
+                j = min(deg, 2u);
+                const uint32_t *row = cols + h.x;
+                for (; j + 1 < deg; j += 2) {
+                    const uint32_t u0 = row[j], u1 = row[j + 1];
+                    const bool f0 = (front32[u0 >> 5] >> (u0 & 31u)) & 1u;
+                    const bool f1 = (front32[u1 >> 5] >> (u1 & 31u)) & 1u;
+                    if (f0 || f1) {
+                        found = true;
+                        par = f0 ? u0 : u1;
+                        j += f0 ? 1u : 2u;
+                        break;
+                    }
+                }
+                if (!found && j < deg) {
+                    const uint32_t u0 = row[j];
+                    j += 1;
+                    if ((front32[u0 >> 5] >> (u0 & 31u)) & 1u) {
+                        found = true;
+                        par = u0;
+                    }
+                }
+            }
+            cnt += j;
+            if (found) degsum += deg;
+        }
+        if (found) {
+            depth[w] = newdepth;
+            if (parent) parent[w] = par;
+        }
+        const uint32_t mask = __ballot_sync(0xffffffffu, found);
+        if (lane == 0 && mask) next32[word] = mask;
+    }
+    cnt = warp_sum64(cnt);
+    degsum = warp_sum64(degsum);
+    if (lane == 0 && cnt) atomicAdd(examined, cnt);
+    if (lane == 0 && degsum) atomicAdd(m_f_next, degsum);
+}
+
 // ---- compaction: next bitmap -> sorted queue, n_f, m_f, visited |= next, V positions ----
 
 __device__ __forceinline__ uint64_t bits_in_word(uint64_t w, uint64_t nwords, uint64_t n)
@@ -364,10 +451,21 @@ __device__ __forceinline__ uint64_t bits_in_word(uint64_t w, uint64_t nwords, ui
     return (w == nwords - 1 && tail) ? tail : 64u;
 }
 
+template <int NT>
+__device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, const uint32_t *vis_cnt, uint32_t *vtile_off,
+                              uint64_t ntiles, uint64_t n, Counters *ctr, const Scratch &sq, const Scratch &sv);
+
+// Per 16,384-vertex tile: the next frontier's count, and visited |= next (with the tile's running
+// visited count).  The last CTA to finish (a ticket taken after a fence, so every other CTA's
+// counts are visible to it) then does the level's one-CTA work: the offsets of the next-frontier
+// positions and of V's positions, the level record, and cleared codec scratch (cmp_scan_body).
 __global__ void __launch_bounds__(kThreads) cmp_count_kernel(const uint64_t *__restrict__ next, uint64_t *visited,
-                                                             uint64_t nwords, uint32_t *tile_cnt, uint32_t *vis_cnt)
+                                                             uint64_t nwords, uint32_t *tile_cnt, uint32_t *vis_cnt,
+                                                             uint32_t *tile_off, uint32_t *vtile_off, uint64_t n,
+                                                             Counters *ctr, Scratch sq, Scratch sv)
 {
     __shared__ uint32_t ws[kThreads / 32];
+    __shared__ bool s_last;
     const uint64_t w0 = (uint64_t)blockIdx.x * kCmpWords + (uint64_t)threadIdx.x * kCmpWordsPerThread;
     uint32_t cnt = 0;
 #pragma unroll
@@ -389,32 +487,39 @@ __global__ void __launch_bounds__(kThreads) cmp_count_kernel(const uint64_t *__r
         for (uint32_t i = 0; i < kThreads / 32; i++) t += ws[i];
         tile_cnt[blockIdx.x] = t;
         vis_cnt[blockIdx.x] += t;  // the next frontier is disjoint from the visited set
+        __threadfence();
+        s_last = atomicAdd(&ctr->cmp_ticket, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    cmp_scan_body<kThreads>(tile_cnt, tile_off, vis_cnt, vtile_off, gridDim.x, n, ctr, sq, sv);
+    if (threadIdx.x == 0) ctr->cmp_ticket = 0u;
 }
 
-// One CTA: offsets of the next-frontier positions and of V's positions (set or clear bits of the
-// visited bitmap), the level record, and cleared codec scratch for the next level.
-__global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *tile_cnt, uint32_t *tile_off,
-                                                                const uint32_t *vis_cnt, uint32_t *vtile_off,
-                                                                uint64_t ntiles, uint64_t n, Counters *ctr,
-                                                                Scratch sq, Scratch sv)
+// The last compaction CTA's work: offsets of the next-frontier positions and of V's positions
+// (set or clear bits of the visited bitmap), the level record, and cleared codec scratch for the
+// next level.  The counts are read with L2-coherent loads: other CTAs wrote them.
+template <int NT>
+__device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, const uint32_t *vis_cnt, uint32_t *vtile_off,
+                              uint64_t ntiles, uint64_t n, Counters *ctr, const Scratch &sq, const Scratch &sv)
 {
     __shared__ unsigned long long sm[33];
-    const uint64_t chunk = (ntiles + kScanThreads - 1) / kScanThreads;
+    const uint64_t chunk = (ntiles + NT - 1) / NT;
     const uint64_t t0 = min(ntiles, (uint64_t)threadIdx.x * chunk), t1 = min(ntiles, t0 + chunk);
     const uint64_t tile_bits = 64ull * kCmpWords;
     // each thread sums its chunk of both count arrays (one tile per thread up to 2^24 vertices)
     unsigned long long lq = 0, lv = 0;
     for (uint64_t t = t0; t < t1; t++) {
-        lq += tile_cnt[t];
-        lv += vis_cnt[t];
+        lq += __ldcg(tile_cnt + t);
+        lv += __ldcg(vis_cnt + t);
     }
     const unsigned long long lb = t1 > t0 ? min(n, t1 * tile_bits) - t0 * tile_bits : 0ull;  // bits in the chunk
     unsigned long long nf_total = 0, vis_total = 0, total = 0;
-    unsigned long long run = cta_excl_scan64<kScanThreads>(lq, sm, &nf_total);
-    cta_excl_scan64<kScanThreads>(lv, sm, &vis_total);
+    unsigned long long run = cta_excl_scan64<NT>(lq, sm, &nf_total);
+    cta_excl_scan64<NT>(lv, sm, &vis_total);
     const bool set_mode = 2ull * vis_total <= n;
-    unsigned long long vrun = cta_excl_scan64<kScanThreads>(set_mode ? lv : lb - lv, sm, &total);
+    unsigned long long vrun = cta_excl_scan64<NT>(set_mode ? lv : lb - lv, sm, &total);
     if (t1 == t0 + 1) {  // the common case: nothing to re-read
         tile_off[t0] = (uint32_t)run;
         vtile_off[t0] = (uint32_t)vrun;
@@ -422,7 +527,7 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
         for (uint64_t t = t0; t < t1; t++) {
             tile_off[t] = (uint32_t)run;
             vtile_off[t] = (uint32_t)vrun;
-            const uint32_t x = tile_cnt[t], y = vis_cnt[t];
+            const uint32_t x = __ldcg(tile_cnt + t), y = __ldcg(vis_cnt + t);
             run += x;
             const uint64_t bits = min(n, (t + 1) * tile_bits) - t * tile_bits;
             vrun += set_mode ? y : bits - y;
@@ -434,10 +539,10 @@ __global__ void __launch_bounds__(kScanThreads) cmp_scan_kernel(const uint32_t *
     // load first: the stores below could alias them, and one thread's dependent round trips are
     // this kernel's critical path)
     if (threadIdx.x == 0) {
-        const unsigned long long m_f = ctr->m_f_next, ex = ctr->examined, hub = ctr->hub_items;
-        const int32_t cq = sq.ctl->code, cv = sv.ctl->code;
-        const uint32_t wq = sq.ctl->where, wv = sv.ctl->where;
-        const unsigned long long dq = sq.ctl->detail, dv = sv.ctl->detail;
+        const unsigned long long m_f = __ldcg(&ctr->m_f_next), ex = __ldcg(&ctr->examined), hub = __ldcg(&ctr->hub_items);
+        const int32_t cq = __ldcg(&sq.ctl->code), cv = __ldcg(&sv.ctl->code);
+        const uint32_t wq = __ldcg(&sq.ctl->where), wv = __ldcg(&sv.ctl->where);
+        const unsigned long long dq = __ldcg(&sq.ctl->detail), dv = __ldcg(&sv.ctl->detail);
         ctr->n_f_next = s_nf;
         ctr->r_m_f = m_f;  // summed by the expansion kernels
         ctr->m_f_next = 0;
@@ -677,7 +782,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
         if (coded) st.kernel_launches[FQ_K_DECODE] += 4 + (overlap ? 1 : 0);
         st.kernel_launches[FQ_K_BOTTOM_UP] += 1;
     }
-    st.kernel_launches[FQ_K_COMPACT] += 3;
+    st.kernel_launches[FQ_K_COMPACT] += 2;
     st.kernel_launches[FQ_K_OTHER] += 2 + (has_log ? 1 : 0);  // loop_begin, loop_end [, log_append]
 
     unsigned long long log_off = ~0ull;
@@ -746,6 +851,7 @@ struct fq_graph {
     uint32_t *q, *q2;
     uint64_t *fbits, *fbits2, *next, *visited;
     uint32_t *iso32;
+    uint4 *hc;        // bottom-up head records (NULL when the graph has 2^32 or more adjacency entries)
     uint8_t *qs, *bs, *vs;
     uint64_t qs_cap, bs_cap;
     HubItem *items;
@@ -938,10 +1044,16 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
     const uint64_t words32 = cdiv(g->n, 32);
     const uint32_t grid = tuned_grid(FQ_TUNE_BU_SWEEP, g->n, std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16),
                                      cdiv(words32, kThreads / 32));
-    bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
-        reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
-        reinterpret_cast<uint32_t *>(g->next), g->off, g->cols, d_depth, d_parent, newdepth, g->n, &g->ctr->examined,
-        &g->ctr->m_f_next, ls);
+    if (g->hc)
+        bu_sweep_head_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
+            reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
+            reinterpret_cast<uint32_t *>(g->next), g->hc, g->cols, d_depth, d_parent, newdepth, g->n,
+            &g->ctr->examined, &g->ctr->m_f_next, ls);
+    else
+        bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
+            reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
+            reinterpret_cast<uint32_t *>(g->next), g->off, g->cols, d_depth, d_parent, newdepth, g->n,
+            &g->ctr->examined, &g->ctr->m_f_next, ls);
     return cudaGetLastError();
 }
 
@@ -949,9 +1061,8 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
 cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
 {
     const uint32_t ct = (uint32_t)g->cmp_tiles;
-    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt);
-    cmp_scan_kernel<<<1, kScanThreads, 0, st>>>(g->tile_cnt, g->tile_off, g->vis_cnt, g->vtile_off, g->cmp_tiles, g->n,
-                                                g->ctr, g->sq, g->sv);
+    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt, g->tile_off,
+                                              g->vtile_off, g->n, g->ctr, g->sq, g->sv);
     static std::atomic<bool> smem_set[64];
     FQ_CU(allow_smem(cmp_extract_kernel, kCmpSmem, smem_set));
     cmp_extract_kernel<<<ct, kThreads, kCmpSmem, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
@@ -1293,6 +1404,8 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     const uint64_t o_next = o; o = al256(o + 8 * nw);
     const uint64_t o_vis = o; o = al256(o + 8 * nw);
     const uint64_t o_iso = o; o = al256(o + 8 * nw);
+    const bool with_hc = m < (1ull << 32);
+    const uint64_t o_hc = o; o = al256(o + (with_hc ? 16 * n : 0));
     const uint64_t o_qs = o; o = al256(o + g->qs_cap);
     const uint64_t o_bs = o; o = al256(o + g->bs_cap);
     const uint64_t o_vs = o; o = al256(o + g->bs_cap);
@@ -1338,6 +1451,7 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     g->next = reinterpret_cast<uint64_t *>(g->mem + o_next);
     g->visited = reinterpret_cast<uint64_t *>(g->mem + o_vis);
     g->iso32 = reinterpret_cast<uint32_t *>(g->mem + o_iso);
+    g->hc = with_hc ? reinterpret_cast<uint4 *>(g->mem + o_hc) : nullptr;
     g->qs = g->mem + o_qs;
     g->bs = g->mem + o_bs;
     g->vs = g->mem + o_vs;
@@ -1355,6 +1469,7 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     }
     iso_kernel<<<(uint32_t)std::min<uint64_t>(cdiv(cdiv(n, 32), 256), 4096), 256>>>(d_offsets, n, g->iso32,
                                                                                      &g->ctr->n_iso);
+    if (g->hc) head_kernel<<<(uint32_t)std::min<uint64_t>(cdiv(n, 256), 8 * (uint64_t)num_sms()), 256>>>(d_offsets, d_cols, n, g->hc);
     unsigned long long n_iso = 0;
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
         cudaMemcpy(&n_iso, &g->ctr->n_iso, sizeof(n_iso), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -1535,7 +1650,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         // 5. compaction (+ V_{d+1} positions, cleared scratch for the next level)
         tm.begin(FQ_K_COMPACT);
         FQ_TRY(step_compact(g, want_visited, st));
-        tm.end(FQ_K_COMPACT, 3);
+        tm.end(FQ_K_COMPACT, 2);
 
         FQ_TRY(cudaMemcpyAsync(g->host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         FQ_TRY(cudaStreamSynchronize(st));

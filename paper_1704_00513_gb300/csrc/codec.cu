@@ -725,8 +725,11 @@ __device__ __forceinline__ uint64_t dec_in_bytes(const DecArgs &a)
     return a.in_bytes_dev ? *a.in_bytes_dev : a.in_bytes_host;
 }
 
-// D0
-__global__ void __launch_bounds__(kEncThreads) dec_tiles_kernel(DecArgs a)
+template <uint32_t NT>
+__device__ void dec_plan_body(const DecArgs &a);
+
+// The per-tile width (and exception) sums of a packed stream, tiles strided over the grid.
+__device__ void dec_tile_sums(const DecArgs &a)
 {
     __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
     const FqHeader h = parse_header(a, dec_in_bytes(a));
@@ -770,8 +773,28 @@ __global__ void __launch_bounds__(kEncThreads) dec_tiles_kernel(DecArgs a)
     }
 }
 
-// D1
-__global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
+// D0, and D1 in the last CTA to finish: per-tile width sums (widths > 32 flagged); then, once every
+// CTA has taken its ticket after a fence (so all tile sums are visible), the last one validates the
+// header and sizes and scans the tile sums (dec_plan_body).
+__global__ void __launch_bounds__(kEncThreads) dec_tiles_kernel(DecArgs a)
+{
+    __shared__ bool s_last;
+    dec_tile_sums(a);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&a.s.ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    dec_plan_body<kEncThreads>(a);
+    if (threadIdx.x == 0) a.s.ctl->ticket = 0u;
+}
+
+// D1 (one CTA of NT threads): header validation, scan of the tile sums into tile offsets, size checks.
+template <uint32_t NT>
+__device__ void dec_plan_body(const DecArgs &a)
 {
     __shared__ unsigned long long sm[33];
     Ctl *c = a.s.ctl;
@@ -785,7 +808,7 @@ __global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
     if (ok && h.mode == kModePacked) {
         const uint8_t *fq = a.in + h.fq_off;
         const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
-        const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
+        const unsigned long long total = cta_chunk_scan_u32<NT>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
         if (threadIdx.x == 0) {
             c->total_b = total;
             if (h.words != 4u * total || h.fq_bytes != 16u + dpad16(5u * h.nb) + 16u * total) ok = false;
@@ -796,8 +819,8 @@ __global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
     if (ok && h.mode == kModePatched) {
         const uint8_t *fq = a.in + h.fq_off;
         const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
-        const unsigned long long total = cta_chunk_scan_u32<kScanThreads>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
-        const unsigned long long tex = cta_chunk_scan_u32<kScanThreads>(a.s.tile_ex, a.s.tile_exoff, ntiles, sm);
+        const unsigned long long total = cta_chunk_scan_u32<NT>(a.s.tile_sum, a.s.tile_off, ntiles, sm);
+        const unsigned long long tex = cta_chunk_scan_u32<NT>(a.s.tile_ex, a.s.tile_exoff, ntiles, sm);
         if (threadIdx.x == 0) {
             c->total_b = total;
             c->total_e = tex;
@@ -823,7 +846,7 @@ __global__ void __launch_bounds__(kScanThreads) dec_plan_kernel(DecArgs a)
         if (a.n_out) *a.n_out = h.n;
         return;
     }
-    if (!ok || c->code != FQ_OK) {  // D0 may have flagged a width > 32
+    if (!ok || __ldcg(&c->code) != FQ_OK) {  // D0 may have flagged a width > 32
         set_error(c, FQ_ECORRUPT, kWhereDecPlan, 0ull);
         c->mode = kModeNone;
         if (a.n_out) *a.n_out = 0;
@@ -1231,7 +1254,6 @@ cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
     DecArgs a{in, in_bytes_host, in_bytes_dev, ids, cap, n_out, 0, nullptr, 0, s};
     const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(cap));
     dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
-    dec_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
     FQ_CUDA_TRY(prepare_unpack());
     dec_unpack_kernel<<<tuned_grid(FQ_TUNE_DEC_UNPACK, cap, grid_for(std::max(tiles * kEncThreads, cap), kEncThreads, 3 * num_sms()),
                                    cdiv(std::max(tiles * kEncThreads, cap), kEncThreads)), kEncThreads, kDecSmem,
@@ -1245,7 +1267,6 @@ cudaError_t decode_fb(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
     DecArgs a{in, in_bytes_host, in_bytes_dev, nullptr, nbits, nullptr, 1, words, nbits, s};
     const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(nbits));
     dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
-    dec_plan_kernel<<<1, kScanThreads, 0, st>>>(a);
     const uint64_t nwords = cdiv(nbits, 64);
     fb_init_kernel<<<grid_for(nwords, 256, 4 * num_sms()), 256, 0, st>>>(a);
     FQ_CUDA_TRY(prepare_unpack());

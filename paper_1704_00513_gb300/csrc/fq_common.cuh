@@ -59,7 +59,7 @@ struct Ctl {
     unsigned long long total_b;
     unsigned long long out_bytes;
     unsigned long long fq_offset;  // byte offset of the FQ stream inside the container
-    uint32_t reserved0;
+    uint32_t ticket;               // CTAs of a launch done with their part (a last-CTA step; 0 between launches)
     uint32_t mode2;                // mode of the mirrored FB stream (kMode*), kModeNone if absent
     unsigned long long out2_bytes;
     unsigned long long total_e;    // patched codec: exceptions over all blocks
@@ -157,6 +157,7 @@ __device__ __forceinline__ void reset_scratch_device(const Scratch &s)
     c->mode2 = kModeNone;
     c->fb_mode = kFbRaw;
     c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = c->total_e = 0;
+    c->ticket = 0;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
@@ -222,6 +223,8 @@ __device__ __forceinline__ unsigned long long cta_excl_scan64(unsigned long long
 // threads; out may equal in.  Returns the 64-bit total to every thread.  Thread i owns a
 // contiguous chunk and reads it kScanWin values at a time with all of a window's loads issued
 // before any is used, so a chunk of a few dozen values costs one memory latency, not one each.
+// The loads bypass L1 (ld.global.cg): the values may have been written by other CTAs of the same
+// launch (a last-CTA scan).
 constexpr uint32_t kScanWin = 16;
 template <uint32_t NT>
 __device__ unsigned long long cta_chunk_scan_u32(const uint32_t *in, uint32_t *out, uint64_t count,
@@ -233,7 +236,7 @@ __device__ unsigned long long cta_chunk_scan_u32(const uint32_t *in, uint32_t *o
     for (uint64_t w = t0; w < t1; w += kScanWin) {
         uint32_t x[kScanWin];
 #pragma unroll
-        for (uint32_t i = 0; i < kScanWin; i++) x[i] = (w + i < t1) ? in[w + i] : 0u;
+        for (uint32_t i = 0; i < kScanWin; i++) x[i] = (w + i < t1) ? __ldcg(in + w + i) : 0u;
 #pragma unroll
         for (uint32_t i = 0; i < kScanWin; i++) local += x[i];
     }
@@ -241,7 +244,7 @@ __device__ unsigned long long cta_chunk_scan_u32(const uint32_t *in, uint32_t *o
     for (uint64_t w = t0; w < t1; w += kScanWin) {
         uint32_t x[kScanWin];
 #pragma unroll
-        for (uint32_t i = 0; i < kScanWin; i++) x[i] = (w + i < t1) ? in[w + i] : 0u;
+        for (uint32_t i = 0; i < kScanWin; i++) x[i] = (w + i < t1) ? __ldcg(in + w + i) : 0u;
 #pragma unroll
         for (uint32_t i = 0; i < kScanWin; i++) {
             if (w + i < t1) out[w + i] = (uint32_t)run;
