@@ -444,13 +444,6 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
 
 // ---- compaction: next bitmap -> sorted queue, n_f, m_f, visited |= next, V positions ----
 
-__device__ __forceinline__ uint64_t bits_in_word(uint64_t w, uint64_t nwords, uint64_t n)
-{
-    if (w >= nwords) return 0;
-    const uint32_t tail = (uint32_t)(n & 63u);
-    return (w == nwords - 1 && tail) ? tail : 64u;
-}
-
 template <int NT>
 __device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, const uint32_t *vis_cnt, uint32_t *vtile_off,
                               uint64_t ntiles, uint64_t n, Counters *ctr, const Scratch &sq, const Scratch &sv);
@@ -592,7 +585,8 @@ constexpr size_t kCmpSmem = (kThreads / 32) * kCmpStage;            // 64 KB per
 
 // The next frontier F_{d+1} as a sorted queue (and as the bitmap the next level's B encode reads),
 // next cleared, and -- when V_{d+1} is coded -- the positions V_{d+1} codes.  One word per thread;
-// the CTA's tile offset comes from cmp_scan_kernel, each warp's from a CTA prefix of warp counts.
+// the CTA's tile offsets come from the count kernel's last CTA, each warp's from a CTA prefix of
+// warp counts.
 __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restrict__ next, uint64_t *__restrict__ fbits,
                                                                const uint64_t *__restrict__ visited, uint64_t nwords,
                                                                uint64_t n, const uint32_t *__restrict__ tile_off,
@@ -604,15 +598,17 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
     __shared__ uint32_t wq[kThreads / 32], wv[kThreads / 32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t w = (uint64_t)blockIdx.x * kCmpWords + threadIdx.x;
+    const bool v_list = want_v != 0;
     uint64_t x = 0, y = 0;
     if (w < nwords) {
         x = next[w];
         fbits[w] = x;  // F_{d+1} as a bitmap for the next level's B encode
         if (x) next[w] = 0;
-        if (want_v) {
+        if (v_list) {
             y = visited[w];
             if (sv.ctl->fb_mode == kFbClear) {
-                const uint64_t nb = bits_in_word(w, nwords, n);
+                const uint32_t tail = (uint32_t)(n & 63u);
+                const uint64_t nb = (w == nwords - 1 && tail) ? tail : 64u;
                 y = ~y & (nb == 64 ? ~0ull : ((1ull << nb) - 1ull));
             }
         }
@@ -624,7 +620,7 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
         wv[warp] = cv;
     }
     __syncthreads();
-    unsigned long long oq = tile_off[blockIdx.x], ov = want_v ? vtile_off[blockIdx.x] : 0ull;
+    unsigned long long oq = tile_off[blockIdx.x], ov = v_list ? vtile_off[blockIdx.x] : 0ull;
     for (uint32_t i = 0; i < warp; i++) {
         oq += wq[i];
         ov += wv[i];
@@ -632,7 +628,7 @@ __global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restr
     const uint64_t wbase = (uint64_t)blockIdx.x * kCmpWords + warp * 32u;
     uint32_t *stage = cstage + warp * 2048u;
     extract_words(x, wbase, oq, q, lane, stage);
-    if (want_v) extract_words(y, wbase, ov, sv.positions, lane, stage);
+    if (v_list) extract_words(y, wbase, ov, sv.positions, lane, stage);
 }
 
 // ---- round-trip check of the overlapped codec stage (FQ_BFS_OVERLAP) ----
@@ -693,10 +689,9 @@ __global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m,
 
 // Direction rule of the host loop: m_f*alpha > m_u  <=>  m_f > floor(m_u/alpha), and
 // n_f*beta < n  <=>  n_f < ceil(n/beta), so no product can overflow.
-// Handles set here: h_enc (0 queue + mirrored bitmap, 1 queue + bitmap from the bitmap, 2 no codec
-// stage) and h_dir (0 top-down, 1 bottom-up, +2 when the level skips the codec stage).
-__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGraphConditionalHandle h_enc,
-                                  cudaGraphConditionalHandle h_dir, int overlap, cudaGraphConditionalHandle h_chk)
+// The handle set here picks the level body: 2 * encode form (0 queue + mirrored bitmap, 1 queue +
+// bitmap from the bitmap, 2 no codec stage) + direction (0 top-down, 1 bottom-up).
+__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGraphConditionalHandle h_case)
 {
     const uint32_t flags = ls->p.flags;
     const unsigned long long alpha = ls->p.alpha, beta = ls->p.beta;
@@ -708,10 +703,8 @@ __global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGrap
     ls->dir = dir;
     const bool coded = codec && ls->n_f >= ls->p.min_codec_ids;
     ls->coded = coded ? 1u : 0u;
-    if (codec) cudaGraphSetConditional(h_enc, !coded ? 2u : (2ull * ls->n_f > n ? 1u : 0u));
-    cudaGraphSetConditional(h_dir, (dir == FQ_TOP_DOWN ? 0u : 1u) + (coded ? 0u : 2u));
-    // overlap: the round-trip check of the form this direction would consume (2: nothing to check)
-    if (overlap) cudaGraphSetConditional(h_chk, coded ? (dir == FQ_TOP_DOWN ? 0u : 1u) : 2u);
+    const uint32_t enc = !coded ? 2u : (2ull * ls->n_f > n ? 1u : 0u);
+    cudaGraphSetConditional(h_case, 2u * enc + (dir == FQ_TOP_DOWN ? 0u : 1u));
 }
 
 // Appends the level's Q_d, B_d [, V_d] to the stream log when they fit (the test loop_end_kernel
@@ -868,6 +861,8 @@ struct fq_graph {
     cudaGraph_t dl_graph;
     cudaGraphExec_t dl_exec;
     cudaStream_t dl_stream;
+    cudaStream_t dl_side[2];  // capture-time side streams of the level bodies (V_d; the overlapped codec stage)
+    cudaEvent_t dl_ev[3];     // their fork and join events
     const int32_t *dl_depth;
     const uint32_t *dl_parent;
     const uint8_t *dl_log;
@@ -1102,6 +1097,7 @@ struct LoopBuild {
     uint32_t *parent;
     uint8_t *log;
     bool codec, want_v, px, overlap;
+    int enc, dir;  // the level case a segment is captured for (seg_level)
 };
 
 cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGraphNode_t *dep, void *func,
@@ -1132,7 +1128,7 @@ cudaError_t add_conditional(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGra
     return cudaSuccess;
 }
 
-// Segments of the loop body, each captured from one stream into its own graph.
+// Segments of the loop body, each captured into its own graph.
 cudaError_t seg_init(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
@@ -1141,63 +1137,47 @@ cudaError_t seg_init(void *p)
     loop_init_kernel<<<1, 1, 0, c.g->dl_stream>>>(c.g->ls, c.g->ctr, c.g->m, c.g->n_iso);
     return cudaGetLastError();
 }
-cudaError_t seg_dense(void *p)
+
+// One level's work before the compaction, for one (encode form, direction) case: the visited stream
+// V_d on a side stream, and on the main stream the Q/B encode, the decode of the consumed form and
+// the expansion of it -- or, with the overlap, the expansion of the raw frontier on the main stream
+// while a second side stream encodes, decodes and compares.  The side streams fork from and join
+// back into the main stream inside the segment, so the level is one child graph with its own
+// parallel branches.
+cudaError_t seg_level(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_encode_q(c.g, true, 0, c.g->ls, c.g->dl_stream, c.px);
-}
-cudaError_t seg_sparse(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_encode_q(c.g, false, 0, c.g->ls, c.g->dl_stream, c.px);
-}
-cudaError_t seg_visited(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_encode_v(c.g, c.g->dl_stream);
-}
-cudaError_t seg_top_down(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    if (c.codec) {
-        const cudaError_t r = step_decode_q(c.g, 0, c.g->ls, c.g->dl_stream);
-        if (r != cudaSuccess) return r;
+    fq_graph *g = c.g;
+    cudaStream_t s0 = g->dl_stream;
+    const bool coded = c.codec && c.enc != 2;
+    const bool ovl = coded && c.overlap;
+    FQ_CU(cudaEventRecord(g->dl_ev[0], s0));
+    if (c.want_v) {
+        FQ_CU(cudaStreamWaitEvent(g->dl_side[0], g->dl_ev[0], 0));
+        FQ_CU(step_encode_v(g, g->dl_side[0]));
+        FQ_CU(cudaEventRecord(g->dl_ev[1], g->dl_side[0]));
     }
-    return step_top_down(c.g, c.codec, 0, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
-}
-cudaError_t seg_bottom_up(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    if (c.codec) {
-        const cudaError_t r = step_decode_b(c.g, c.g->dl_stream);
-        if (r != cudaSuccess) return r;
+    cudaStream_t cst = s0;
+    if (ovl) {
+        FQ_CU(cudaStreamWaitEvent(g->dl_side[1], g->dl_ev[0], 0));
+        cst = g->dl_side[1];
     }
-    return step_bottom_up(c.g, c.codec, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
+    if (coded) {
+        FQ_CU(step_encode_q(g, c.enc == 1, 0, g->ls, cst, c.px));
+        FQ_CU(c.dir == FQ_TOP_DOWN ? step_decode_q(g, 0, g->ls, cst) : step_decode_b(g, cst));
+        if (ovl) {
+            FQ_CU(c.dir == FQ_TOP_DOWN ? step_check_q(g, 0, g->ls, cst) : step_check_b(g, cst));
+            FQ_CU(cudaEventRecord(g->dl_ev[2], cst));
+        }
+    }
+    const bool consume_decoded = coded && !ovl;
+    if (c.dir == FQ_TOP_DOWN) FQ_CU(step_top_down(g, consume_decoded, 0, 0, c.depth, c.parent, g->ls, s0));
+    else FQ_CU(step_bottom_up(g, consume_decoded, 0, c.depth, c.parent, g->ls, s0));
+    if (c.want_v) FQ_CU(cudaStreamWaitEvent(s0, g->dl_ev[1], 0));
+    if (ovl) FQ_CU(cudaStreamWaitEvent(s0, g->dl_ev[2], 0));
+    return cudaSuccess;
 }
-cudaError_t seg_check_td(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    const cudaError_t r = step_decode_q(c.g, 0, c.g->ls, c.g->dl_stream);
-    if (r != cudaSuccess) return r;
-    return step_check_q(c.g, 0, c.g->ls, c.g->dl_stream);
-}
-cudaError_t seg_check_bu(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    const cudaError_t r = step_decode_b(c.g, c.g->dl_stream);
-    if (r != cudaSuccess) return r;
-    return step_check_b(c.g, c.g->dl_stream);
-}
-cudaError_t seg_top_down_plain(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_top_down(c.g, false, 0, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
-}
-cudaError_t seg_bottom_up_plain(void *p)
-{
-    const LoopBuild &c = *static_cast<const LoopBuild *>(p);
-    return step_bottom_up(c.g, false, 0, c.depth, c.parent, c.g->ls, c.g->dl_stream);
-}
+
 cudaError_t seg_compact(void *p)
 {
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
@@ -1208,115 +1188,70 @@ cudaError_t seg_compact(void *p)
     return cudaGetLastError();
 }
 
-// Build the device-driven loop for these buffers and mode:
-//   init -> while(h_while) { begin -> [if h_dense: Q+B from bitmap | Q+B mirrored] ->
-//                            [if h_dir: top-down | bottom-up] -> compact [-> log] -> end }
-// with V's encode on a parallel branch from begin to compact (overlapped with the rest).  With the
-// overlap the expansion switch holds only raw bodies and forms a branch of its own; the Q/B encode
-// is followed by the round-trip switch h_chk (decode + compare for top-down | bottom-up) on a
-// second branch; the compaction waits for all three.
+// Build the device-driven loop for these buffers and mode, as a linear chain inside the while node:
+//   init -> while(h_while) { begin -> switch(h_case: 6 level bodies) -> compact [-> log] -> end }
+// loop_begin picks the case = 2 * (encode form: 0 mirrored, 1 from the bitmap, 2 none) + direction.
+// Every parallel branch (V_d beside the level; with the overlap, the codec stage beside the
+// expansion) forks and joins inside a case body, which is a plain child graph.  A node that joins
+// a conditional node with another branch directly in the while body was, on rare launches, never
+// started by the executor although every branch had completed, so the body keeps no such join.
 cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
 {
     fq_graph *g = b.g;
     cudaStream_t cs = g->dl_stream;
-    cudaGraph_t sg_init = nullptr, sg_dense = nullptr, sg_sparse = nullptr, sg_v = nullptr, sg_td = nullptr,
-                sg_bu = nullptr, sg_tdp = nullptr, sg_bup = nullptr, sg_cmp = nullptr, sg_ctd = nullptr,
-                sg_cbu = nullptr, top = nullptr;
-    LoopBuild ctx = b;
-    const bool ovl = b.codec && b.overlap;
-    cudaError_t e = capture_segment(cs, &sg_init, seg_init, &ctx);
-    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_dense, seg_dense, &ctx);
-    if (e == cudaSuccess && b.codec) e = capture_segment(cs, &sg_sparse, seg_sparse, &ctx);
-    if (e == cudaSuccess && b.want_v) e = capture_segment(cs, &sg_v, seg_visited, &ctx);
-    if (e == cudaSuccess && b.codec && !ovl) e = capture_segment(cs, &sg_td, seg_top_down, &ctx);
-    if (e == cudaSuccess && b.codec && !ovl) e = capture_segment(cs, &sg_bu, seg_bottom_up, &ctx);
-    if (e == cudaSuccess && ovl) e = capture_segment(cs, &sg_ctd, seg_check_td, &ctx);
-    if (e == cudaSuccess && ovl) e = capture_segment(cs, &sg_cbu, seg_check_bu, &ctx);
-    if (e == cudaSuccess) e = capture_segment(cs, &sg_tdp, seg_top_down_plain, &ctx);
-    if (e == cudaSuccess) e = capture_segment(cs, &sg_bup, seg_bottom_up_plain, &ctx);
-    if (e == cudaSuccess) e = capture_segment(cs, &sg_cmp, seg_compact, &ctx);
+    constexpr int kCases = 6;
+    cudaGraph_t sg_init = nullptr, sg_cmp = nullptr, top = nullptr;
+    cudaGraph_t sg_case[kCases] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = capture_segment(cs, &sg_init, seg_init, const_cast<LoopBuild *>(&b));
+    for (int k = 0; k < kCases && e == cudaSuccess; k++) {
+        LoopBuild ctx = b;
+        ctx.enc = b.codec ? k / 2 : 2;  // without the codec stage every case is the raw level
+        ctx.dir = k % 2;
+        e = capture_segment(cs, &sg_case[k], seg_level, &ctx);
+    }
+    if (e == cudaSuccess) e = capture_segment(cs, &sg_cmp, seg_compact, const_cast<LoopBuild *>(&b));
     if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
     if (e != cudaSuccess) goto done;
     {
-        cudaGraphNode_t n_init, n_while, n_begin, n_last, tmp;
-        cudaGraph_t body, enc[3], dir[4], chk[2];
-        cudaGraphConditionalHandle h_while, h_enc, h_dir, h_chk;
+        cudaGraphNode_t n_init, n_while, n_begin, n_sw, n_cmp, n_end;
+        cudaGraph_t body, cases[kCases];
+        cudaGraphConditionalHandle h_while, h_case;
         if ((e = cudaGraphAddChildGraphNode(&n_init, top, nullptr, 0, sg_init)) != cudaSuccess) goto done;
         if ((e = cudaGraphConditionalHandleCreate(&h_while, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) goto done;
         if ((e = add_conditional(&n_while, top, &n_init, h_while, cudaGraphCondTypeWhile, 1, &body)) != cudaSuccess)
             goto done;
-        h_enc = 0;  // only a graph with the codec stage has the encode switch
-        if (b.codec && (e = cudaGraphConditionalHandleCreate(&h_enc, body, 0, 0)) != cudaSuccess) goto done;
-        if ((e = cudaGraphConditionalHandleCreate(&h_dir, body, 0, 0)) != cudaSuccess) goto done;
-        h_chk = 0;  // only the overlapped stage has the round-trip switch
-        if (ovl && (e = cudaGraphConditionalHandleCreate(&h_chk, body, 0, 0)) != cudaSuccess) goto done;
+        if ((e = cudaGraphConditionalHandleCreate(&h_case, body, 0, 0)) != cudaSuccess) goto done;
         {
             LoopState *ls = g->ls;
             uint64_t n = g->n;
-            int codec = b.codec ? 1 : 0, overlap = ovl ? 1 : 0;
-            void *args[] = {&ls, &n, &codec, &h_enc, &h_dir, &overlap, &h_chk};
+            int codec = b.codec ? 1 : 0;
+            void *args[] = {&ls, &n, &codec, &h_case};
             if ((e = add_kernel_node(&n_begin, body, nullptr, (void *)loop_begin_kernel, args)) != cudaSuccess) goto done;
         }
-        n_last = n_begin;
-        if (b.codec) {  // switch: mirrored, from the bitmap, or (below the threshold) no encode
-            if ((e = add_conditional(&tmp, body, &n_last, h_enc, cudaGraphCondTypeSwitch, 3, enc)) != cudaSuccess) goto done;
-            n_last = tmp;
-            cudaGraphNode_t c0, c1;
-            if ((e = cudaGraphAddChildGraphNode(&c0, enc[0], nullptr, 0, sg_sparse)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c1, enc[1], nullptr, 0, sg_dense)) != cudaSuccess) goto done;
+        if ((e = add_conditional(&n_sw, body, &n_begin, h_case, cudaGraphCondTypeSwitch, kCases, cases)) != cudaSuccess)
+            goto done;
+        for (int k = 0; k < kCases; k++) {
+            cudaGraphNode_t c;
+            if ((e = cudaGraphAddChildGraphNode(&c, cases[k], nullptr, 0, sg_case[k])) != cudaSuccess) goto done;
         }
-        // overlap: after the encode, the round-trip check of the form the direction names (value 2,
-        // no body: an uncoded level); the expansion below hangs off begin instead of the encode
-        cudaGraphNode_t n_chk = nullptr;
-        if (ovl) {
-            if ((e = add_conditional(&n_chk, body, &n_last, h_chk, cudaGraphCondTypeSwitch, 2, chk)) != cudaSuccess)
-                goto done;
-            cudaGraphNode_t c0, c1;
-            if ((e = cudaGraphAddChildGraphNode(&c0, chk[0], nullptr, 0, sg_ctd)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c1, chk[1], nullptr, 0, sg_cbu)) != cudaSuccess) goto done;
-            n_last = n_begin;
-        }
-        // V_d is coded on a branch of its own, beside the Q/B encode, decode and expansion (it reads
-        // only the previous compaction's positions and the visited bitmap, which this level's
-        // expansion does not touch); the compaction waits for both branches.
-        cudaGraphNode_t n_v = nullptr;
-        if (b.want_v && (e = cudaGraphAddChildGraphNode(&n_v, body, &n_begin, 1, sg_v)) != cudaSuccess) goto done;
-        // switch: top-down / bottom-up, each with the decode of the coded form, or (+2) on the raw form
-        if ((e = add_conditional(&tmp, body, &n_last, h_dir, cudaGraphCondTypeSwitch, 4, dir)) != cudaSuccess) goto done;
-        n_last = tmp;
-        {
-            cudaGraphNode_t c0, c1, c2, c3;
-            // without the codec stage the switch never takes cases 0 and 1; they hold the raw bodies
-            // too, so that no case is an empty graph
-            const bool dec = b.codec && !ovl;  // the coded bodies decode and consume; raw otherwise
-            if ((e = cudaGraphAddChildGraphNode(&c0, dir[0], nullptr, 0, dec ? sg_td : sg_tdp)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c1, dir[1], nullptr, 0, dec ? sg_bu : sg_bup)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c2, dir[2], nullptr, 0, sg_tdp)) != cudaSuccess) goto done;
-            if ((e = cudaGraphAddChildGraphNode(&c3, dir[3], nullptr, 0, sg_bup)) != cudaSuccess) goto done;
-        }
-        {
-            cudaGraphNode_t deps[3] = {n_last, nullptr, nullptr};
-            size_t nd = 1;
-            if (n_v) deps[nd++] = n_v;
-            if (n_chk) deps[nd++] = n_chk;
-            if ((e = cudaGraphAddChildGraphNode(&tmp, body, deps, nd, sg_cmp)) != cudaSuccess) goto done;
-        }
-        n_last = tmp;
+        if ((e = cudaGraphAddChildGraphNode(&n_cmp, body, &n_sw, 1, sg_cmp)) != cudaSuccess) goto done;
         {
             LoopState *ls = g->ls;
             const Counters *ctr = g->ctr;
             fq_level_record *recs = g->recs;
             uint64_t n = g->n;
             uint64_t n_iso = g->n_iso;
-            int codec = b.codec ? 1 : 0, want_v = b.want_v ? 1 : 0, has_log = b.log ? 1 : 0, overlap = ovl ? 1 : 0;
+            int codec = b.codec ? 1 : 0, want_v = b.want_v ? 1 : 0, has_log = b.log ? 1 : 0;
+            int overlap = b.codec && b.overlap ? 1 : 0;
             void *args[] = {&ls, &ctr, &recs, &n, &n_iso, &codec, &want_v, &has_log, &overlap, &h_while};
-            if ((e = add_kernel_node(&tmp, body, &n_last, (void *)loop_end_kernel, args)) != cudaSuccess) goto done;
+            if ((e = add_kernel_node(&n_end, body, &n_cmp, (void *)loop_end_kernel, args)) != cudaSuccess) goto done;
         }
     }
 done:
-    for (cudaGraph_t *gp : {&sg_init, &sg_dense, &sg_sparse, &sg_v, &sg_td, &sg_bu, &sg_tdp, &sg_bup, &sg_cmp, &sg_ctd,
-                            &sg_cbu})
-        if (*gp) cudaGraphDestroy(*gp);  // child-graph nodes hold their own copies
+    if (sg_init) cudaGraphDestroy(sg_init);  // child-graph nodes hold their own copies
+    if (sg_cmp) cudaGraphDestroy(sg_cmp);
+    for (int k = 0; k < kCases; k++)
+        if (sg_case[k]) cudaGraphDestroy(sg_case[k]);
     if (e != cudaSuccess) {
         note_cuda_error(e, __LINE__);
         if (top) cudaGraphDestroy(top);
@@ -1333,6 +1268,10 @@ void fq_graph_destroy_locked(fq_graph *g)
     if (g->dl_exec) cudaGraphExecDestroy(g->dl_exec);
     if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
     if (g->dl_stream) cudaStreamDestroy(g->dl_stream);
+    for (int i = 0; i < 2; i++)
+        if (g->dl_side[i]) cudaStreamDestroy(g->dl_side[i]);
+    for (int i = 0; i < 3; i++)
+        if (g->dl_ev[i]) cudaEventDestroy(g->dl_ev[i]);
     if (g->ov_stream) cudaStreamDestroy(g->ov_stream);
     for (int i = 0; i < 2; i++)
         if (g->ov_ev[i]) cudaEventDestroy(g->ov_ev[i]);
@@ -1526,8 +1465,12 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             if (g->dl_graph) cudaGraphDestroy(g->dl_graph);
             g->dl_exec = nullptr;
             g->dl_graph = nullptr;
-            if (!g->dl_stream) FQ_TRY(cudaStreamCreateWithFlags(&g->dl_stream, cudaStreamNonBlocking));
-            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited, px, overlap};
+            if (!g->dl_stream) {
+                FQ_TRY(cudaStreamCreateWithFlags(&g->dl_stream, cudaStreamNonBlocking));
+                for (int i = 0; i < 2; i++) FQ_TRY(cudaStreamCreateWithFlags(&g->dl_side[i], cudaStreamNonBlocking));
+                for (int i = 0; i < 3; i++) FQ_TRY(cudaEventCreateWithFlags(&g->dl_ev[i], cudaEventDisableTiming));
+            }
+            LoopBuild b{g, d_depth, d_parent, d_stream_log, codec, want_visited, px, overlap, 0, 0};
             FQ_TRY(build_device_loop(b, &g->dl_graph));
             FQ_TRY(cudaGraphInstantiate(&g->dl_exec, g->dl_graph, 0));
             g->dl_depth = d_depth;

@@ -13,7 +13,17 @@ __device__ __forceinline__ uint64_t dcdiv(uint64_t a, uint64_t b) { return (a + 
 __device__ __forceinline__ uint32_t ld_u32(const uint8_t *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
 
-constexpr uint32_t kSpinLimit = 1u << 22;  // polls before a bounded wait gives up
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls before a bounded wait gives up ...
+constexpr uint64_t kWaitLimitNs = 200ull * 1000ull * 1000ull;  // ... or this much time, whichever comes first
+constexpr uint32_t kTryWaitHintNs = 20000;  // longest a single poll may suspend the thread
+
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // ---- TMA staging helpers (1-D bulk copies into shared memory, completion on an mbarrier) ----
 
@@ -41,17 +51,22 @@ __device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, uint32_t
                  : "memory");
 }
 
-// Wait until phase `parity` of `bar` completes; bounded: gives up after kSpinLimit polls.
+// Wait until phase `parity` of `bar` completes; bounded in time: a poll suspends the thread for at
+// most kTryWaitHintNs, and the wait gives up after kWaitLimitNs of global time (or kSpinLimit polls).
+// A bound on polls alone is not one on time: how long an unsatisfied try_wait suspends is up to the
+// hardware unless the hint caps it.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
 {
+    const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < kSpinLimit; i++) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
+            : "r"(smem_addr(bar)), "r"(parity), "r"(kTryWaitHintNs)
             : "memory");
         if (ok) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
     }
     return false;
 }

@@ -54,6 +54,15 @@ struct MsState {
 // fq_msbfs_barrier_test settings, read at each launch.
 std::atomic<uint32_t> g_bar_extra{0}, g_bar_spins{0};
 
+constexpr uint64_t kBarrierLimitNs = 2ull * 1000ull * 1000ull * 1000ull;  // a barrier wait gives up after 2 s
+
+__device__ __forceinline__ uint64_t barrier_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ bool grid_sync(const MsState &s, int *s_abort)
 {
     __syncthreads();
@@ -67,8 +76,10 @@ __device__ __forceinline__ bool grid_sync(const MsState &s, int *s_abort)
             atomicAdd(s.bar + 1, 1u);
         } else {
             uint32_t spins = 0;
+            const uint64_t t0 = barrier_ns();
             while (*gen == my_gen) {
-                if (++spins > s.spin_limit || *reinterpret_cast<volatile unsigned int *>(s.abort_flag)) {
+                if (++spins > s.spin_limit || barrier_ns() - t0 > kBarrierLimitNs ||
+                    *reinterpret_cast<volatile unsigned int *>(s.abort_flag)) {
                     if (atomicExch(s.abort_flag, 1u) == 0u) set_error(s.err, FQ_ETIMEOUT, kWhereBfs, 0);
                     break;
                 }
