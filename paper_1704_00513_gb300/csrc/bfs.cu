@@ -371,7 +371,11 @@ __global__ void head_kernel(const int64_t *__restrict__ off, const uint32_t *__r
 }
 
 // The bottom-up sweep of bu_sweep_kernel over head records: the first two neighbours come with the
-// record (their frontier bits are tested together), the rest of the list is scanned as there.
+// record (their frontier bits are tested together), the rest of the list is scanned as there.  A
+// warp takes 32 words (1,024 vertices) at a time: one coalesced load of their done masks (visited |
+// isolated), a ballot of the words that still hold unvisited vertices, and only those words are
+// swept -- late levels, where almost every word is done, cost one load per 32 words instead of a
+// dependent load per word.
 __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t *__restrict__ front32,
                                                                  const uint32_t *__restrict__ visited32,
                                                                  const uint32_t *__restrict__ iso32,
@@ -386,55 +390,63 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t nwords = (n + 31) / 32;
     unsigned long long cnt = 0, degsum = 0;
-    for (uint64_t word = gw; word * 32u < n; word += nw) {
-        const uint32_t done = visited32[word] | iso32[word];
-        if (done == 0xffffffffu) continue;
-        const uint64_t w = word * 32u + lane;
-        bool found = false;
-        uint32_t par = 0;
-        if (w < n && !((done >> lane) & 1u)) {
-            const uint4 h = hc[w];
-            const uint32_t deg = h.y;
-            const bool h0 = deg > 0 && ((front32[h.z >> 5] >> (h.z & 31u)) & 1u);
-            const bool h1 = deg > 1 && ((front32[h.w >> 5] >> (h.w & 31u)) & 1u);
-            uint32_t j;  // entries examined
-            if (h0 || h1) {
-                found = true;
-                par = h0 ? h.z : h.w;
-                j = h0 ? 1u : 2u;
-            } else {
-                j = min(deg, 2u);
-                const uint32_t *row = cols + h.x;
-                for (; j + 1 < deg; j += 2) {
-                    const uint32_t u0 = row[j], u1 = row[j + 1];
-                    const bool f0 = (front32[u0 >> 5] >> (u0 & 31u)) & 1u;
-                    const bool f1 = (front32[u1 >> 5] >> (u1 & 31u)) & 1u;
-                    if (f0 || f1) {
-                        found = true;
-                        par = f0 ? u0 : u1;
-                        j += f0 ? 1u : 2u;
-                        break;
+    for (uint64_t chunk = gw; chunk * 32u < nwords; chunk += nw) {
+        const uint64_t my_word = chunk * 32u + lane;
+        const uint32_t my_done = my_word < nwords ? (visited32[my_word] | iso32[my_word]) : 0xffffffffu;
+        uint32_t pending = __ballot_sync(0xffffffffu, my_done != 0xffffffffu);
+        while (pending) {
+            const uint32_t src = (uint32_t)__ffs(pending) - 1u;
+            pending &= pending - 1u;
+            const uint32_t done = __shfl_sync(0xffffffffu, my_done, src);
+            const uint64_t word = chunk * 32u + src;
+            const uint64_t w = word * 32u + lane;
+            bool found = false;
+            uint32_t par = 0;
+            if (w < n && !((done >> lane) & 1u)) {
+                const uint4 h = hc[w];
+                const uint32_t deg = h.y;
+                const bool h0 = deg > 0 && ((front32[h.z >> 5] >> (h.z & 31u)) & 1u);
+                const bool h1 = deg > 1 && ((front32[h.w >> 5] >> (h.w & 31u)) & 1u);
+                uint32_t j;  // entries examined
+                if (h0 || h1) {
+                    found = true;
+                    par = h0 ? h.z : h.w;
+                    j = h0 ? 1u : 2u;
+                } else {
+                    j = min(deg, 2u);
+                    const uint32_t *row = cols + h.x;
+                    for (; j + 1 < deg; j += 2) {
+                        const uint32_t u0 = row[j], u1 = row[j + 1];
+                        const bool f0 = (front32[u0 >> 5] >> (u0 & 31u)) & 1u;
+                        const bool f1 = (front32[u1 >> 5] >> (u1 & 31u)) & 1u;
+                        if (f0 || f1) {
+                            found = true;
+                            par = f0 ? u0 : u1;
+                            j += f0 ? 1u : 2u;
+                            break;
+                        }
+                    }
+                    if (!found && j < deg) {
+                        const uint32_t u0 = row[j];
+                        j += 1;
+                        if ((front32[u0 >> 5] >> (u0 & 31u)) & 1u) {
+                            found = true;
+                            par = u0;
+                        }
                     }
                 }
-                if (!found && j < deg) {
-                    const uint32_t u0 = row[j];
-                    j += 1;
-                    if ((front32[u0 >> 5] >> (u0 & 31u)) & 1u) {
-                        found = true;
-                        par = u0;
-                    }
-                }
+                cnt += j;
+                if (found) degsum += deg;
             }
-            cnt += j;
-            if (found) degsum += deg;
+            if (found) {
+                depth[w] = newdepth;
+                if (parent) parent[w] = par;
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, found);
+            if (lane == 0 && mask) next32[word] = mask;
         }
-        if (found) {
-            depth[w] = newdepth;
-            if (parent) parent[w] = par;
-        }
-        const uint32_t mask = __ballot_sync(0xffffffffu, found);
-        if (lane == 0 && mask) next32[word] = mask;
     }
     cnt = warp_sum64(cnt);
     degsum = warp_sum64(degsum);
@@ -1039,8 +1051,9 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
     const uint64_t words32 = cdiv(g->n, 32);
     const uint32_t grid = tuned_grid(FQ_TUNE_BU_SWEEP, g->n, std::min<uint64_t>(cdiv(words32, kThreads / 32), (uint64_t)sms * 16),
                                      cdiv(words32, kThreads / 32));
-    if (g->hc)
-        bu_sweep_head_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
+    if (g->hc)  // one warp per 32 words at a time: no more warps than chunks of 32 words
+        bu_sweep_head_kernel<<<std::max<uint32_t>((uint32_t)std::min<uint64_t>(grid, cdiv(cdiv(words32, 32), kThreads / 32)), 1),
+                               kThreads, 0, st>>>(
             reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
             reinterpret_cast<uint32_t *>(g->next), g->hc, g->cols, d_depth, d_parent, newdepth, g->n,
             &g->ctr->examined, &g->ctr->m_f_next, ls);
