@@ -518,6 +518,7 @@ def run_fqbfs(args, world, rank, local):
             level_lines.append({"root": int(r), "level": rec["level"],
                                 "direction": "bottom_up" if rec["direction"] else "top_down",
                                 "n_f": rec["n_f"], "m_f": rec["m_f"], "m_u": rec["m_u"], "examined": rec["examined"],
+                                "cols_read": rec["cols_read"],
                                 "q_bytes": rec["q_bytes"], "b_bytes": rec["b_bytes"], "v_bytes": rec["v_bytes"],
                                 "kernel_ms": {k: round(v, 5) for k, v in rec["kernel_ms"].items() if v},
                                 "model_bytes": {k: v for k, v in mb.items() if v}})

@@ -348,6 +348,10 @@ typedef struct fq_level_record {
     uint64_t m_f;             /* sum of degrees over F_d                                        */
     uint64_t m_u;             /* sum of degrees over vertices not yet visited                   */
     uint64_t examined;        /* adjacency entries read while expanding F_d                     */
+    uint64_t cols_read;       /* of those, the entries read from the column array: all of them
+                                 top-down; bottom-up, those past the two that each vertex's
+                                 16-byte head record holds (the handle keeps head records when
+                                 the graph has fewer than 2^32 adjacency entries)               */
     uint64_t q_bytes, b_bytes, v_bytes; /* |Q_d|, |B_d|, |V_d| (0 when not encoded)             */
     uint64_t log_offset;      /* offset of Q_d, then B_d, then V_d in the stream log (or ~0)    */
     float kernel_ms[FQ_NUM_KCLASS]; /* FQ_BFS_TIMING, host-driven loop: this level's kernel time
@@ -364,8 +368,8 @@ typedef struct fq_level_record {
  *   top_down  4 per edge examined + 20 per frontier vertex (offsets pair + queue id) + 8 per
  *             discovered vertex (depth, parent);
  *   bottom_up 4 N/8 (frontier, visited, isolated and next bitmaps) + 16 per unvisited vertex of
- *             nonzero degree (its offsets pair; isolated vertices are skipped unread) + 4 per edge
- *             examined + 8 per discovered vertex;
+ *             nonzero degree (its offsets pair or head record; isolated vertices are skipped
+ *             unread) + 4 per column entry read (cols_read) + 8 per discovered vertex;
  *   compact   3 N/8 + 20 per discovered vertex.
  * A coded level is one with q_bytes > 0; V_d is coded when v_bytes > 0. */
 void fq_bfs_level_bytes(uint64_t n, uint64_t n_isolated, uint32_t root_isolated, const fq_level_record *rec,

@@ -56,7 +56,9 @@ struct Counters {
     unsigned long long r_detail_q, r_detail_v;
     unsigned long long n_iso;      // degree-0 vertices (counted by iso_kernel at handle creation)
     uint32_t cmp_ticket, pad32;    // compaction CTAs done with their counts (the last one resets it)
-    unsigned long long pad[13];
+    unsigned long long cols_read;  // live: bottom-up reads of the column array (entries past the head records)
+    unsigned long long r_cols_read;
+    unsigned long long pad[11];
 };
 static_assert(sizeof(Counters) == 256, "counter block is 256 bytes");
 
@@ -148,7 +150,7 @@ __global__ void iso_kernel(const int64_t *off, uint64_t n, uint32_t *iso32, unsi
 // documents each term), added into out[].  Shared by both level-loop drivers and the host-side
 // entry point, so the bench's roofline numerator can be recomputed from the level records.
 struct LevelIn {
-    uint64_t n, n_iso, visited, n_f, examined, n_f_next, qb, bb, vb;
+    uint64_t n, n_iso, visited, n_f, examined, cols_read, n_f_next, qb, bb, vb;
     uint32_t dir, root_iso;
     bool coded, want_v;
 };
@@ -163,11 +165,12 @@ __host__ __device__ inline void level_bytes(const LevelIn &x, uint64_t *out)
         out[FQ_K_TOP_DOWN] += 4 * x.examined + 20 * x.n_f + 8 * x.n_f_next;
     } else {
         if (x.coded) out[FQ_K_DECODE] += x.bb + nbytes;
-        // the sweep reads the offsets pair of every vertex that is neither visited nor isolated;
-        // isolated vertices other than an isolated root are never visited
+        // the sweep reads 16 bytes (the offsets pair, or the head record) of every vertex that is
+        // neither visited nor isolated, and the column entries its records do not hold; isolated
+        // vertices other than an isolated root are never visited
         const uint64_t iso_unvisited = x.n_iso - (x.root_iso && x.n_iso ? 1u : 0u);
         const uint64_t swept = x.n > x.visited + iso_unvisited ? x.n - x.visited - iso_unvisited : 0u;
-        out[FQ_K_BOTTOM_UP] += 4 * nbytes + 16 * swept + 4 * x.examined + 8 * x.n_f_next;
+        out[FQ_K_BOTTOM_UP] += 4 * nbytes + 16 * swept + 4 * x.cols_read + 8 * x.n_f_next;
     }
     out[FQ_K_COMPACT] += 3 * nbytes + 20 * x.n_f_next;
 }
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_kernel(const uint32_t *__re
                                                             const uint32_t *__restrict__ cols, int32_t *depth,
                                                             uint32_t *parent, int32_t newdepth, uint64_t n,
                                                             unsigned long long *examined, unsigned long long *m_f_next,
-                                                            const LoopState *ls)
+                                                            unsigned long long *cols_read, const LoopState *ls)
 {
     if (ls) newdepth = (int32_t)ls->d + 1;
     const uint32_t lane = threadIdx.x & 31u;
@@ -352,7 +355,10 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_kernel(const uint32_t *__re
     }
     cnt = warp_sum64(cnt);
     degsum = warp_sum64(degsum);
-    if (lane == 0 && cnt) atomicAdd(examined, cnt);
+    if (lane == 0 && cnt) {
+        atomicAdd(examined, cnt);
+        atomicAdd(cols_read, cnt);  // every entry this sweep examines comes from cols
+    }
     if (lane == 0 && degsum) atomicAdd(m_f_next, degsum);
 }
 
@@ -384,14 +390,15 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
                                                                  const uint32_t *__restrict__ cols, int32_t *depth,
                                                                  uint32_t *parent, int32_t newdepth, uint64_t n,
                                                                  unsigned long long *examined,
-                                                                 unsigned long long *m_f_next, const LoopState *ls)
+                                                                 unsigned long long *m_f_next,
+                                                                 unsigned long long *cols_read, const LoopState *ls)
 {
     if (ls) newdepth = (int32_t)ls->d + 1;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nwords = (n + 31) / 32;
-    unsigned long long cnt = 0, degsum = 0;
+    unsigned long long cnt = 0, degsum = 0, tail = 0;
     for (uint64_t chunk = gw; chunk * 32u < nwords; chunk += nw) {
         const uint64_t my_word = chunk * 32u + lane;
         const uint32_t my_done = my_word < nwords ? (visited32[my_word] | iso32[my_word]) : 0xffffffffu;
@@ -438,6 +445,7 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
                     }
                 }
                 cnt += j;
+                tail += j - min(j, min(deg, 2u));  // entries past the record's two came from cols
                 if (found) degsum += deg;
             }
             if (found) {
@@ -450,8 +458,10 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
     }
     cnt = warp_sum64(cnt);
     degsum = warp_sum64(degsum);
+    tail = warp_sum64(tail);
     if (lane == 0 && cnt) atomicAdd(examined, cnt);
     if (lane == 0 && degsum) atomicAdd(m_f_next, degsum);
+    if (lane == 0 && tail) atomicAdd(cols_read, tail);
 }
 
 // ---- compaction: next bitmap -> sorted queue, n_f, m_f, visited |= next, V positions ----
@@ -545,6 +555,7 @@ __device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, cons
     // this kernel's critical path)
     if (threadIdx.x == 0) {
         const unsigned long long m_f = __ldcg(&ctr->m_f_next), ex = __ldcg(&ctr->examined), hub = __ldcg(&ctr->hub_items);
+        const unsigned long long cr = __ldcg(&ctr->cols_read);
         const int32_t cq = __ldcg(&sq.ctl->code), cv = __ldcg(&sv.ctl->code);
         const uint32_t wq = __ldcg(&sq.ctl->where), wv = __ldcg(&sv.ctl->where);
         const unsigned long long dq = __ldcg(&sq.ctl->detail), dv = __ldcg(&sv.ctl->detail);
@@ -555,6 +566,8 @@ __device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, cons
         ctr->v_count = vcount;
         ctr->r_examined = ex;
         ctr->examined = 0;
+        ctr->r_cols_read = cr;
+        ctr->cols_read = 0;
         ctr->r_hub_items = hub;
         ctr->hub_items = 0;
         ctr->r_err_q = cq;
@@ -776,7 +789,9 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     const unsigned long long nbytes = (n + 7) / 8;
     const bool dense = 2ull * n_f > n;
 
-    const LevelIn lin{n, n_iso, ls->visited, n_f, examined, nf_next, qb, bb, vb, dir, ls->root_iso, coded, want_v != 0};
+    const unsigned long long cols_read = dir == FQ_TOP_DOWN ? m_f : ctr->r_cols_read;
+    const LevelIn lin{n, n_iso, ls->visited, n_f, examined, cols_read, nf_next, qb, bb, vb, dir, ls->root_iso, coded,
+                      want_v != 0};
     level_bytes(lin, st.kernel_bytes);
     if (coded) st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
     if (want_v) st.kernel_launches[FQ_K_ENCODE] += 2;
@@ -808,6 +823,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
         r.m_f = m_f;
         r.m_u = ls->m_u;
         r.examined = examined;
+        r.cols_read = cols_read;
         r.q_bytes = qb;
         r.b_bytes = bb;
         r.v_bytes = vb;
@@ -1056,12 +1072,12 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
                                kThreads, 0, st>>>(
             reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
             reinterpret_cast<uint32_t *>(g->next), g->hc, g->cols, d_depth, d_parent, newdepth, g->n,
-            &g->ctr->examined, &g->ctr->m_f_next, ls);
+            &g->ctr->examined, &g->ctr->m_f_next, &g->ctr->cols_read, ls);
     else
         bu_sweep_kernel<<<std::max<uint32_t>(grid, 1), kThreads, 0, st>>>(
             reinterpret_cast<const uint32_t *>(fin), reinterpret_cast<const uint32_t *>(g->visited), g->iso32,
             reinterpret_cast<uint32_t *>(g->next), g->off, g->cols, d_depth, d_parent, newdepth, g->n,
-            &g->ctr->examined, &g->ctr->m_f_next, ls);
+            &g->ctr->examined, &g->ctr->m_f_next, &g->ctr->cols_read, ls);
     return cudaGetLastError();
 }
 
@@ -1315,8 +1331,9 @@ void fq_bfs_level_bytes(uint64_t n, uint64_t n_isolated, uint32_t root_isolated,
 {
     if (!rec || !out) return;
     for (int k = 0; k < FQ_NUM_KCLASS; k++) out[k] = 0;
-    const LevelIn lin{n, n_isolated, visited, rec->n_f, rec->examined, n_f_next, rec->q_bytes, rec->b_bytes,
-                      rec->v_bytes, rec->direction, root_isolated ? 1u : 0u, rec->q_bytes > 0, rec->v_bytes > 0};
+    const LevelIn lin{n, n_isolated, visited, rec->n_f, rec->examined, rec->cols_read, n_f_next, rec->q_bytes,
+                      rec->b_bytes, rec->v_bytes, rec->direction, root_isolated ? 1u : 0u, rec->q_bytes > 0,
+                      rec->v_bytes > 0};
     level_bytes(lin, out);
 }
 
@@ -1625,8 +1642,9 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         const uint64_t qb = coded ? hc->q_bytes : 0, bb = coded ? hc->b_bytes : 0, vb = want_visited ? hc->v_bytes : 0;
 
         // algorithmic bytes of this level (design model)
-        const LevelIn lin{n, g->n_iso, visited_count, n_f, examined, nf_next, qb, bb, vb, (uint32_t)dir, root_iso,
-                          coded, want_visited};
+        const uint64_t cols_read = dir == FQ_TOP_DOWN ? m_f : hc->r_cols_read;
+        const LevelIn lin{n, g->n_iso, visited_count, n_f, examined, cols_read, nf_next, qb, bb, vb, (uint32_t)dir,
+                          root_iso, coded, want_visited};
         level_bytes(lin, stats.kernel_bytes);
 
         uint64_t log_off = ~0ull;
@@ -1650,6 +1668,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
             r.m_f = m_f;
             r.m_u = m_u;
             r.examined = examined;
+            r.cols_read = cols_read;
             r.q_bytes = qb;
             r.b_bytes = bb;
             r.v_bytes = vb;

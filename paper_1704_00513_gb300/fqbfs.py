@@ -54,7 +54,7 @@ class fq_bfs_stats(ctypes.Structure):
 
 class fq_level_record(ctypes.Structure):
     _fields_ = [("level", _u32), ("direction", _u32), ("n_f", _u64), ("m_f", _u64), ("m_u", _u64),
-                ("examined", _u64), ("q_bytes", _u64), ("b_bytes", _u64), ("v_bytes", _u64),
+                ("examined", _u64), ("cols_read", _u64), ("q_bytes", _u64), ("b_bytes", _u64), ("v_bytes", _u64),
                 ("log_offset", _u64), ("kernel_ms", ctypes.c_float * 6)]
 
 

@@ -30,8 +30,8 @@ def _records(off, cols, root):
     recs = []
     for s, st in zip(sched, streams):
         recs.append(dict(level=s["level"], direction=s["direction"], n_f=s["n_f"], m_f=s["m_f"], m_u=s["m_u"],
-                         examined=s["examined"], q_bytes=st["Q"].size, b_bytes=st["B"].size, v_bytes=st["V"].size,
-                         log_offset=0))
+                         examined=s["examined"], cols_read=s["examined"], q_bytes=st["Q"].size,
+                         b_bytes=st["B"].size, v_bytes=st["V"].size, log_offset=0))
     return depth, recs
 
 
@@ -59,7 +59,7 @@ def _check_graph(off, cols, root):
             got = fqbfs.level_bytes(n, n_iso, deg[root] == 0, rr, visited, nxt)
             if direction == fqbfs.FQ_BOTTOM_UP:
                 swept = _swept_by_count(off, depth, r["level"])
-                assert got["bottom_up"] == 4 * nbytes + 16 * swept + 4 * r["examined"] + 8 * nxt, r["level"]
+                assert got["bottom_up"] == 4 * nbytes + 16 * swept + 4 * r["cols_read"] + 8 * nxt, r["level"]
                 assert got["top_down"] == 0
                 assert got["decode"] == r["b_bytes"] + nbytes
                 total_bu += got["bottom_up"]
@@ -90,8 +90,9 @@ def test_model_with_an_isolated_root_and_isolated_vertices():
 
 
 def test_uncoded_level_charges_no_codec_bytes():
-    rec = dict(level=3, direction=fqbfs.FQ_BOTTOM_UP, n_f=1000, m_f=5000, m_u=9000, examined=7000, q_bytes=0,
-               b_bytes=0, v_bytes=0, log_offset=0)
+    rec = dict(level=3, direction=fqbfs.FQ_BOTTOM_UP, n_f=1000, m_f=5000, m_u=9000, examined=7000, cols_read=2500,
+               q_bytes=0, b_bytes=0, v_bytes=0, log_offset=0)
     got = fqbfs.level_bytes(1 << 20, 1000, False, rec, 500_000, 2000)
     assert got["encode"] == 0 and got["decode"] == 0
-    assert got["bottom_up"] == 4 * (1 << 17) + 16 * ((1 << 20) - 500_000 - 1000) + 4 * 7000 + 8 * 2000
+    # the column bytes are the entries actually read from cols, not all entries examined
+    assert got["bottom_up"] == 4 * (1 << 17) + 16 * ((1 << 20) - 500_000 - 1000) + 4 * 2500 + 8 * 2000

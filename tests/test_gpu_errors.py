@@ -110,6 +110,19 @@ def test_allocator_hook_refusal_gives_enomem(rmat14):
     g.close()
 
 
+def _bu_cols_past_head(off, cols, depth, d):
+    """Column entries a bottom-up sweep of level d reads beyond each vertex's first two (which the
+    handle's head records hold): per unvisited vertex of degree > 0, e - 2 when it examines e > 2
+    entries, e being the position of its first neighbour in F_d plus one, or its degree."""
+    total = 0
+    for v in np.nonzero(((depth < 0) | (depth > d)) & (np.diff(off) > 0))[0]:
+        row = cols[off[v]:off[v + 1]]
+        hit = np.nonzero(depth[row] == d)[0]
+        e = int(hit[0]) + 1 if hit.size else row.size
+        total += max(0, e - 2)
+    return total
+
+
 @pytest.mark.parametrize("flags", [0, fqbfs.FQ_BFS_FORCE_BOTTOM_UP, fqbfs.FQ_BFS_DEVICE_LOOP])
 def test_kernel_bytes_equal_the_model_of_the_oracle_levels(rmat14, flags):
     off, cols, roots = rmat14
@@ -132,7 +145,10 @@ def test_kernel_bytes_equal_the_model_of_the_oracle_levels(rmat14, flags):
                 want[k] += v
             if rec["direction"] == fqbfs.FQ_BOTTOM_UP:   # the offsets the sweep reads, counted directly
                 swept = np.count_nonzero(((ref < 0) | (ref > rec["level"])) & (deg > 0))
+                assert rec["cols_read"] == _bu_cols_past_head(off_h, cols_h, ref, rec["level"])
                 one = fqbfs.level_bytes(n, n_iso, deg[r] == 0, rec, visited, nxt)["bottom_up"]
-                assert one == 4 * ((n + 7) // 8) + 16 * swept + 4 * rec["examined"] + 8 * nxt
+                assert one == 4 * ((n + 7) // 8) + 16 * swept + 4 * rec["cols_read"] + 8 * nxt
+            else:
+                assert rec["cols_read"] == rec["examined"]
         assert res.stats["kernel_bytes"] == want
     g.close()
