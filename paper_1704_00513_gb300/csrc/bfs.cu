@@ -5,8 +5,8 @@
 //   1. encode F_d as Q_d (sorted queue, FQ) and B_d (bitmap, FB), and the visited bitmap as
 //      V_d -- the compress steps before the thesis' ALLGATHERV/ALLTOALLV; the byte counts are
 //      the exchange volume.  When 2|F_d| <= n the set positions of the frontier bitmap are the
-//      queue itself, so one encode call writes Q_d and B_d together; V_d's positions were
-//      extracted by the previous level's compaction;
+//      queue itself, so one encode call writes Q_d and B_d together; V_d's positions are
+//      extracted from the visited bitmap (on a parallel branch with the device-driven loop);
 //   2. choose the direction from (n_f, m_f, m_u): top-down -> bottom-up when m_f*alpha > m_u,
 //      back when n_f*beta < n (direction optimisation, sec. 3.1);
 //   3. decode the form that direction consumes (Q_d for top-down, B_d for bottom-up) -- the
@@ -14,8 +14,8 @@
 //   4. expand: top-down over the decoded queue (t = A (x) f masked by the visited list) or
 //      bottom-up against the decoded bitmap; depth/parent written by the discovering thread;
 //   5. compact the next-frontier bitmap into the sorted queue F_{d+1} (popcount + prefix sum,
-//      the popcount-indexed sparse vector of sec. 3.1), visited |= next, count n_f and m_f, and
-//      extract the positions V_{d+1} will code.
+//      the popcount-indexed sparse vector of sec. 3.1), visited |= next, count n_f, m_f and
+//      the visited bits per tile that V_{d+1}'s extraction starts from.
 // The host reads one 256-byte counter record per level (termination test and direction).
 #include <algorithm>
 #include <cstring>
@@ -33,8 +33,9 @@ namespace {
 constexpr uint32_t kHubDegree = 256;   // top-down: vertices of at least this degree are split
 constexpr uint32_t kHubChunk = 2048;   //   into chunks of this many edges, one CTA each
 constexpr uint32_t kThreads = 256;
-constexpr uint32_t kCmpWordsPerThread = 1;
-constexpr uint32_t kCmpWords = kThreads * kCmpWordsPerThread;  // 256 words = 16384 vertices per tile
+// Compaction tiles: a tile is `sub` sub-tiles of 256 words (16,384 vertices each, one word per
+// thread), `sub` chosen per handle so that the tiles fit in one wave of the extract kernel.
+constexpr uint32_t kCmpSubWords = kThreads;
 
 struct HubItem {
     uint32_t v;
@@ -43,7 +44,8 @@ struct HubItem {
 };
 
 // Device counters (first 256 bytes of the handle's allocation).  "live" fields are updated
-// during a level; cmp_scan_kernel copies the ones it clears into the r_* record the host reads.
+// during a level; the compaction's extract kernel (its first CTA) copies the ones it clears into
+// the r_* record the host reads.
 struct Counters {
     unsigned long long n_f_next;   // |F_{d+1}|                         (cmp_scan)
     unsigned long long m_f_next;   // live: degree sum over F_{d+1}     (expansion kernels)
@@ -55,7 +57,7 @@ struct Counters {
     uint32_t r_where_q, r_where_v;
     unsigned long long r_detail_q, r_detail_v;
     unsigned long long n_iso;      // degree-0 vertices (counted by iso_kernel at handle creation)
-    uint32_t cmp_ticket, pad32;    // compaction CTAs done with their counts (the last one resets it)
+    uint32_t pad32a, pad32;
     unsigned long long cols_read;  // live: bottom-up reads of the column array (entries past the head records)
     unsigned long long r_cols_read;
     unsigned long long pad[11];
@@ -99,8 +101,8 @@ __device__ __forceinline__ unsigned long long td_visit(uint32_t w, uint32_t src,
 
 // Level 0: the root, V_0's single position, cleared codec scratch.
 __global__ void bfs_init_kernel(const int64_t *off, uint32_t root, uint64_t n, int32_t *depth, uint32_t *parent,
-                                uint32_t *q, uint64_t *fbits, uint64_t *visited, uint32_t *vis_cnt, Counters *ctr,
-                                Scratch sq, Scratch sv, const LoopState *ls)
+                                uint32_t *q, uint64_t *fbits, uint64_t *visited, uint32_t *vis_cnt, uint64_t tile_bits,
+                                Counters *ctr, Scratch sq, Scratch sv, const LoopState *ls)
 {
     if (ls) root = ls->p.root;  // device-driven loop: the root is a run parameter
     if (threadIdx.x != 0) return;
@@ -111,7 +113,7 @@ __global__ void bfs_init_kernel(const int64_t *off, uint32_t root, uint64_t n, i
     q[0] = root;
     fbits[root >> 6] |= 1ull << (root & 63u);
     visited[root >> 6] |= 1ull << (root & 63u);
-    vis_cnt[root / (64u * kCmpWords)] = 1;
+    vis_cnt[root / tile_bits] = 1;  // the visited count of the root's compaction tile
     ctr->n_f_next = 1;
     ctr->r_m_f = (unsigned long long)(off[root + 1] - off[root]);
     ctr->m_f_next = 0;
@@ -465,122 +467,92 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
 }
 
 // ---- compaction: next bitmap -> sorted queue, n_f, m_f, visited |= next, V positions ----
+// Two launches per level and no one-CTA step: the count kernel writes each tile's counts, and
+// every CTA of the extract kernel sums the counts of the tiles before its own (a few hundred
+// words from L2) for its output offsets and the level's totals.
 
-template <int NT>
-__device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, const uint32_t *vis_cnt, uint32_t *vtile_off,
-                              uint64_t ntiles, uint64_t n, Counters *ctr, const Scratch &sq, const Scratch &sv);
-
-// Per 16,384-vertex tile: the next frontier's count, and visited |= next (with the tile's running
-// visited count).  The last CTA to finish (a ticket taken after a fence, so every other CTA's
-// counts are visible to it) then does the level's one-CTA work: the offsets of the next-frontier
-// positions and of V's positions, the level record, and cleared codec scratch (cmp_scan_body).
+// Per tile: the next frontier's count, visited |= next, and (when V_{d+1} is coded) the tile's
+// visited count after the update.  Every sub-tile's loads are issued before any is used.
 __global__ void __launch_bounds__(kThreads) cmp_count_kernel(const uint64_t *__restrict__ next, uint64_t *visited,
-                                                             uint64_t nwords, uint32_t *tile_cnt, uint32_t *vis_cnt,
-                                                             uint32_t *tile_off, uint32_t *vtile_off, uint64_t n,
-                                                             Counters *ctr, Scratch sq, Scratch sv)
+                                                             uint64_t nwords, uint32_t sub, uint32_t *tile_cnt,
+                                                             uint32_t *vis_cnt, int want_v)
 {
-    __shared__ uint32_t ws[kThreads / 32];
-    __shared__ bool s_last;
-    const uint64_t w0 = (uint64_t)blockIdx.x * kCmpWords + (uint64_t)threadIdx.x * kCmpWordsPerThread;
-    uint32_t cnt = 0;
+    __shared__ uint32_t ws[kThreads / 32], wv[kThreads / 32];
+    constexpr uint32_t kAhead = 4;  // sub-tiles whose words are in flight together
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t w0 = (uint64_t)blockIdx.x * sub * kCmpSubWords + threadIdx.x;
+    uint32_t cnt = 0, vc = 0;
+    for (uint32_t s0 = 0; s0 < sub; s0 += kAhead) {
+        uint64_t x[kAhead], v[kAhead];
 #pragma unroll
-    for (uint32_t j = 0; j < kCmpWordsPerThread; j++) {
-        if (w0 + j < nwords) {
-            const uint64_t x = next[w0 + j];
-            if (x) {
-                visited[w0 + j] |= x;
-                cnt += __popcll(x);
+        for (uint32_t j = 0; j < kAhead; j++) {
+            const uint64_t w = w0 + (uint64_t)(s0 + j) * kCmpSubWords;
+            const bool in = s0 + j < sub && w < nwords;
+            x[j] = in ? next[w] : 0ull;
+            v[j] = (in && want_v) ? visited[w] : 0ull;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kAhead; j++) {
+            const uint64_t w = w0 + (uint64_t)(s0 + j) * kCmpSubWords;
+            if (x[j]) {
+                if (want_v) visited[w] = v[j] | x[j];
+                else visited[w] |= x[j];
             }
+            cnt += (uint32_t)__popcll(x[j]);
+            vc += (uint32_t)__popcll(v[j] | x[j]);  // the next frontier is disjoint from the visited set
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31u) == 0) ws[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (uint32_t i = 0; i < kThreads / 32; i++) t += ws[i];
-        tile_cnt[blockIdx.x] = t;
-        vis_cnt[blockIdx.x] += t;  // the next frontier is disjoint from the visited set
-        __threadfence();
-        s_last = atomicAdd(&ctr->cmp_ticket, 1u) == gridDim.x - 1;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    vc = __reduce_add_sync(0xffffffffu, vc);
+    if (lane == 0) {
+        ws[warp] = cnt;
+        wv[warp] = vc;
     }
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    cmp_scan_body<kThreads>(tile_cnt, tile_off, vis_cnt, vtile_off, gridDim.x, n, ctr, sq, sv);
-    if (threadIdx.x == 0) ctr->cmp_ticket = 0u;
+    if (threadIdx.x == 0) {
+        uint32_t t = 0, tv = 0;
+        for (uint32_t i = 0; i < kThreads / 32; i++) {
+            t += ws[i];
+            tv += wv[i];
+        }
+        tile_cnt[blockIdx.x] = t;
+        vis_cnt[blockIdx.x] = tv;
+    }
 }
 
-// The last compaction CTA's work: offsets of the next-frontier positions and of V's positions
-// (set or clear bits of the visited bitmap), the level record, and cleared codec scratch for the
-// next level.  The counts are read with L2-coherent loads: other CTAs wrote them.
-template <int NT>
-__device__ void cmp_scan_body(const uint32_t *tile_cnt, uint32_t *tile_off, const uint32_t *vis_cnt, uint32_t *vtile_off,
-                              uint64_t ntiles, uint64_t n, Counters *ctr, const Scratch &sq, const Scratch &sv)
+// The level record and cleared codec scratch (first thread of the extract kernel's first CTA):
+// the level's live counters and codec status are snapshot into the r_* fields and cleared for the
+// next level, and V_{d+1}'s control block gets its count and mode.  Every load comes first: the
+// stores could alias them, and this thread's round trips are on the kernel's critical path.
+__device__ __forceinline__ void cmp_snapshot(Counters *ctr, const Scratch &sq, const Scratch &sv,
+                                             unsigned long long nf, unsigned long long vis,
+                                             unsigned long long vcount, bool set_mode)
 {
-    __shared__ unsigned long long sm[33];
-    const uint64_t chunk = (ntiles + NT - 1) / NT;
-    const uint64_t t0 = min(ntiles, (uint64_t)threadIdx.x * chunk), t1 = min(ntiles, t0 + chunk);
-    const uint64_t tile_bits = 64ull * kCmpWords;
-    // each thread sums its chunk of both count arrays (one tile per thread up to 2^24 vertices)
-    unsigned long long lq = 0, lv = 0;
-    for (uint64_t t = t0; t < t1; t++) {
-        lq += __ldcg(tile_cnt + t);
-        lv += __ldcg(vis_cnt + t);
-    }
-    const unsigned long long lb = t1 > t0 ? min(n, t1 * tile_bits) - t0 * tile_bits : 0ull;  // bits in the chunk
-    unsigned long long nf_total = 0, vis_total = 0, total = 0;
-    unsigned long long run = cta_excl_scan64<NT>(lq, sm, &nf_total);
-    cta_excl_scan64<NT>(lv, sm, &vis_total);
-    const bool set_mode = 2ull * vis_total <= n;
-    unsigned long long vrun = cta_excl_scan64<NT>(set_mode ? lv : lb - lv, sm, &total);
-    if (t1 == t0 + 1) {  // the common case: nothing to re-read
-        tile_off[t0] = (uint32_t)run;
-        vtile_off[t0] = (uint32_t)vrun;
-    } else {
-        for (uint64_t t = t0; t < t1; t++) {
-            tile_off[t] = (uint32_t)run;
-            vtile_off[t] = (uint32_t)vrun;
-            const uint32_t x = __ldcg(tile_cnt + t), y = __ldcg(vis_cnt + t);
-            run += x;
-            const uint64_t bits = min(n, (t + 1) * tile_bits) - t * tile_bits;
-            vrun += set_mode ? y : bits - y;
-        }
-    }
-    const unsigned long long s_nf = nf_total, s_vis = vis_total;
-    const unsigned long long vcount = total;
-    // snapshot the level's live counters and codec status, then clear for the next level (every
-    // load first: the stores below could alias them, and one thread's dependent round trips are
-    // this kernel's critical path)
-    if (threadIdx.x == 0) {
-        const unsigned long long m_f = __ldcg(&ctr->m_f_next), ex = __ldcg(&ctr->examined), hub = __ldcg(&ctr->hub_items);
-        const unsigned long long cr = __ldcg(&ctr->cols_read);
-        const int32_t cq = __ldcg(&sq.ctl->code), cv = __ldcg(&sv.ctl->code);
-        const uint32_t wq = __ldcg(&sq.ctl->where), wv = __ldcg(&sv.ctl->where);
-        const unsigned long long dq = __ldcg(&sq.ctl->detail), dv = __ldcg(&sv.ctl->detail);
-        ctr->n_f_next = s_nf;
-        ctr->r_m_f = m_f;  // summed by the expansion kernels
-        ctr->m_f_next = 0;
-        ctr->vis_count = s_vis;
-        ctr->v_count = vcount;
-        ctr->r_examined = ex;
-        ctr->examined = 0;
-        ctr->r_cols_read = cr;
-        ctr->cols_read = 0;
-        ctr->r_hub_items = hub;
-        ctr->hub_items = 0;
-        ctr->r_err_q = cq;
-        ctr->r_where_q = wq;
-        ctr->r_detail_q = dq;
-        ctr->r_err_v = cv;
-        ctr->r_where_v = wv;
-        ctr->r_detail_v = dv;
-        reset_scratch_device(sq);
-        reset_scratch_device(sv);
-        sv.ctl->n = vcount;
-        sv.ctl->fb_mode = set_mode ? kFbSet : kFbClear;
-    }
+    const unsigned long long m_f = ctr->m_f_next, ex = ctr->examined, hub = ctr->hub_items, cr = ctr->cols_read;
+    const int32_t cq = sq.ctl->code, cv = sv.ctl->code;
+    const uint32_t wq = sq.ctl->where, wv = sv.ctl->where;
+    const unsigned long long dq = sq.ctl->detail, dv = sv.ctl->detail;
+    ctr->n_f_next = nf;
+    ctr->r_m_f = m_f;  // summed by the expansion kernels
+    ctr->m_f_next = 0;
+    ctr->vis_count = vis;
+    ctr->v_count = vcount;
+    ctr->r_examined = ex;
+    ctr->examined = 0;
+    ctr->r_cols_read = cr;
+    ctr->cols_read = 0;
+    ctr->r_hub_items = hub;
+    ctr->hub_items = 0;
+    ctr->r_err_q = cq;
+    ctr->r_where_q = wq;
+    ctr->r_detail_q = dq;
+    ctr->r_err_v = cv;
+    ctr->r_where_v = wv;
+    ctr->r_detail_v = dv;
+    reset_scratch_device(sq);
+    reset_scratch_device(sv);
+    sv.ctl->n = vcount;
+    sv.ctl->fb_mode = set_mode ? kFbSet : kFbClear;
 }
 
 // Positions of the set bits of the warp's 32 words (lane L holds word wbase + L) written to
@@ -608,52 +580,159 @@ __device__ __forceinline__ void extract_words(uint64_t x, uint64_t wbase, unsign
 constexpr size_t kCmpStage = 2048 * sizeof(uint32_t);               // one warp's stage
 constexpr size_t kCmpSmem = (kThreads / 32) * kCmpStage;            // 64 KB per CTA
 
-// The next frontier F_{d+1} as a sorted queue (and as the bitmap the next level's B encode reads),
-// next cleared, and -- when V_{d+1} is coded -- the positions V_{d+1} codes.  One word per thread;
-// the CTA's tile offsets come from the count kernel's last CTA, each warp's from a CTA prefix of
-// warp counts.
-__global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restrict__ next, uint64_t *__restrict__ fbits,
-                                                               const uint64_t *__restrict__ visited, uint64_t nwords,
-                                                               uint64_t n, const uint32_t *__restrict__ tile_off,
-                                                               const uint32_t *__restrict__ vtile_off, uint32_t *q,
-                                                               Scratch sv, int want_v)
+// Sums over the compaction tiles' counts, by every CTA: the counts of the tiles before its own
+// (its output offset) and of all tiles.  cnt2 may be null (its sums are then 0).
+struct TileSums {
+    unsigned long long before, total, before2, total2;
+};
+
+__device__ __forceinline__ TileSums cta_tile_sums(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ cnt2,
+                                                  uint32_t ntiles, unsigned long long (*red)[kThreads / 32])
 {
-    static_assert(kCmpWordsPerThread == 1, "one word per thread");
-    extern __shared__ __align__(16) uint32_t cstage[];  // [warps][2048]
-    __shared__ uint32_t wq[kThreads / 32], wv[kThreads / 32];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint64_t w = (uint64_t)blockIdx.x * kCmpWords + threadIdx.x;
-    const bool v_list = want_v != 0;
-    uint64_t x = 0, y = 0;
-    if (w < nwords) {
-        x = next[w];
-        fbits[w] = x;  // F_{d+1} as a bitmap for the next level's B encode
-        if (x) next[w] = 0;
-        if (v_list) {
-            y = visited[w];
-            if (sv.ctl->fb_mode == kFbClear) {
-                const uint32_t tail = (uint32_t)(n & 63u);
-                const uint64_t nb = (w == nwords - 1 && tail) ? tail : 64u;
-                y = ~y & (nb == 64 ? ~0ull : ((1ull << nb) - 1ull));
-            }
+    unsigned long long b = 0, t = 0, b2 = 0, t2 = 0;
+    for (uint32_t i = threadIdx.x; i < ntiles; i += kThreads) {
+        const uint32_t c = cnt[i], c2 = cnt2 ? cnt2[i] : 0u;
+        t += c;
+        t2 += c2;
+        if (i < blockIdx.x) {
+            b += c;
+            b2 += c2;
         }
     }
-    const uint32_t cq = __reduce_add_sync(0xffffffffu, (uint32_t)__popcll(x));
-    const uint32_t cv = __reduce_add_sync(0xffffffffu, (uint32_t)__popcll(y));
+    b = warp_sum64(b);
+    t = warp_sum64(t);
+    b2 = warp_sum64(b2);
+    t2 = warp_sum64(t2);
     if (lane == 0) {
-        wq[warp] = cq;
-        wv[warp] = cv;
+        red[0][warp] = b;
+        red[1][warp] = t;
+        red[2][warp] = b2;
+        red[3][warp] = t2;
     }
     __syncthreads();
-    unsigned long long oq = tile_off[blockIdx.x], ov = v_list ? vtile_off[blockIdx.x] : 0ull;
-    for (uint32_t i = 0; i < warp; i++) {
-        oq += wq[i];
-        ov += wv[i];
+    TileSums r{0, 0, 0, 0};
+    for (uint32_t i = 0; i < kThreads / 32; i++) {
+        r.before += red[0][i];
+        r.total += red[1][i];
+        r.before2 += red[2][i];
+        r.total2 += red[3][i];
     }
-    const uint64_t wbase = (uint64_t)blockIdx.x * kCmpWords + warp * 32u;
-    uint32_t *stage = cstage + warp * 2048u;
-    extract_words(x, wbase, oq, q, lane, stage);
-    if (v_list) extract_words(y, wbase, ov, sv.positions, lane, stage);
+    return r;
+}
+
+// Sub-tiles of a compaction tile whose words one thread holds at once (their loads in flight
+// together); tiles of more sub-tiles are taken in rounds of this many.
+constexpr uint32_t kCmpAhead = 4;
+
+// The positions of a tile's sub-tiles [s0, s0 + kCmpAhead) from the words x[] the threads hold
+// (thread i: word i of each sub-tile), written from out[o] on in increasing order; o advances by
+// the count.  Within a sub-tile each warp's offset is a prefix of warp counts.
+__device__ __forceinline__ void cmp_extract_round(const uint64_t (&x)[kCmpAhead], uint64_t tile_w0, uint32_t s0,
+                                                  uint32_t sub, unsigned long long &o, uint32_t *out, uint32_t *stage,
+                                                  uint32_t *wc)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (uint32_t j = 0; j < kCmpAhead; j++) {
+        if (s0 + j >= sub) break;  // uniform over the CTA
+        const uint32_t c = __reduce_add_sync(0xffffffffu, (uint32_t)__popcll(x[j]));
+        if (lane == 0) wc[warp] = c;
+        __syncthreads();
+        unsigned long long p = o;
+        for (uint32_t i = 0; i < kThreads / 32; i++) {
+            if (i < warp) p += wc[i];
+            o += wc[i];
+        }
+        extract_words(x[j], tile_w0 + (uint64_t)(s0 + j) * kCmpSubWords + warp * 32u, p, out, lane, stage);
+        __syncthreads();  // the warp counts are rewritten by the next sub-tile
+    }
+}
+
+// The next frontier F_{d+1} as a sorted queue (and as the bitmap the next level's B encode reads),
+// next cleared, and the level record (first CTA).  Each CTA's offset and the level's totals come
+// from the tile counts (cta_tile_sums); the visited counts give V_{d+1}'s size and mode.
+__global__ void __launch_bounds__(kThreads) cmp_extract_kernel(uint64_t *__restrict__ next, uint64_t *__restrict__ fbits,
+                                                               uint64_t nwords, uint64_t n, uint32_t sub, uint32_t ntiles,
+                                                               const uint32_t *__restrict__ tile_cnt,
+                                                               const uint32_t *__restrict__ vis_cnt, uint32_t *q,
+                                                               Counters *ctr, Scratch sq, Scratch sv, int want_v)
+{
+    extern __shared__ __align__(16) uint32_t cstage[];  // [warps][2048]
+    __shared__ uint32_t wc[kThreads / 32];
+    __shared__ unsigned long long red[4][kThreads / 32];
+    const uint64_t tile_w0 = (uint64_t)blockIdx.x * sub * kCmpSubWords;
+    uint64_t x[kCmpAhead];
+#pragma unroll
+    for (uint32_t j = 0; j < kCmpAhead; j++) {  // the first round's words, in flight with the sums
+        const uint64_t w = tile_w0 + (uint64_t)j * kCmpSubWords + threadIdx.x;
+        x[j] = (j < sub && w < nwords) ? next[w] : 0ull;
+    }
+    const TileSums ts = cta_tile_sums(tile_cnt, want_v ? vis_cnt : nullptr, ntiles, red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const bool set_mode = 2ull * ts.total2 <= n;
+        cmp_snapshot(ctr, sq, sv, ts.total, ts.total2, set_mode ? ts.total2 : (unsigned long long)n - ts.total2,
+                     set_mode);
+    }
+    uint32_t *stage = cstage + (threadIdx.x >> 5) * 2048u;
+    unsigned long long o = ts.before;
+    for (uint32_t s0 = 0; s0 < sub; s0 += kCmpAhead) {
+        if (s0) {
+#pragma unroll
+            for (uint32_t j = 0; j < kCmpAhead; j++) {
+                const uint64_t w = tile_w0 + (uint64_t)(s0 + j) * kCmpSubWords + threadIdx.x;
+                x[j] = (s0 + j < sub && w < nwords) ? next[w] : 0ull;
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kCmpAhead; j++) {
+            const uint64_t w = tile_w0 + (uint64_t)(s0 + j) * kCmpSubWords + threadIdx.x;
+            if (s0 + j < sub && w < nwords) {
+                fbits[w] = x[j];  // F_{d+1} as a bitmap for the next level's B encode
+                if (x[j]) next[w] = 0;
+            }
+        }
+        cmp_extract_round(x, tile_w0, s0, sub, o, q, stage, wc);
+    }
+}
+
+// V_d's positions (step 1 of a level, before V_d's encode): the set bits of the visited bitmap when
+// at most half are set, else the clear ones (bits past n excluded), from the per-tile visited
+// counts the last compaction wrote (level 0: the root's tile holds 1).  The visited bitmap does not
+// change until the level's compaction, so this runs beside the level's other work.
+__global__ void __launch_bounds__(kThreads) v_extract_kernel(const uint64_t *__restrict__ visited, uint64_t nwords,
+                                                             uint64_t n, uint32_t sub, uint32_t ntiles,
+                                                             const uint32_t *__restrict__ vis_cnt, Scratch sv)
+{
+    extern __shared__ __align__(16) uint32_t cstage[];  // [warps][2048]
+    __shared__ uint32_t wc[kThreads / 32];
+    __shared__ unsigned long long red[4][kThreads / 32];
+    const uint64_t tile_w0 = (uint64_t)blockIdx.x * sub * kCmpSubWords;
+    const uint32_t tail = (uint32_t)(n & 63u);
+    uint64_t y[kCmpAhead];
+#pragma unroll
+    for (uint32_t j = 0; j < kCmpAhead; j++) {
+        const uint64_t w = tile_w0 + (uint64_t)j * kCmpSubWords + threadIdx.x;
+        y[j] = (j < sub && w < nwords) ? visited[w] : 0ull;
+    }
+    const TileSums ts = cta_tile_sums(vis_cnt, nullptr, ntiles, red);
+    const bool set_mode = 2ull * ts.total <= n;
+    // clear mode: the clear bits before this tile are its bits before it minus the set ones
+    unsigned long long o = set_mode ? ts.before : min((unsigned long long)n, 64ull * tile_w0) - ts.before;
+    uint32_t *stage = cstage + (threadIdx.x >> 5) * 2048u;
+    for (uint32_t s0 = 0; s0 < sub; s0 += kCmpAhead) {
+#pragma unroll
+        for (uint32_t j = 0; j < kCmpAhead; j++) {
+            const uint64_t w = tile_w0 + (uint64_t)(s0 + j) * kCmpSubWords + threadIdx.x;
+            const bool in = s0 + j < sub && w < nwords;
+            if (s0) y[j] = in ? visited[w] : 0ull;
+            if (in && !set_mode) {
+                const uint64_t nb = (w == nwords - 1 && tail) ? tail : 64u;
+                y[j] = ~y[j] & (nb == 64 ? ~0ull : ((1ull << nb) - 1ull));
+            }
+        }
+        cmp_extract_round(y, tile_w0, s0, sub, o, sv.positions, stage, wc);
+    }
 }
 
 // ---- round-trip check of the overlapped codec stage (FQ_BFS_OVERLAP) ----
@@ -794,7 +873,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
                       want_v != 0};
     level_bytes(lin, st.kernel_bytes);
     if (coded) st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
-    if (want_v) st.kernel_launches[FQ_K_ENCODE] += 2;
+    if (want_v) st.kernel_launches[FQ_K_ENCODE] += 3;  // positions, widths, pack
     if (dir == FQ_TOP_DOWN) {
         if (coded) st.kernel_launches[FQ_K_DECODE] += 3 + (overlap ? 1 : 0);
         st.kernel_launches[FQ_K_TOP_DOWN] += 2;
@@ -877,8 +956,8 @@ struct fq_graph {
     uint64_t qs_cap, bs_cap;
     HubItem *items;
     uint64_t items_cap;
-    uint32_t *tile_cnt, *tile_off, *vis_cnt, *vtile_off;
-    uint64_t cmp_tiles;
+    uint32_t *tile_cnt, *vis_cnt;  // compaction: per-tile counts of the next frontier and of the visited set
+    uint32_t cmp_tiles, cmp_sub;    //   tiles, and 256-word sub-tiles per tile
     uint8_t *host;  // pinned: Counters copy, then LoopState and level records (device-driven loop)
     cudaEvent_t ev[2 * FQ_NUM_KCLASS];
     cudaStream_t ov_stream;  // FQ_BFS_OVERLAP, host-driven loop: the codec stage's stream
@@ -968,10 +1047,10 @@ cudaError_t step_init(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_
     FQ_CU(cudaMemsetAsync(g->fbits, 0, 8 * (nwords + 2), st));
     FQ_CU(cudaMemsetAsync(g->next, 0, 8 * (nwords + 2), st));
     FQ_CU(cudaMemsetAsync(g->visited, 0, 8 * (nwords + 2), st));
-    FQ_CU(cudaMemsetAsync(g->vis_cnt, 0, 4 * g->cmp_tiles, st));
+    FQ_CU(cudaMemsetAsync(g->vis_cnt, 0, 4 * (uint64_t)g->cmp_tiles, st));
     FQ_CU(cudaMemsetAsync(g->ctr, 0, sizeof(Counters), st));
     bfs_init_kernel<<<1, 256, 0, st>>>(g->off, root, n, d_depth, d_parent, g->q, g->fbits, g->visited, g->vis_cnt,
-                                       g->ctr, g->sq, g->sv, ls);
+                                       64ull * kCmpSubWords * g->cmp_sub, g->ctr, g->sq, g->sv, ls);
     return cudaGetLastError();
 }
 
@@ -1005,9 +1084,15 @@ cudaError_t step_encode_q(fq_graph *g, bool dense, uint64_t n_f, const LoopState
     return cudaSuccess;
 }
 
-// Step 1 (V_d): the visited bitmap's positions, extracted by the previous compaction.
+// Step 1 (V_d): the visited bitmap's positions (set or clear, by the mode the previous compaction
+// chose), then their FB encode.
 cudaError_t step_encode_v(fq_graph *g, cudaStream_t st)
 {
+    static std::atomic<bool> smem_set[64];
+    FQ_CU(allow_smem(v_extract_kernel, kCmpSmem, smem_set));
+    v_extract_kernel<<<g->cmp_tiles, kThreads, kCmpSmem, st>>>(g->visited, g->nwords, g->n, g->cmp_sub, g->cmp_tiles,
+                                                               g->vis_cnt, g->sv);
+    FQ_CU(cudaGetLastError());
     return encode_fb_positions(g->visited, g->n, g->vs, g->bs_cap, reinterpret_cast<uint64_t *>(&g->ctr->v_bytes),
                                g->sv, st);
 }
@@ -1081,16 +1166,17 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
     return cudaGetLastError();
 }
 
-// Step 5: compaction (+ V_{d+1} positions, cleared scratch for the next level).
+// Step 5: compaction (+ the visited counts V_{d+1}'s extraction starts from, cleared scratch for the
+// next level).
 cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
 {
-    const uint32_t ct = (uint32_t)g->cmp_tiles;
-    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->tile_cnt, g->vis_cnt, g->tile_off,
-                                              g->vtile_off, g->n, g->ctr, g->sq, g->sv);
+    const uint32_t ct = g->cmp_tiles;
+    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->cmp_sub, g->tile_cnt, g->vis_cnt,
+                                              want_v ? 1 : 0);
     static std::atomic<bool> smem_set[64];
     FQ_CU(allow_smem(cmp_extract_kernel, kCmpSmem, smem_set));
-    cmp_extract_kernel<<<ct, kThreads, kCmpSmem, st>>>(g->next, g->fbits, g->visited, g->nwords, g->n, g->tile_off,
-                                                       g->vtile_off, g->q, g->sv, want_v ? 1 : 0);
+    cmp_extract_kernel<<<ct, kThreads, kCmpSmem, st>>>(g->next, g->fbits, g->nwords, g->n, g->cmp_sub, ct, g->tile_cnt,
+                                                       g->vis_cnt, g->q, g->ctr, g->sq, g->sv, want_v ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1361,7 +1447,11 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     g->qs_cap = fq_queue_bound(n);
     g->bs_cap = fq_bitmap_bound(n);
     g->items_cap = m / kHubChunk + m / kHubDegree + 16;  // every hub holds >= kHubDegree edges
-    g->cmp_tiles = std::max<uint64_t>(1, cdiv(g->nwords, kCmpWords));
+    {  // compaction tiles: at most one wave of the extract kernel (3 CTAs of 64 KB shared memory per SM)
+        const uint64_t subs = std::max<uint64_t>(1, cdiv(g->nwords, kCmpSubWords));
+        g->cmp_sub = (uint32_t)cdiv(subs, 3 * (uint64_t)num_sms());
+        g->cmp_tiles = (uint32_t)cdiv(subs, g->cmp_sub);
+    }
     uint64_t o = 0;
     const uint64_t o_ctr = o; o = al256(o + sizeof(Counters));
     const uint64_t o_wq = o; o = al256(o + work_q);
@@ -1379,10 +1469,8 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     const uint64_t o_bs = o; o = al256(o + g->bs_cap);
     const uint64_t o_vs = o; o = al256(o + g->bs_cap);
     const uint64_t o_items = o; o = al256(o + sizeof(HubItem) * g->items_cap);
-    const uint64_t o_tc = o; o = al256(o + 4 * g->cmp_tiles);
-    const uint64_t o_to = o; o = al256(o + 4 * g->cmp_tiles);
-    const uint64_t o_vc = o; o = al256(o + 4 * g->cmp_tiles);
-    const uint64_t o_vo = o; o = al256(o + 4 * g->cmp_tiles);
+    const uint64_t o_tc = o; o = al256(o + 4 * (uint64_t)g->cmp_tiles);
+    const uint64_t o_vc = o; o = al256(o + 4 * (uint64_t)g->cmp_tiles);
     const uint64_t o_ls = o; o = al256(o + sizeof(LoopState));
     const uint64_t o_recs = o; o = al256(o + sizeof(fq_level_record) * kMaxDeviceRecords);
     g->mem_bytes = o;
@@ -1426,9 +1514,7 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     g->vs = g->mem + o_vs;
     g->items = reinterpret_cast<HubItem *>(g->mem + o_items);
     g->tile_cnt = reinterpret_cast<uint32_t *>(g->mem + o_tc);
-    g->tile_off = reinterpret_cast<uint32_t *>(g->mem + o_to);
     g->vis_cnt = reinterpret_cast<uint32_t *>(g->mem + o_vc);
-    g->vtile_off = reinterpret_cast<uint32_t *>(g->mem + o_vo);
     g->ls = reinterpret_cast<LoopState *>(g->mem + o_ls);
     g->recs = reinterpret_cast<fq_level_record *>(g->mem + o_recs);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++) cudaEventCreate(&g->ev[i]);
@@ -1597,7 +1683,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         }
         if (want_visited) {
             FQ_TRY(step_encode_v(g, cst));
-            enc_launches += 2;
+            enc_launches += 3;
         }
         tm.end(FQ_K_ENCODE, enc_launches);
 
@@ -1620,7 +1706,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         }
         if (ovl) FQ_TRY(cudaStreamWaitEvent(st, g->ov_ev[1], 0));
 
-        // 5. compaction (+ V_{d+1} positions, cleared scratch for the next level)
+        // 5. compaction (+ the visited counts per tile, cleared scratch for the next level)
         tm.begin(FQ_K_COMPACT);
         FQ_TRY(step_compact(g, want_visited, st));
         tm.end(FQ_K_COMPACT, 2);

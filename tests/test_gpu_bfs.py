@@ -185,6 +185,39 @@ def test_rmat24_full_size_every_level_eight_roots(rmat24):
     g.close()
 
 
+def test_ragged_vertex_count_with_multi_subtile_compaction():
+    """A uniform random graph on 9,000,017 vertices (average degree about 4): the compaction's tiles
+    then span two 16,384-vertex sub-tiles each, the last tile is partial and the last bitmap word
+    holds 17 vertices, and the visited stream passes from set to clear positions on the way.  Both
+    level-loop drivers must give the oracle's depths, schedule and every level's Q, B, V."""
+    import concurrent.futures as cf
+    n = 9_000_017
+    u = inputs.uniform32(97, 1, 0, 2 * n, device="cuda") % n
+    v = inputs.uniform32(97, 2, 0, 2 * n, device="cuda") % n
+    off_d, cols_d = inputs.edges_to_csr(u, v, n)
+    del u, v
+    off, cols = off_d.cpu().numpy(), cols_d.cpu().numpy().view(np.uint32)
+    roots = inputs.pick_roots(off_d, 2, seed=97)
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        refs = list(ex.map(lambda r: _oracle_root(off, cols, r), roots))
+    g = fqbfs.Graph(off_d, cols_d)
+    for root, (ref_depth, sched, ref_streams) in zip(roots, refs):
+        assert any(2 * int(np.count_nonzero((ref_depth >= 0) & (ref_depth <= d))) > n for d in range(len(sched)))
+        for loop in (fqbfs.FQ_BFS_DEVICE_LOOP, 0):
+            res = g.bfs(root, flags=loop | fqbfs.FQ_BFS_VISITED_STREAM, record_streams=True, max_levels=64)
+            assert np.array_equal(res.depth.cpu().numpy(), ref_depth), (root, loop)
+            assert res.stats["levels"] == len(sched) == len(res.levels) == len(res.streams) == len(ref_streams)
+            for got, want in zip(res.levels, sched):
+                for k in ("n_f", "m_f", "m_u", "direction", "examined"):
+                    assert got[k] == want[k], (root, got["level"], k)
+            for got, want in zip(res.streams, ref_streams):
+                for k in ("Q", "B", "V"):
+                    assert np.array_equal(got[k].cpu().numpy(), want[k]), (root, got["level"], k)
+    g.close()
+    del off_d, cols_d
+    torch.cuda.empty_cache()
+
+
 @LOOPS
 def test_rmat16_without_codec_stage_same_depths_and_schedule(rmat16, loop):
     off, cols, roots = rmat16
