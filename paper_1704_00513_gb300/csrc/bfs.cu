@@ -83,28 +83,56 @@ struct LoopState {
 };
 constexpr uint32_t kMaxDeviceRecords = 4096;
 
-// Top-down visit of edge (src, w): the thread whose atomicOr sets w's bit in the next-frontier
-// bitmap discovers w, writes depth and parent, and returns deg(w) for the next level's m_f.
-__device__ __forceinline__ unsigned long long td_visit(uint32_t w, uint32_t src, const uint32_t *__restrict__ visited32,
-                                                       uint32_t *next32, int32_t *depth, uint32_t *parent,
-                                                       int32_t newdepth, const int64_t *__restrict__ off)
+// Top-down visits of the K edges (src[c], w[c]) one thread holds, of which seen[c] marks those whose
+// target is already visited (or absent).  For each remaining target the thread whose atomicOr sets
+// its bit in the next-frontier bitmap discovers it, writes depth and parent, and adds deg(w) to the
+// next level's m_f.  The steps run edge-parallel -- every next-frontier load, then every claim,
+// then every discovery's stores and degree loads -- so the K edges' round trips overlap instead of
+// following each other.
+template <int K>
+__device__ __forceinline__ unsigned long long td_visit_batch(const uint32_t (&w)[K], const uint32_t (&src)[K],
+                                                             const bool (&seen)[K], uint32_t *next32, int32_t *depth,
+                                                             uint32_t *parent, int32_t newdepth,
+                                                             const int64_t *__restrict__ off)
 {
-    const uint32_t bit = 1u << (w & 31u), wi = w >> 5;
-    if (visited32[wi] & bit) return 0;
-    if (next32[wi] & bit) return 0;
-    const uint32_t old = atomicOr(&next32[wi], bit);
-    if (old & bit) return 0;
-    depth[w] = newdepth;
-    if (parent) parent[w] = src;
-    return (unsigned long long)(off[w + 1] - off[w]);
+    uint32_t old[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) old[c] = seen[c] ? ~0u : next32[w[c] >> 5];  // claimed already this level?
+#pragma unroll
+    for (int c = 0; c < K; c++) {
+        const uint32_t bit = 1u << (w[c] & 31u);
+        if (!(old[c] & bit)) old[c] = atomicOr(&next32[w[c] >> 5], bit);
+    }
+    long long lo[K], hi[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) {
+        lo[c] = hi[c] = 0;
+        if (!(old[c] & (1u << (w[c] & 31u)))) {  // this thread's claim set the bit: it discovers w
+            depth[w[c]] = newdepth;
+            if (parent) parent[w[c]] = src[c];
+            lo[c] = off[w[c]];
+            hi[c] = off[w[c] + 1];
+        }
+    }
+    unsigned long long degsum = 0;
+#pragma unroll
+    for (int c = 0; c < K; c++) degsum += (unsigned long long)(hi[c] - lo[c]);
+    return degsum;
 }
 
 // Level 0: the root, V_0's single position, cleared codec scratch.
 __global__ void bfs_init_kernel(const int64_t *off, uint32_t root, uint64_t n, int32_t *depth, uint32_t *parent,
                                 uint32_t *q, uint64_t *fbits, uint64_t *visited, uint32_t *vis_cnt, uint64_t tile_bits,
-                                Counters *ctr, Scratch sq, Scratch sv, const LoopState *ls)
+                                uint32_t ntiles, uint32_t *last_set, uint32_t *last_clear, Counters *ctr, Scratch sq,
+                                Scratch sv, const LoopState *ls)
 {
     if (ls) root = ls->p.root;  // device-driven loop: the root is a run parameter
+    // per compaction tile, 1 + its last set / clear vertex of the visited bitmap {root} (0: none)
+    for (uint32_t t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint64_t last = min(n, (uint64_t)(t + 1) * tile_bits) - 1;  // the tile's last vertex
+        last_set[t] = root / tile_bits == t ? root + 1u : 0u;
+        last_clear[t] = last != root ? (uint32_t)(last + 1) : (last > (uint64_t)t * tile_bits ? (uint32_t)last : 0u);
+    }
     if (threadIdx.x != 0) return;
     reset_scratch_device(sq);
     reset_scratch_device(sv);
@@ -256,9 +284,7 @@ __global__ void __launch_bounds__(kThreads) td_expand_kernel(const uint32_t *__r
 #pragma unroll
             for (uint32_t r = 0; r < kU; r++)
                 seen[r] = w[r] == 0xffffffffu || ((visited32[w[r] >> 5] >> (w[r] & 31u)) & 1u);
-#pragma unroll
-            for (uint32_t r = 0; r < kU; r++)
-                if (!seen[r]) degsum += td_visit(w[r], src[r], visited32, next32, depth, parent, newdepth, off);
+            degsum += td_visit_batch<kU>(w, src, seen, next32, depth, parent, newdepth, off);
         }
     }
     degsum = warp_sum64(degsum);
@@ -286,12 +312,13 @@ __global__ void __launch_bounds__(kThreads) td_hub_kernel(const HubItem *__restr
             w[c] = j < h.count ? cols[h.start + j] : 0xffffffffu;
         }
         bool seen[kPer];
+        uint32_t src[kPer];
 #pragma unroll
-        for (uint32_t c = 0; c < kPer; c++)  // ... then their visited bits ...
+        for (uint32_t c = 0; c < kPer; c++) {  // ... then their visited bits ...
             seen[c] = w[c] == 0xffffffffu || ((visited32[w[c] >> 5] >> (w[c] & 31u)) & 1u);
-#pragma unroll
-        for (uint32_t c = 0; c < kPer; c++)  // ... then the claims
-            if (!seen[c]) degsum += td_visit(w[c], h.v, visited32, next32, depth, parent, newdepth, off);
+            src[c] = h.v;
+        }
+        degsum += td_visit_batch<(int)kPer>(w, src, seen, next32, depth, parent, newdepth, off);  // ... then the claims
     }
     degsum = warp_sum64(degsum);
     if ((threadIdx.x & 31u) == 0 && degsum) atomicAdd(m_f_next, degsum);
@@ -474,14 +501,16 @@ __global__ void __launch_bounds__(kThreads) bu_sweep_head_kernel(const uint32_t 
 // Per tile: the next frontier's count, visited |= next, and (when V_{d+1} is coded) the tile's
 // visited count after the update.  Every sub-tile's loads are issued before any is used.
 __global__ void __launch_bounds__(kThreads) cmp_count_kernel(const uint64_t *__restrict__ next, uint64_t *visited,
-                                                             uint64_t nwords, uint32_t sub, uint32_t *tile_cnt,
-                                                             uint32_t *vis_cnt, int want_v)
+                                                             uint64_t nwords, uint64_t n, uint32_t sub,
+                                                             uint32_t *tile_cnt, uint32_t *vis_cnt, uint32_t *last_set,
+                                                             uint32_t *last_clear, int want_v)
 {
-    __shared__ uint32_t ws[kThreads / 32], wv[kThreads / 32];
+    __shared__ uint32_t ws[kThreads / 32], wv[kThreads / 32], wls[kThreads / 32], wlc[kThreads / 32];
     constexpr uint32_t kAhead = 4;  // sub-tiles whose words are in flight together
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t w0 = (uint64_t)blockIdx.x * sub * kCmpSubWords + threadIdx.x;
     uint32_t cnt = 0, vc = 0;
+    uint32_t ls = 0, lc = 0;  // 1 + the last set / clear vertex of the updated visited bitmap (0: none)
     for (uint32_t s0 = 0; s0 < sub; s0 += kAhead) {
         uint64_t x[kAhead], v[kAhead];
 #pragma unroll
@@ -499,24 +528,42 @@ __global__ void __launch_bounds__(kThreads) cmp_count_kernel(const uint64_t *__r
                 else visited[w] |= x[j];
             }
             cnt += (uint32_t)__popcll(x[j]);
-            vc += (uint32_t)__popcll(v[j] | x[j]);  // the next frontier is disjoint from the visited set
+            const uint64_t nv = v[j] | x[j];
+            vc += (uint32_t)__popcll(nv);  // the next frontier is disjoint from the visited set
+            if (want_v && s0 + j < sub && w < nwords) {
+                const uint32_t tail = (uint32_t)(n & 63u);
+                const uint64_t in_n = (w == nwords - 1 && tail) ? (1ull << tail) - 1ull : ~0ull;
+                const uint64_t clr = ~nv & in_n;
+                if (nv) ls = max(ls, (uint32_t)(w * 64u + 64u - (uint32_t)__clzll((long long)nv)));
+                if (clr) lc = max(lc, (uint32_t)(w * 64u + 64u - (uint32_t)__clzll((long long)clr)));
+            }
         }
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
     vc = __reduce_add_sync(0xffffffffu, vc);
+    ls = __reduce_max_sync(0xffffffffu, ls);
+    lc = __reduce_max_sync(0xffffffffu, lc);
     if (lane == 0) {
         ws[warp] = cnt;
         wv[warp] = vc;
+        wls[warp] = ls;
+        wlc[warp] = lc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t t = 0, tv = 0;
+        uint32_t t = 0, tv = 0, tls = 0, tlc = 0;
         for (uint32_t i = 0; i < kThreads / 32; i++) {
             t += ws[i];
             tv += wv[i];
+            tls = max(tls, wls[i]);
+            tlc = max(tlc, wlc[i]);
         }
         tile_cnt[blockIdx.x] = t;
         vis_cnt[blockIdx.x] = tv;
+        if (want_v) {
+            last_set[blockIdx.x] = tls;
+            last_clear[blockIdx.x] = tlc;
+        }
     }
 }
 
@@ -707,6 +754,7 @@ __global__ void __launch_bounds__(kThreads) v_extract_kernel(const uint64_t *__r
     extern __shared__ __align__(16) uint32_t cstage[];  // [warps][2048]
     __shared__ uint32_t wc[kThreads / 32];
     __shared__ unsigned long long red[4][kThreads / 32];
+    if (sv.ctl->skip_pos) return;  // V_d is coded as raw words (fbw_kernel decided it from the bitmap)
     const uint64_t tile_w0 = (uint64_t)blockIdx.x * sub * kCmpSubWords;
     const uint32_t tail = (uint32_t)(n & 63u);
     uint64_t y[kCmpAhead];
@@ -732,6 +780,266 @@ __global__ void __launch_bounds__(kThreads) v_extract_kernel(const uint64_t *__r
             }
         }
         cmp_extract_round(y, tile_w0, s0, sub, o, sv.positions, stage, wc);
+    }
+}
+
+// ---- V_d's block widths from the visited bitmap ----
+// V_d codes the positions of the members -- the set bits of the visited bitmap when at most half
+// are set, else its clear bits below n -- as blocks of 128 positions (sec. 5.1), whose width b is
+// the bit length of the largest gap (p - p_prev - 1) inside the block; the container falls back to
+// the raw bitmap when that is not larger than the coded positions.  Once the visited set is
+// dense, that is the usual outcome, and the stream's size -- so the decision -- needs only the sum
+// of the widths, which this kernel takes from the bitmap without writing any position: member
+// ranks come from the per-tile counts, each member's predecessor from the per-tile last members,
+// and the gaps inside a word from zero-run tests on its bits.  When the sum says raw, the positions
+// extraction and the widths pass are skipped (Ctl::skip_pos) and the pack kernel copies the words.
+
+// Position of the j-th (0-based) set bit of x (j < popcount(x)).
+__device__ __forceinline__ uint32_t select64(uint64_t x, uint32_t j)
+{
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t s = 32; s >= 1; s >>= 1) {
+        const uint32_t c = (uint32_t)__popcll(x & ((1ull << s) - 1ull));
+        if (j >= c) {
+            j -= c;
+            x >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+// Bit length of the largest gap between consecutive set bits of y at or between bit lo and bit hi
+// (both set): the longest zero run strictly inside (lo, hi), found by doubling -- r_L marks the bits
+// that start L zeros -- so the answer is the number of L in 1, 2, 4, .., 32 with a run of L zeros.
+__device__ __forceinline__ uint32_t inner_gap_bits(uint64_t y, uint32_t lo, uint32_t hi)
+{
+    if (hi <= lo + 1u) return 0u;
+    const uint64_t between = ((1ull << hi) - 1ull) & ~((2ull << lo) - 1ull);
+    uint64_t r = ~y & between;
+    uint32_t b = 0;
+#pragma unroll
+    for (uint32_t L = 1; L <= 32; L <<= 1) {
+        if (!r) break;
+        b++;
+        r &= r >> L;
+    }
+    return b;
+}
+
+// One CTA per sub-tile of 256 words, one word per thread.  The members before the sub-tile, and
+// the last of them, come from the per-tile counts and last members of the tiles before its own and
+// from the earlier sub-tiles of its tile (whose words it reads).  Each word's members and their
+// block segments (at most two: a block start falls in a word at most once) give each segment's
+// largest-gap bit length, combined per block in shared memory; the blocks that start and end in the
+// sub-tile add their widths to the sub-tile's sum (wpart[]), the others go through wb[] (atomicMax;
+// the sub-tile holding a block's first member names it in span[]).  The last CTA to finish adds the
+// sums and the named blocks' widths (clearing wb[] for the next call) and takes the container's
+// decision.  No counter is shared by all CTAs but the finishing ticket.  Sparse member sets (below
+// n/16) are left to the positions path: there the positions are few and a scan of every word would
+// cost more.
+constexpr uint32_t kSubBlocks = 64u * kCmpSubWords / kBlock + 2u;  // blocks one sub-tile's members touch
+
+__device__ __forceinline__ uint64_t member_word(const uint64_t *__restrict__ visited, uint64_t w, uint64_t nwords,
+                                                uint32_t tail, bool set_mode)
+{
+    if (w >= nwords) return 0ull;
+    const uint64_t y = visited[w];
+    return set_mode ? y : ~y & ((w == nwords - 1 && tail) ? (1ull << tail) - 1ull : ~0ull);
+}
+
+__global__ void __launch_bounds__(kThreads) fbw_kernel(const uint64_t *__restrict__ visited, uint64_t nwords, uint64_t n,
+                                                       uint32_t sub, uint32_t ntiles,
+                                                       const uint32_t *__restrict__ vis_cnt,
+                                                       const uint32_t *__restrict__ last_set,
+                                                       const uint32_t *__restrict__ last_clear, uint32_t *wb,
+                                                       uint32_t *span, uint32_t *wpart, Scratch sv)
+{
+    __shared__ unsigned long long red[4][kThreads / 32];
+    __shared__ uint32_t wcnt[kThreads / 32];
+    __shared__ long long wlast[kThreads / 32];
+    __shared__ uint32_t smax[kSubBlocks];
+    __shared__ bool s_last;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t tile = blockIdx.x / sub, s = blockIdx.x % sub;
+    const uint32_t tail = (uint32_t)(n & 63u);
+    const uint64_t tile_w0 = (uint64_t)tile * sub * kCmpSubWords;
+    const uint64_t w = tile_w0 + (uint64_t)s * kCmpSubWords + threadIdx.x;
+    const uint64_t y_raw = w < nwords ? visited[w] : 0ull;  // in flight with the sums below
+    for (uint32_t i = threadIdx.x; i < kSubBlocks; i += kThreads) smax[i] = 0u;
+    // tile sums over the tiles before this one (the CTA index of cta_tile_sums is the tile's)
+    unsigned long long vb = 0, vt = 0;
+    uint32_t lm_set = 0, lm_clr = 0;
+    for (uint32_t i = threadIdx.x; i < ntiles; i += kThreads) {
+        const uint32_t c = vis_cnt[i];
+        vt += c;
+        if (i < tile) {
+            vb += c;
+            lm_set = max(lm_set, last_set[i]);
+            lm_clr = max(lm_clr, last_clear[i]);
+        }
+    }
+    vb = warp_sum64(vb);
+    vt = warp_sum64(vt);
+    lm_set = __reduce_max_sync(0xffffffffu, lm_set);
+    lm_clr = __reduce_max_sync(0xffffffffu, lm_clr);
+    if (lane == 0) {
+        red[0][warp] = vb;
+        red[1][warp] = vt;
+        red[2][warp] = lm_set;
+        red[3][warp] = lm_clr;
+    }
+    __syncthreads();
+    vb = vt = 0;
+    lm_set = lm_clr = 0;
+    for (uint32_t i = 0; i < kThreads / 32; i++) {
+        vb += red[0][i];
+        vt += red[1][i];
+        lm_set = max(lm_set, (uint32_t)red[2][i]);
+        lm_clr = max(lm_clr, (uint32_t)red[3][i]);
+    }
+    const bool set_mode = 2ull * vt <= n;
+    const unsigned long long members = set_mode ? vt : (unsigned long long)n - vt;
+    if (members == 0 || 16ull * members < n) return;  // the same test in every CTA
+    // members before the tile, and the last of them (-1: none); then the tile's earlier sub-tiles
+    unsigned long long R = set_mode ? vb : min((unsigned long long)n, 64ull * tile_w0) - vb;
+    long long P = (long long)(set_mode ? lm_set : lm_clr) - 1;
+    {
+        uint32_t cnt = 0;
+        long long lp = -1;
+        for (uint32_t e = 0; e < s; e++) {
+            const uint64_t we = tile_w0 + (uint64_t)e * kCmpSubWords + threadIdx.x;
+            const uint64_t ye = member_word(visited, we, nwords, tail, set_mode);
+            cnt += (uint32_t)__popcll(ye);
+            if (ye) lp = max(lp, (long long)(we * 64u + 63u - (uint32_t)__clzll((long long)ye)));
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+#pragma unroll
+        for (uint32_t o = 16; o > 0; o >>= 1) lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o));
+        __syncthreads();  // red[] was read above by every thread
+        if (lane == 0) {
+            red[0][warp] = cnt;
+            red[1][warp] = (unsigned long long)lp;
+        }
+        __syncthreads();
+        for (uint32_t i = 0; i < kThreads / 32; i++) {
+            R += red[0][i];
+            P = max(P, (long long)red[1][i]);
+        }
+    }
+    const uint64_t y = (w < nwords && !set_mode) ? ~y_raw & ((w == nwords - 1 && tail) ? (1ull << tail) - 1ull : ~0ull)
+                                                 : y_raw;
+    const uint32_t c = (uint32_t)__popcll(y);
+    const long long lastpos = c ? (long long)(w * 64u + 63u - (uint32_t)__clzll((long long)y)) : -1ll;
+    // count and last member over this sub-tile's words up to this one (inclusive)
+    uint32_t incl = c;
+    long long lmax = lastpos;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t yc = __shfl_up_sync(0xffffffffu, incl, o);
+        const long long yl = __shfl_up_sync(0xffffffffu, lmax, o);
+        if (lane >= o) {
+            incl += yc;
+            lmax = max(lmax, yl);
+        }
+    }
+    if (lane == 31) {
+        wcnt[warp] = incl;
+        wlast[warp] = lmax;
+    }
+    __syncthreads();
+    unsigned long long Rw = R + incl - c;  // members before this word
+    long long Pw = P;                      // the last of them
+    const long long lprev = __shfl_up_sync(0xffffffffu, lmax, 1);
+    if (lane > 0) Pw = max(Pw, lprev);
+    uint32_t tot = 0;
+    for (uint32_t i = 0; i < kThreads / 32; i++) {
+        if (i < warp) {
+            Rw += wcnt[i];
+            Pw = max(Pw, wlast[i]);
+        }
+        tot += wcnt[i];
+    }
+    const unsigned long long kfirst = R / kBlock;  // the first block this sub-tile's members touch
+    if (c) {
+        const uint32_t lo = (uint32_t)__ffsll((long long)y) - 1u;
+        const uint32_t hi = 63u - (uint32_t)__clzll((long long)y);
+        const uint32_t j0 = (uint32_t)((kBlock - Rw % kBlock) % kBlock);  // in-word index of a block start
+        if (j0 > 0) {  // members [0, min(j0, c)) close block Rw / 128; member 0's gap is inside it
+            const uint32_t hiA = j0 >= c ? hi : 63u - (uint32_t)__clzll((long long)(y & ((1ull << select64(y, j0)) - 1ull)));
+            uint32_t v = inner_gap_bits(y, lo, hiA);
+            const unsigned long long g = (unsigned long long)((long long)(w * 64u + lo) - Pw - 1);  // Rw > 0: Pw >= 0
+            v = max(v, g ? 64u - (uint32_t)__clzll((long long)g) : 0u);
+            if (v) atomicMax(&smax[Rw / kBlock - kfirst], v);
+        }
+        if (j0 < c) {  // members [j0, c) open block (Rw + j0) / 128; member j0's gap is outside it
+            const uint32_t loB = select64(y, j0);
+            const uint32_t v = inner_gap_bits(y, loB, hi);
+            if (v) atomicMax(&smax[(Rw + j0) / kBlock - kfirst], v);
+        }
+    }
+    if (threadIdx.x == 0) span[blockIdx.x] = 0xffffffffu;
+    __syncthreads();
+    uint32_t local = 0;  // widths of the blocks that start and end in this sub-tile
+    if (tot) {
+        const unsigned long long end = R + tot;  // members before the next sub-tile
+        const uint32_t nloc = (uint32_t)((end - 1) / kBlock - kfirst + 1);
+        for (uint32_t j = threadIdx.x; j < nloc; j += kThreads) {
+            const unsigned long long k = kfirst + j;
+            const bool owned = k * kBlock >= R;  // its first member is in this sub-tile
+            const bool complete = min(k * kBlock + kBlock, members) <= end;
+            if (owned && complete) {
+                local += smax[j];
+            } else {
+                if (smax[j]) atomicMax(&wb[k], smax[j]);
+                if (owned) span[blockIdx.x] = (uint32_t)k;  // at most one: the sub-tile's last block
+            }
+        }
+    }
+    local = __reduce_add_sync(0xffffffffu, local);
+    if (lane == 0) wcnt[warp] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (uint32_t i = 0; i < kThreads / 32; i++) t += wcnt[i];
+        wpart[blockIdx.x] = t;
+    }
+    // the last CTA: the sub-tiles' sums and the listed blocks' widths, the container's decision,
+    // wb[] cleared
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&sv.ctl->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long sum = 0;
+    for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) {
+        sum += __ldcg(wpart + i);
+        const uint32_t k = __ldcg(span + i);
+        if (k != 0xffffffffu) {
+            sum += __ldcg(wb + k);
+            wb[k] = 0u;
+        }
+    }
+    sum = warp_sum64(sum);
+    if (lane == 0) red[0][warp] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long total = 0;
+        for (uint32_t i = 0; i < kThreads / 32; i++) total += red[0][i];
+        // the FB container's rule: raw words unless the header plus the FQ stream (packed, or raw ids
+        // when packing does not pay) is smaller
+        const unsigned long long nb = (members + kBlock - 1) / kBlock;
+        const unsigned long long packed = 16ull + (5ull * nb + 15ull) / 16ull * 16ull + 16ull * total;
+        const unsigned long long rawq = 16ull + (4ull * members + 15ull) / 16ull * 16ull;
+        const unsigned long long fq = packed < rawq ? packed : rawq;
+        const unsigned long long fbr = 16ull + (8ull * ((n + 63) / 64) + 15ull) / 16ull * 16ull;
+        if (16ull + fq >= fbr) {
+            sv.ctl->total_b = total;
+            sv.ctl->skip_pos = 1u;
+        }
+        sv.ctl->ticket = 0u;
     }
 }
 
@@ -873,7 +1181,7 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
                       want_v != 0};
     level_bytes(lin, st.kernel_bytes);
     if (coded) st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
-    if (want_v) st.kernel_launches[FQ_K_ENCODE] += 3;  // positions, widths, pack
+    if (want_v) st.kernel_launches[FQ_K_ENCODE] += 4;  // width sum from the bitmap, positions, widths, pack
     if (dir == FQ_TOP_DOWN) {
         if (coded) st.kernel_launches[FQ_K_DECODE] += 3 + (overlap ? 1 : 0);
         st.kernel_launches[FQ_K_TOP_DOWN] += 2;
@@ -957,6 +1265,10 @@ struct fq_graph {
     HubItem *items;
     uint64_t items_cap;
     uint32_t *tile_cnt, *vis_cnt;  // compaction: per-tile counts of the next frontier and of the visited set
+    uint32_t *last_set, *last_clear;  // per tile: 1 + its last set / clear vertex of the visited bitmap (0: none)
+    uint32_t *wb;                     // V_d's block widths from the bitmap (fbw_kernel; zero between calls)
+    uint32_t *wspan;                  //   per sub-tile: the block it starts that runs past it (or none), then
+                                      //   the widths of the blocks it holds whole
     uint32_t cmp_tiles, cmp_sub;    //   tiles, and 256-word sub-tiles per tile
     uint8_t *host;  // pinned: Counters copy, then LoopState and level records (device-driven loop)
     cudaEvent_t ev[2 * FQ_NUM_KCLASS];
@@ -1050,7 +1362,8 @@ cudaError_t step_init(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_
     FQ_CU(cudaMemsetAsync(g->vis_cnt, 0, 4 * (uint64_t)g->cmp_tiles, st));
     FQ_CU(cudaMemsetAsync(g->ctr, 0, sizeof(Counters), st));
     bfs_init_kernel<<<1, 256, 0, st>>>(g->off, root, n, d_depth, d_parent, g->q, g->fbits, g->visited, g->vis_cnt,
-                                       64ull * kCmpSubWords * g->cmp_sub, g->ctr, g->sq, g->sv, ls);
+                                       64ull * kCmpSubWords * g->cmp_sub, g->cmp_tiles, g->last_set, g->last_clear, g->ctr,
+                                       g->sq, g->sv, ls);
     return cudaGetLastError();
 }
 
@@ -1084,10 +1397,14 @@ cudaError_t step_encode_q(fq_graph *g, bool dense, uint64_t n_f, const LoopState
     return cudaSuccess;
 }
 
-// Step 1 (V_d): the visited bitmap's positions (set or clear, by the mode the previous compaction
-// chose), then their FB encode.
+// Step 1 (V_d): the width sum from the bitmap (a dense visited set usually ends as raw words, and
+// then nothing more is computed), else the visited bitmap's positions (set or clear, by the mode
+// the previous compaction chose) and their FB encode.
 cudaError_t step_encode_v(fq_graph *g, cudaStream_t st)
 {
+    fbw_kernel<<<g->cmp_tiles * g->cmp_sub, kThreads, 0, st>>>(g->visited, g->nwords, g->n, g->cmp_sub, g->cmp_tiles, g->vis_cnt,
+                                                 g->last_set, g->last_clear, g->wb, g->wspan, g->wspan + g->cmp_tiles * g->cmp_sub,
+                                                 g->sv);
     static std::atomic<bool> smem_set[64];
     FQ_CU(allow_smem(v_extract_kernel, kCmpSmem, smem_set));
     v_extract_kernel<<<g->cmp_tiles, kThreads, kCmpSmem, st>>>(g->visited, g->nwords, g->n, g->cmp_sub, g->cmp_tiles,
@@ -1171,8 +1488,8 @@ cudaError_t step_bottom_up(fq_graph *g, bool codec, int32_t newdepth, int32_t *d
 cudaError_t step_compact(fq_graph *g, bool want_v, cudaStream_t st)
 {
     const uint32_t ct = g->cmp_tiles;
-    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->cmp_sub, g->tile_cnt, g->vis_cnt,
-                                              want_v ? 1 : 0);
+    cmp_count_kernel<<<ct, kThreads, 0, st>>>(g->next, g->visited, g->nwords, g->n, g->cmp_sub, g->tile_cnt, g->vis_cnt,
+                                              g->last_set, g->last_clear, want_v ? 1 : 0);
     static std::atomic<bool> smem_set[64];
     FQ_CU(allow_smem(cmp_extract_kernel, kCmpSmem, smem_set));
     cmp_extract_kernel<<<ct, kThreads, kCmpSmem, st>>>(g->next, g->fbits, g->nwords, g->n, g->cmp_sub, ct, g->tile_cnt,
@@ -1471,6 +1788,10 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     const uint64_t o_items = o; o = al256(o + sizeof(HubItem) * g->items_cap);
     const uint64_t o_tc = o; o = al256(o + 4 * (uint64_t)g->cmp_tiles);
     const uint64_t o_vc = o; o = al256(o + 4 * (uint64_t)g->cmp_tiles);
+    const uint64_t o_ls_t = o; o = al256(o + 4 * (uint64_t)g->cmp_tiles);
+    const uint64_t o_lc_t = o; o = al256(o + 4 * (uint64_t)g->cmp_tiles);
+    const uint64_t o_wb = o; o = al256(o + 4 * (n / 128 + 2));
+    const uint64_t o_span = o; o = al256(o + 8 * (uint64_t)g->cmp_tiles * g->cmp_sub);  // span[], then wpart[]
     const uint64_t o_ls = o; o = al256(o + sizeof(LoopState));
     const uint64_t o_recs = o; o = al256(o + sizeof(fq_level_record) * kMaxDeviceRecords);
     g->mem_bytes = o;
@@ -1515,6 +1836,10 @@ fq_status fq_graph_create(const int64_t *d_offsets, const uint32_t *d_cols, uint
     g->items = reinterpret_cast<HubItem *>(g->mem + o_items);
     g->tile_cnt = reinterpret_cast<uint32_t *>(g->mem + o_tc);
     g->vis_cnt = reinterpret_cast<uint32_t *>(g->mem + o_vc);
+    g->last_set = reinterpret_cast<uint32_t *>(g->mem + o_ls_t);
+    g->last_clear = reinterpret_cast<uint32_t *>(g->mem + o_lc_t);
+    g->wb = reinterpret_cast<uint32_t *>(g->mem + o_wb);
+    g->wspan = reinterpret_cast<uint32_t *>(g->mem + o_span);
     g->ls = reinterpret_cast<LoopState *>(g->mem + o_ls);
     g->recs = reinterpret_cast<fq_level_record *>(g->mem + o_recs);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++) cudaEventCreate(&g->ev[i]);
@@ -1683,7 +2008,7 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         }
         if (want_visited) {
             FQ_TRY(step_encode_v(g, cst));
-            enc_launches += 3;
+            enc_launches += 4;
         }
         tm.end(FQ_K_ENCODE, enc_launches);
 

@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
 {
     __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
     __shared__ uint32_t hist[kPx ? kEncWarps : 1][33];
+    if (a.s.ctl->skip_pos) return;  // FB: the widths were summed from the bitmap, which is coded raw
     const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {

@@ -63,6 +63,9 @@ struct Ctl {
     uint32_t mode2;                // mode of the mirrored FB stream (kMode*), kModeNone if absent
     unsigned long long out2_bytes;
     unsigned long long total_e;    // patched codec: exceptions over all blocks
+    uint32_t skip_pos;             // FB: the width sum (total_b) came from the bitmap and the stream is raw
+                                   // words, so no positions are extracted and no widths pass runs
+    uint32_t pad0;
 };
 static_assert(sizeof(Ctl) <= 256, "control block must fit its slot");
 
@@ -158,6 +161,7 @@ __device__ __forceinline__ void reset_scratch_device(const Scratch &s)
     c->fb_mode = kFbRaw;
     c->n = c->nb = c->popcount = c->total_b = c->out_bytes = c->fq_offset = c->out2_bytes = c->total_e = 0;
     c->ticket = 0;
+    c->skip_pos = 0;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)

@@ -218,6 +218,45 @@ def test_ragged_vertex_count_with_multi_subtile_compaction():
     torch.cuda.empty_cache()
 
 
+def _star_then_pairs(n, members, seed):
+    """Root 0 joined to every vertex of `members`; each of those joined to one further vertex, so the
+    visited set after level 1 is {0} + members and level 2 adds up to as many more."""
+    rng = np.random.default_rng(seed)
+    edges = [(0, int(v)) for v in members]
+    rest = np.setdiff1d(np.arange(1, n), members)
+    if rest.size:
+        edges += [(int(v), int(w)) for v, w in zip(members, rng.choice(rest, size=len(members)))]
+    return csr_from_edges(n, edges)
+
+
+@pytest.mark.parametrize("pattern", ["random", "clustered"])
+def test_visited_stream_across_the_raw_threshold(pattern):
+    """V_d's container choice (raw words against coded positions) is taken from a width sum over the
+    visited bitmap once the members (set bits, or clear bits past half) reach n/16.  Visited sets of
+    densities stepping across the point where the raw bitmap starts to win -- in set and in clear
+    mode, scattered at random or in runs with empty words between them, on 4 compaction tiles with a
+    ragged last word -- must give the oracle's V stream at every level, with both loop drivers."""
+    n = 3 * 16384 + 1000 + 17
+    rng = np.random.default_rng(11 if pattern == "random" else 12)
+    fracs = [0.05, 0.07] + [0.14 + 0.01 * i for i in range(17)] + [0.55, 0.62] + [0.66 + 0.01 * i for i in range(20)]
+    for f in fracs:
+        k = int(f * n)
+        if pattern == "random":
+            members = np.sort(rng.choice(np.arange(1, n), size=k, replace=False))
+        else:  # runs of 1..300 vertices at random starts
+            chosen = np.zeros(n, bool)
+            while chosen.sum() < k:
+                a = int(rng.integers(1, n))
+                chosen[a:a + int(rng.integers(1, 300))] = True
+            members = np.nonzero(chosen)[0]
+            members = members[members > 0][:k]
+        off, cols = _star_then_pairs(n, members, seed=int(1000 * f))
+        g = fqbfs.Graph(*to_dev(off, cols))
+        for loop in (0, fqbfs.FQ_BFS_DEVICE_LOOP):
+            check_run(g, off, cols, 0, flags=loop)
+        g.close()
+
+
 @LOOPS
 def test_rmat16_without_codec_stage_same_depths_and_schedule(rmat16, loop):
     off, cols, roots = rmat16
