@@ -729,46 +729,45 @@ __device__ __forceinline__ uint64_t dec_in_bytes(const DecArgs &a)
 template <uint32_t NT>
 __device__ void dec_plan_body(const DecArgs &a);
 
-// The per-tile width (and exception) sums of a packed stream, tiles strided over the grid.
+// The per-tile width (and exception) sums of a packed stream: a CTA takes kEncThreads / kTileBlocks
+// tiles at a time (one thread per block), tile groups strided over the grid.
 __device__ void dec_tile_sums(const DecArgs &a)
 {
+    constexpr uint32_t kTilesPerPass = kEncThreads / kTileBlocks;  // 4
+    constexpr uint32_t kWarpsPerTile = kTileBlocks / 32u;          // 2
     __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
     const FqHeader h = parse_header(a, dec_in_bytes(a));
     if (!h.ok || (h.mode != kModePacked && h.mode != kModePatched)) return;
     const bool px = h.mode == kModePatched;
     const uint8_t *wd = a.in + h.fq_off + h.hdr + 4 * h.nb;
     const uint64_t ntiles = dcdiv(h.nb, kTileBlocks);
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint32_t warp = threadIdx.x >> 5;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * kTilesPerPass; t0 < ntiles; t0 += (uint64_t)gridDim.x * kTilesPerPass) {
+        const uint64_t k = t0 * kTileBlocks + threadIdx.x;  // tile t0 + threadIdx.x / 64, its block threadIdx.x % 64
         uint32_t b = 0, e = 0;
-        if (threadIdx.x < kTileBlocks) {
-            const uint64_t k = t * kTileBlocks + threadIdx.x;
-            if (k < h.nb) {
-                b = wd[k];
-                if (b > 32u) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.fq_off + h.hdr + 4 * h.nb + k);
-                if (px) {  // exception count: at most 127 (slot 0 never), none at width 32
-                    e = wd[h.nb + k];
-                    if (e > 127u || (b == 32u && e)) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.hdr + 5 * h.nb + k);
-                }
+        if (k < h.nb) {
+            b = wd[k];
+            if (b > 32u) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.fq_off + h.hdr + 4 * h.nb + k);
+            if (px) {  // exception count: at most 127 (slot 0 never), none at width 32
+                e = wd[h.nb + k];
+                if (e > 127u || (b == 32u && e)) set_error(a.s.ctl, FQ_ECORRUPT, kWhereDecPlan, h.hdr + 5 * h.nb + k);
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-            e += __shfl_xor_sync(0xffffffffu, e, o);
-        }
+        b = __reduce_add_sync(0xffffffffu, b);
+        e = __reduce_add_sync(0xffffffffu, e);
         if ((threadIdx.x & 31u) == 0) {
-            ws[threadIdx.x >> 5] = b;
-            we[threadIdx.x >> 5] = e;
+            ws[warp] = b;
+            we[warp] = e;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < kTilesPerPass && t0 + threadIdx.x < ntiles) {
             uint32_t sum = 0, sume = 0;
-            for (uint32_t i = 0; i < kEncWarps; i++) {
-                sum += ws[i];
-                sume += we[i];
+            for (uint32_t i = 0; i < kWarpsPerTile; i++) {
+                sum += ws[threadIdx.x * kWarpsPerTile + i];
+                sume += we[threadIdx.x * kWarpsPerTile + i];
             }
-            a.s.tile_sum[t] = sum;
-            if (px) a.s.tile_ex[t] = sume;
+            a.s.tile_sum[t0 + threadIdx.x] = sum;
+            if (px) a.s.tile_ex[t0 + threadIdx.x] = sume;
         }
         __syncthreads();
     }
@@ -1249,12 +1248,19 @@ cudaError_t encode_fb(const uint64_t *words, uint64_t nbits, uint8_t *out, uint6
     return encode_fb_positions(words, nbits, out, cap, out_bytes, s, st);
 }
 
+// The tile-sum kernel's grid: four tiles per CTA per pass, at most two CTAs per SM (its last CTA's
+// ticket is one atomic per CTA on a single counter, and small streams need few CTAs).
+static uint32_t dec_tiles_grid(uint64_t tiles)
+{
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(cdiv(tiles, kEncThreads / kTileBlocks), 2 * (uint64_t)num_sms()));
+}
+
 cudaError_t decode_fq(const uint8_t *in, uint64_t in_bytes_host, const uint64_t *in_bytes_dev, uint32_t *ids,
                       uint64_t cap, uint64_t *n_out, const Scratch &s, cudaStream_t st)
 {
     DecArgs a{in, in_bytes_host, in_bytes_dev, ids, cap, n_out, 0, nullptr, 0, s};
     const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(cap));
-    dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
+    dec_tiles_kernel<<<dec_tiles_grid(tiles), kEncThreads, 0, st>>>(a);
     FQ_CUDA_TRY(prepare_unpack());
     dec_unpack_kernel<<<tuned_grid(FQ_TUNE_DEC_UNPACK, cap, grid_for(std::max(tiles * kEncThreads, cap), kEncThreads, 3 * num_sms()),
                                    cdiv(std::max(tiles * kEncThreads, cap), kEncThreads)), kEncThreads, kDecSmem,
@@ -1267,7 +1273,7 @@ cudaError_t decode_fb(const uint8_t *in, uint64_t in_bytes_host, const uint64_t 
 {
     DecArgs a{in, in_bytes_host, in_bytes_dev, nullptr, nbits, nullptr, 1, words, nbits, s};
     const uint64_t tiles = std::max<uint64_t>(1, enc_tiles(nbits));
-    dec_tiles_kernel<<<(uint32_t)std::min<uint64_t>(tiles, 8 * num_sms()), kEncThreads, 0, st>>>(a);
+    dec_tiles_kernel<<<dec_tiles_grid(tiles), kEncThreads, 0, st>>>(a);
     const uint64_t nwords = cdiv(nbits, 64);
     fb_init_kernel<<<grid_for(nwords, 256, 4 * num_sms()), 256, 0, st>>>(a);
     FQ_CUDA_TRY(prepare_unpack());
