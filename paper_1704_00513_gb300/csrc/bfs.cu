@@ -79,9 +79,15 @@ struct LoopState {
     int32_t status, soft_status;  // a hard error stops the loop; ENOSPC of the log does not
     uint32_t coded;               // this level runs the codec stage (the frontier reaches the threshold)
     uint32_t root_iso;            // the root has degree 0 (it is visited, and isolated)
+    uint32_t small;               // this level's codec stage is the one-CTA form (codec_small)
+    uint32_t pad_small;
     fq_bfs_stats stats;
 };
 constexpr uint32_t kMaxDeviceRecords = 4096;
+// Level bodies of the device-driven loop: 2 * encode form + direction (0..5), and the top-down
+// level whose small frontier takes the one-CTA codec stage.
+constexpr uint32_t kCaseSmall = 6;
+constexpr int kCases = 7;
 
 // Top-down visits of the K edges (src[c], w[c]) one thread holds, of which seen[c] marks those whose
 // target is already visited (or absent).  For each remaining target the thread whose atomicOr sets
@@ -1102,8 +1108,9 @@ __global__ void loop_init_kernel(LoopState *ls, const Counters *ctr, uint64_t m,
 // Direction rule of the host loop: m_f*alpha > m_u  <=>  m_f > floor(m_u/alpha), and
 // n_f*beta < n  <=>  n_f < ceil(n/beta), so no product can overflow.
 // The handle set here picks the level body: 2 * encode form (0 queue + mirrored bitmap, 1 queue +
-// bitmap from the bitmap, 2 no codec stage) + direction (0 top-down, 1 bottom-up).
-__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGraphConditionalHandle h_case)
+// bitmap from the bitmap, 2 no codec stage) + direction (0 top-down, 1 bottom-up), or kCaseSmall for
+// a mirrored top-down level of at most kSmallIds ids when the one-CTA codec stage applies.
+__global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, int small_ok, cudaGraphConditionalHandle h_case)
 {
     const uint32_t flags = ls->p.flags;
     const unsigned long long alpha = ls->p.alpha, beta = ls->p.beta;
@@ -1116,7 +1123,9 @@ __global__ void loop_begin_kernel(LoopState *ls, uint64_t n, int codec, cudaGrap
     const bool coded = codec && ls->n_f >= ls->p.min_codec_ids;
     ls->coded = coded ? 1u : 0u;
     const uint32_t enc = !coded ? 2u : (2ull * ls->n_f > n ? 1u : 0u);
-    cudaGraphSetConditional(h_case, 2u * enc + (dir == FQ_TOP_DOWN ? 0u : 1u));
+    const bool small = small_ok && enc == 0u && dir == FQ_TOP_DOWN && ls->n_f <= kSmallIds;
+    ls->small = small ? 1u : 0u;
+    cudaGraphSetConditional(h_case, small ? kCaseSmall : 2u * enc + (dir == FQ_TOP_DOWN ? 0u : 1u));
 }
 
 // Appends the level's Q_d, B_d [, V_d] to the stream log when they fit (the test loop_end_kernel
@@ -1180,10 +1189,11 @@ __global__ void loop_end_kernel(LoopState *ls_out, const Counters *ctr_in, fq_le
     const LevelIn lin{n, n_iso, ls->visited, n_f, examined, cols_read, nf_next, qb, bb, vb, dir, ls->root_iso, coded,
                       want_v != 0};
     level_bytes(lin, st.kernel_bytes);
-    if (coded) st.kernel_launches[FQ_K_ENCODE] += dense ? 8 : 2;
+    const bool small = ls->small != 0u;
+    if (coded) st.kernel_launches[FQ_K_ENCODE] += small ? 1 : (dense ? 8 : 2);
     if (want_v) st.kernel_launches[FQ_K_ENCODE] += 4;  // width sum from the bitmap, positions, widths, pack
     if (dir == FQ_TOP_DOWN) {
-        if (coded) st.kernel_launches[FQ_K_DECODE] += 3 + (overlap ? 1 : 0);
+        if (coded && !small) st.kernel_launches[FQ_K_DECODE] += 3 + (overlap ? 1 : 0);
         st.kernel_launches[FQ_K_TOP_DOWN] += 2;
     } else {
         if (coded) st.kernel_launches[FQ_K_DECODE] += 4 + (overlap ? 1 : 0);
@@ -1414,6 +1424,20 @@ cudaError_t step_encode_v(fq_graph *g, cudaStream_t st)
                                g->sv, st);
 }
 
+// Steps 1 and 3 of a small top-down level in one launch: Q_d with its mirrored B_d, and Q_d's decode.
+cudaError_t step_codec_small(fq_graph *g, uint64_t n_f, const LoopState *ls, cudaStream_t st)
+{
+    Mirror mb;
+    mb.out = g->bs;
+    mb.cap = g->bs_cap;
+    mb.out_bytes = reinterpret_cast<uint64_t *>(&g->ctr->b_bytes);
+    mb.words = g->fbits;
+    mb.nbits = g->n;
+    const uint64_t *n_dev = ls ? reinterpret_cast<const uint64_t *>(&ls->n_f) : nullptr;
+    return codec_small(g->q, n_f, n_dev, g->qs, g->qs_cap, reinterpret_cast<uint64_t *>(&g->ctr->q_bytes), mb, g->q2,
+                       kSmallIds, reinterpret_cast<uint64_t *>(&g->ctr->dec_n), g->sq, st);
+}
+
 // Step 3, top-down: decode Q_d.
 cudaError_t step_decode_q(fq_graph *g, uint64_t n_f, const LoopState *ls, cudaStream_t st)
 {
@@ -1529,7 +1553,7 @@ struct LoopBuild {
     uint32_t *parent;
     uint8_t *log;
     bool codec, want_v, px, overlap;
-    int enc, dir;  // the level case a segment is captured for (seg_level)
+    int enc, dir;  // the level case a segment is captured for (seg_level); enc 3: kCaseSmall
 };
 
 cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t gr, const cudaGraphNode_t *dep, void *func,
@@ -1581,8 +1605,9 @@ cudaError_t seg_level(void *p)
     const LoopBuild &c = *static_cast<const LoopBuild *>(p);
     fq_graph *g = c.g;
     cudaStream_t s0 = g->dl_stream;
+    const bool small = c.enc == 3;  // kCaseSmall: a mirrored top-down level, one-CTA codec stage
     const bool coded = c.codec && c.enc != 2;
-    const bool ovl = coded && c.overlap;
+    const bool ovl = coded && c.overlap && !small;
     FQ_CU(cudaEventRecord(g->dl_ev[0], s0));
     if (c.want_v) {
         FQ_CU(cudaStreamWaitEvent(g->dl_side[0], g->dl_ev[0], 0));
@@ -1594,7 +1619,9 @@ cudaError_t seg_level(void *p)
         FQ_CU(cudaStreamWaitEvent(g->dl_side[1], g->dl_ev[0], 0));
         cst = g->dl_side[1];
     }
-    if (coded) {
+    if (small) {
+        FQ_CU(step_codec_small(g, 0, g->ls, cst));
+    } else if (coded) {
         FQ_CU(step_encode_q(g, c.enc == 1, 0, g->ls, cst, c.px));
         FQ_CU(c.dir == FQ_TOP_DOWN ? step_decode_q(g, 0, g->ls, cst) : step_decode_b(g, cst));
         if (ovl) {
@@ -1621,8 +1648,9 @@ cudaError_t seg_compact(void *p)
 }
 
 // Build the device-driven loop for these buffers and mode, as a linear chain inside the while node:
-//   init -> while(h_while) { begin -> switch(h_case: 6 level bodies) -> compact [-> log] -> end }
-// loop_begin picks the case = 2 * (encode form: 0 mirrored, 1 from the bitmap, 2 none) + direction.
+//   init -> while(h_while) { begin -> switch(h_case: 7 level bodies) -> compact [-> log] -> end }
+// loop_begin picks the case = 2 * (encode form: 0 mirrored, 1 from the bitmap, 2 none) + direction,
+// or kCaseSmall (a small mirrored top-down level: the one-CTA codec stage).
 // Every parallel branch (V_d beside the level; with the overlap, the codec stage beside the
 // expansion) forks and joins inside a case body, which is a plain child graph.  A node that joins
 // a conditional node with another branch directly in the while body was, on rare launches, never
@@ -1631,14 +1659,17 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
 {
     fq_graph *g = b.g;
     cudaStream_t cs = g->dl_stream;
-    constexpr int kCases = 6;
     cudaGraph_t sg_init = nullptr, sg_cmp = nullptr, top = nullptr;
-    cudaGraph_t sg_case[kCases] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t sg_case[kCases] = {};
     cudaError_t e = capture_segment(cs, &sg_init, seg_init, const_cast<LoopBuild *>(&b));
     for (int k = 0; k < kCases && e == cudaSuccess; k++) {
         LoopBuild ctx = b;
         ctx.enc = b.codec ? k / 2 : 2;  // without the codec stage every case is the raw level
         ctx.dir = k % 2;
+        if (k == (int)kCaseSmall) {  // enc 3: the one-CTA codec stage (top-down, mirrored)
+            ctx.enc = b.codec ? 3 : 2;
+            ctx.dir = FQ_TOP_DOWN;
+        }
         e = capture_segment(cs, &sg_case[k], seg_level, &ctx);
     }
     if (e == cudaSuccess) e = capture_segment(cs, &sg_cmp, seg_compact, const_cast<LoopBuild *>(&b));
@@ -1657,7 +1688,8 @@ cudaError_t build_device_loop(const LoopBuild &b, cudaGraph_t *out)
             LoopState *ls = g->ls;
             uint64_t n = g->n;
             int codec = b.codec ? 1 : 0;
-            void *args[] = {&ls, &n, &codec, &h_case};
+            int small_ok = b.codec && !b.px && !b.overlap ? 1 : 0;
+            void *args[] = {&ls, &n, &codec, &small_ok, &h_case};
             if ((e = add_kernel_node(&n_begin, body, nullptr, (void *)loop_begin_kernel, args)) != cudaSuccess) goto done;
         }
         if ((e = add_conditional(&n_sw, body, &n_begin, h_case, cudaGraphCondTypeSwitch, kCases, cases)) != cudaSuccess)
@@ -1999,9 +2031,14 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         tm.cls_st[FQ_K_ENCODE] = tm.cls_st[FQ_K_DECODE] = ovl ? cst : nullptr;
 
         // 1. encode F_d (Q_d and B_d), and V_d
+        // a small mirrored top-down level takes the one-CTA codec stage (encode and decode together)
+        const bool small = coded && !px && !ovl && dir == FQ_TOP_DOWN && 2 * n_f <= n && n_f <= kSmallIds;
         tm.begin(FQ_K_ENCODE);
         int enc_launches = 0;
-        if (coded) {
+        if (small) {
+            FQ_TRY(step_codec_small(g, n_f, nullptr, cst));
+            enc_launches = 1;
+        } else if (coded) {
             const bool dense = 2 * n_f > n;
             FQ_TRY(step_encode_q(g, dense, n_f, nullptr, cst, px));
             enc_launches = dense ? 8 : 2;
@@ -2014,10 +2051,10 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
 
         // 3 + 4. decode the consumed form (overlap: decode and compare with the raw form), expand
         tm.begin(FQ_K_DECODE);
-        if (coded && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, cst));
+        if (coded && !small && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, cst));
         if (coded && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, cst));
         if (ovl) FQ_TRY(dir == FQ_TOP_DOWN ? step_check_q(g, n_f, nullptr, cst) : step_check_b(g, cst));
-        tm.end(FQ_K_DECODE, coded ? (dir == FQ_TOP_DOWN ? 3 : 4) + (ovl ? 1 : 0) : 0);
+        tm.end(FQ_K_DECODE, coded && !small ? (dir == FQ_TOP_DOWN ? 3 : 4) + (ovl ? 1 : 0) : 0);
         if (ovl) FQ_TRY(cudaEventRecord(g->ov_ev[1], cst));
         const bool consume_decoded = coded && !ovl;
         if (dir == FQ_TOP_DOWN) {

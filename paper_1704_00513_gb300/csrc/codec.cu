@@ -336,15 +336,13 @@ __device__ __forceinline__ void px_width(const uint32_t g[4], uint32_t lane, uin
 }
 
 // W: every warp issues the loads of its eight blocks before using any of them.
+// W for tile t (all threads of the CTA; ws, we, hist: the CTA's shared scratch).
 template <bool kPx>
-__global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
+__device__ __forceinline__ void enc_widths_tile(const EncArgs &a, uint64_t n, uint64_t nb, uint64_t t, uint32_t *ws,
+                                                uint32_t *we, uint32_t (*hist)[33])
 {
-    __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
-    __shared__ uint32_t hist[kPx ? kEncWarps : 1][33];
-    if (a.s.ctl->skip_pos) return;  // FB: the widths were summed from the bitmap, which is coded raw
-    const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    {
         const uint64_t k0 = t * kTileBlocks + warp * kBlocksPerWarp;
         uint32_t v[kBlocksPerWarp][4];
         load_blocks8(a.ids, k0, n, lane, v);
@@ -392,6 +390,16 @@ __global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
     }
 }
 
+template <bool kPx>
+__global__ void __launch_bounds__(kEncThreads, 4) enc_widths_kernel(EncArgs a)
+{
+    __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
+    __shared__ uint32_t hist[kPx ? kEncWarps : 1][33];
+    if (a.s.ctl->skip_pos) return;  // FB: the widths were summed from the bitmap, which is coded raw
+    const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) enc_widths_tile<kPx>(a, n, nb, t, ws, we, hist);
+}
+
 // Raw bodies (FQ raw ids, or FB raw words) for whichever output the decision chose them; every
 // thread of the grid takes a strided share.
 __device__ void enc_raw_bodies(const EncArgs &a, const EncPlan &p, uint64_t n, uint64_t tid, uint64_t stride)
@@ -422,53 +430,24 @@ __device__ void enc_raw_bodies(const EncArgs &a, const EncPlan &p, uint64_t n, u
     }
 }
 
-// P: decision, headers (CTA 0), then the packed body tile by tile -- one warp per group of
-// kBlocksPerWarp blocks, offsets from the tile's width bytes (two per lane, one warp scan) -- or
-// the raw bodies.  Packed words go to the output and, identical, to the mirror's inner stream.
+// P for tile t, whose blocks' payload starts at width sum `prefix` (exceptions: `prefix_e`) of the
+// stream -- every warp of the CTA; pk: the CTA's per-warp staging rows.
 template <bool kPx>
-__global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
+__device__ __forceinline__ void enc_pack_tile(const EncArgs &a, const EncPlan &p, uint64_t n, uint64_t nb,
+                                              unsigned long long total, unsigned long long total_e, uint64_t t,
+                                              unsigned long long prefix, unsigned long long prefix_e,
+                                              uint32_t (*pk)[4 * 32 + 4])
 {
-    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
-    __shared__ unsigned long long s_part[kEncWarps], s_parte[kEncWarps];
-    const Ctl *c = a.s.ctl;
-    const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
-    const unsigned long long total = c->total_b, total_e = kPx ? c->total_e : 0ull;
-    const EncPlan p = enc_decide(a, n, nb, total, total_e, *reinterpret_cast<const volatile int32_t *>(&c->code));
-    if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, total, total_e, p);
-    if (p.fatal) return;
-    enc_raw_bodies(a, p, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
     const uint32_t packed_mode = kPx ? kModePatched : kModePacked;
     const bool pk1 = p.mode == packed_mode, pk2 = p.mode2 == packed_mode;
-    if (!pk1 && !pk2) return;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint64_t off1 = a.fb ? 16u : 0u, off2 = 16u;  // where each output's FQ stream starts
     const uint64_t hdr = kPx ? kPxHeader : 16u;
     const uint64_t payload = hdr + dpad16((kPx ? 6u : 5u) * nb);
     const uint64_t xpos = payload + 16u * total, xhigh = xpos + dpad16(total_e);  // patched: exception areas
-    unsigned long long prefix = 0, prefix_e = 0;  // width and exception sums of tiles [0, done)
-    uint64_t done = 0;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        // add the width (and exception) sums of tiles [done, t)
-        unsigned long long part = 0, parte = 0;
-        for (uint64_t i = done + threadIdx.x; i < t; i += blockDim.x) {
-            part += a.s.tile_sum[i];
-            if (kPx) parte += a.s.tile_ex[i];
-        }
-        part = warp_sum64(part);
-        if (kPx) parte = warp_sum64(parte);
-        if (lane == 0) {
-            s_part[warp] = part;
-            s_parte[warp] = parte;
-        }
-        __syncthreads();
-        for (uint32_t w = 0; w < kEncWarps; w++) {
-            prefix += s_part[w];
-            if (kPx) prefix_e += s_parte[w];
-        }
-        __syncthreads();
-        done = t;
+    {
         const uint64_t k0 = t * kTileBlocks + warp * kBlocksPerWarp;
-        if (k0 >= nb) continue;
+        if (k0 >= nb) return;
         uint32_t v[kBlocksPerWarp][4];
         load_blocks8(a.ids, k0, n, lane, v);
         const uint64_t kk = t * kTileBlocks + 2 * lane;
@@ -540,6 +519,50 @@ __global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
             if (pk1) store_block_words(a.out + off1 + rel, w4, b, lane, 0, ~0ull);
             if (pk2) store_block_words(a.m_out + off2 + rel, w4, b, lane, 0, ~0ull);
         }
+    }
+}
+
+// P: decision, headers (CTA 0), then the packed body tile by tile -- one warp per group of
+// kBlocksPerWarp blocks, offsets from the tile's width bytes (two per lane, one warp scan) -- or
+// the raw bodies.  Packed words go to the output and, identical, to the mirror's inner stream.
+template <bool kPx>
+__global__ void __launch_bounds__(kEncThreads, 3) enc_pack_kernel(EncArgs a)
+{
+    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
+    __shared__ unsigned long long s_part[kEncWarps], s_parte[kEncWarps];
+    const Ctl *c = a.s.ctl;
+    const uint64_t n = enc_count(a), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    const unsigned long long total = c->total_b, total_e = kPx ? c->total_e : 0ull;
+    const EncPlan p = enc_decide(a, n, nb, total, total_e, *reinterpret_cast<const volatile int32_t *>(&c->code));
+    if (blockIdx.x == 0 && threadIdx.x == 0) enc_finalize(a, n, nb, total, total_e, p);
+    if (p.fatal) return;
+    enc_raw_bodies(a, p, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+    const uint32_t packed_mode = kPx ? kModePatched : kModePacked;
+    if (p.mode != packed_mode && p.mode2 != packed_mode) return;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    unsigned long long prefix = 0, prefix_e = 0;  // width and exception sums of tiles [0, done)
+    uint64_t done = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // add the width (and exception) sums of tiles [done, t)
+        unsigned long long part = 0, parte = 0;
+        for (uint64_t i = done + threadIdx.x; i < t; i += blockDim.x) {
+            part += a.s.tile_sum[i];
+            if (kPx) parte += a.s.tile_ex[i];
+        }
+        part = warp_sum64(part);
+        if (kPx) parte = warp_sum64(parte);
+        if (lane == 0) {
+            s_part[warp] = part;
+            s_parte[warp] = parte;
+        }
+        __syncthreads();
+        for (uint32_t w = 0; w < kEncWarps; w++) {
+            prefix += s_part[w];
+            if (kPx) prefix_e += s_parte[w];
+        }
+        __syncthreads();
+        done = t;
+        enc_pack_tile<kPx>(a, p, n, nb, total, total_e, t, prefix, prefix_e, pk);
     }
 }
 
@@ -948,11 +971,10 @@ __device__ __forceinline__ GroupMeta group_meta(const DecArgs &a, const uint8_t 
 // CTA barrier.  A group's payload is one contiguous range: lane 0 stages it into the warp's own
 // shared-memory buffer with one TMA bulk copy while the warp decodes the previous group from the
 // other buffer (extract, prefix-sum the gaps, validate, 128-bit stores).
-__global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
+// dbuf: [kEncWarps][2][kDecStage] bytes (128-byte aligned); bars, patch: the CTA's shared scratch.
+__device__ __forceinline__ void dec_unpack_body(const DecArgs &a, uint8_t *dbuf, unsigned long long (*bars)[2],
+                                                uint32_t (*patch)[kBlock])
 {
-    extern __shared__ __align__(128) uint8_t dbuf[];  // [kEncWarps][2][kDecStage]
-    __shared__ __align__(8) unsigned long long bars[kEncWarps][2];
-    __shared__ uint32_t patch[kEncWarps][kBlock];  // patched: one block's high parts by slot
     const Ctl *c = a.s.ctl;
     const uint32_t mode = c->mode;
     if (mode != kModePacked && mode != kModeRaw && mode != kModePatched) return;
@@ -1147,6 +1169,57 @@ __global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
     }
 }
 
+__global__ void __launch_bounds__(kEncThreads, 3) dec_unpack_kernel(DecArgs a)
+{
+    extern __shared__ __align__(128) uint8_t dbuf[];  // [kEncWarps][2][kDecStage]
+    __shared__ __align__(8) unsigned long long bars[kEncWarps][2];
+    __shared__ uint32_t patch[kEncWarps][kBlock];  // patched: one block's high parts by slot
+    dec_unpack_body(a, dbuf, bars, patch);
+}
+
+// A small frontier's whole codec stage in one CTA (at most kSmallTiles tiles of ids): W and P of
+// the FQ encode with its FB mirror, then D0, D1 and D2 of the decode -- the same steps as the five
+// launches of the general path, each starting after the previous one's writes (CTA barriers), the
+// decode reading only the stream bytes just written.  For a frontier this small the general path
+// is bound by its launches and their grid-wide handoffs, not by its work.
+__global__ void __launch_bounds__(kEncThreads, 1) small_codec_kernel(EncArgs ea, DecArgs da)
+{
+    extern __shared__ __align__(128) uint8_t dbuf[];  // [kEncWarps][2][kDecStage]
+    __shared__ __align__(8) unsigned long long bars[kEncWarps][2];
+    __shared__ uint32_t patch[kEncWarps][kBlock];
+    __shared__ uint32_t ws[kEncWarps], we[kEncWarps];
+    __shared__ uint32_t hist[1][33];
+    __shared__ uint32_t pk[kEncWarps][4 * 32 + 4];
+    Ctl *c = ea.s.ctl;
+    const uint64_t n = enc_count(ea), nb = dcdiv(n, kBlock), ntiles = dcdiv(nb, kTileBlocks);
+    if (ntiles > kSmallTiles) {  // the caller picks this path only for small frontiers
+        if (threadIdx.x == 0) set_error(c, FQ_EINVAL, kWhereEncWidths, n);
+        return;
+    }
+    for (uint64_t t = 0; t < ntiles; t++) enc_widths_tile<false>(ea, n, nb, t, ws, we, hist);  // ends in a barrier
+    unsigned long long total = 0;
+    for (uint64_t t = 0; t < ntiles; t++) total += ea.s.tile_sum[t];
+    const EncPlan p = enc_decide(ea, n, nb, total, 0ull, *reinterpret_cast<const volatile int32_t *>(&c->code));
+    if (threadIdx.x == 0) enc_finalize(ea, n, nb, total, 0ull, p);
+    if (!p.fatal) {
+        enc_raw_bodies(ea, p, n, threadIdx.x, blockDim.x);
+        if (p.mode == kModePacked || p.mode2 == kModePacked) {
+            unsigned long long prefix = 0;
+            for (uint64_t t = 0; t < ntiles; t++) {
+                enc_pack_tile<false>(ea, p, n, nb, total, 0ull, t, prefix, 0ull, pk);
+                prefix += ea.s.tile_sum[t];
+            }
+        }
+    }
+    __syncthreads();  // the stream and its size are written
+    if (p.fatal || p.err != FQ_OK) return;  // the encode's error is the stage's status
+    dec_tile_sums(da);
+    __syncthreads();
+    dec_plan_body<kEncThreads>(da);
+    __syncthreads();
+    dec_unpack_body(da, dbuf, bars, patch);
+}
+
 __global__ void reset_status_kernel(Scratch s) { reset_scratch_device(s); }
 
 uint32_t grid_for(uint64_t items, uint32_t per_cta, uint32_t max_ctas)
@@ -1227,6 +1300,19 @@ cudaError_t encode_fq_mirror(const uint32_t *ids, uint64_t n_host, const uint64_
 {
     EncArgs a{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words, m.nbits, 0};
     return launch_encode(a, n_dev ? n_max : n_host, st);
+}
+
+cudaError_t codec_small(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint8_t *out, uint64_t cap,
+                        uint64_t *out_bytes, const Mirror &m, uint32_t *ids_out, uint64_t dec_cap, uint64_t *n_out,
+                        const Scratch &s, cudaStream_t st)
+{
+    static std::atomic<bool> done[64];
+    FQ_CUDA_TRY(allow_smem(small_codec_kernel, kDecSmem, done));
+    const EncArgs ea{ids, n_host, n_dev, out, cap, out_bytes, 0, 0, nullptr, s, m.out, m.cap, m.out_bytes, m.words,
+                     m.nbits, 0};
+    const DecArgs da{out, 0, out_bytes, ids_out, dec_cap, n_out, 0, nullptr, 0, s};
+    small_codec_kernel<<<1, kEncThreads, kDecSmem, st>>>(ea, da);
+    return cudaGetLastError();
 }
 
 cudaError_t encode_fb_positions(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap,

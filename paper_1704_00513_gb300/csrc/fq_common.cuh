@@ -127,6 +127,13 @@ struct Mirror {
 cudaError_t encode_fq_mirror(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint64_t n_max,
                              uint8_t *out, uint64_t cap, uint64_t *out_bytes, const Mirror &mirror,
                              const Scratch &s, cudaStream_t st);
+// Frontiers of at most kSmallIds ids: the mirrored encode (as encode_fq_mirror) and the decode of
+// the FQ stream it wrote (as decode_fq, into ids_out) in one launch of one CTA.
+constexpr uint32_t kSmallTiles = 1;
+constexpr uint64_t kSmallIds = (uint64_t)kSmallTiles * kTileBlocks * kBlock;  // 8,192
+cudaError_t codec_small(const uint32_t *ids, uint64_t n_host, const uint64_t *n_dev, uint8_t *out, uint64_t cap,
+                        uint64_t *out_bytes, const Mirror &mirror, uint32_t *ids_out, uint64_t dec_cap,
+                        uint64_t *n_out, const Scratch &s, cudaStream_t st);
 // FB encode when the positions to code are already in s.positions with count and mode set in
 // s.ctl (n, fb_mode), e.g. by the BFS compaction.
 cudaError_t encode_fb_positions(const uint64_t *words, uint64_t nbits, uint8_t *out, uint64_t cap,

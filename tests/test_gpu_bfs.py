@@ -257,6 +257,29 @@ def test_visited_stream_across_the_raw_threshold(pattern):
         g.close()
 
 
+@pytest.mark.parametrize("k", [1, 8191, 8192, 8193])
+def test_small_frontier_codec_stage_at_its_limit(k):
+    """A top-down level whose mirrored frontier holds at most 8,192 ids takes the one-CTA codec
+    stage (encode and decode in one launch); one id more takes the general one.  Root 0 reaches k
+    leaves, each leaf one more vertex, and a separate 1,500-vertex clique keeps the unexplored edge
+    count high enough that both levels stay top-down: streams, depths and records must equal the
+    oracle's on either side of the limit, with both loop drivers."""
+    n = 2 * k + 1 + 1500
+    leaves = torch.arange(1, k + 1, dtype=torch.int64)
+    cq = torch.arange(2 * k + 1, n, dtype=torch.int64)
+    cu, cv = torch.meshgrid(cq, cq, indexing="ij")
+    u = torch.cat([torch.zeros(k, dtype=torch.int64), leaves, cu.reshape(-1)])
+    v = torch.cat([leaves, leaves + k, cv.reshape(-1)])
+    off_t, cols_t = inputs.edges_to_csr(u, v, n)
+    off, cols = off_t.numpy(), cols_t.numpy().view(np.uint32)
+    g = fqbfs.Graph(*to_dev(off, cols))
+    for loop in (0, fqbfs.FQ_BFS_DEVICE_LOOP):
+        res = check_run(g, off, cols, 0, flags=loop)
+        assert [r["direction"] for r in res.levels[:3]] == [fqbfs.FQ_TOP_DOWN] * 3
+        assert [r["n_f"] for r in res.levels[:3]] == [1, k, k]
+    g.close()
+
+
 @LOOPS
 def test_rmat16_without_codec_stage_same_depths_and_schedule(rmat16, loop):
     off, cols, roots = rmat16
@@ -471,8 +494,15 @@ def test_overlapped_codec_stage_gives_the_serial_results(rmat16, loop, extra):
         for k in ("levels", "directions", "reached", "reached_edges", "edges_examined", "raw_queue_bytes",
                   "enc_queue_bytes", "raw_bitmap_bytes", "enc_bitmap_bytes", "enc_visited_bytes", "kernel_bytes"):
             assert a.stats[k] == b.stats[k], k
-        coded = sum(1 for x in a.levels if x["q_bytes"])
-        assert b.stats["kernel_launches"]["decode"] == a.stats["kernel_launches"]["decode"] + coded  # + the compares
+        # decode launches per coded level: 3 (queue) or 4 (bitmap), with the overlap + 1 for the compare;
+        # a serial top-down level of at most 8,192 mirrored ids decodes inside its one-CTA codec stage
+        n = off.size - 1
+        coded = [x for x in a.levels if x["q_bytes"]]
+        per = [3 if x["direction"] == fqbfs.FQ_TOP_DOWN else 4 for x in coded]
+        small = [x["direction"] == fqbfs.FQ_TOP_DOWN and not (extra & fqbfs.FQ_BFS_PATCHED) and
+                 2 * x["n_f"] <= n and x["n_f"] <= 8192 for x in coded]
+        assert a.stats["kernel_launches"]["decode"] == sum(0 if sm else c for c, sm in zip(per, small))
+        assert b.stats["kernel_launches"]["decode"] == sum(c + 1 for c in per)
         assert len(a.streams) == len(b.streams) == len(a.levels)
         for sa, sb in zip(a.streams, b.streams):
             for key in ("Q", "B", "V"):
