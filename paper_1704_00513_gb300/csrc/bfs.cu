@@ -855,16 +855,17 @@ __device__ __forceinline__ uint64_t member_word(const uint64_t *__restrict__ vis
     return set_mode ? y : ~y & ((w == nwords - 1 && tail) ? (1ull << tail) - 1ull : ~0ull);
 }
 
-__global__ void __launch_bounds__(kThreads) fbw_kernel(const uint64_t *__restrict__ visited, uint64_t nwords, uint64_t n,
-                                                       uint32_t sub, uint32_t ntiles,
-                                                       const uint32_t *__restrict__ vis_cnt,
-                                                       const uint32_t *__restrict__ last_set,
-                                                       const uint32_t *__restrict__ last_clear, uint32_t *wb,
-                                                       uint32_t *span, uint32_t *wpart, Scratch sv)
+__global__ void __launch_bounds__(kThreads, 6) fbw_kernel(const uint64_t *__restrict__ visited, uint64_t nwords, uint64_t n,
+                                                          uint32_t sub, uint32_t ntiles,
+                                                          const uint32_t *__restrict__ vis_cnt,
+                                                          const uint32_t *__restrict__ last_set,
+                                                          const uint32_t *__restrict__ last_clear, uint32_t *wb,
+                                                          uint32_t *span, uint32_t *wpart, Scratch sv)
 {
-    __shared__ unsigned long long red[4][kThreads / 32];
-    __shared__ uint32_t wcnt[kThreads / 32];
-    __shared__ long long wlast[kThreads / 32];
+    // Counts and positions fit 32 bits (n < 2^32); a position p is carried as p + 1, 0 for none.
+    __shared__ uint32_t red[4][kThreads / 32];
+    __shared__ uint32_t tsum[4];
+    __shared__ uint32_t wcnt[kThreads / 32], wlast[kThreads / 32];
     __shared__ uint32_t smax[kSubBlocks];
     __shared__ bool s_last;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -872,79 +873,89 @@ __global__ void __launch_bounds__(kThreads) fbw_kernel(const uint64_t *__restric
     const uint32_t tail = (uint32_t)(n & 63u);
     const uint64_t tile_w0 = (uint64_t)tile * sub * kCmpSubWords;
     const uint64_t w = tile_w0 + (uint64_t)s * kCmpSubWords + threadIdx.x;
-    const uint64_t y_raw = w < nwords ? visited[w] : 0ull;  // in flight with the sums below
+    const uint64_t in_n_last = tail ? (1ull << tail) - 1ull : ~0ull;  // the last word's bits below n
+    // every load of the prologue first: this word, the tile's earlier sub-tiles' words (both modes'
+    // members are counted, the mode is known only after the sums), the earlier tiles' records (warp 0)
+    const uint64_t y_raw = w < nwords ? visited[w] : 0ull;
+    uint64_t ye[kCmpAhead];
+#pragma unroll
+    for (uint32_t e = 0; e < kCmpAhead; e++) {
+        const uint64_t we = tile_w0 + (uint64_t)e * kCmpSubWords + threadIdx.x;
+        ye[e] = (e < s && we < nwords) ? visited[we] : 0ull;
+    }
     for (uint32_t i = threadIdx.x; i < kSubBlocks; i += kThreads) smax[i] = 0u;
-    // tile sums over the tiles before this one (the CTA index of cta_tile_sums is the tile's)
-    unsigned long long vb = 0, vt = 0;
-    uint32_t lm_set = 0, lm_clr = 0;
-    for (uint32_t i = threadIdx.x; i < ntiles; i += kThreads) {
-        const uint32_t c = vis_cnt[i];
-        vt += c;
-        if (i < tile) {
-            vb += c;
-            lm_set = max(lm_set, last_set[i]);
-            lm_clr = max(lm_clr, last_clear[i]);
+    if (warp == 0) {  // visited before / in all tiles, last set / clear vertex before this tile
+        uint32_t vb = 0, vt = 0, ls = 0, lc = 0;
+        for (uint32_t i = lane; i < ntiles; i += 32u) {
+            const uint32_t c = vis_cnt[i];
+            vt += c;
+            if (i < tile) {
+                vb += c;
+                ls = max(ls, last_set[i]);
+                lc = max(lc, last_clear[i]);
+            }
+        }
+        vb = __reduce_add_sync(0xffffffffu, vb);
+        vt = __reduce_add_sync(0xffffffffu, vt);
+        ls = __reduce_max_sync(0xffffffffu, ls);
+        lc = __reduce_max_sync(0xffffffffu, lc);
+        if (lane == 0) {
+            tsum[0] = vb;
+            tsum[1] = vt;
+            tsum[2] = ls;
+            tsum[3] = lc;
         }
     }
-    vb = warp_sum64(vb);
-    vt = warp_sum64(vt);
-    lm_set = __reduce_max_sync(0xffffffffu, lm_set);
-    lm_clr = __reduce_max_sync(0xffffffffu, lm_clr);
+    uint32_t es = 0, ec = 0, els = 0, elc = 0;  // the earlier sub-tiles: set, clear, last set + 1, last clear + 1
+    auto earlier = [&](uint32_t e, uint64_t y1) {
+        const uint64_t we = tile_w0 + (uint64_t)e * kCmpSubWords + threadIdx.x;
+        if (e >= s || we >= nwords) return;
+        const uint64_t y0 = ~y1 & (we == nwords - 1 ? in_n_last : ~0ull);
+        es += (uint32_t)__popcll(y1);
+        ec += (uint32_t)__popcll(y0);
+        if (y1) els = max(els, (uint32_t)(we * 64u + 64u - (uint32_t)__clzll((long long)y1)));
+        if (y0) elc = max(elc, (uint32_t)(we * 64u + 64u - (uint32_t)__clzll((long long)y0)));
+    };
+#pragma unroll
+    for (uint32_t e = 0; e < kCmpAhead; e++) earlier(e, ye[e]);
+    for (uint32_t e = kCmpAhead; e < s; e++) {  // tiles of more sub-tiles (graphs above 29.9M vertices)
+        const uint64_t we = tile_w0 + (uint64_t)e * kCmpSubWords + threadIdx.x;
+        earlier(e, we < nwords ? visited[we] : 0ull);
+    }
+    es = __reduce_add_sync(0xffffffffu, es);
+    ec = __reduce_add_sync(0xffffffffu, ec);
+    els = __reduce_max_sync(0xffffffffu, els);
+    elc = __reduce_max_sync(0xffffffffu, elc);
     if (lane == 0) {
-        red[0][warp] = vb;
-        red[1][warp] = vt;
-        red[2][warp] = lm_set;
-        red[3][warp] = lm_clr;
+        red[0][warp] = es;
+        red[1][warp] = ec;
+        red[2][warp] = els;
+        red[3][warp] = elc;
     }
     __syncthreads();
-    vb = vt = 0;
-    lm_set = lm_clr = 0;
     for (uint32_t i = 0; i < kThreads / 32; i++) {
-        vb += red[0][i];
-        vt += red[1][i];
-        lm_set = max(lm_set, (uint32_t)red[2][i]);
-        lm_clr = max(lm_clr, (uint32_t)red[3][i]);
+        if (i == 0) es = ec = els = elc = 0;
+        es += red[0][i];
+        ec += red[1][i];
+        els = max(els, red[2][i]);
+        elc = max(elc, red[3][i]);
     }
+    const uint32_t vb = tsum[0], vt = tsum[1];
     const bool set_mode = 2ull * vt <= n;
-    const unsigned long long members = set_mode ? vt : (unsigned long long)n - vt;
+    const uint32_t members = set_mode ? vt : (uint32_t)(n - vt);
     if (members == 0 || 16ull * members < n) return;  // the same test in every CTA
-    // members before the tile, and the last of them (-1: none); then the tile's earlier sub-tiles
-    unsigned long long R = set_mode ? vb : min((unsigned long long)n, 64ull * tile_w0) - vb;
-    long long P = (long long)(set_mode ? lm_set : lm_clr) - 1;
-    {
-        uint32_t cnt = 0;
-        long long lp = -1;
-        for (uint32_t e = 0; e < s; e++) {
-            const uint64_t we = tile_w0 + (uint64_t)e * kCmpSubWords + threadIdx.x;
-            const uint64_t ye = member_word(visited, we, nwords, tail, set_mode);
-            cnt += (uint32_t)__popcll(ye);
-            if (ye) lp = max(lp, (long long)(we * 64u + 63u - (uint32_t)__clzll((long long)ye)));
-        }
-        cnt = __reduce_add_sync(0xffffffffu, cnt);
-#pragma unroll
-        for (uint32_t o = 16; o > 0; o >>= 1) lp = max(lp, __shfl_xor_sync(0xffffffffu, lp, o));
-        __syncthreads();  // red[] was read above by every thread
-        if (lane == 0) {
-            red[0][warp] = cnt;
-            red[1][warp] = (unsigned long long)lp;
-        }
-        __syncthreads();
-        for (uint32_t i = 0; i < kThreads / 32; i++) {
-            R += red[0][i];
-            P = max(P, (long long)red[1][i]);
-        }
-    }
-    const uint64_t y = (w < nwords && !set_mode) ? ~y_raw & ((w == nwords - 1 && tail) ? (1ull << tail) - 1ull : ~0ull)
-                                                 : y_raw;
+    // members before this sub-tile, and the last of them + 1 (0: none)
+    const uint32_t R = set_mode ? vb + es : (uint32_t)min((unsigned long long)n, 64ull * tile_w0) - vb + ec;
+    const uint32_t P1 = set_mode ? max(tsum[2], els) : max(tsum[3], elc);
+    const uint64_t y = (w < nwords && !set_mode) ? ~y_raw & (w == nwords - 1 ? in_n_last : ~0ull) : y_raw;
     const uint32_t c = (uint32_t)__popcll(y);
-    const long long lastpos = c ? (long long)(w * 64u + 63u - (uint32_t)__clzll((long long)y)) : -1ll;
-    // count and last member over this sub-tile's words up to this one (inclusive)
-    uint32_t incl = c;
-    long long lmax = lastpos;
+    const uint32_t last1 = c ? (uint32_t)(w * 64u + 64u - (uint32_t)__clzll((long long)y)) : 0u;
+    // count and last member + 1 over this sub-tile's words up to this one (inclusive)
+    uint32_t incl = c, lmax = last1;
 #pragma unroll
     for (uint32_t o = 1; o < 32; o <<= 1) {
         const uint32_t yc = __shfl_up_sync(0xffffffffu, incl, o);
-        const long long yl = __shfl_up_sync(0xffffffffu, lmax, o);
+        const uint32_t yl = __shfl_up_sync(0xffffffffu, lmax, o);
         if (lane >= o) {
             incl += yc;
             lmax = max(lmax, yl);
@@ -955,32 +966,32 @@ __global__ void __launch_bounds__(kThreads) fbw_kernel(const uint64_t *__restric
         wlast[warp] = lmax;
     }
     __syncthreads();
-    unsigned long long Rw = R + incl - c;  // members before this word
-    long long Pw = P;                      // the last of them
-    const long long lprev = __shfl_up_sync(0xffffffffu, lmax, 1);
-    if (lane > 0) Pw = max(Pw, lprev);
+    uint32_t Rw = R + incl - c;  // members before this word
+    uint32_t Pw1 = P1;           // the last of them + 1
+    const uint32_t lprev = __shfl_up_sync(0xffffffffu, lmax, 1);
+    if (lane > 0) Pw1 = max(Pw1, lprev);
     uint32_t tot = 0;
     for (uint32_t i = 0; i < kThreads / 32; i++) {
         if (i < warp) {
             Rw += wcnt[i];
-            Pw = max(Pw, wlast[i]);
+            Pw1 = max(Pw1, wlast[i]);
         }
         tot += wcnt[i];
     }
-    const unsigned long long kfirst = R / kBlock;  // the first block this sub-tile's members touch
+    const uint32_t kfirst = R / kBlock;  // the first block this sub-tile's members touch
     if (c) {
         const uint32_t lo = (uint32_t)__ffsll((long long)y) - 1u;
         const uint32_t hi = 63u - (uint32_t)__clzll((long long)y);
-        const uint32_t j0 = (uint32_t)((kBlock - Rw % kBlock) % kBlock);  // in-word index of a block start
+        const uint32_t j0 = (kBlock - Rw % kBlock) % kBlock;  // in-word index of a block start
+        const uint32_t loB = j0 < c ? select64(y, j0) : 64u;
         if (j0 > 0) {  // members [0, min(j0, c)) close block Rw / 128; member 0's gap is inside it
-            const uint32_t hiA = j0 >= c ? hi : 63u - (uint32_t)__clzll((long long)(y & ((1ull << select64(y, j0)) - 1ull)));
+            const uint32_t hiA = j0 >= c ? hi : 63u - (uint32_t)__clzll((long long)(y & ((1ull << loB) - 1ull)));
             uint32_t v = inner_gap_bits(y, lo, hiA);
-            const unsigned long long g = (unsigned long long)((long long)(w * 64u + lo) - Pw - 1);  // Rw > 0: Pw >= 0
-            v = max(v, g ? 64u - (uint32_t)__clzll((long long)g) : 0u);
+            const uint32_t g = (uint32_t)(w * 64u + lo) - Pw1;  // Rw > 0, so Pw1 >= 1: the gap p - p_prev - 1
+            v = max(v, g ? 32u - (uint32_t)__clz(g) : 0u);
             if (v) atomicMax(&smax[Rw / kBlock - kfirst], v);
         }
         if (j0 < c) {  // members [j0, c) open block (Rw + j0) / 128; member j0's gap is outside it
-            const uint32_t loB = select64(y, j0);
             const uint32_t v = inner_gap_bits(y, loB, hi);
             if (v) atomicMax(&smax[(Rw + j0) / kBlock - kfirst], v);
         }
@@ -989,17 +1000,17 @@ __global__ void __launch_bounds__(kThreads) fbw_kernel(const uint64_t *__restric
     __syncthreads();
     uint32_t local = 0;  // widths of the blocks that start and end in this sub-tile
     if (tot) {
-        const unsigned long long end = R + tot;  // members before the next sub-tile
-        const uint32_t nloc = (uint32_t)((end - 1) / kBlock - kfirst + 1);
+        const uint32_t end = R + tot;  // members before the next sub-tile
+        const uint32_t nloc = (end - 1) / kBlock - kfirst + 1;
         for (uint32_t j = threadIdx.x; j < nloc; j += kThreads) {
-            const unsigned long long k = kfirst + j;
-            const bool owned = k * kBlock >= R;  // its first member is in this sub-tile
-            const bool complete = min(k * kBlock + kBlock, members) <= end;
+            const uint32_t k = kfirst + j;
+            const bool owned = (uint64_t)k * kBlock >= R;  // its first member is in this sub-tile
+            const bool complete = min((uint64_t)k * kBlock + kBlock, (uint64_t)members) <= end;
             if (owned && complete) {
                 local += smax[j];
             } else {
                 if (smax[j]) atomicMax(&wb[k], smax[j]);
-                if (owned) span[blockIdx.x] = (uint32_t)k;  // at most one: the sub-tile's last block
+                if (owned) span[blockIdx.x] = k;  // at most one: the sub-tile's last block
             }
         }
     }
@@ -1020,23 +1031,35 @@ __global__ void __launch_bounds__(kThreads) fbw_kernel(const uint64_t *__restric
     if (!s_last) return;
     __threadfence();
     unsigned long long sum = 0;
-    for (uint32_t i = threadIdx.x; i < gridDim.x; i += kThreads) {
-        sum += __ldcg(wpart + i);
-        const uint32_t k = __ldcg(span + i);
-        if (k != 0xffffffffu) {
-            sum += __ldcg(wb + k);
-            wb[k] = 0u;
+    constexpr uint32_t kPer = 8;  // entries per thread whose loads are in flight together
+    for (uint32_t i0 = 0; i0 < gridDim.x; i0 += kThreads * kPer) {
+        uint32_t kk[kPer], wv[kPer];
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; j++) {
+            const uint32_t i = i0 + j * kThreads + threadIdx.x;
+            kk[j] = i < gridDim.x ? __ldcg(span + i) : 0xffffffffu;
+            sum += i < gridDim.x ? __ldcg(wpart + i) : 0u;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; j++) wv[j] = kk[j] != 0xffffffffu ? __ldcg(wb + kk[j]) : 0u;
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; j++) {
+            if (kk[j] != 0xffffffffu) {
+                sum += wv[j];
+                wb[kk[j]] = 0u;
+            }
         }
     }
     sum = warp_sum64(sum);
-    if (lane == 0) red[0][warp] = sum;
+    __syncthreads();
+    if (lane == 0) red[0][warp] = (uint32_t)sum;  // at most 32 per block and under 2^25 blocks
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long total = 0;
         for (uint32_t i = 0; i < kThreads / 32; i++) total += red[0][i];
         // the FB container's rule: raw words unless the header plus the FQ stream (packed, or raw ids
         // when packing does not pay) is smaller
-        const unsigned long long nb = (members + kBlock - 1) / kBlock;
+        const unsigned long long nb = ((unsigned long long)members + kBlock - 1) / kBlock;
         const unsigned long long packed = 16ull + (5ull * nb + 15ull) / 16ull * 16ull + 16ull * total;
         const unsigned long long rawq = 16ull + (4ull * members + 15ull) / 16ull * 16ull;
         const unsigned long long fq = packed < rawq ? packed : rawq;
