@@ -276,7 +276,10 @@ fq_status fq_set_allocator(const fq_allocator *a);
 #define FQ_BFS_VISITED_STREAM 0x1u /* also encode the visited bitmap V_d every level          */
 #define FQ_BFS_FORCE_TOP_DOWN 0x2u /* ignore the switching rule: top-down at every level        */
 #define FQ_BFS_FORCE_BOTTOM_UP 0x4u/* bottom-up at every level after level 0                    */
-#define FQ_BFS_TIMING 0x8u         /* time every kernel class with CUDA events (fills stats)    */
+#define FQ_BFS_TIMING 0x8u         /* time every kernel class with CUDA events (fills stats); each
+                                      level's launches are then captured as a graph and launched
+                                      whole, so the events see the kernels back to back rather than
+                                      the host's submission of each one (host-driven loop only)  */
 #define FQ_BFS_NO_CODEC 0x10u      /* skip the codec stage: expand the raw queue/bitmap (the plain
                                       BFS the codec stage is measured against; no streams)      */
 #define FQ_BFS_PATCHED 0x40u       /* the per-level queue streams Q_d in the FQX format (patched
@@ -295,7 +298,8 @@ fq_status fq_set_allocator(const fq_allocator *a);
 #define FQ_BFS_DEVICE_LOOP 0x20u   /* run the level loop on the device: one CUDA graph (built on
                                       the first call per handle, output buffers and stream-log
                                       buffer, then reused) whose while node repeats the level and
-                                      whose if/else nodes pick the encode form and the direction,
+                                      whose switch node picks the level body (encode form and
+                                      direction, or the one-CTA codec stage of a small frontier),
                                       so no level waits on the host.  Same results, records and
                                       streams as the host-driven loop; FQ_BFS_TIMING is ignored
                                       (kernel_ms stay 0).  Needs a driver with conditional graph

@@ -1306,6 +1306,7 @@ struct fq_graph {
     uint8_t *host;  // pinned: Counters copy, then LoopState and level records (device-driven loop)
     cudaEvent_t ev[2 * FQ_NUM_KCLASS];
     cudaStream_t ov_stream;  // FQ_BFS_OVERLAP, host-driven loop: the codec stage's stream
+    cudaStream_t tm_stream;  // FQ_BFS_TIMING, host-driven loop: where each level is captured
     cudaEvent_t ov_ev[2];    //   fork (after the previous compaction) and join (before this one)
     // device-driven level loop: state, records and the cached executable graph with its key
     LoopState *ls;
@@ -1346,16 +1347,22 @@ struct Timer {
     double *ms;
     uint64_t *launches;
     cudaStream_t cls_st[FQ_NUM_KCLASS];  // the stream each class's launches go to (0: st)
+    bool ext = false;                    // recording inside a stream capture: as event record nodes
     cudaStream_t of(int k) const { return cls_st[k] ? cls_st[k] : st; }
+    void record(cudaEvent_t e, cudaStream_t s) const
+    {
+        if (ext) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
+    }
     void begin(int k)
     {
         nvtxRangePushA(kClassRange[k]);
-        if (on) cudaEventRecord(g->ev[2 * k], of(k));
+        if (on) record(g->ev[2 * k], of(k));
     }
     void end(int k, int nlaunch)
     {
         if (launches) launches[k] += nlaunch;
-        if (on) cudaEventRecord(g->ev[2 * k + 1], of(k));
+        if (on) record(g->ev[2 * k + 1], of(k));
         nvtxRangePop();
     }
     // Adds the class's elapsed time since begin() to ms[k] and returns it (0 when not timing).
@@ -1760,6 +1767,7 @@ void fq_graph_destroy_locked(fq_graph *g)
     for (int i = 0; i < 3; i++)
         if (g->dl_ev[i]) cudaEventDestroy(g->dl_ev[i]);
     if (g->ov_stream) cudaStreamDestroy(g->ov_stream);
+    if (g->tm_stream) cudaStreamDestroy(g->tm_stream);
     for (int i = 0; i < 2; i++)
         if (g->ov_ev[i]) cudaEventDestroy(g->ov_ev[i]);
     for (int i = 0; i < 2 * FQ_NUM_KCLASS; i++)
@@ -2045,56 +2053,89 @@ fq_status fq_bfs_run(fq_graph *g, uint32_t root, int32_t *d_depth, uint32_t *d_p
         // with the overlap the codec stage forks onto its own stream after the previous compaction
         // and joins before this level's compaction, while the expansion consumes the raw frontier
         const bool ovl = overlap && coded;
-        cudaStream_t cst = st;
-        if (ovl) {
-            FQ_TRY(cudaEventRecord(g->ov_ev[0], st));
-            FQ_TRY(cudaStreamWaitEvent(g->ov_stream, g->ov_ev[0], 0));
-            cst = g->ov_stream;
-        }
-        tm.cls_st[FQ_K_ENCODE] = tm.cls_st[FQ_K_DECODE] = ovl ? cst : nullptr;
-
-        // 1. encode F_d (Q_d and B_d), and V_d
         // a small mirrored top-down level takes the one-CTA codec stage (encode and decode together)
         const bool small = coded && !px && !ovl && dir == FQ_TOP_DOWN && 2 * n_f <= n && n_f <= kSmallIds;
-        tm.begin(FQ_K_ENCODE);
-        int enc_launches = 0;
-        if (small) {
-            FQ_TRY(step_codec_small(g, n_f, nullptr, cst));
-            enc_launches = 1;
-        } else if (coded) {
-            const bool dense = 2 * n_f > n;
-            FQ_TRY(step_encode_q(g, dense, n_f, nullptr, cst, px));
-            enc_launches = dense ? 8 : 2;
-        }
-        if (want_visited) {
-            FQ_TRY(step_encode_v(g, cst));
-            enc_launches += 4;
-        }
-        tm.end(FQ_K_ENCODE, enc_launches);
-
-        // 3 + 4. decode the consumed form (overlap: decode and compare with the raw form), expand
-        tm.begin(FQ_K_DECODE);
-        if (coded && !small && dir == FQ_TOP_DOWN) FQ_TRY(step_decode_q(g, n_f, nullptr, cst));
-        if (coded && dir == FQ_BOTTOM_UP) FQ_TRY(step_decode_b(g, cst));
-        if (ovl) FQ_TRY(dir == FQ_TOP_DOWN ? step_check_q(g, n_f, nullptr, cst) : step_check_b(g, cst));
-        tm.end(FQ_K_DECODE, coded && !small ? (dir == FQ_TOP_DOWN ? 3 : 4) + (ovl ? 1 : 0) : 0);
-        if (ovl) FQ_TRY(cudaEventRecord(g->ov_ev[1], cst));
-        const bool consume_decoded = coded && !ovl;
-        if (dir == FQ_TOP_DOWN) {
-            tm.begin(FQ_K_TOP_DOWN);
-            FQ_TRY(step_top_down(g, consume_decoded, n_f, newdepth, d_depth, d_parent, nullptr, st));
-            tm.end(FQ_K_TOP_DOWN, 2);
+#define FQ_LV(expr)                                   \
+    do {                                              \
+        const cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) return _e;             \
+    } while (0)
+        // the level's launches, on stream lst
+        auto launch_level = [&](cudaStream_t lst) -> cudaError_t {
+            cudaStream_t cst = lst;
+            if (ovl) {
+                FQ_LV(cudaEventRecord(g->ov_ev[0], lst));
+                FQ_LV(cudaStreamWaitEvent(g->ov_stream, g->ov_ev[0], 0));
+                cst = g->ov_stream;
+            }
+            tm.cls_st[FQ_K_ENCODE] = tm.cls_st[FQ_K_DECODE] = ovl ? cst : nullptr;
+            // 1. encode F_d (Q_d and B_d), and V_d
+            tm.begin(FQ_K_ENCODE);
+            int enc_launches = 0;
+            if (small) {
+                FQ_LV(step_codec_small(g, n_f, nullptr, cst));
+                enc_launches = 1;
+            } else if (coded) {
+                const bool dense = 2 * n_f > n;
+                FQ_LV(step_encode_q(g, dense, n_f, nullptr, cst, px));
+                enc_launches = dense ? 8 : 2;
+            }
+            if (want_visited) {
+                FQ_LV(step_encode_v(g, cst));
+                enc_launches += 4;
+            }
+            tm.end(FQ_K_ENCODE, enc_launches);
+            // 3 + 4. decode the consumed form (overlap: decode and compare with the raw form), expand
+            tm.begin(FQ_K_DECODE);
+            if (coded && !small && dir == FQ_TOP_DOWN) FQ_LV(step_decode_q(g, n_f, nullptr, cst));
+            if (coded && dir == FQ_BOTTOM_UP) FQ_LV(step_decode_b(g, cst));
+            if (ovl) FQ_LV(dir == FQ_TOP_DOWN ? step_check_q(g, n_f, nullptr, cst) : step_check_b(g, cst));
+            tm.end(FQ_K_DECODE, coded && !small ? (dir == FQ_TOP_DOWN ? 3 : 4) + (ovl ? 1 : 0) : 0);
+            if (ovl) FQ_LV(cudaEventRecord(g->ov_ev[1], cst));
+            const bool consume_decoded = coded && !ovl;
+            if (dir == FQ_TOP_DOWN) {
+                tm.begin(FQ_K_TOP_DOWN);
+                FQ_LV(step_top_down(g, consume_decoded, n_f, newdepth, d_depth, d_parent, nullptr, lst));
+                tm.end(FQ_K_TOP_DOWN, 2);
+            } else {
+                tm.begin(FQ_K_BOTTOM_UP);
+                FQ_LV(step_bottom_up(g, consume_decoded, newdepth, d_depth, d_parent, nullptr, lst));
+                tm.end(FQ_K_BOTTOM_UP, 1);
+            }
+            if (ovl) FQ_LV(cudaStreamWaitEvent(lst, g->ov_ev[1], 0));
+            // 5. compaction (+ the visited counts per tile, cleared scratch for the next level)
+            tm.begin(FQ_K_COMPACT);
+            FQ_LV(step_compact(g, want_visited, lst));
+            tm.end(FQ_K_COMPACT, 2);
+            return cudaSuccess;
+        };
+#undef FQ_LV
+        if (!tm.on) {
+            FQ_TRY(launch_level(st));
         } else {
-            tm.begin(FQ_K_BOTTOM_UP);
-            FQ_TRY(step_bottom_up(g, consume_decoded, newdepth, d_depth, d_parent, nullptr, st));
-            tm.end(FQ_K_BOTTOM_UP, 1);
+            // Timed: the level is captured as a graph and launched whole, so the class events measure
+            // the kernels back to back as the device-driven loop runs them, not the host's submission
+            // of each launch.  (The capture stream is the handle's own: the caller's may be the
+            // legacy stream, which cannot capture.)
+            std::lock_guard<std::mutex> lock(g_capture_mu);  // no handle is created or freed meanwhile
+            if (!g->tm_stream) FQ_TRY(cudaStreamCreateWithFlags(&g->tm_stream, cudaStreamNonBlocking));
+            FQ_TRY(cudaStreamBeginCapture(g->tm_stream, cudaStreamCaptureModeRelaxed));
+            tm.st = g->tm_stream;
+            tm.ext = true;
+            const cudaError_t le = launch_level(g->tm_stream);
+            tm.ext = false;
+            tm.st = st;
+            cudaGraph_t lg = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(g->tm_stream, &lg);
+            cudaGraphExec_t lx = nullptr;
+            cudaError_t xe = le != cudaSuccess ? le : ce;
+            if (xe == cudaSuccess) xe = cudaGraphInstantiate(&lx, lg, 0);
+            if (xe == cudaSuccess) xe = cudaGraphLaunch(lx, st);
+            if (xe == cudaSuccess) xe = cudaStreamSynchronize(st);
+            if (lx) cudaGraphExecDestroy(lx);
+            if (lg) cudaGraphDestroy(lg);
+            FQ_TRY(xe);
         }
-        if (ovl) FQ_TRY(cudaStreamWaitEvent(st, g->ov_ev[1], 0));
-
-        // 5. compaction (+ the visited counts per tile, cleared scratch for the next level)
-        tm.begin(FQ_K_COMPACT);
-        FQ_TRY(step_compact(g, want_visited, st));
-        tm.end(FQ_K_COMPACT, 2);
 
         FQ_TRY(cudaMemcpyAsync(g->host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         FQ_TRY(cudaStreamSynchronize(st));
