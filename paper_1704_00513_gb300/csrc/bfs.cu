@@ -47,7 +47,7 @@ struct HubItem {
 // during a level; the compaction's extract kernel (its first CTA) copies the ones it clears into
 // the r_* record the host reads.
 struct Counters {
-    unsigned long long n_f_next;   // |F_{d+1}|                         (cmp_scan)
+    unsigned long long n_f_next;   // |F_{d+1}|                         (cmp_extract, first CTA)
     unsigned long long m_f_next;   // live: degree sum over F_{d+1}     (expansion kernels)
     unsigned long long examined;   // live: bottom-up adjacency reads
     unsigned long long hub_items;  // live: top-down hub work items
