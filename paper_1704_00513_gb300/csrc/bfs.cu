@@ -863,11 +863,15 @@ __global__ void __launch_bounds__(kThreads, 6) fbw_kernel(const uint64_t *__rest
                                                           uint32_t *span, uint32_t *wpart, Scratch sv)
 {
     // Counts and positions fit 32 bits (n < 2^32); a position p is carried as p + 1, 0 for none.
-    __shared__ uint32_t red[4][kThreads / 32];
-    __shared__ uint32_t tsum[4];
+    __shared__ uint32_t red[8][kThreads / 32];
     __shared__ uint32_t wcnt[kThreads / 32], wlast[kThreads / 32];
     __shared__ uint32_t smax[kSubBlocks];
     __shared__ bool s_last;
+    {  // a sparse member set (its count and mode were set by the last compaction) is left to the
+       // positions path before anything else is read
+        const unsigned long long m0 = sv.ctl->n;
+        if (m0 == 0 || 16ull * m0 < n) return;
+    }
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t tile = blockIdx.x / sub, s = blockIdx.x % sub;
     const uint32_t tail = (uint32_t)(n & 63u);
@@ -875,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 6) fbw_kernel(const uint64_t *__rest
     const uint64_t w = tile_w0 + (uint64_t)s * kCmpSubWords + threadIdx.x;
     const uint64_t in_n_last = tail ? (1ull << tail) - 1ull : ~0ull;  // the last word's bits below n
     // every load of the prologue first: this word, the tile's earlier sub-tiles' words (both modes'
-    // members are counted, the mode is known only after the sums), the earlier tiles' records (warp 0)
+    // members are counted, the mode is known only after the sums), the earlier tiles' records
     const uint64_t y_raw = w < nwords ? visited[w] : 0ull;
     uint64_t ye[kCmpAhead];
 #pragma unroll
@@ -884,26 +888,14 @@ __global__ void __launch_bounds__(kThreads, 6) fbw_kernel(const uint64_t *__rest
         ye[e] = (e < s && we < nwords) ? visited[we] : 0ull;
     }
     for (uint32_t i = threadIdx.x; i < kSubBlocks; i += kThreads) smax[i] = 0u;
-    if (warp == 0) {  // visited before / in all tiles, last set / clear vertex before this tile
-        uint32_t vb = 0, vt = 0, ls = 0, lc = 0;
-        for (uint32_t i = lane; i < ntiles; i += 32u) {
-            const uint32_t c = vis_cnt[i];
-            vt += c;
-            if (i < tile) {
-                vb += c;
-                ls = max(ls, last_set[i]);
-                lc = max(lc, last_clear[i]);
-            }
-        }
-        vb = __reduce_add_sync(0xffffffffu, vb);
-        vt = __reduce_add_sync(0xffffffffu, vt);
-        ls = __reduce_max_sync(0xffffffffu, ls);
-        lc = __reduce_max_sync(0xffffffffu, lc);
-        if (lane == 0) {
-            tsum[0] = vb;
-            tsum[1] = vt;
-            tsum[2] = ls;
-            tsum[3] = lc;
+    uint32_t vb = 0, vt = 0, ls = 0, lc = 0;  // visited before / in all tiles, last set / clear + 1 before the tile
+    for (uint32_t i = threadIdx.x; i < ntiles; i += kThreads) {
+        const uint32_t c = vis_cnt[i];
+        vt += c;
+        if (i < tile) {
+            vb += c;
+            ls = max(ls, last_set[i]);
+            lc = max(lc, last_clear[i]);
         }
     }
     uint32_t es = 0, ec = 0, els = 0, elc = 0;  // the earlier sub-tiles: set, clear, last set + 1, last clear + 1
@@ -922,31 +914,42 @@ __global__ void __launch_bounds__(kThreads, 6) fbw_kernel(const uint64_t *__rest
         const uint64_t we = tile_w0 + (uint64_t)e * kCmpSubWords + threadIdx.x;
         earlier(e, we < nwords ? visited[we] : 0ull);
     }
+    vb = __reduce_add_sync(0xffffffffu, vb);
+    vt = __reduce_add_sync(0xffffffffu, vt);
+    ls = __reduce_max_sync(0xffffffffu, ls);
+    lc = __reduce_max_sync(0xffffffffu, lc);
     es = __reduce_add_sync(0xffffffffu, es);
     ec = __reduce_add_sync(0xffffffffu, ec);
     els = __reduce_max_sync(0xffffffffu, els);
     elc = __reduce_max_sync(0xffffffffu, elc);
     if (lane == 0) {
-        red[0][warp] = es;
-        red[1][warp] = ec;
-        red[2][warp] = els;
-        red[3][warp] = elc;
+        red[0][warp] = vb;
+        red[1][warp] = vt;
+        red[2][warp] = ls;
+        red[3][warp] = lc;
+        red[4][warp] = es;
+        red[5][warp] = ec;
+        red[6][warp] = els;
+        red[7][warp] = elc;
     }
     __syncthreads();
+    vb = vt = ls = lc = es = ec = els = elc = 0;
     for (uint32_t i = 0; i < kThreads / 32; i++) {
-        if (i == 0) es = ec = els = elc = 0;
-        es += red[0][i];
-        ec += red[1][i];
-        els = max(els, red[2][i]);
-        elc = max(elc, red[3][i]);
+        vb += red[0][i];
+        vt += red[1][i];
+        ls = max(ls, red[2][i]);
+        lc = max(lc, red[3][i]);
+        es += red[4][i];
+        ec += red[5][i];
+        els = max(els, red[6][i]);
+        elc = max(elc, red[7][i]);
     }
-    const uint32_t vb = tsum[0], vt = tsum[1];
     const bool set_mode = 2ull * vt <= n;
     const uint32_t members = set_mode ? vt : (uint32_t)(n - vt);
-    if (members == 0 || 16ull * members < n) return;  // the same test in every CTA
+    if (members == 0 || 16ull * members < n) return;  // (as tested on entry; the same in every CTA)
     // members before this sub-tile, and the last of them + 1 (0: none)
     const uint32_t R = set_mode ? vb + es : (uint32_t)min((unsigned long long)n, 64ull * tile_w0) - vb + ec;
-    const uint32_t P1 = set_mode ? max(tsum[2], els) : max(tsum[3], elc);
+    const uint32_t P1 = set_mode ? max(ls, els) : max(lc, elc);
     const uint64_t y = (w < nwords && !set_mode) ? ~y_raw & (w == nwords - 1 ? in_n_last : ~0ull) : y_raw;
     const uint32_t c = (uint32_t)__popcll(y);
     const uint32_t last1 = c ? (uint32_t)(w * 64u + 64u - (uint32_t)__clzll((long long)y)) : 0u;
