@@ -792,10 +792,10 @@ __global__ void __launch_bounds__(kThreads) v_extract_kernel(const uint64_t *__r
 // ---- V_d's block widths from the visited bitmap ----
 // V_d codes the positions of the members -- the set bits of the visited bitmap when at most half
 // are set, else its clear bits below n -- as blocks of 128 positions (sec. 5.1), whose width b is
-// the bit length of the largest gap (p - p_prev - 1) inside the block; the container falls back to
-// the raw bitmap when that is not larger than the coded positions.  Once the visited set is
-// dense, that is the usual outcome, and the stream's size -- so the decision -- needs only the sum
-// of the widths, which this kernel takes from the bitmap without writing any position: member
+// the bit length of the largest gap (p - p_prev - 1) inside the block; the container is the raw
+// bitmap unless the coded positions are strictly smaller.  Once the visited set is dense, raw is
+// the usual outcome, and the stream's size -- so the decision -- needs only the sum of the
+// widths, which this kernel takes from the bitmap without writing any position: member
 // ranks come from the per-tile counts, each member's predecessor from the per-tile last members,
 // and the gaps inside a word from zero-run tests on its bits.  When the sum says raw, the positions
 // extraction and the widths pass are skipped (Ctl::skip_pos) and the pack kernel copies the words.
